@@ -1,0 +1,280 @@
+/*
+ * smc_oracle.c -- CPU oracle for the particle-parallel SMC sweep over a PPL
+ * control-flow graph (PCFG), Lunden et al. 2022, Section 3.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, single-threaded
+ * restatement against which the CUDA library is checked.  It shares no code
+ * with the CUDA path; only tests/, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  Compile with -ffp-contract=off so that every
+ * a*b+c below is two roundings unless written as fma().
+ *
+ * What each part follows:
+ *   - Algorithm 1 (SMC over PCFGs) and the RootPPL inference loop of
+ *     Section 3.3: init, propagate to the next checkpoint, stop when every
+ *     particle is at b_stop, else resample and repeat; sim(b_stop,s) =
+ *     (b_stop,s,true).
+ *   - Normalising constant: log Z accumulates log((1/N) sum_n w_n) at every
+ *     checkpoint (Section 3.3, "normalizing constants").
+ *   - Systematic resampling (Section 3.3): one uniform u per checkpoint,
+ *     a_i = min{ j : N P_j / S > i + u }, P_j the running sum of weights.
+ *   - Models: the state-space model of Eq. 2 / Fig. 3 (generalised to
+ *     x_t = a x_{t-1} + b + q z), the CRBD model of Listing 1, a rate-shift
+ *     variant of it, and the weighted geometric program of Fig. 2a.
+ *
+ * Random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11) with
+ * key (seed_lo, seed_hi XOR run_id) and counter (particle slot n,
+ * checkpoint index k, draw index d, stream tag); one 128-bit block per
+ * variate.  Tag 0 = model draws, 1 = resampling uniform, 2 = rate-shift
+ * multipliers.  Published definition, implemented here independently.
+ */
+#include "smc_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PC_STOP (-1)
+
+/* ------------------------- Philox4x32-10 ------------------------- */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; round++) {
+    if (round > 0) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    c0 = hi1 ^ c1 ^ k0;
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ k1;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+void orc_philox_many(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+  for (int64_t i = 0; i < n; i++) orc_philox4x32_10(ctr + 4 * i, key + 2 * i, out + 4 * i);
+}
+
+static void make_key(uint64_t seed, uint32_t run_id, uint32_t key[2]) {
+  key[0] = (uint32_t)(seed & 0xffffffffu);
+  key[1] = (uint32_t)(seed >> 32) ^ run_id;
+}
+
+typedef struct {
+  uint32_t key[2];
+  uint32_t n, k, d, tag;
+} stream_t;
+
+static void stream_init(stream_t *s, const uint32_t key[2], uint32_t n, uint32_t k, uint32_t tag) {
+  s->key[0] = key[0];
+  s->key[1] = key[1];
+  s->n = n;
+  s->k = k;
+  s->d = 0;
+  s->tag = tag;
+}
+
+static void next_block(stream_t *s, uint32_t w[4]) {
+  uint32_t c[4] = {s->n, s->k, s->d, s->tag};
+  orc_philox4x32_10(c, s->key, w);
+  s->d += 1;
+}
+
+/* FP64 uniforms: the odd 53-bit integer ((w_hi:w_lo) >> 11) | 1 times 2^-53,
+ * exact, strictly inside (0,1).  First uses (w1:w0), second (w3:w2). */
+static double u_first_d(const uint32_t w[4]) {
+  uint64_t x = ((uint64_t)w[1] << 32) | (uint64_t)w[0];
+  return (double)((x >> 11) | 1u) * 0x1p-53;
+}
+static double u_second_d(const uint32_t w[4]) {
+  uint64_t x = ((uint64_t)w[3] << 32) | (uint64_t)w[2];
+  return (double)((x >> 11) | 1u) * 0x1p-53;
+}
+/* FP32 uniforms: the odd 24-bit integer (w >> 8) | 1 times 2^-24.
+ * First uses w0, second w1. */
+static float u_first_f(const uint32_t w[4]) { return (float)((w[0] >> 8) | 1u) * 0x1p-24f; }
+static float u_second_f(const uint32_t w[4]) { return (float)((w[1] >> 8) | 1u) * 0x1p-24f; }
+
+/* run-level constants computed once in double */
+typedef struct {
+  double corr;   /* CRBD: (n_tips - 1) ln 2 - ln n_tips! */
+  double lg_lc;  /* LG: log(r_sd) + 0.5 log(2 pi) */
+} model_consts;
+
+#define LN2_D 0.69314718055994530942
+#define HALF_LOG_2PI_D 0.91893853320467274178
+
+static int model_setup(const orc_model *m, model_consts *mc) {
+  mc->corr = 0.0;
+  mc->lg_lc = 0.0;
+  if (m->kind == ORC_LG) {
+    if (!m->obs || m->T <= 0 || !(m->r_sd > 0)) return ORC_EINVAL;
+    mc->lg_lc = log(m->r_sd) + HALF_LOG_2PI_D;
+  } else if (m->kind == ORC_CRBD || m->kind == ORC_RATESHIFT) {
+    if (m->n_nodes < 3 || !m->parent || !m->left || !m->age || !m->preorder) return ORC_EINVAL;
+    if (m->kind == ORC_RATESHIFT && m->lam_stack_cap < 1) return ORC_EINVAL;
+    int32_t tips = (m->n_nodes + 1) / 2;
+    double lnfact = 0.0;
+    for (int32_t i = 2; i <= tips; i++) lnfact = lnfact + log((double)i);
+    mc->corr = (double)(tips - 1) * LN2_D - lnfact;
+  } else if (m->kind != ORC_GEOMETRIC) {
+    return ORC_EINVAL;
+  }
+  return ORC_OK;
+}
+
+/* ------------- normaliser and systematic resampling (always FP64) ------------- */
+
+/* m = max_n logw_n; S = sum_n exp(logw_n - m) left to right;
+ * increment = m + (log S - log N).  Returns nonzero if every weight is zero. */
+static int normaliser(const double *lw, int64_t N, double *m, double *S, double *incr) {
+  double mx = -INFINITY;
+  for (int64_t i = 0; i < N; i++)
+    if (lw[i] > mx) mx = lw[i];
+  *m = mx;
+  if (mx == -INFINITY) {
+    *S = 0.0;
+    *incr = -INFINITY;
+    return 1;
+  }
+  double s = 0.0;
+  for (int64_t i = 0; i < N; i++) s = s + exp(lw[i] - mx);
+  *S = s;
+  *incr = mx + (log(s) - log((double)N));
+  return 0;
+}
+
+static double resample_uniform(const uint32_t key[2], uint32_t k) {
+  uint32_t c[4] = {0u, k, 0u, 1u};
+  uint32_t w[4];
+  orc_philox4x32_10(c, key, w);
+  return u_first_d(w);
+}
+
+#define BOUNDARY_EPS 1e-12
+
+/* a_i = min{ j : q_j > i + u } with q_j = P_j * (N / S) and P_j the
+ * left-to-right running sum of exp(logw_j - m); if no j qualifies
+ * (rounding at the top) a_i = N - 1.  flag[i] = 1 when i + u lies within
+ * 1e-12 N of q_{a_i} or of q_{a_i - 1}. */
+static void systematic(const double *lw, int64_t N, double u, double mx, double S, int32_t *anc,
+                       int32_t *flag) {
+  double *q = malloc((size_t)N * sizeof(double));
+  double r = (double)N / S;
+  double P = 0.0;
+  for (int64_t j = 0; j < N; j++) {
+    P = P + exp(lw[j] - mx);
+    q[j] = P * r;
+  }
+  const double tol = BOUNDARY_EPS * (double)N;
+  int64_t j = 0;
+  for (int64_t i = 0; i < N; i++) {
+    double y = (double)i + u;
+    while (j < N && !(q[j] > y)) j++;
+    int64_t a = j < N ? j : N - 1;
+    anc[i] = (int32_t)a;
+    int f = fabs(q[a] - y) < tol;
+    if (a > 0 && fabs(q[a - 1] - y) < tol) f = 1;
+    flag[i] = f;
+  }
+  free(q);
+}
+
+int orc_resample(const double *logw, int64_t N, double u, int32_t *anc, int32_t *flag,
+                 double *incr, double *m_out, double *S_out) {
+  double mx, S, inc;
+  if (N <= 0) return ORC_EINVAL;
+  int r = normaliser(logw, N, &mx, &S, &inc);
+  if (incr) *incr = inc;
+  if (m_out) *m_out = mx;
+  if (S_out) *S_out = S;
+  if (r) return ORC_EDEGENERATE;
+  int32_t *f = flag ? flag : malloc((size_t)N * sizeof(int32_t));
+  systematic(logw, N, u, mx, S, anc, f);
+  if (!flag) free(f);
+  return ORC_OK;
+}
+
+int orc_n_fields(const orc_model *m, int32_t *n_real, int32_t *n_int, int32_t *stack_cap) {
+  *stack_cap = 0;
+  switch (m->kind) {
+    case ORC_LG: *n_real = 1; *n_int = 1; return ORC_OK;
+    case ORC_CRBD: *n_real = 2; *n_int = 1; return ORC_OK;
+    case ORC_RATESHIFT: *n_real = 2; *n_int = 2; *stack_cap = m->lam_stack_cap; return ORC_OK;
+    case ORC_GEOMETRIC: *n_real = 0; *n_int = 2; return ORC_OK;
+  }
+  return ORC_EINVAL;
+}
+
+/* ------------------ precision instantiations ------------------ */
+#define R double
+#define SFX(x) x##_d
+#define LOGR log
+#define EXPR exp
+#define COSR cos
+#define SQRTR sqrt
+#define FMAR fma
+#define FABSR fabs
+#define FLOORR floor
+#define LGAMMAR lgamma
+#define LN2R LN2_D
+#define TWO_PIR 6.28318530717958647692
+#include "smc_oracle_prec.inc"
+#undef R
+#undef SFX
+#undef LOGR
+#undef EXPR
+#undef COSR
+#undef SQRTR
+#undef FMAR
+#undef FABSR
+#undef FLOORR
+#undef LGAMMAR
+#undef LN2R
+#undef TWO_PIR
+
+#define R float
+#define SFX(x) x##_f
+#define LOGR logf
+#define EXPR expf
+#define COSR cosf
+#define SQRTR sqrtf
+#define FMAR fmaf
+#define FABSR fabsf
+#define FLOORR floorf
+#define LGAMMAR lgammaf
+#define LN2R 0.693147182f
+#define TWO_PIR 6.28318548f
+#include "smc_oracle_prec.inc"
+
+/* ------------------------- exported ------------------------- */
+
+int orc_sample(int32_t dist, int32_t precision, double p1, double p2, uint64_t seed,
+               uint32_t run_id, int64_t n, double *out, int32_t *blocks_used) {
+  uint32_t key[2];
+  make_key(seed, run_id, key);
+  if (precision == ORC_FP64) return sample_d(dist, p1, p2, key, n, out, blocks_used);
+  if (precision == ORC_FP32) return sample_f(dist, p1, p2, key, n, out, blocks_used);
+  return ORC_EINVAL;
+}
+
+int orc_smc_run(const orc_model *m, const orc_cfg *c, orc_out *o) {
+  if (!m || !c || !o || c->N <= 0 || c->N > 0x7fffffff) return ORC_EINVAL;
+  if (m->depth_cap < 0 || m->call_limit < 0) return ORC_EINVAL;
+  if (m->precision == ORC_FP64) return smc_run_d(m, c, o);
+  if (m->precision == ORC_FP32) return smc_run_f(m, c, o);
+  return ORC_EINVAL;
+}

@@ -1,0 +1,99 @@
+/*
+ * smc_oracle.h -- interface of the CPU oracle for the particle-SMC sweep over
+ * a PPL control-flow graph (Lunden et al., "Compiling Universal Probabilistic
+ * Programming Languages with Efficient Parallel Sequential Monte Carlo
+ * Inference", Section 3).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The oracle is a plain, slow, single-threaded
+ * restatement of Algorithm 1 (SMC over PCFGs) and of the models it runs.  It
+ * shares no code with the CUDA library.  Only the test suite, the smoke check
+ * and the benchmark's CPU-baseline leg may load it; the product path never
+ * does.
+ */
+#ifndef SMC_ORACLE_H
+#define SMC_ORACLE_H
+#include <stdint.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+#define ORC_EDEGENERATE (-4)
+#define ORC_ESTEPLIMIT (-5)
+
+#define ORC_LG 1
+#define ORC_CRBD 2
+#define ORC_RATESHIFT 3
+#define ORC_GEOMETRIC 4
+
+#define ORC_FP64 0
+#define ORC_FP32 1 /* FP32 particle arithmetic, FP64 normaliser / scan / log Z */
+
+typedef struct {
+  int32_t kind;
+  int32_t precision;
+  /* linear-Gaussian (Eq. 2 family): x0~N(x0_mean,x0_sd), x=a x+b+N(0,q_sd), y~N(x,r_sd) */
+  int32_t T;
+  int32_t n_nodes;
+  const double *obs;
+  double x0_mean, x0_sd, a, b, q_sd, r_sd;
+  /* birth-death tree models (Listing 1 and the rate-shift reading) */
+  const int32_t *parent, *left, *right, *preorder;
+  const double *age;
+  double rho;
+  double lambda_fixed, mu_fixed;  /* used when fixed_rates != 0 */
+  double lambda_scale, mu_scale;  /* Gamma(1, scale) priors otherwise */
+  double sigma;                   /* rate-shift log-normal sd */
+  const double *fixed_mult;       /* rate-shift: per-node multipliers, or NULL */
+  int32_t fixed_rates;
+  int32_t depth_cap;              /* hidden-lineage recursion cap (frames) */
+  int32_t call_limit;             /* undetected-calls per segment before a kill */
+  int32_t lam_stack_cap;          /* rate-shift pending-rate stack capacity */
+  /* weighted geometric test program (Fig. 2a) */
+  double geo_p, geo_logw;
+} orc_model;
+
+typedef struct {
+  int64_t N;
+  uint64_t seed;
+  uint32_t run_id;
+  int32_t max_segments;
+  const int32_t *follow_anc; /* [n_follow][N] ancestors from another implementation, or NULL */
+  int32_t n_follow;
+  int32_t pad_;
+} orc_cfg;
+
+typedef struct {
+  double log_z;
+  int64_t n_flagged;        /* resampled particles whose offset lies within 1e-12 N of a boundary */
+  int64_t n_flag_mismatch;  /* follow mode: differing ancestors that were flagged */
+  int64_t n_hard_mismatch;  /* follow mode: differing ancestors that were not flagged */
+  int64_t n_overflow;       /* particles killed by the recursion-depth cap */
+  int64_t n_limit;          /* particles killed by the per-segment call limit */
+  int32_t n_segments;
+  int32_t n_resamples;
+  /* caller-owned outputs (any may be NULL) */
+  double *final_logw;   /* [N] */
+  double *real_fields;  /* [n_real][N] (FP32 values widened exactly) */
+  int32_t *int_fields;  /* [n_int][N]; field 0 is the block index (pc) */
+  double *stack;        /* [lam_stack_cap][N] (rate-shift) */
+  int32_t *ancestors;   /* [anc_capacity][N] */
+  double *incr;         /* [incr_capacity] per-segment log-Z increments */
+  int32_t anc_capacity;
+  int32_t incr_capacity;
+} orc_out;
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void orc_philox_many(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
+int orc_sample(int32_t dist, int32_t precision, double p1, double p2, uint64_t seed,
+               uint32_t run_id, int64_t n, double *out, int32_t *blocks_used);
+int orc_resample(const double *logw, int64_t N, double u, int32_t *anc, int32_t *flag,
+                 double *incr, double *m_out, double *S_out);
+int orc_smc_run(const orc_model *m, const orc_cfg *c, orc_out *o);
+int orc_n_fields(const orc_model *m, int32_t *n_real, int32_t *n_int, int32_t *stack_cap);
+#ifdef __cplusplus
+}
+#endif
+#endif
