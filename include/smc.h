@@ -1,0 +1,224 @@
+/*
+ * smc.h -- C ABI of the GB300 particle-SMC library.
+ *
+ * The library runs Sequential Monte Carlo over a PPL control-flow graph
+ * (PCFG) as defined in Lunden et al., "Compiling Universal Probabilistic
+ * Programming Languages with Efficient Parallel Sequential Monte Carlo
+ * Inference" (ESOP 2022): a PCFG is the 6-tuple (B, S, sim, b0, b_stop, L)
+ * of Section 3.1; Algorithm 1 (Section 3.2) propagates every particle with
+ * sim() until all have reached a checkpoint, then resamples; the RootPPL
+ * engine of Section 3.3 stops when every particle is at b_stop, stores the
+ * particle state as separate arrays, duplicates particles with a custom
+ * aligned copy, resamples systematically and estimates the normalising
+ * constant.
+ *
+ * Conventions for every call:
+ *   - Plain C types only; device pointers are CUDA device addresses; a
+ *     `stream` argument is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).
+ *   - The return value is an smc_status: 0 = success, < 0 = error (nothing
+ *     useful was produced), > 0 = success with a warning.  No call aborts,
+ *     traps or throws across the ABI; device-side failures come back as
+ *     status words.  smc_last_error() gives a thread-local message for the
+ *     last non-zero status of the calling thread.
+ *   - The library never frees caller buffers.  Handles are opaque and are
+ *     released only by their *_destroy call.
+ *   - FP64 is used for the normaliser, the cumulative-weight scan and the
+ *     log-Z accumulation in every precision mode.
+ */
+#ifndef SMC_H
+#define SMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t smc_status;
+#define SMC_OK 0
+#define SMC_EINVAL (-1)       /* bad argument; nothing was launched */
+#define SMC_ENOMEM (-2)       /* device or host allocation failed */
+#define SMC_ECUDA (-3)        /* a CUDA runtime call failed (see smc_last_error) */
+#define SMC_EDEGENERATE (-4)  /* every particle weight became zero; log Z = -inf */
+#define SMC_ESTEPLIMIT (-5)   /* max_segments reached before every particle hit b_stop */
+#define SMC_ETIMEOUT (-6)     /* a bounded wait gave up (server wait, device barrier) */
+#define SMC_EBUSY (-7)        /* resource temporarily unavailable (server full) */
+#define SMC_WKILLED 1         /* success; some particles were killed by the recursion-depth
+                                 cap, the per-segment call limit or the stack capacity */
+
+/* Built-in block tables (the B, S and sim of Section 3.1).
+ *   LG         state-space model of Eq. 2 / Fig. 3, generalised to
+ *              x0 ~ N(x0_mean, x0_sd^2), x_t = a x_{t-1} + b + q_sd z, y_t ~ N(x_t, r_sd^2);
+ *              blocks: 0 init (jumps to iter without a checkpoint), 1 iter (checkpoint).
+ *   CRBD       constant-rate birth-death model of Listing 1 on a fixed tree:
+ *              block 0 draws the priors and weights by the correction factor,
+ *              block 1 simulates one branch of the left-first preorder, including the
+ *              hidden side lineages (simBranch / crbdGoesUndetected / iter) on an
+ *              explicit per-particle stack, and weights lnProb1+lnProb2+lnProb3.
+ *   RATESHIFT  CRBD with a per-branch LogNormal(0, sigma^2) multiplier on the birth rate,
+ *              inherited from the parent branch; pending parent rates are kept on a
+ *              PSTATE stack that resampling copies only up to its stack pointer.
+ *   GEOMETRIC  the weighted geometric program of Fig. 2a with a checkpoint after each flip.
+ * Every model uses b_stop = -1 as its block index. */
+#define SMC_MODEL_LG 1
+#define SMC_MODEL_CRBD 2
+#define SMC_MODEL_RATESHIFT 3
+#define SMC_MODEL_GEOMETRIC 4
+
+#define SMC_PREC_FP64 0 /* FP64 particle arithmetic and log-weights */
+#define SMC_PREC_FP32 1 /* FP32 particle arithmetic and log-weights; FP64 reductions */
+
+#define SMC_MEM_HOST 0
+#define SMC_MEM_DEVICE 1
+
+#define SMC_MAX_DEPTH 64 /* largest hidden-lineage recursion cap the CRBD blocks accept */
+
+typedef struct smc_model_s *smc_model_t;
+
+/* Model description.  All pointers are HOST pointers; smc_model_register copies
+ * what it needs into device memory owned by the model handle. */
+typedef struct {
+  int32_t kind;     /* SMC_MODEL_* */
+  int32_t T;        /* LG: number of observations (= checkpoints) */
+  int32_t n_nodes;  /* tree models: 2 * tips - 1 */
+  int32_t fixed_rates;   /* tree models: 1 = use lambda_fixed / mu_fixed, 0 = Gamma priors */
+  const double *obs;     /* LG: y_1..y_T, [T] */
+  double x0_mean, x0_sd, a, b, q_sd, r_sd; /* LG parameters */
+  /* tree arrays, root = node 0: parent[root] = -1, left/right = -1 at tips,
+   * age = time before present (tips 0), preorder = left-first node order, root first */
+  const int32_t *parent, *left, *right, *preorder;
+  const double *age;
+  double rho;                      /* sampling fraction */
+  double lambda_fixed, mu_fixed;   /* fixed_rates = 1 */
+  double lambda_scale, mu_scale;   /* fixed_rates = 0: lambda ~ Gamma(1, lambda_scale),
+                                      mu ~ Gamma(1, mu_scale), shape-scale */
+  double sigma;                    /* RATESHIFT: log-normal sd of the per-branch multiplier */
+  const double *fixed_mult;        /* RATESHIFT: optional per-node multipliers [n_nodes], or NULL */
+  int32_t depth_cap;               /* hidden-lineage recursion cap in frames, 1..SMC_MAX_DEPTH */
+  int32_t call_limit;              /* undetected-lineage calls per particle per segment */
+  int32_t lam_stack_cap;           /* RATESHIFT: pending-rate stack capacity (>= tree need) */
+  int32_t pad_;
+  double geo_p, geo_logw;          /* GEOMETRIC: heads probability, log weight per heads */
+} smc_model_desc;
+
+/* Per-run configuration. */
+typedef struct {
+  int64_t n_particles;   /* N >= 1 */
+  uint64_t seed;         /* Philox key = (seed_lo32, seed_hi32 XOR run_id) */
+  uint32_t run_id;
+  int32_t precision;     /* SMC_PREC_* */
+  int32_t max_segments;  /* 0 = the model's own segment count (unbounded models: 1 << 20) */
+  int32_t record_all_ancestors; /* 1: keep every resampling's ancestors, 0: only the last */
+  void *workspace;       /* optional caller-owned device workspace (>= smc_workspace_bytes);
+                            NULL = the model handle allocates and caches one */
+  size_t workspace_bytes;
+} smc_run_cfg;
+
+/* Counters of one run (host struct, filled by smc_run before it returns). */
+typedef struct {
+  int32_t n_segments;       /* segments executed (= log-Z increments) */
+  int32_t n_resamples;      /* resampling steps executed */
+  int64_t n_near_boundary;  /* resampled offsets within 1e-12 N of a cumulative-weight boundary */
+  int64_t n_overflow;       /* particle-segments killed by the depth cap or stack capacity */
+  int64_t n_limit;          /* particle-segments killed by the call limit */
+  double device_ms;         /* GPU time of the run (CUDA events) */
+} smc_counters;
+
+/* Outputs of one run.  `where` says whether every pointer below is host or
+ * device memory.  Any pointer may be NULL (that output is skipped). */
+typedef struct {
+  int32_t where;             /* SMC_MEM_HOST or SMC_MEM_DEVICE */
+  int32_t ancestors_rows;    /* capacity of `ancestors` in rows of N */
+  double *log_z;             /* [1] log of the normalising-constant estimate */
+  double *final_logw;        /* [N] log-weights after the last segment (not resampled) */
+  int32_t *ancestors;        /* [rows][N]: row r = ancestors of resampling r (record_all), or the
+                                last resampling's ancestors in row 0 */
+  double *real_fields;       /* [n_real][N] final real state fields, field-major, widened to f64 */
+  int32_t *int_fields;       /* [n_int][N] final int fields; field 0 is the block index */
+  double *stack;             /* [stack_cap][N] final PSTATE stack (RATESHIFT), entries >= sp are 0 */
+  smc_counters counters;     /* filled on return */
+} smc_result;
+
+/* Register a model: validates `d`, copies observations / tree arrays to device
+ * memory owned by the returned handle.  Section 3.1 (the PCFG being run) and
+ * Section 3.3 (observations as shared global constant data).
+ * Errors: SMC_EINVAL (bad description), SMC_ENOMEM, SMC_ECUDA. */
+smc_status smc_model_register(const smc_model_desc *d, smc_model_t *out);
+
+/* Release a model handle and everything it owns.  NULL is ignored.  The caller
+ * must ensure no run using the handle is in flight. */
+void smc_model_destroy(smc_model_t m);
+
+/* Shape of a model's PSTATE: number of real and int fields, stack capacity and
+ * the number of checkpoints a run takes (0 if it is not known in advance). */
+smc_status smc_model_info(smc_model_t m, int32_t *n_real, int32_t *n_int, int32_t *stack_cap,
+                          int32_t *n_segments);
+
+/* Device workspace a run of `c` on `m` needs, in bytes. */
+smc_status smc_workspace_bytes(smc_model_t m, const smc_run_cfg *c, size_t *bytes);
+
+/* Run Algorithm 1 with N particles on model m (Section 3.2) in the RootPPL loop
+ * order (Section 3.3): every segment runs one fused CUDA kernel that gathers each
+ * particle from its systematic-resampling ancestor, executes blocks until the next
+ * checkpoint with per-warp PC-sorted dispatch, and reduces the population's weights
+ * (FP64 log-sum-exp and prefix scan); the log-Z increment of every segment is added
+ * and resampling stops once every particle is at b_stop.  The call enqueues on
+ * `stream` and returns after the stream has completed the run (results valid).
+ * A model handle runs one call at a time.
+ * Errors: SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA, SMC_EDEGENERATE (log_z = -inf),
+ * SMC_ESTEPLIMIT.  Warning: SMC_WKILLED. */
+smc_status smc_run(smc_model_t m, const smc_run_cfg *c, smc_result *r, void *stream);
+
+/* ---------------- resampling primitives on caller device buffers ----------------
+ * These are the normaliser / scan / systematic search / gather of Section 3.3 as
+ * standalone HBM-streaming kernels.  All pointers are device pointers. */
+
+/* Scratch bytes smc_resample needs for a population of N. */
+size_t smc_resample_workspace_bytes(int64_t N);
+
+/* Systematic resampling of one population (Section 3.3, parallel systematic
+ * resampling): m = max logw, S = sum exp(logw - m), P_j = running sum,
+ * ancestors[i] = min{ j : P_j * (N / S) > i + u } (N - 1 if none).
+ * logw [N] f64 in, ancestors [N] int32 out, out3 [3] f64 out = {m, S, m + (log S - log N)},
+ * n_near [1] int64 out (offsets within 1e-12 N of a boundary).  u in (0,1).
+ * Errors: SMC_EINVAL (N < 1, u outside (0,1), NULL pointer, workspace too small),
+ * SMC_ECUDA.  An all -inf population gives ancestors = identity and out3 = {-inf, 0, -inf}. */
+smc_status smc_resample(const double *logw, int64_t N, double u, int32_t *ancestors,
+                        double *out3, int64_t *n_near, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
+/* Particle duplication with a stack-pointer-bounded copy (Section 3.3): for each
+ * field f and particle i, dst[f][i] = src[f][anc[i]] (fields field-major, elem_bytes
+ * 4 or 8 each); if sp != NULL, stack rows s >= sp[anc[i]] are not copied (they are
+ * left as they were in dst).  Arrays: src/dst [n_fields][N], anc [N], sp [N] or NULL.
+ * Errors: SMC_EINVAL, SMC_ECUDA. */
+smc_status smc_gather(const void *src, void *dst, const int32_t *anc, const int32_t *sp,
+                      int64_t N, int32_t n_fields, int32_t elem_bytes, void *stream);
+
+/* ---------------- random-number parity hooks ---------------- */
+
+/* Raw Philox4x32-10 blocks: out[i] = philox(ctr[i], key[i]); ctr [n][4], key [n][2],
+ * out [n][4] uint32, device pointers.  Errors: SMC_EINVAL, SMC_ECUDA. */
+smc_status smc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                      void *stream);
+
+/* n variates of one recipe, variate i drawn from counter (i, 0, d, 0) with d from 0:
+ * dist 0 uniform(0,1), 1 normal(p1, p2), 2 exponential(rate p1), 3 gamma(1, scale p1),
+ * 4 uniform(p1, p2), 5 bernoulli(p1), 6 poisson(p1), 7 lognormal(0, p1).
+ * out [n] f64 and blocks [n] int32 (Philox blocks consumed, may be NULL) are device
+ * pointers.  Errors: SMC_EINVAL, SMC_ECUDA. */
+smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uint64_t seed,
+                      uint32_t run_id, int64_t n, double *out, int32_t *blocks, void *stream);
+
+/* Thread-local description of the calling thread's last error ("" if none). */
+const char *smc_last_error(void);
+
+/* Library version string. */
+const char *smc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMC_H */

@@ -1,0 +1,279 @@
+// smc_device.cuh -- device building blocks of the particle-SMC engine:
+// counter-based random numbers, the variate recipes used by SAMPLE, and
+// warp/block FP64 reductions used by the normaliser and the scan.
+//
+// Random numbers (Section 3.3 gives each particle its own seed; here the
+// generator is counter-based so no per-particle RNG state exists at all):
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key
+// (seed_lo32, seed_hi32 ^ run_id), counter (particle slot n, checkpoint index
+// k, draw index d, tag) with tag 0 = model draws, 1 = resampling uniform,
+// 2 = rate-shift multipliers.  One 128-bit block per variate.
+//
+// The library is compiled with -fmad=false: an expression a*b+c below is two
+// roundings; a fused multiply-add is always written as fma().
+#pragma once
+#include <cstdint>
+#include <math.h>
+
+namespace smc {
+
+constexpr int PC_STOP = -1;
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr float kLn2f = 0.693147182f;
+constexpr double kTwoPi = 6.28318530717958647692;
+constexpr float kTwoPif = 6.28318548f;
+constexpr double kBoundaryEps = 1e-12;
+
+struct Block4 {
+  uint32_t w0, w1, w2, w3;
+};
+
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+// Philox4x32 with 10 rounds: each round multiplies counter words 0 and 2 by
+// the two round constants, swaps and xors in the key; the key is bumped by
+// the two Weyl constants between rounds.
+__host__ __device__ __forceinline__ Block4 philox(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                  uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = mulhi32(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = mulhi32(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return Block4{c0, c1, c2, c3};
+}
+
+// A particle's draw stream for one segment: counter (n, k, d, tag), d counts blocks.
+struct Stream {
+  uint32_t k0, k1, n, k, d, tag;
+  __device__ __forceinline__ Block4 next() {
+    Block4 b = philox(n, k, d, tag, k0, k1);
+    d += 1;
+    return b;
+  }
+};
+
+// ---- uniforms: exact odd-integer grids strictly inside (0,1) ----
+template <typename R>
+struct Unif;
+template <>
+struct Unif<double> {
+  // ((w_hi:w_lo) >> 11) | 1, times 2^-53 (53-bit integer: exact in double)
+  __device__ __forceinline__ static double first(const Block4& b) {
+    const uint64_t x = ((uint64_t)b.w1 << 32) | b.w0;
+    return (double)((x >> 11) | 1ull) * 0x1p-53;
+  }
+  __device__ __forceinline__ static double second(const Block4& b) {
+    const uint64_t x = ((uint64_t)b.w3 << 32) | b.w2;
+    return (double)((x >> 11) | 1ull) * 0x1p-53;
+  }
+};
+template <>
+struct Unif<float> {
+  // (w >> 8) | 1, times 2^-24 (24-bit integer: exact in float)
+  __device__ __forceinline__ static float first(const Block4& b) {
+    return (float)((b.w0 >> 8) | 1u) * 0x1p-24f;
+  }
+  __device__ __forceinline__ static float second(const Block4& b) {
+    return (float)((b.w1 >> 8) | 1u) * 0x1p-24f;
+  }
+};
+
+// ---- precision-overloaded math (IEEE library calls, no fast-math) ----
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_cos(double x) { return cos(x); }
+__device__ __forceinline__ float m_cos(float x) { return cosf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float m_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double m_lgamma(double x) { return lgamma(x); }
+__device__ __forceinline__ float m_lgamma(float x) { return lgammaf(x); }
+__device__ __forceinline__ double m_floor(double x) { return floor(x); }
+__device__ __forceinline__ float m_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double m_fabs(double x) { return fabs(x); }
+__device__ __forceinline__ float m_fabs(float x) { return fabsf(x); }
+
+template <typename R>
+struct C;
+template <>
+struct C<double> {
+  static constexpr double ln2 = kLn2, two_pi = kTwoPi;
+};
+template <>
+struct C<float> {
+  static constexpr float ln2 = kLn2f, two_pi = kTwoPif;
+};
+
+template <typename R>
+__device__ __forceinline__ R neg_inf() {
+  return -(R)INFINITY;
+}
+
+// ---- variates (SAMPLE) ----
+template <typename R>
+__device__ __forceinline__ R uniform01(Stream& s) {
+  return Unif<R>::first(s.next());
+}
+
+// Box-Muller, cosine branch: sqrt(-2 ln u1) * cos(2 pi u2)
+template <typename R>
+__device__ __forceinline__ R normal01(Stream& s) {
+  const Block4 b = s.next();
+  const R u1 = Unif<R>::first(b);
+  const R u2 = Unif<R>::second(b);
+  const R rad = m_sqrt((R)-2.0 * m_log(u1));
+  return rad * m_cos(C<R>::two_pi * u2);
+}
+
+// Exponential(rate): -ln(u) / rate
+template <typename R>
+__device__ __forceinline__ R exponential(Stream& s, R rate) {
+  const R u = uniform01<R>(s);
+  return -m_log(u) / rate;
+}
+
+// Gamma(shape 1, scale theta): theta * (-ln u)
+template <typename R>
+__device__ __forceinline__ R gamma1(Stream& s, R theta) {
+  const R u = uniform01<R>(s);
+  return theta * -m_log(u);
+}
+
+// Uniform(lo, hi): fma(hi - lo, u, lo)
+template <typename R>
+__device__ __forceinline__ R uniform_ab(Stream& s, R lo, R hi) {
+  const R u = uniform01<R>(s);
+  return m_fma(hi - lo, u, lo);
+}
+
+template <typename R>
+__device__ __forceinline__ bool bernoulli(Stream& s, R p) {
+  return uniform01<R>(s) < p;
+}
+
+// Poisson(mean): sequential-search inversion below 10 (one uniform, at most
+// 200 terms); Hormann's transformed rejection with squeeze (PTRS, 1993) from
+// 10 up, one block per trial, at most 1000 trials.
+template <typename R>
+__device__ __noinline__ int poisson(Stream& s, R mean) {
+  if (mean < (R)10.0) {
+    const R u = uniform01<R>(s);
+    int k = 0;
+    R p = m_exp(-mean);
+    R acc = p;
+    while (u > acc && k < 200) {
+      k += 1;
+      p = p * mean / (R)k;
+      acc = acc + p;
+    }
+    return k;
+  }
+  const R slam = m_sqrt(mean);
+  const R loglam = m_log(mean);
+  const R b = (R)0.931 + (R)2.53 * slam;
+  const R a = (R)-0.059 + (R)0.02483 * b;
+  const R invalpha = (R)1.1239 + (R)1.1328 / (b - (R)3.4);
+  const R vr = (R)0.9277 - (R)3.6224 / (b - (R)2.0);
+  for (int trial = 0; trial < 1000; ++trial) {
+    const Block4 blk = s.next();
+    const R U = Unif<R>::first(blk) - (R)0.5;
+    const R V = Unif<R>::second(blk);
+    const R us = (R)0.5 - m_fabs(U);
+    const R kr = m_floor(((R)2.0 * a / us + b) * U + mean + (R)0.43);
+    if (us >= (R)0.07 && V <= vr) return (int)kr;
+    if (kr < (R)0.0 || (us < (R)0.013 && V > us)) continue;
+    if (m_log(V) + m_log(invalpha) - m_log(a / (us * us) + b) <=
+        -mean + kr * loglam - m_lgamma(kr + (R)1.0))
+      return (int)kr;
+  }
+  return (int)m_floor(mean);
+}
+
+// LogNormal(0, sigma) = exp(sigma * N(0,1))
+template <typename R>
+__device__ __forceinline__ R lognormal(Stream& s, R sigma) {
+  return m_exp(sigma * normal01<R>(s));
+}
+
+// ---- FP64 warp / block primitives (deterministic association order) ----
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_incl_scan(double v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = v + t;
+  }
+  return v;
+}
+
+// Block max over TPB threads; every thread gets the result.  `sh` >= TPB/32 doubles.
+template <int TPB>
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double r = sh[0];
+#pragma unroll
+  for (int w = 1; w < TPB / 32; ++w) r = fmax(r, sh[w]);
+  return r;
+}
+
+// Block inclusive scan over TPB threads (warp scans, then the warp totals
+// scanned in order by every thread).  `sh` >= TPB/32 doubles.
+template <int TPB>
+__device__ __forceinline__ double block_incl_scan(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_incl_scan(v);
+  __syncthreads();
+  if (lane == 31) sh[wid] = v;
+  __syncthreads();
+  double off = 0.0;
+  for (int w = 0; w < wid; ++w) off = off + sh[w];
+  return wid > 0 ? off + v : v;
+}
+
+// Block inclusive prefix max over TPB threads.  `sh` >= TPB/32 doubles.
+template <int TPB>
+__device__ __forceinline__ double block_incl_max(double v, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = fmax(v, t);
+  }
+  __syncthreads();
+  if (lane == 31) sh[wid] = v;
+  __syncthreads();
+  for (int w = 0; w < wid; ++w) v = fmax(v, sh[w]);
+  return v;
+}
+
+}  // namespace smc

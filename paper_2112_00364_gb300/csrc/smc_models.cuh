@@ -1,0 +1,397 @@
+// smc_models.cuh -- the built-in PCFG block tables (the B, S and sim of
+// Section 3.1) and the per-warp PC-sorted dispatch loop that runs them.
+//
+// A model supplies:
+//   Lane           per-particle registers for one segment (PSTATE fields that
+//                  cross checkpoints plus segment-local scratch);
+//   init/gather/store  PSTATE <-> registers (gather = Section 3.3's particle
+//                  duplication, reading the ancestor's slot of the SoA arrays);
+//   block(b, ...)  one basic block; sets pc to the successor and `ckpt` when
+//                  the block ends in a checkpoint (Algorithm 1's c_n).
+// Block index PC_STOP (-1) is b_stop: sim(b_stop, s) = (b_stop, s, true).
+#pragma once
+#include "../../include/smc.h"
+#include "smc_device.cuh"
+
+namespace smc {
+
+// Model constants resident in device memory (Section 3.3: observations and
+// the tree are shared global constants, not per-particle state).
+struct ModelDev {
+  int kind, T, n_nodes, fixed_rates, depth_cap, call_limit, lam_stack_cap, pad_;
+  const double* obs;
+  const int* parent;
+  const int* left;
+  const int* preorder;
+  const double* age;
+  const double* fixed_mult;
+  double x0_mean, x0_sd, a, b, q_sd, r_sd, lg_lc, corr;
+  double rho, lambda_fixed, mu_fixed, lambda_scale, mu_scale, sigma, geo_p, geo_logw;
+};
+
+// One buffer of the double-buffered SoA PSTATE (Section 3.3's separate arrays
+// per field): real fields [n_real][N], int fields [n_int][N] (field 0 = block
+// index), stack rows [cap][N].  Field-major with particle index fastest so a
+// warp touches 32 consecutive elements of every field.
+struct StateView {
+  void* real;
+  int32_t* ints;
+  void* stack;
+  template <typename R>
+  __device__ __forceinline__ R& rf(int f, int i, int N) const {
+    return reinterpret_cast<R*>(real)[(size_t)f * N + i];
+  }
+  __device__ __forceinline__ int32_t& inf_(int f, int i, int N) const {
+    return ints[(size_t)f * N + i];
+  }
+  template <typename R>
+  __device__ __forceinline__ R& st(int s, int i, int N) const {
+    return reinterpret_cast<R*>(stack)[(size_t)s * N + i];
+  }
+};
+
+// ------------------------------------------------------------------------
+// Linear-Gaussian state-space model (Eq. 2 family, blocks of Fig. 3):
+//   block 0 `init`: x = x0_mean + x0_sd z, then a non-checkpoint jump to iter;
+//   block 1 `iter`: x = a x + (b + q_sd z); observe y_k ~ N(x, r_sd^2);
+//                   checkpoint; NEXT = b_stop after the T-th observation.
+// The observation index equals the checkpoint index k (all particles reach
+// every checkpoint together), so t is not stored per particle.
+// ------------------------------------------------------------------------
+template <typename Real>
+struct LgModel {
+  using R = Real;
+  static constexpr int NB = 2, N_REAL = 1, N_INT = 1;
+  static constexpr bool HAS_STACK = false;
+  struct Lane {
+    int pc;
+    bool ckpt;
+    R x, logw;
+    int overflow, limited;
+  };
+  __device__ static void init(Lane& L) {
+    L.pc = 0;
+    L.x = (R)0;
+    L.logw = (R)0;
+  }
+  __device__ static void gather(Lane& L, const StateView& Sc, const StateView&, int a, int, int N,
+                                const ModelDev&) {
+    L.x = Sc.rf<R>(0, a, N);
+    L.pc = Sc.inf_(0, a, N);
+    L.logw = (R)0;
+  }
+  __device__ static void store(const Lane& L, const StateView& Sn, int i, int N) {
+    Sn.rf<R>(0, i, N) = L.x;
+    Sn.inf_(0, i, N) = L.pc;
+  }
+  __device__ static void begin(Lane& L) {
+    L.ckpt = false;
+    L.overflow = L.limited = 0;
+  }
+  __device__ static void block(int b, Lane& L, Stream& s, const ModelDev& md, const StateView&, int,
+                               int k, int) {
+    if (b == 0) {
+      const R z0 = normal01<R>(s);
+      L.x = m_fma((R)md.x0_sd, z0, (R)md.x0_mean);
+      L.pc = 1;
+      return;
+    }
+    const R z = normal01<R>(s);
+    L.x = m_fma((R)md.a, L.x, m_fma((R)md.q_sd, z, (R)md.b));
+    const R y = (R)md.obs[k];
+    const R dz = (y - L.x) / (R)md.r_sd;
+    const R lp = (R)-0.5 * (dz * dz) - (R)md.lg_lc;
+    L.logw = L.logw + lp;
+    L.pc = (k + 1 == md.T) ? PC_STOP : 1;
+    L.ckpt = true;
+  }
+};
+
+// ------------------------------------------------------------------------
+// Weighted geometric program (Fig. 2a) with a checkpoint after every flip:
+// block 0 flips Bernoulli(p); heads -> weight geo_logw and loop, tails ->
+// b_stop.  Particles finish at different checkpoints; finished ones keep
+// taking part in resampling.
+// ------------------------------------------------------------------------
+template <typename Real>
+struct GeoModel {
+  using R = Real;
+  static constexpr int NB = 1, N_REAL = 0, N_INT = 2;
+  static constexpr bool HAS_STACK = false;
+  struct Lane {
+    int pc, count;
+    bool ckpt;
+    R logw;
+    int overflow, limited;
+  };
+  __device__ static void init(Lane& L) {
+    L.pc = 0;
+    L.count = 0;
+    L.logw = (R)0;
+  }
+  __device__ static void gather(Lane& L, const StateView& Sc, const StateView&, int a, int, int N,
+                                const ModelDev&) {
+    L.pc = Sc.inf_(0, a, N);
+    L.count = Sc.inf_(1, a, N);
+    L.logw = (R)0;
+  }
+  __device__ static void store(const Lane& L, const StateView& Sn, int i, int N) {
+    Sn.inf_(0, i, N) = L.pc;
+    Sn.inf_(1, i, N) = L.count;
+  }
+  __device__ static void begin(Lane& L) {
+    L.ckpt = false;
+    L.overflow = L.limited = 0;
+  }
+  __device__ static void block(int, Lane& L, Stream& s, const ModelDev& md, const StateView&, int,
+                               int, int) {
+    const bool heads = bernoulli<R>(s, (R)md.geo_p);
+    L.count += 1;
+    if (heads) {
+      L.logw = L.logw + (R)md.geo_logw;
+      L.pc = 0;
+    } else {
+      L.pc = PC_STOP;
+    }
+    L.ckpt = true;
+  }
+};
+
+// ------------------------------------------------------------------------
+// Birth-death tree models (Listing 1).  PSTATE crossing checkpoints:
+// real 0 = lambda (RATESHIFT: the root rate lambda0), real 1 = mu, int 0 =
+// block index; RATESHIFT adds int 1 = stack pointer and the pending-rate
+// stack rows.  Segment-local scratch (the hidden-lineage call stack of
+// crbdGoesUndetected / iter) never crosses a checkpoint, so it lives in the
+// lane's registers and thread-local memory.
+//
+// Blocks (checkpoints only after 0 and 5):
+//   0 PRIOR      lambda ~ Gamma(1, ls), mu ~ Gamma(1, ms); weight(corrFactor)
+//   1 BRANCH     simTree body for node v = preorder[k]: lnProb1 = -mu dt,
+//                lnProb2 = ln lambda (internal) or ln rho (tip), n ~ Poisson(lambda dt)
+//   2 SIMBRANCH  simBranch loop: next hidden event time ~ U(stop, start)
+//   3 UNDET      crbdGoesUndetected(t): dur ~ Exp(mu); if dur > t, detected
+//                with prob rho; j ~ Poisson(lambda min(dur, t)); push a frame
+//   4 ITER       iter loop of the top frame: next event ~ U(t - bl, t), or pop
+//   5 END        weight(lnProb1 + (lnProb2 + lnProb3)); checkpoint
+// A detected hidden lineage makes lnProb3 = -inf and ends the branch at once.
+// A call deeper than depth_cap, or the (call_limit+1)-th call of a segment,
+// kills the particle (lnProb3 = -inf) and is counted.
+// ------------------------------------------------------------------------
+template <typename Real, bool RS>
+struct TreeModel {
+  using R = Real;
+  static constexpr int NB = 6, N_REAL = 2, N_INT = RS ? 2 : 1;
+  static constexpr bool HAS_STACK = RS;
+  enum { PRIOR = 0, BRANCH = 1, SIMBRANCH = 2, UNDET = 3, ITER = 4, END = 5 };
+  struct Lane {
+    int pc, sp, v, n_top, fsp, calls;
+    bool ckpt;
+    int overflow, limited;
+    R lam, mu, logw;
+    R lam_b, start, stop, lnp1, lnp2, lnp3, cur_t;
+    R fr_t[SMC_MAX_DEPTH], fr_bl[SMC_MAX_DEPTH];
+    int fr_rem[SMC_MAX_DEPTH];
+  };
+  __device__ static void init(Lane& L) {
+    L.pc = PRIOR;
+    L.sp = 0;
+    L.lam = L.mu = (R)0;
+    L.logw = (R)0;
+  }
+  __device__ static void gather(Lane& L, const StateView& Sc, const StateView& Sn, int a, int i,
+                                int N, const ModelDev&) {
+    L.lam = Sc.rf<R>(0, a, N);
+    L.mu = Sc.rf<R>(1, a, N);
+    L.pc = Sc.inf_(0, a, N);
+    L.logw = (R)0;
+    if (RS) {
+      // stack-pointer-bounded copy: only rows [0, sp) of the ancestor's stack
+      L.sp = Sc.inf_(1, a, N);
+      for (int r = 0; r < L.sp; ++r) Sn.st<R>(r, i, N) = Sc.st<R>(r, a, N);
+    }
+  }
+  __device__ static void store(const Lane& L, const StateView& Sn, int i, int N) {
+    Sn.rf<R>(0, i, N) = L.lam;
+    Sn.rf<R>(1, i, N) = L.mu;
+    Sn.inf_(0, i, N) = L.pc;
+    if (RS) Sn.inf_(1, i, N) = L.sp;
+  }
+  __device__ static void begin(Lane& L) {
+    L.ckpt = false;
+    L.overflow = L.limited = 0;
+  }
+  __device__ __forceinline__ static void ret_true(Lane& L) {
+    // an undetected call returned true: to simBranch (no frame left) or to
+    // the iter loop of the frame below
+    if (L.fsp == 0) {
+      L.lnp3 = L.lnp3 + C<R>::ln2;
+      L.pc = SIMBRANCH;
+    } else {
+      L.pc = ITER;
+    }
+  }
+  __device__ static void block(int b, Lane& L, Stream& s, const ModelDev& md, const StateView& S,
+                               int i, int k, int N) {
+    switch (b) {
+      case PRIOR: {
+        if (md.fixed_rates) {
+          L.lam = (R)md.lambda_fixed;
+          L.mu = (R)md.mu_fixed;
+        } else {
+          L.lam = gamma1<R>(s, (R)md.lambda_scale);
+          L.mu = gamma1<R>(s, (R)md.mu_scale);
+        }
+        if (RS) {
+          S.st<R>(0, i, N) = L.lam;  // the root's rate, pending for its children
+          L.sp = 1;
+        }
+        L.logw = L.logw + (R)md.corr;
+        L.pc = BRANCH;
+        L.ckpt = true;
+        return;
+      }
+      case BRANCH: {
+        const int v = md.preorder[k];
+        const int p = md.parent[v];
+        L.v = v;
+        R lam = L.lam;
+        if (RS) {
+          R lam_p;
+          if (L.sp <= 0) {
+            lam_p = L.lam;
+          } else if (md.left[p] == v) {
+            lam_p = S.st<R>(L.sp - 1, i, N);  // left child: parent's rate stays pending
+          } else {
+            L.sp -= 1;  // right child: last use of the parent's rate
+            lam_p = S.st<R>(L.sp, i, N);
+          }
+          R mult;
+          if (md.fixed_mult) {
+            mult = (R)md.fixed_mult[v];
+          } else {
+            Stream sm{s.k0, s.k1, s.n, s.k, 0u, 2u};
+            mult = lognormal<R>(sm, (R)md.sigma);
+          }
+          lam = lam_p * mult;
+        }
+        L.lam_b = lam;
+        L.start = (R)md.age[p];
+        L.stop = (R)md.age[v];
+        const R dt = L.start - L.stop;
+        L.lnp1 = -L.mu * dt;
+        L.lnp2 = (md.left[v] >= 0) ? m_log(lam) : m_log((R)md.rho);
+        L.n_top = poisson<R>(s, lam * dt);
+        L.lnp3 = (R)0;
+        L.fsp = 0;
+        L.calls = 0;
+        L.pc = SIMBRANCH;
+        return;
+      }
+      case SIMBRANCH: {
+        if (L.n_top == 0) {
+          L.pc = END;
+          return;
+        }
+        L.n_top -= 1;
+        L.cur_t = uniform_ab<R>(s, L.stop, L.start);
+        L.pc = UNDET;
+        return;
+      }
+      case UNDET: {
+        if (L.fsp + 1 > md.depth_cap) {
+          L.overflow = 1;
+          L.lnp3 = neg_inf<R>();
+          L.pc = END;
+          return;
+        }
+        L.calls += 1;
+        if (L.calls > md.call_limit) {
+          L.limited = 1;
+          L.lnp3 = neg_inf<R>();
+          L.pc = END;
+          return;
+        }
+        const R t = L.cur_t;
+        const R dur = exponential<R>(s, L.mu);
+        if (dur > t) {
+          if (bernoulli<R>(s, (R)md.rho)) {
+            L.lnp3 = neg_inf<R>();
+            L.pc = END;
+            return;
+          }
+        }
+        const R bl = dur < t ? dur : t;
+        const int j = poisson<R>(s, L.lam_b * bl);
+        if (j == 0) {
+          ret_true(L);
+          return;
+        }
+        L.fr_t[L.fsp] = t;
+        L.fr_bl[L.fsp] = bl;
+        L.fr_rem[L.fsp] = j;
+        L.fsp += 1;
+        L.pc = ITER;
+        return;
+      }
+      case ITER: {
+        const int f = L.fsp - 1;
+        if (L.fr_rem[f] == 0) {
+          L.fsp = f;
+          ret_true(L);
+          return;
+        }
+        L.fr_rem[f] -= 1;
+        const R t = L.fr_t[f];
+        const R lo = t - L.fr_bl[f];
+        L.cur_t = uniform_ab<R>(s, lo, t);
+        L.pc = UNDET;
+        return;
+      }
+      default: {  // END
+        L.logw = L.logw + (L.lnp1 + (L.lnp2 + L.lnp3));
+        if (RS && md.left[L.v] >= 0) {
+          if (L.sp < md.lam_stack_cap) {
+            S.st<R>(L.sp, i, N) = L.lam_b;
+            L.sp += 1;
+          } else {
+            L.logw = neg_inf<R>();
+            L.overflow += 1;
+          }
+        }
+        L.pc = (k + 1 == md.n_nodes) ? PC_STOP : BRANCH;
+        L.ckpt = true;
+        return;
+      }
+    }
+  }
+};
+
+// Per-warp PC-sorted dispatch: while any lane of the warp is still inside
+// its segment, pick the block index shared by the most such lanes (ties to
+// the larger index) and run that block on exactly those lanes.  The choice
+// is warp-uniform, so every block body runs without intra-warp divergence
+// on its block index.
+template <class M>
+__device__ __forceinline__ void run_segment(typename M::Lane& L, Stream& s, const ModelDev& md,
+                                            const StateView& S, int i, int k, int N, bool active) {
+  if (active) M::begin(L);
+  for (;;) {
+    const unsigned act = __ballot_sync(0xffffffffu, active);
+    if (act == 0u) break;
+    int sel;
+    if (M::NB == 1) {
+      sel = 0;
+    } else {
+      const unsigned peers = __match_any_sync(0xffffffffu, active ? L.pc : -2);
+      const unsigned key = active ? ((unsigned)__popc(peers) << 8) | (unsigned)L.pc : 0u;
+      sel = (int)(__reduce_max_sync(0xffffffffu, key) & 0xffu);
+    }
+    if (active && L.pc == sel) {
+      M::block(sel, L, s, md, S, i, k, N);
+      if (L.ckpt) active = false;
+    }
+  }
+}
+
+}  // namespace smc

@@ -1,0 +1,303 @@
+"""Python binding of the C ABI in include/smc.h (ctypes, argument marshalling only).
+
+Every step of the SMC path runs in the CUDA library ``libsmc.so``; this module
+only builds the C structs, hands over host (numpy) or device (torch CUDA)
+pointers and raises on a negative status.  There is no fallback: if the
+library cannot be loaded the import of ``lib()`` fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libsmc.so"
+
+OK, EINVAL, ENOMEM, ECUDA, EDEGENERATE, ESTEPLIMIT, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+WKILLED = 1
+MODEL_LG, MODEL_CRBD, MODEL_RATESHIFT, MODEL_GEOMETRIC = 1, 2, 3, 4
+KINDS = {"lg": MODEL_LG, "crbd": MODEL_CRBD, "rateshift": MODEL_RATESHIFT,
+         "geometric": MODEL_GEOMETRIC}
+PREC_FP64, PREC_FP32 = 0, 1
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
+MEM_HOST, MEM_DEVICE = 0, 1
+MAX_DEPTH = 64
+DIST = {"uniform": 0, "normal": 1, "exponential": 2, "gamma1": 3, "uniform_ab": 4,
+        "bernoulli": 5, "poisson": 6, "lognormal": 7}
+
+_i32p = C.POINTER(C.c_int32)
+_f64p = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+
+class SmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"smc status {status}: {msg}")
+        self.status = status
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("T", C.c_int32), ("n_nodes", C.c_int32), ("fixed_rates", C.c_int32),
+        ("obs", _f64p),
+        ("x0_mean", C.c_double), ("x0_sd", C.c_double), ("a", C.c_double), ("b", C.c_double),
+        ("q_sd", C.c_double), ("r_sd", C.c_double),
+        ("parent", _i32p), ("left", _i32p), ("right", _i32p), ("preorder", _i32p),
+        ("age", _f64p),
+        ("rho", C.c_double), ("lambda_fixed", C.c_double), ("mu_fixed", C.c_double),
+        ("lambda_scale", C.c_double), ("mu_scale", C.c_double), ("sigma", C.c_double),
+        ("fixed_mult", _f64p),
+        ("depth_cap", C.c_int32), ("call_limit", C.c_int32), ("lam_stack_cap", C.c_int32),
+        ("pad_", C.c_int32),
+        ("geo_p", C.c_double), ("geo_logw", C.c_double),
+    ]
+
+
+class RunCfg(C.Structure):
+    _fields_ = [("n_particles", C.c_int64), ("seed", C.c_uint64), ("run_id", C.c_uint32),
+                ("precision", C.c_int32), ("max_segments", C.c_int32),
+                ("record_all_ancestors", C.c_int32), ("workspace", _vp),
+                ("workspace_bytes", C.c_size_t)]
+
+
+class Counters(C.Structure):
+    _fields_ = [("n_segments", C.c_int32), ("n_resamples", C.c_int32),
+                ("n_near_boundary", C.c_int64), ("n_overflow", C.c_int64),
+                ("n_limit", C.c_int64), ("device_ms", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("where", C.c_int32), ("ancestors_rows", C.c_int32), ("log_z", _vp),
+                ("final_logw", _vp), ("ancestors", _vp), ("real_fields", _vp),
+                ("int_fields", _vp), ("stack", _vp), ("counters", Counters)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsmc.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+
+        if not _build.up_to_date():
+            _build.build()
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"CUDA library missing: {LIB_PATH}")
+        L = C.CDLL(str(LIB_PATH))
+        L.smc_model_register.argtypes = [C.POINTER(ModelDesc), C.POINTER(_vp)]
+        L.smc_model_register.restype = C.c_int32
+        L.smc_model_destroy.argtypes = [_vp]
+        L.smc_model_destroy.restype = None
+        L.smc_model_info.argtypes = [_vp, _i32p, _i32p, _i32p, _i32p]
+        L.smc_model_info.restype = C.c_int32
+        L.smc_workspace_bytes.argtypes = [_vp, C.POINTER(RunCfg), C.POINTER(C.c_size_t)]
+        L.smc_workspace_bytes.restype = C.c_int32
+        L.smc_run.argtypes = [_vp, C.POINTER(RunCfg), C.POINTER(Result), _vp]
+        L.smc_run.restype = C.c_int32
+        L.smc_resample_workspace_bytes.argtypes = [C.c_int64]
+        L.smc_resample_workspace_bytes.restype = C.c_size_t
+        L.smc_resample.argtypes = [_vp, C.c_int64, C.c_double, _vp, _vp, _vp, _vp, C.c_size_t, _vp]
+        L.smc_resample.restype = C.c_int32
+        L.smc_gather.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int32, _vp]
+        L.smc_gather.restype = C.c_int32
+        L.smc_philox.argtypes = [_vp, _vp, _vp, C.c_int64, _vp]
+        L.smc_philox.restype = C.c_int32
+        L.smc_sample.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint64,
+                                 C.c_uint32, C.c_int64, _vp, _vp, _vp]
+        L.smc_sample.restype = C.c_int32
+        L.smc_last_error.argtypes = []
+        L.smc_last_error.restype = C.c_char_p
+        L.smc_version.argtypes = []
+        L.smc_version.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st: int) -> int:
+    if st < 0:
+        raise SmcError(st, lib().smc_last_error().decode())
+    return st
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Model:
+    """A registered model (owns device copies of its observations / tree)."""
+
+    def __init__(self, kind: str, *, obs=None, tree=None, x0_mean=0.0, x0_sd=1.0, a=0.9, b=0.0,
+                 q_sd=1.0, r_sd=0.5, rho=1.0, rates=None, lambda_scale=1.0, mu_scale=0.5,
+                 sigma=0.3, fixed_mult=None, depth_cap=MAX_DEPTH, call_limit=1 << 16,
+                 lam_stack_cap=0, geo_p=0.5, geo_logw=float(np.log(1.5))):
+        d = ModelDesc()
+        keep = []
+        d.kind = KINDS[kind]
+        d.x0_mean, d.x0_sd, d.a, d.b, d.q_sd, d.r_sd = x0_mean, x0_sd, a, b, q_sd, r_sd
+        if obs is not None:
+            o = np.ascontiguousarray(obs, dtype=np.float64)
+            keep.append(o)
+            d.obs, d.T = o.ctypes.data_as(_f64p), o.shape[0]
+        if tree is not None:
+            arr = {k: np.ascontiguousarray(getattr(tree, k), dtype=np.int32)
+                   for k in ("parent", "left", "right", "preorder")}
+            age = np.ascontiguousarray(tree.age, dtype=np.float64)
+            keep += list(arr.values()) + [age]
+            d.parent, d.left, d.right, d.preorder = (arr[k].ctypes.data_as(_i32p)
+                                                     for k in ("parent", "left", "right", "preorder"))
+            d.age, d.n_nodes = age.ctypes.data_as(_f64p), tree.n_nodes
+        d.rho = rho
+        if rates is not None:
+            d.fixed_rates, d.lambda_fixed, d.mu_fixed = 1, rates[0], rates[1]
+        d.lambda_scale, d.mu_scale, d.sigma = lambda_scale, mu_scale, sigma
+        if fixed_mult is not None:
+            fm = np.ascontiguousarray(fixed_mult, dtype=np.float64)
+            keep.append(fm)
+            d.fixed_mult = fm.ctypes.data_as(_f64p)
+        d.depth_cap, d.call_limit, d.lam_stack_cap = depth_cap, call_limit, lam_stack_cap
+        d.geo_p, d.geo_logw = geo_p, geo_logw
+        h = _vp()
+        _check(lib().smc_model_register(C.byref(d), C.byref(h)))
+        self.handle = h
+        self.kind = kind
+        nr, ni, sc, ns = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().smc_model_info(h, C.byref(nr), C.byref(ni), C.byref(sc), C.byref(ns)))
+        self.n_real, self.n_int, self.stack_cap, self.n_segments = nr.value, ni.value, sc.value, ns.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().smc_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self, N: int, precision: str = "fp64", max_segments: int = 0,
+                        record_all_ancestors: bool = False) -> int:
+        cfg = _cfg(N, 0, 0, precision, max_segments, record_all_ancestors, None)
+        out = C.c_size_t()
+        _check(lib().smc_workspace_bytes(self.handle, C.byref(cfg), C.byref(out)))
+        return out.value
+
+
+def _cfg(N, seed, run_id, precision, max_segments, record_all, workspace):
+    c = RunCfg()
+    c.n_particles, c.seed, c.run_id = N, seed, run_id
+    c.precision = PRECISIONS[precision]
+    c.max_segments, c.record_all_ancestors = max_segments, int(record_all)
+    if workspace is not None:
+        c.workspace, c.workspace_bytes = _ptr(workspace), workspace.numel() * workspace.element_size()
+    return c
+
+
+def run(model: Model, N: int, seed: int, run_id: int = 0, precision: str = "fp64",
+        max_segments: int = 0, record_all_ancestors: bool = False, where: str = "host",
+        stream=None, workspace=None, outputs: dict | None = None) -> dict:
+    """smc_run.  where="host": outputs are numpy arrays; where="device": outputs are
+    torch CUDA tensors (allocated here unless passed in `outputs`)."""
+    cfg = _cfg(N, seed, run_id, precision, max_segments, record_all_ancestors, workspace)
+    rows = 1
+    if record_all_ancestors:
+        rows = max(1, (max_segments or model.n_segments or 4096) - 1)
+    shapes = dict(log_z=((1,), "f8"), final_logw=((N,), "f8"), ancestors=((rows, N), "i4"),
+                  real_fields=((model.n_real, N), "f8"), int_fields=((model.n_int, N), "i4"),
+                  stack=((model.stack_cap, N), "f8"))
+    out = dict(outputs or {})
+    if where == "host":
+        for k, (shp, dt) in shapes.items():
+            if k not in out and (k != "stack" or model.stack_cap) and (k != "real_fields" or model.n_real):
+                out[k] = np.zeros(shp, dtype=dt)
+    else:
+        import torch
+
+        tmap = {"f8": torch.float64, "i4": torch.int32}
+        for k, (shp, dt) in shapes.items():
+            if k not in out and (k != "stack" or model.stack_cap) and (k != "real_fields" or model.n_real):
+                out[k] = torch.zeros(shp, dtype=tmap[dt], device="cuda")
+    r = Result()
+    r.where = MEM_HOST if where == "host" else MEM_DEVICE
+    r.ancestors_rows = rows
+    for k in shapes:
+        setattr(r, k, _ptr(out.get(k)))
+    st = lib().smc_run(model.handle, C.byref(cfg), C.byref(r), _stream(stream))
+    if st < 0 and st not in (EDEGENERATE, ESTEPLIMIT):
+        _check(st)
+    c = r.counters
+    res = dict(status=st, n_segments=c.n_segments, n_resamples=c.n_resamples,
+               n_near_boundary=c.n_near_boundary, n_overflow=c.n_overflow, n_limit=c.n_limit,
+               device_ms=c.device_ms, **out)
+    res["log_z_value"] = float(out["log_z"][0]) if where == "host" else None
+    if record_all_ancestors and "ancestors" in out:
+        res["ancestors"] = out["ancestors"][: c.n_resamples]
+    return res
+
+
+def resample_workspace_bytes(N: int) -> int:
+    return int(lib().smc_resample_workspace_bytes(N))
+
+
+def resample(logw, u: float, ancestors=None, out3=None, n_near=None, workspace=None, stream=None):
+    """Standalone FP64 systematic resampling of a device population (torch f64 CUDA)."""
+    import torch
+
+    N = logw.numel()
+    dev = logw.device
+    anc = ancestors if ancestors is not None else torch.empty(N, dtype=torch.int32, device=dev)
+    o3 = out3 if out3 is not None else torch.empty(3, dtype=torch.float64, device=dev)
+    nn = n_near if n_near is not None else torch.empty(1, dtype=torch.int64, device=dev)
+    ws = workspace if workspace is not None else torch.empty(
+        resample_workspace_bytes(N), dtype=torch.uint8, device=dev)
+    _check(lib().smc_resample(_ptr(logw), N, u, _ptr(anc), _ptr(o3), _ptr(nn), _ptr(ws),
+                              ws.numel() * ws.element_size(), _stream(stream)))
+    return anc, o3, nn
+
+
+def gather(src, dst, anc, sp=None, stream=None):
+    """dst[f][i] = src[f][anc[i]] for 2-D [n_fields, N] device tensors of 4- or 8-byte elements."""
+    n_fields, N = src.shape
+    _check(lib().smc_gather(_ptr(src), _ptr(dst), _ptr(anc), _ptr(sp), N, n_fields,
+                            src.element_size(), _stream(stream)))
+    return dst
+
+
+def philox(ctr, key, stream=None):
+    """Raw Philox4x32-10 blocks for int32-typed device tensors ctr [n,4], key [n,2]."""
+    import torch
+
+    out = torch.empty_like(ctr)
+    _check(lib().smc_philox(_ptr(ctr), _ptr(key), _ptr(out), ctr.shape[0], _stream(stream)))
+    return out
+
+
+def sample(dist: str, n: int, p1: float = 0.0, p2: float = 0.0, seed: int = 1, run_id: int = 0,
+           precision: str = "fp64", stream=None):
+    import torch
+
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    blocks = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(lib().smc_sample(DIST[dist], PRECISIONS[precision], p1, p2, seed, run_id, n,
+                            _ptr(out), _ptr(blocks), _stream(stream)))
+    return out, blocks
+
+
+def version() -> str:
+    return lib().smc_version().decode()

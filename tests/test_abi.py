@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every symbol include/smc.h
+declares; host-side argument validation works without a GPU (CPU only)."""
+import ctypes as C
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_2112_00364_gb300 import smc
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def _declared_functions():
+    names = set()
+    for h in sorted((ROOT / "include").glob("*.h")):
+        text = h.read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(smc_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    L = smc.lib()
+    names = _declared_functions()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_version_string():
+    assert "sm_103a" in smc.version()
+
+
+def test_register_rejects_bad_descriptions():
+    L = smc.lib()
+    d = smc.ModelDesc()
+    h = C.c_void_p()
+    d.kind = 99
+    assert L.smc_model_register(C.byref(d), C.byref(h)) == smc.EINVAL
+    assert b"kind" in L.smc_last_error()
+    d.kind = smc.MODEL_LG
+    d.T = 0
+    assert L.smc_model_register(C.byref(d), C.byref(h)) == smc.EINVAL
+    assert L.smc_model_register(None, C.byref(h)) == smc.EINVAL
+
+
+def test_register_rejects_bad_trees():
+    import inputs
+
+    tree = inputs.yule_tree(8, seed=1)
+    bad = inputs.Tree(tree.parent.copy(), tree.left.copy(), tree.right.copy(), tree.age.copy(),
+                      tree.preorder.copy())
+    bad.preorder[[1, 2]] = bad.preorder[[2, 1]]  # not a left-first preorder any more
+    with pytest.raises(smc.SmcError) as e:
+        smc.Model("crbd", tree=bad)
+    assert e.value.status == smc.EINVAL
+    with pytest.raises(smc.SmcError):
+        smc.Model("crbd", tree=tree, depth_cap=smc.MAX_DEPTH + 1)
+    with pytest.raises(smc.SmcError):
+        smc.Model("crbd", tree=tree, rho=0.0)
+    with pytest.raises(smc.SmcError):
+        smc.Model("rateshift", tree=tree, lam_stack_cap=0)
+
+
+def test_resample_argument_checks():
+    L = smc.lib()
+    assert L.smc_resample(None, 10, 0.5, None, None, None, None, 0, None) == smc.EINVAL
+    assert L.smc_resample_workspace_bytes(0) == 0
+    assert L.smc_resample_workspace_bytes(1 << 20) > 0
+    assert L.smc_gather(None, None, None, None, 10, 1, 8, None) == smc.EINVAL
+    assert L.smc_sample(9, 0, 0.0, 0.0, 1, 0, 10, None, None, None) == smc.EINVAL
