@@ -111,6 +111,8 @@ typedef struct {
   int32_t precision;     /* SMC_PREC_* */
   int32_t max_segments;  /* 0 = the model's own segment count (unbounded models: 1 << 20) */
   int32_t record_all_ancestors; /* 1: keep every resampling's ancestors, 0: only the last */
+  int32_t time_kernels;  /* 1: time every segment-kernel launch with CUDA events (counters) */
+  int32_t pad_;
   void *workspace;       /* optional caller-owned device workspace (>= smc_workspace_bytes);
                             NULL = the model handle allocates and caches one */
   size_t workspace_bytes;
@@ -124,6 +126,9 @@ typedef struct {
   int64_t n_overflow;       /* particle-segments killed by the depth cap or stack capacity */
   int64_t n_limit;          /* particle-segments killed by the call limit */
   double device_ms;         /* GPU time of the run (CUDA events) */
+  double kernel_ms;         /* time_kernels = 1: summed duration of the segment-kernel launches */
+  int32_t kernel_launches;  /* segment-kernel launches of the run */
+  int32_t pad_;
 } smc_counters;
 
 /* Outputs of one run.  `where` says whether every pointer below is host or

@@ -74,14 +74,19 @@ template <typename R>
 struct Unif;
 template <>
 struct Unif<double> {
-  // ((w_hi:w_lo) >> 11) | 1, times 2^-53 (53-bit integer: exact in double)
+  // ((w_hi:w_lo) >> 11) | 1, times 2^-53.  Built without an int->FP64
+  // conversion: 1 + (x >> 12) 2^-52 is assembled from bits, then
+  // (that - 1) + 2^-53 = (2 (x >> 12) + 1) 2^-53 = ((x >> 11) | 1) 2^-53,
+  // both subtractions exact.
+  __device__ __forceinline__ static double from64(uint64_t x) {
+    const double one_plus = __longlong_as_double((long long)(0x3FF0000000000000ull | (x >> 12)));
+    return (one_plus - 1.0) + 0x1p-53;
+  }
   __device__ __forceinline__ static double first(const Block4& b) {
-    const uint64_t x = ((uint64_t)b.w1 << 32) | b.w0;
-    return (double)((x >> 11) | 1ull) * 0x1p-53;
+    return from64(((uint64_t)b.w1 << 32) | b.w0);
   }
   __device__ __forceinline__ static double second(const Block4& b) {
-    const uint64_t x = ((uint64_t)b.w3 << 32) | b.w2;
-    return (double)((x >> 11) | 1ull) * 0x1p-53;
+    return from64(((uint64_t)b.w3 << 32) | b.w2);
   }
 };
 template <>
@@ -250,14 +255,21 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 // scanned in order by every thread).  `sh` >= TPB/32 doubles.
 template <int TPB>
 __device__ __forceinline__ double block_incl_scan(double v, double* sh) {
+  static_assert(TPB <= 1024 && TPB % 32 == 0, "block size");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   v = warp_incl_scan(v);
   __syncthreads();
   if (lane == 31) sh[wid] = v;
   __syncthreads();
-  double off = 0.0;
-  for (int w = 0; w < wid; ++w) off = off + sh[w];
-  return wid > 0 ? off + v : v;
+  if (wid == 0) {  // exclusive scan of the warp totals by the first warp
+    const double t = lane < TPB / 32 ? sh[lane] : 0.0;
+    const double it = warp_incl_scan(t);
+    const double ex = __shfl_up_sync(0xffffffffu, it, 1);
+    __syncwarp();
+    if (lane < TPB / 32) sh[lane] = lane ? ex : 0.0;
+  }
+  __syncthreads();
+  return wid > 0 ? sh[wid] + v : v;
 }
 
 // Block inclusive prefix max over TPB threads.  `sh` >= TPB/32 doubles.

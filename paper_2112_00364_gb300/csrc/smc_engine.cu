@@ -17,9 +17,15 @@
 //             m = max M_t, c_t = exp(M_t - m), exclusive tile offsets
 //             O_t = sum_{t'<t} c_t' s_t', S = total, log Z += m + (log S - log N),
 //             the resampling uniform u_k and r = N / S.
-// The running sum used by the next search is P_j = O_t + c_t E_j and the
-// scaled boundary is q_j = P_j r.  The run stops after the segment in which
-// every particle reached b_stop (no resampling after it).
+// The running sum used by the next search is P_j = min(O_t + c_t E_j, O_{t+1})
+// (the tile offsets are made monotone with a running max, and the clamp keeps
+// P monotone across tile seams) and the scaled boundary is q_j = P_j r.  The
+// run stops after the segment in which every particle reached b_stop (no
+// resampling after it).
+//
+// Tiles are sized so that the grid is a whole multiple of the SM count times
+// the resident CTAs per SM (all CTAs of a segment run in one wave, equally
+// loaded), with at most TPB particles per tile.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,7 +41,7 @@
 namespace smc {
 
 struct RunState {
-  double log_z, m, S, r, u;
+  double log_z, m, S, r, u, inv_r;
   unsigned long long n_near, n_overflow, n_limit;
   int32_t done, status, n_segments, n_resamples;
   uint32_t arrive;
@@ -50,40 +56,71 @@ struct StepArgs {
   double* tile_M;  // [n_tiles]
   double* tile_s;  // [n_tiles]
   int32_t* tile_alive;
-  double* tile_c;  // [n_tiles] written by the combine
-  double* tile_O;  // [n_tiles]
-  int32_t* anc;    // ancestor rows
-  double* incr;    // [max_segments] per-segment log-Z increments
+  double* tile_c;     // [n_tiles] written by the combine: exp(M_t - m)
+  double* tile_invc;  // [n_tiles] 1 / c_t (0 where c_t = 0)
+  double* tile_O;     // [n_tiles + 1] monotone exclusive offsets, O_T >= S
+  double* tile_q;     // [n_tiles + 1] O_t * r
+  int32_t* anc;       // ancestor rows
+  double* incr;       // [max_segments] per-segment log-Z increments
   RunState* rs;
-  int N, n_tiles, max_segments, record_all, anc_rows;
+  int N, n_tiles, tile, max_segments, record_all, anc_rows;
   uint32_t k0, k1;
 };
 
-__device__ __forceinline__ double q_at(int j, const double* __restrict__ E,
-                                       const double* __restrict__ tO, const double* __restrict__ tc,
-                                       double r, int tile) {
-  const int t = j / tile;
-  return (tO[t] + tc[t] * E[j]) * r;
+// Non-negative doubles order like their bit patterns read as int64, so the
+// searches below compare bits on the integer pipes and spend FP64 work only on
+// the few boundary values they actually form.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// q_j = min(O_t + c_t E_j, O_{t+1}) * r for j in tile t.
+__device__ __forceinline__ double q_at(int j, const StepArgs& A, const double* __restrict__ E,
+                                       double r) {
+  const int t = j / A.tile;
+  const double P = fmin(A.tile_O[t] + A.tile_c[t] * E[j], A.tile_O[t + 1]);
+  return P * r;
 }
 
-// a_i = min{ j : q_j > i + u } by binary search (N - 1 if none); flags the
-// offset when it lies within 1e-12 N of q_a or q_{a-1}.
-__device__ __forceinline__ int systematic_search(int i, const double* E, const double* tO,
-                                                 const double* tc, double r, double u, int N,
-                                                 int tile, bool* near) {
+// a_i = min{ j : q_j > i + u } (N - 1 if none).  Tile first: t = max{t : O_t r <= y};
+// inside the tile the threshold e* = (y / r - O_t) / c_t on E locates the
+// candidate, and the exact q_j then fixes it up by +-1 if rounding moved it.
+// If no element of tile t qualifies, the first element of tile t+1 does.
+// Flags the offset when it lies within 1e-12 N of q_a or q_{a-1}.
+__device__ __forceinline__ int systematic_search(int i, const StepArgs& A, const double* E,
+                                                 double r, double inv_r, double u, bool* near) {
+  const int N = A.N, T = A.n_tiles;
   const double y = (double)i + u;
-  int lo = 0, hi = N;
+  const long long yb = dbits(y);
+  int lo = 0, hi = T;  // tile_q[0] = 0 <= y
   while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (q_at(mid, E, tO, tc, r, tile) > y)
-      hi = mid;
+    const int mid = (lo + hi + 1) >> 1;
+    if (dbits(A.tile_q[mid]) <= yb)
+      lo = mid;
     else
-      lo = mid + 1;
+      hi = mid - 1;
   }
-  const int a = lo < N ? lo : N - 1;
+  int a;
+  if (lo >= T) {
+    a = N - 1;
+  } else {
+    const int t = lo;
+    const int j0 = t * A.tile, j1 = min(N, j0 + A.tile);
+    const long long eb = dbits((y * inv_r - A.tile_O[t]) * A.tile_invc[t]);
+    int l = j0, h = j1;  // first j in [j0, j1) with E_j > e*
+    while (l < h) {
+      const int mid = (l + h) >> 1;
+      if (dbits(E[mid]) > eb)
+        h = mid;
+      else
+        l = mid + 1;
+    }
+    int j = l;
+    while (j < j1 && dbits(q_at(j, A, E, r)) <= yb) ++j;
+    while (j > j0 && dbits(q_at(j - 1, A, E, r)) > yb) --j;
+    a = j < j1 ? j : (j1 < N ? j1 : N - 1);
+  }
   const double tol = kBoundaryEps * (double)N;
-  bool f = fabs(q_at(a, E, tO, tc, r, tile) - y) < tol;
-  if (a > 0 && fabs(q_at(a - 1, E, tO, tc, r, tile) - y) < tol) f = true;
+  bool f = fabs(q_at(a, A, E, r) - y) < tol;
+  if (a > 0 && fabs(q_at(a - 1, A, E, r) - y) < tol) f = true;
   *near = f;
   return a;
 }
@@ -98,6 +135,7 @@ template <int TPB>
 __device__ void combine_tiles(const StepArgs& A, int k, double* sh) {
   RunState* rs = A.rs;
   const int nt = A.n_tiles;
+  double* shx = sh + TPB / 32 + 1;  // [TPB + 1] scratch after the block-op area
   double mloc = -INFINITY;
   int alive = 0;
   for (int t = threadIdx.x; t < nt; t += TPB) {
@@ -119,7 +157,8 @@ __device__ void combine_tiles(const StepArgs& A, int k, double* sh) {
     }
     return;
   }
-  double carry = 0.0;
+  // exclusive offsets O_t of v_t = c_t s_t, made monotone by a running max
+  double carry = 0.0, omax = 0.0;
   for (int base = 0; base < nt; base += TPB) {
     const int t = base + threadIdx.x;
     double c = 0.0, v = 0.0;
@@ -129,19 +168,30 @@ __device__ void combine_tiles(const StepArgs& A, int k, double* sh) {
       v = __ldcg(A.tile_s + t) * c;
     }
     const double incl = block_incl_scan<TPB>(v, sh);
-    // exclusive value of thread t = inclusive value of thread t-1
     __syncthreads();
-    sh[TPB / 32 + 1 + threadIdx.x] = incl;
+    shx[threadIdx.x + 1] = incl;
     __syncthreads();
-    const double excl = threadIdx.x ? sh[TPB / 32 + threadIdx.x] : 0.0;
+    const double excl = threadIdx.x ? shx[threadIdx.x] : 0.0;
+    const double chunk_total = shx[TPB];
+    const double O = block_incl_max<TPB>(fmax(carry + excl, omax), sh);
     if (t < nt) {
       A.tile_c[t] = c;
-      A.tile_O[t] = carry + excl;
+      A.tile_invc[t] = c > 0.0 ? 1.0 / c : 0.0;
+      A.tile_O[t] = O;
     }
-    carry = carry + sh[TPB / 32 + TPB];
+    __syncthreads();
+    if (threadIdx.x == TPB - 1) shx[0] = O;
+    __syncthreads();
+    omax = shx[0];
+    carry = carry + chunk_total;
+    __syncthreads();
   }
+  const double S = carry;
+  const double r = (double)A.N / S;
+  if (threadIdx.x == 0) A.tile_O[nt] = fmax(S, omax);
+  __syncthreads();
+  for (int t = threadIdx.x; t <= nt; t += TPB) A.tile_q[t] = A.tile_O[t] * r;
   if (threadIdx.x == 0) {
-    const double S = carry;
     const double inc = m + (log(S) - log((double)A.N));
     rs->log_z = rs->log_z + inc;
     A.incr[k] = inc;
@@ -156,7 +206,8 @@ __device__ void combine_tiles(const StepArgs& A, int k, double* sh) {
     } else {
       const Block4 b = philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1);
       rs->u = Unif<double>::first(b);
-      rs->r = (double)A.N / S;
+      rs->r = r;
+      rs->inv_r = S / (double)A.N;
     }
     rs->arrive = 0;
   }
@@ -165,13 +216,13 @@ __device__ void combine_tiles(const StepArgs& A, int k, double* sh) {
 template <class M, int TPB>
 __global__ void __launch_bounds__(TPB) step_kernel(const StepArgs A, const int k) {
   using R = typename M::R;
-  __shared__ double sh[TPB / 32 + 2 + TPB];
+  __shared__ double sh[TPB / 32 + 2 + TPB + 1];
   __shared__ int sh_last;
   RunState* rs = A.rs;
   if (*(volatile int32_t*)&rs->done) return;
   const int N = A.N;
-  const int i = blockIdx.x * TPB + threadIdx.x;
-  const bool valid = i < N;
+  const int i = blockIdx.x * A.tile + threadIdx.x;
+  const bool valid = (int)threadIdx.x < A.tile && i < N;
   const int nb = k & 1, cb = nb ^ 1;
   const StateView Sc = A.state[cb];
   const StateView Sn = A.state[nb];
@@ -181,8 +232,8 @@ __global__ void __launch_bounds__(TPB) step_kernel(const StepArgs A, const int k
     if (k == 0) {
       M::init(L);
     } else {
-      const double r = rs->r, u = rs->u;
-      const int a = systematic_search(i, A.E[cb], A.tile_O, A.tile_c, r, u, N, TPB, &near);
+      const double r = rs->r, u = rs->u, inv_r = rs->inv_r;
+      const int a = systematic_search(i, A, A.E[cb], r, inv_r, u, &near);
       const int row = A.record_all ? k - 1 : 0;
       if (row < A.anc_rows) A.anc[(size_t)row * N + i] = a;
       M::gather(L, Sc, Sn, a, i, N, A.md);
@@ -259,19 +310,31 @@ struct smc_model_s {
   void* ws = nullptr;        // cached workspace
   size_t ws_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> ev_seg;  // per-launch timing pairs (time_kernels)
 };
 
 namespace {
 
+#define SMC_ARG(...) __VA_ARGS__
 constexpr int kTPB = 256;
 constexpr int kMaxAncRows = 4096;
 constexpr int kMaxSegments = 1 << 24;
 
 struct Layout {
-  size_t real[2], ints[2], stack[2], logw, E[2], tM, ts, talive, tc, tO, rs, anc, incr, fin_real,
-      fin_int, fin_stack, total;
-  int n_tiles, anc_rows, max_segments;
+  size_t real[2], ints[2], stack[2], logw, E[2], tM, ts, talive, tc, tinvc, tO, tq, rs, anc, incr,
+      fin_real, fin_int, fin_stack, total;
+  int n_tiles, tile, anc_rows, max_segments;
 };
+
+// Particles per tile: one wave of equally loaded CTAs when N is small enough,
+// full TPB-particle tiles otherwise.
+int tile_size(int64_t N, int ctas_per_sm, int n_sms) {
+  const int64_t slots = (int64_t)std::max(1, ctas_per_sm) * std::max(1, n_sms);
+  int64_t t = (N + slots - 1) / slots;
+  if (t < 32) t = std::min<int64_t>(32, N);
+  if (t > kTPB) t = kTPB;
+  return (int)std::max<int64_t>(1, t);
+}
 
 int model_fields(int kind, int* n_real, int* n_int) {
   switch (kind) {
@@ -283,11 +346,12 @@ int model_fields(int kind, int* n_real, int* n_int) {
   return -1;
 }
 
-Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
+Layout make_layout(const smc_model_s* m, const smc_run_cfg* c, int ctas_per_sm, int n_sms) {
   Layout L{};
   const size_t N = (size_t)c->n_particles;
   const size_t rb = c->precision == SMC_PREC_FP32 ? 4 : 8;
-  L.n_tiles = (int)((N + kTPB - 1) / kTPB);
+  L.tile = tile_size((int64_t)N, ctas_per_sm, n_sms);
+  L.n_tiles = (int)((N + L.tile - 1) / L.tile);
   L.max_segments = c->max_segments > 0 ? c->max_segments
                    : (m->n_segments_known > 0 ? m->n_segments_known : (1 << 20));
   const int max_res = std::max(1, L.max_segments - 1);
@@ -311,7 +375,9 @@ Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
   L.ts = take(8 * (size_t)L.n_tiles);
   L.talive = take(4 * (size_t)L.n_tiles);
   L.tc = take(8 * (size_t)L.n_tiles);
-  L.tO = take(8 * (size_t)L.n_tiles);
+  L.tinvc = take(8 * (size_t)L.n_tiles);
+  L.tO = take(8 * (size_t)(L.n_tiles + 1));
+  L.tq = take(8 * (size_t)(L.n_tiles + 1));
   L.rs = take(sizeof(RunState));
   L.anc = take(4 * N * (size_t)L.anc_rows);
   L.incr = take(8 * (size_t)L.max_segments);
@@ -328,20 +394,46 @@ cudaError_t launch_segment(const StepArgs& A, int k, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-typedef cudaError_t (*seg_fn)(const StepArgs&, int, cudaStream_t);
+template <class M>
+int occupancy() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<M, kTPB>, kTPB, 0) != cudaSuccess)
+    return 1;
+  return std::max(1, n);
+}
 
-seg_fn pick_segment(int kind, int prec) {
+typedef cudaError_t (*seg_fn)(const StepArgs&, int, cudaStream_t);
+struct SegKernel {
+  seg_fn launch;
+  int (*occ)();
+};
+
+SegKernel pick_segment(int kind, int prec) {
   const bool f32 = prec == SMC_PREC_FP32;
+#define SMC_SEG(M) SegKernel{launch_segment<M>, occupancy<M>}
   switch (kind) {
-    case SMC_MODEL_LG: return f32 ? launch_segment<LgModel<float>> : launch_segment<LgModel<double>>;
+    case SMC_MODEL_LG: return f32 ? SMC_SEG(LgModel<float>) : SMC_SEG(LgModel<double>);
     case SMC_MODEL_CRBD:
-      return f32 ? launch_segment<TreeModel<float, false>> : launch_segment<TreeModel<double, false>>;
+      return f32 ? SMC_SEG(SMC_ARG(TreeModel<float, false>)) : SMC_SEG(SMC_ARG(TreeModel<double, false>));
     case SMC_MODEL_RATESHIFT:
-      return f32 ? launch_segment<TreeModel<float, true>> : launch_segment<TreeModel<double, true>>;
-    case SMC_MODEL_GEOMETRIC:
-      return f32 ? launch_segment<GeoModel<float>> : launch_segment<GeoModel<double>>;
+      return f32 ? SMC_SEG(SMC_ARG(TreeModel<float, true>)) : SMC_SEG(SMC_ARG(TreeModel<double, true>));
+    case SMC_MODEL_GEOMETRIC: return f32 ? SMC_SEG(GeoModel<float>) : SMC_SEG(GeoModel<double>);
   }
-  return nullptr;
+#undef SMC_SEG
+  return SegKernel{nullptr, nullptr};
+}
+
+// device properties of the current device, cached per device
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+    cached[dev] = n;
+  }
+  return cached[dev];
 }
 
 smc_status check_tree(const smc_model_desc* d) {
@@ -490,6 +582,7 @@ extern "C" void smc_model_destroy(smc_model_t m) {
   if (m->dev_blob) cudaFree(m->dev_blob);
   if (m->ev0) cudaEventDestroy(m->ev0);
   if (m->ev1) cudaEventDestroy(m->ev1);
+  for (cudaEvent_t e : m->ev_seg) cudaEventDestroy(e);
   delete m;
 }
 
@@ -518,7 +611,8 @@ extern "C" smc_status smc_workspace_bytes(smc_model_t m, const smc_run_cfg* c, s
   smc_status st = check_cfg(m, c);
   if (st) return st;
   if (!bytes) return set_error(SMC_EINVAL, "NULL bytes");
-  *bytes = make_layout(m, c).total;
+  const SegKernel sk = pick_segment(m->desc.kind, c->precision);
+  *bytes = make_layout(m, c, sk.occ(), sm_count()).total;
   return SMC_OK;
 }
 
@@ -529,7 +623,8 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
   if (r->where != SMC_MEM_HOST && r->where != SMC_MEM_DEVICE)
     return set_error(SMC_EINVAL, "result.where must be SMC_MEM_HOST or SMC_MEM_DEVICE");
   cudaStream_t cs = (cudaStream_t)stream;
-  const Layout Ly = make_layout(m, c);
+  const SegKernel sk = pick_segment(m->desc.kind, c->precision);
+  const Layout Ly = make_layout(m, c, sk.occ(), sm_count());
   char* ws;
   if (c->workspace) {
     if (c->workspace_bytes < Ly.total)
@@ -561,29 +656,55 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
   A.tile_s = (double*)(ws + Ly.ts);
   A.tile_alive = (int32_t*)(ws + Ly.talive);
   A.tile_c = (double*)(ws + Ly.tc);
+  A.tile_invc = (double*)(ws + Ly.tinvc);
   A.tile_O = (double*)(ws + Ly.tO);
+  A.tile_q = (double*)(ws + Ly.tq);
   A.anc = (int32_t*)(ws + Ly.anc);
   A.incr = (double*)(ws + Ly.incr);
   A.rs = (RunState*)(ws + Ly.rs);
   A.N = N;
   A.n_tiles = Ly.n_tiles;
+  A.tile = Ly.tile;
   A.max_segments = Ly.max_segments;
   A.record_all = c->record_all_ancestors ? 1 : 0;
   A.anc_rows = Ly.anc_rows;
   A.k0 = (uint32_t)(c->seed & 0xffffffffu);
   A.k1 = (uint32_t)(c->seed >> 32) ^ c->run_id;
-  seg_fn fn = pick_segment(m->desc.kind, c->precision);
+  seg_fn fn = sk.launch;
   SMC_CUDA_TRY(cudaMemsetAsync(A.rs, 0, sizeof(RunState), cs));
   SMC_CUDA_TRY(cudaEventRecord(m->ev0, cs));
   RunState hrs;
+  int launched = 0;
+  const bool timed = c->time_kernels != 0;
+  // one kernel per segment; with time_kernels an event pair brackets each launch
+  auto launch = [&](int k) -> smc_status {
+    if (timed) {
+      while ((int)m->ev_seg.size() < 2 * (launched + 1)) {
+        cudaEvent_t e;
+        SMC_CUDA_TRY(cudaEventCreate(&e));
+        m->ev_seg.push_back(e);
+      }
+      SMC_CUDA_TRY(cudaEventRecord(m->ev_seg[2 * launched], cs));
+    }
+    SMC_CUDA_TRY(fn(A, k, cs));
+    if (timed) SMC_CUDA_TRY(cudaEventRecord(m->ev_seg[2 * launched + 1], cs));
+    ++launched;
+    return SMC_OK;
+  };
   if (m->n_segments_known > 0 && Ly.max_segments >= m->n_segments_known) {
-    for (int k = 0; k < m->n_segments_known; ++k) SMC_CUDA_TRY(fn(A, k, cs));
+    for (int k = 0; k < m->n_segments_known; ++k) {
+      smc_status ls = launch(k);
+      if (ls) return ls;
+    }
   } else {
     // segment count unknown (or capped): poll the device termination flag
     const int chunk = 16;
     for (int k0 = 0; k0 < Ly.max_segments; k0 += chunk) {
       const int k1 = std::min(Ly.max_segments, k0 + chunk);
-      for (int k = k0; k < k1; ++k) SMC_CUDA_TRY(fn(A, k, cs));
+      for (int k = k0; k < k1; ++k) {
+        smc_status ls = launch(k);
+        if (ls) return ls;
+      }
       SMC_CUDA_TRY(cudaMemcpyAsync(&hrs, A.rs, sizeof(RunState), cudaMemcpyDeviceToHost, cs));
       SMC_CUDA_TRY(cudaStreamSynchronize(cs));
       if (hrs.done) break;
@@ -640,6 +761,13 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
   ct.n_overflow = (int64_t)hrs.n_overflow;
   ct.n_limit = (int64_t)hrs.n_limit;
   ct.device_ms = ms;
+  ct.kernel_launches = launched;
+  ct.kernel_ms = 0.0;
+  if (timed)
+    for (int q = 0; q < launched; ++q) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, m->ev_seg[2 * q], m->ev_seg[2 * q + 1]) == cudaSuccess) ct.kernel_ms += t;
+    }
   if (hrs.status == SMC_EDEGENERATE) return set_error(SMC_EDEGENERATE, "all particle weights are zero");
   if (hrs.status == SMC_ESTEPLIMIT) return set_error(SMC_ESTEPLIMIT, "max_segments reached");
   if (hrs.n_overflow || hrs.n_limit) return SMC_WKILLED;

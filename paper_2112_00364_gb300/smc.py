@@ -59,14 +59,16 @@ class ModelDesc(C.Structure):
 class RunCfg(C.Structure):
     _fields_ = [("n_particles", C.c_int64), ("seed", C.c_uint64), ("run_id", C.c_uint32),
                 ("precision", C.c_int32), ("max_segments", C.c_int32),
-                ("record_all_ancestors", C.c_int32), ("workspace", _vp),
+                ("record_all_ancestors", C.c_int32), ("time_kernels", C.c_int32),
+                ("pad_", C.c_int32), ("workspace", _vp),
                 ("workspace_bytes", C.c_size_t)]
 
 
 class Counters(C.Structure):
     _fields_ = [("n_segments", C.c_int32), ("n_resamples", C.c_int32),
                 ("n_near_boundary", C.c_int64), ("n_overflow", C.c_int64),
-                ("n_limit", C.c_int64), ("device_ms", C.c_double)]
+                ("n_limit", C.c_int64), ("device_ms", C.c_double), ("kernel_ms", C.c_double),
+                ("kernel_launches", C.c_int32), ("pad_", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -199,8 +201,9 @@ class Model:
         return out.value
 
 
-def _cfg(N, seed, run_id, precision, max_segments, record_all, workspace):
+def _cfg(N, seed, run_id, precision, max_segments, record_all, workspace, time_kernels=False):
     c = RunCfg()
+    c.time_kernels = int(time_kernels)
     c.n_particles, c.seed, c.run_id = N, seed, run_id
     c.precision = PRECISIONS[precision]
     c.max_segments, c.record_all_ancestors = max_segments, int(record_all)
@@ -211,10 +214,12 @@ def _cfg(N, seed, run_id, precision, max_segments, record_all, workspace):
 
 def run(model: Model, N: int, seed: int, run_id: int = 0, precision: str = "fp64",
         max_segments: int = 0, record_all_ancestors: bool = False, where: str = "host",
-        stream=None, workspace=None, outputs: dict | None = None) -> dict:
+        stream=None, workspace=None, outputs: dict | None = None,
+        time_kernels: bool = False) -> dict:
     """smc_run.  where="host": outputs are numpy arrays; where="device": outputs are
     torch CUDA tensors (allocated here unless passed in `outputs`)."""
-    cfg = _cfg(N, seed, run_id, precision, max_segments, record_all_ancestors, workspace)
+    cfg = _cfg(N, seed, run_id, precision, max_segments, record_all_ancestors, workspace,
+               time_kernels)
     rows = 1
     if record_all_ancestors:
         rows = max(1, (max_segments or model.n_segments or 4096) - 1)
@@ -244,7 +249,8 @@ def run(model: Model, N: int, seed: int, run_id: int = 0, precision: str = "fp64
     c = r.counters
     res = dict(status=st, n_segments=c.n_segments, n_resamples=c.n_resamples,
                n_near_boundary=c.n_near_boundary, n_overflow=c.n_overflow, n_limit=c.n_limit,
-               device_ms=c.device_ms, **out)
+               device_ms=c.device_ms, kernel_ms=c.kernel_ms,
+               kernel_launches=c.kernel_launches, **out)
     res["log_z_value"] = float(out["log_z"][0]) if where == "host" else None
     if record_all_ancestors and "ancestors" in out:
         res["ancestors"] = out["ancestors"][: c.n_resamples]
