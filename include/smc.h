@@ -194,6 +194,24 @@ smc_status smc_resample(const double *logw, int64_t N, double u, int32_t *ancest
                         double *out3, int64_t *n_near, void *workspace, size_t workspace_bytes,
                         void *stream);
 
+/* The paper has no counterpart to this entry point: it exists for callers that
+ * cannot allocate device memory themselves (code whose device memory belongs to
+ * another framework's pool, paths where cudaMalloc's implicit device-wide
+ * synchronisation is not allowed, hosts that forbid allocation after start-up).
+ * It computes exactly what smc_resample computes, but its tile scratch is a
+ * fixed array compiled into the library (131,136 bytes, held on every GPU that
+ * loads the library until the process exits) instead of a workspace argument,
+ * and it calls no allocating routine.  Limit: N <= SMC_RESAMPLE_STATIC_MAX_N
+ * (larger N returns SMC_EINVAL with a message).  The first call on each device
+ * resolves the array's device address (cudaGetSymbolAddress, with that device
+ * current), so make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race and must be serialised by the
+ * caller (e.g. one stream).  Arguments, layouts and other errors as for
+ * smc_resample; n_near is zeroed on `stream` by the call. */
+#define SMC_RESAMPLE_STATIC_MAX_N (((int64_t)1) << 24)
+smc_status smc_resample_static(const double *logw, int64_t N, double u, int32_t *ancestors,
+                               double *out3, int64_t *n_near, void *stream);
+
 /* Particle duplication with a stack-pointer-bounded copy (Section 3.3): for each
  * field f and particle i, dst[f][i] = src[f][anc[i]] (fields field-major, elem_bytes
  * 4 or 8 each); if sp != NULL, stack rows s >= sp[anc[i]] are not copied (they are

@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "smc_device.cuh"
 #include "smc_internal.h"
@@ -302,6 +303,76 @@ extern "C" smc_status smc_resample(const double* logw, int64_t N, double u, int3
   double* tc = (double*)(w + 2 * align_up(8 * (size_t)nt, 256));
   double* tO = (double*)(w + 3 * align_up(8 * (size_t)nt, 256));
   double* r = (double*)(w + 3 * align_up(8 * (size_t)nt, 256) + align_up(8 * (size_t)(nt + 1), 256));
+  SMC_CUDA_TRY(cudaMemsetAsync(n_near, 0, sizeof(int64_t), cs));
+  rs_tile_reduce<<<nt, RS_TPB, 0, cs>>>(logw, N, tM, ts);
+  SMC_CUDA_TRY(cudaGetLastError());
+  rs_combine<<<1, RS_TPB, 0, cs>>>(tM, ts, nt, N, tc, tO, out3, r);
+  SMC_CUDA_TRY(cudaGetLastError());
+  rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, N, u, tM, tc, tO, out3, r, ancestors,
+                                      reinterpret_cast<unsigned long long*>(n_near));
+  SMC_CUDA_TRY(cudaGetLastError());
+  return SMC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// smc_resample_static: smc_resample with its scratch in a fixed device array.
+//
+// Some callers cannot call cudaMalloc (code whose device memory is owned by
+// another framework's pool, paths where an allocation's implicit device-wide
+// synchronisation is not allowed, hosts that forbid allocation after start-up).
+// For them the tile scratch of the three resampling kernels lives in this
+// file-scope array, sized for populations of up to SMC_RESAMPLE_STATIC_MAX_N
+// particles (4096 tiles): 3 x 4096 tile values + 4097 offsets + N/S, 131,136
+// bytes that every GPU which loads the library keeps until the process exits.
+// Every call shares the array and it keeps the last call's contents; nothing in
+// it has to start at zero (each call writes every entry it later reads), but two
+// calls that overlap on the GPU race on it.
+constexpr int kStaticTiles = (int)((SMC_RESAMPLE_STATIC_MAX_N + RS_TILE - 1) / RS_TILE);
+constexpr int kStaticDoubles = 3 * kStaticTiles + (kStaticTiles + 1) + 7;
+static __device__ __align__(256) double g_resample_scratch[kStaticDoubles];
+
+namespace {
+std::mutex g_static_mu;
+double* g_static_ptr[128] = {nullptr};  // device address of the array, per device
+
+// Once per device, with that device current: resolve the array's device address.
+smc_status static_scratch(double** out) {
+  int dev = -1;
+  SMC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return set_error(SMC_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_resample_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_resample_scratch)");
+    g_static_ptr[dev] = (double*)p;
+  }
+  *out = g_static_ptr[dev];
+  return SMC_OK;
+}
+}  // namespace
+
+extern "C" smc_status smc_resample_static(const double* logw, int64_t N, double u,
+                                          int32_t* ancestors, double* out3, int64_t* n_near,
+                                          void* stream) {
+  if (!logw || !ancestors || !out3 || !n_near) return set_error(SMC_EINVAL, "NULL pointer");
+  if (N < 1) return set_error(SMC_EINVAL, "N must be >= 1");
+  if (N > SMC_RESAMPLE_STATIC_MAX_N)
+    return set_error(SMC_EINVAL, "N = %lld exceeds the static scratch limit of %lld particles",
+                     (long long)N, (long long)SMC_RESAMPLE_STATIC_MAX_N);
+  if (!(u > 0.0 && u < 1.0)) return set_error(SMC_EINVAL, "u must be in (0,1)");
+  if ((reinterpret_cast<uintptr_t>(logw) & 15) != 0)
+    return set_error(SMC_EINVAL, "logw must be 16-byte aligned");
+  double* base = nullptr;
+  smc_status st = static_scratch(&base);
+  if (st) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  const int nt = (int)((N + RS_TILE - 1) / RS_TILE);
+  double* tM = base;
+  double* ts = base + kStaticTiles;
+  double* tc = base + 2 * kStaticTiles;
+  double* tO = base + 3 * kStaticTiles;            // nt + 1 entries
+  double* r = base + 4 * kStaticTiles + 1;
   SMC_CUDA_TRY(cudaMemsetAsync(n_near, 0, sizeof(int64_t), cs));
   rs_tile_reduce<<<nt, RS_TPB, 0, cs>>>(logw, N, tM, ts);
   SMC_CUDA_TRY(cudaGetLastError());

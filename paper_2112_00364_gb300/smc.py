@@ -105,6 +105,8 @@ def lib():
         L.smc_resample_workspace_bytes.restype = C.c_size_t
         L.smc_resample.argtypes = [_vp, C.c_int64, C.c_double, _vp, _vp, _vp, _vp, C.c_size_t, _vp]
         L.smc_resample.restype = C.c_int32
+        L.smc_resample_static.argtypes = [_vp, C.c_int64, C.c_double, _vp, _vp, _vp, _vp]
+        L.smc_resample_static.restype = C.c_int32
         L.smc_gather.argtypes = [_vp, _vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int32, _vp]
         L.smc_gather.restype = C.c_int32
         L.smc_philox.argtypes = [_vp, _vp, _vp, C.c_int64, _vp]
@@ -274,6 +276,25 @@ def resample(logw, u: float, ancestors=None, out3=None, n_near=None, workspace=N
         resample_workspace_bytes(N), dtype=torch.uint8, device=dev)
     _check(lib().smc_resample(_ptr(logw), N, u, _ptr(anc), _ptr(o3), _ptr(nn), _ptr(ws),
                               ws.numel() * ws.element_size(), _stream(stream)))
+    return anc, o3, nn
+
+
+RESAMPLE_STATIC_MAX_N = 1 << 24
+
+
+def resample_static(logw, u: float, ancestors=None, out3=None, n_near=None, stream=None):
+    """smc_resample without a workspace: for callers that cannot allocate device
+    memory; scratch is a fixed array inside the library (N <= 2^24, calls on the
+    GPU must not overlap)."""
+    import torch
+
+    N = logw.numel()
+    dev = logw.device
+    anc = ancestors if ancestors is not None else torch.empty(N, dtype=torch.int32, device=dev)
+    o3 = out3 if out3 is not None else torch.empty(3, dtype=torch.float64, device=dev)
+    nn = n_near if n_near is not None else torch.empty(1, dtype=torch.int64, device=dev)
+    _check(lib().smc_resample_static(_ptr(logw), N, u, _ptr(anc), _ptr(o3), _ptr(nn),
+                                     _stream(stream)))
     return anc, o3, nn
 
 
