@@ -127,8 +127,9 @@ typedef struct {
   int64_t n_limit;          /* particle-segments killed by the call limit */
   double device_ms;         /* GPU time of the run (CUDA events) */
   double kernel_ms;         /* time_kernels = 1: summed duration of the segment-kernel launches */
-  int32_t kernel_launches;  /* segment-kernel launches of the run */
-  int32_t pad_;
+  int32_t kernel_launches;  /* segment-kernel launches of the run (one per wave and CTA size) */
+  smc_status status;        /* this run's own status (0, SMC_WKILLED, SMC_EDEGENERATE,
+                               SMC_ESTEPLIMIT) */
 } smc_counters;
 
 /* Outputs of one run.  `where` says whether every pointer below is host or
@@ -175,6 +176,20 @@ smc_status smc_workspace_bytes(smc_model_t m, const smc_run_cfg *c, size_t *byte
  * Errors: SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA, SMC_EDEGENERATE (log_z = -inf),
  * SMC_ESTEPLIMIT.  Warning: SMC_WKILLED. */
 smc_status smc_run(smc_model_t m, const smc_run_cfg *c, smc_result *r, void *stream);
+
+/* Run n_runs independent SMC runs (Algorithm 1 each) in one sequence of waves:
+ * every wave advances every unfinished run by one segment, all runs' tiles in the
+ * same kernel launches, each run resampled by its own last-arriving CTA, so
+ * uneven runs fill the GPU together instead of one after another.  ms[q],
+ * cfgs[q], res[q] describe run q exactly as for smc_run (cfg.workspace is
+ * ignored: the batch takes stream-ordered device memory for the call and returns
+ * it).  Every run must use the same precision.  A run's results are identical
+ * to what smc_run gives for the same model and configuration (its tiling
+ * depends only on its own N).  Each run's own status is res[q].counters.status.
+ * Returns SMC_OK once every run has finished, or a call-level error
+ * (SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA) with no results. */
+smc_status smc_run_batch(const smc_model_t *ms, const smc_run_cfg *cfgs, smc_result *res,
+                         int32_t n_runs, void *stream);
 
 /* ---------------- resampling primitives on caller device buffers ----------------
  * These are the normaliser / scan / systematic search / gather of Section 3.3 as

@@ -1,31 +1,33 @@
-// smc_engine.cu -- model registration and smc_run: Algorithm 1 (SMC over
-// PCFGs) in the RootPPL loop order of Section 3.3, one fused kernel launch
-// per segment.
+// smc_engine.cu -- model registration, smc_run and smc_run_batch: Algorithm 1
+// (SMC over PCFGs) in the RootPPL loop order of Section 3.3.
 //
-// Segment k's kernel, one particle per thread, one tile of TPB particles per CTA:
-//   prologue  (k > 0) systematic resampling search for this particle's
-//             ancestor a_i = min{ j : q_j > i + u } over the previous
-//             segment's weights, then the particle duplication of
-//             Section 3.3: the ancestor's SoA fields are read straight into
-//             registers (the gather is fused into the load), the pending
-//             stack is copied only up to its stack pointer;
+// Execution is organised in waves.  One wave advances every resident run by
+// one segment; it is one launch of wave_kernel per block-size bucket.  Each
+// CTA of a wave owns one tile (a run and a contiguous slice of its particles,
+// one particle per thread):
+//   prologue  (segment k > 0) systematic-resampling search for each particle's
+//             ancestor a_i = min{ j : q_j > i + u } over the previous segment's
+//             weights, then the particle duplication of Section 3.3: the
+//             ancestor's SoA fields are read straight into registers (the gather
+//             is fused into the load); a PSTATE stack is copied only up to its
+//             stack pointer;
 //   segment   blocks run until the next checkpoint with per-warp PC-sorted
 //             dispatch (smc_models.cuh); draws from Philox counters;
-//   epilogue  the tile's FP64 max M_t, e_j = exp(logw_j - M_t) and its
-//             inclusive scan E_j (written out for the next segment's search),
-//             tile total s_t; the last CTA to finish combines the tiles:
-//             m = max M_t, c_t = exp(M_t - m), exclusive tile offsets
-//             O_t = sum_{t'<t} c_t' s_t', S = total, log Z += m + (log S - log N),
-//             the resampling uniform u_k and r = N / S.
-// The running sum used by the next search is P_j = min(O_t + c_t E_j, O_{t+1})
-// (the tile offsets are made monotone with a running max, and the clamp keeps
-// P monotone across tile seams) and the scaled boundary is q_j = P_j r.  The
-// run stops after the segment in which every particle reached b_stop (no
-// resampling after it).
+//   epilogue  the tile's FP64 max M_t, e_j = exp(logw_j - M_t), its inclusive
+//             scan E_j (kept for the next segment's search) and total s_t; the
+//             run's last CTA to finish combines the run's tiles: m = max M_t,
+//             c_t = exp(M_t - m), monotone exclusive offsets O_t of c_t s_t,
+//             S = total, log Z += m + (log S - log N), the resampling uniform u_k
+//             and r = N / S.
+// The running sum the next search uses is P_j = min(O_t + c_t E_j, O_{t+1}) and
+// its scaled boundary q_j = P_j r.  A run stops after the segment in which every
+// particle reached b_stop (no resampling after it); its later CTAs return at once.
 //
-// Tiles are sized so that the grid is a whole multiple of the SM count times
-// the resident CTAs per SM (all CTAs of a segment run in one wave, equally
-// loaded), with at most TPB particles per tile.
+// A run's tile size depends only on its N (tile = ceil(N / 456) clamped to
+// 32..256, 456 = 152 SMs x 3 CTAs), so a run gives the same bits alone and in a
+// batch.  The CTA size of a run is the smallest of 32/64/128/256 threads that
+// holds its tile; runs of different CTA sizes are launched as separate kernels
+// of the same wave.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,37 +37,16 @@
 #include <vector>
 
 #include "smc_device.cuh"
+#include "smc_engine.h"
 #include "smc_internal.h"
 #include "smc_models.cuh"
 
 namespace smc {
 
-struct RunState {
-  double log_z, m, S, r, u, inv_r;
-  unsigned long long n_near, n_overflow, n_limit;
-  int32_t done, status, n_segments, n_resamples;
-  uint32_t arrive;
-  int32_t pad_[3];
-};
-
-struct StepArgs {
-  ModelDev md;
-  StateView state[2];
-  double* logw;    // [N] log-weights of the latest segment (f64; FP32 values widened)
-  double* E[2];    // [N] tile-local inclusive scans, double-buffered by segment parity
-  double* tile_M;  // [n_tiles]
-  double* tile_s;  // [n_tiles]
-  int32_t* tile_alive;
-  double* tile_c;     // [n_tiles] written by the combine: exp(M_t - m)
-  double* tile_invc;  // [n_tiles] 1 / c_t (0 where c_t = 0)
-  double* tile_O;     // [n_tiles + 1] monotone exclusive offsets, O_T >= S
-  double* tile_q;     // [n_tiles + 1] O_t * r
-  int32_t* anc;       // ancestor rows
-  double* incr;       // [max_segments] per-segment log-Z increments
-  RunState* rs;
-  int N, n_tiles, tile, max_segments, record_all, anc_rows;
-  uint32_t k0, k1;
-};
+__device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned long long v) {
+  v = __reduce_add_sync(0xffffffffu, (unsigned)v);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
 
 // Non-negative doubles order like their bit patterns read as int64, so the
 // searches below compare bits on the integer pipes and spend FP64 work only on
@@ -73,7 +54,7 @@ struct StepArgs {
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
 // q_j = min(O_t + c_t E_j, O_{t+1}) * r for j in tile t.
-__device__ __forceinline__ double q_at(int j, const StepArgs& A, const double* __restrict__ E,
+__device__ __forceinline__ double q_at(int j, const RunDev& A, const double* __restrict__ E,
                                        double r) {
   const int t = j / A.tile;
   const double P = fmin(A.tile_O[t] + A.tile_c[t] * E[j], A.tile_O[t + 1]);
@@ -82,11 +63,11 @@ __device__ __forceinline__ double q_at(int j, const StepArgs& A, const double* _
 
 // a_i = min{ j : q_j > i + u } (N - 1 if none).  Tile first: t = max{t : O_t r <= y};
 // inside the tile the threshold e* = (y / r - O_t) / c_t on E locates the
-// candidate, and the exact q_j then fixes it up by +-1 if rounding moved it.
-// If no element of tile t qualifies, the first element of tile t+1 does.
-// Flags the offset when it lies within 1e-12 N of q_a or q_{a-1}.
-__device__ __forceinline__ int systematic_search(int i, const StepArgs& A, const double* E,
-                                                 double r, double inv_r, double u, bool* near) {
+// candidate, and the exact q_j then fixes it up if rounding moved it.  If no
+// element of tile t qualifies, the first element of tile t+1 does.  Flags the
+// offset when it lies within 1e-12 N of q_a or q_{a-1}.
+__device__ __forceinline__ int systematic_search(int i, const RunDev& A, const double* E, double r,
+                                                 double inv_r, double u, bool* near) {
   const int N = A.N, T = A.n_tiles;
   const double y = (double)i + u;
   const long long yb = dbits(y);
@@ -125,17 +106,13 @@ __device__ __forceinline__ int systematic_search(int i, const StepArgs& A, const
   return a;
 }
 
-__device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned long long v) {
-  v = __reduce_add_sync(0xffffffffu, (unsigned)v);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
-}
-
-// The last CTA of a segment: combine the tile reductions (all FP64).
+// The run's last CTA of a segment: combine the tile reductions (all FP64).
+// `sh` holds >= TPB/32 + TPB + 2 doubles.
 template <int TPB>
-__device__ void combine_tiles(const StepArgs& A, int k, double* sh) {
+__device__ void combine_tiles(const RunDev& A, int k, double* sh) {
   RunState* rs = A.rs;
   const int nt = A.n_tiles;
-  double* shx = sh + TPB / 32 + 1;  // [TPB + 1] scratch after the block-op area
+  double* shx = sh + TPB / 32 + 1;
   double mloc = -INFINITY;
   int alive = 0;
   for (int t = threadIdx.x; t < nt; t += TPB) {
@@ -197,7 +174,6 @@ __device__ void combine_tiles(const StepArgs& A, int k, double* sh) {
     A.incr[k] = inc;
     rs->m = m;
     rs->S = S;
-    rs->n_segments = k + 1;
     if (!alive) {
       rs->done = 1;
     } else if (k + 1 >= A.max_segments) {
@@ -209,19 +185,18 @@ __device__ void combine_tiles(const StepArgs& A, int k, double* sh) {
       rs->r = r;
       rs->inv_r = S / (double)A.N;
     }
+    rs->n_segments = k + 1;
     rs->arrive = 0;
   }
 }
 
+// One tile of one run for segment k (the whole per-CTA body of a wave).
 template <class M, int TPB>
-__global__ void __launch_bounds__(TPB) step_kernel(const StepArgs A, const int k) {
-  using R = typename M::R;
-  __shared__ double sh[TPB / 32 + 2 + TPB + 1];
-  __shared__ int sh_last;
+__device__ __forceinline__ void step_tile(const RunDev& A, const int t, const int k, double* sh,
+                                          int* sh_last) {
   RunState* rs = A.rs;
-  if (*(volatile int32_t*)&rs->done) return;
   const int N = A.N;
-  const int i = blockIdx.x * A.tile + threadIdx.x;
+  const int i = t * A.tile + threadIdx.x;
   const bool valid = (int)threadIdx.x < A.tile && i < N;
   const int nb = k & 1, cb = nb ^ 1;
   const StateView Sc = A.state[cb];
@@ -260,20 +235,45 @@ __global__ void __launch_bounds__(TPB) step_kernel(const StepArgs A, const int k
   if (valid) A.E[nb][i] = E;
   alive = __syncthreads_or(alive);
   if (threadIdx.x == TPB - 1) {
-    A.tile_M[blockIdx.x] = Mt;
-    A.tile_s[blockIdx.x] = E;
+    A.tile_M[t] = Mt;
+    A.tile_s[t] = E;
   }
-  if (threadIdx.x == 0) A.tile_alive[blockIdx.x] = alive;
+  if (threadIdx.x == 0) A.tile_alive[t] = alive;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned prev = atomicAdd(&rs->arrive, 1u);
-    sh_last = (prev == (unsigned)gridDim.x - 1u);
+    *sh_last = (prev == (unsigned)A.n_tiles - 1u);
   }
   __syncthreads();
-  if (sh_last) {
+  if (*sh_last) {
     __threadfence();
     combine_tiles<TPB>(A, k, sh);
+  }
+}
+
+// One wave: CTA b runs tile cta_map[b].y of run cta_map[b].x.
+template <typename R, int TPB>
+__global__ void __launch_bounds__(TPB) wave_kernel(const RunDev* __restrict__ runs,
+                                                   const int2* __restrict__ cta_map) {
+  __shared__ __align__(16) RunDev sr;
+  __shared__ double sh[TPB / 32 + 2 + TPB + 1];
+  __shared__ int sh_last;
+  const int2 rt = cta_map[blockIdx.x];
+  {
+    const int* src = reinterpret_cast<const int*>(runs + rt.x);
+    int* dst = reinterpret_cast<int*>(&sr);
+    for (int w = threadIdx.x; w < (int)(sizeof(RunDev) / 4); w += TPB) dst[w] = src[w];
+  }
+  __syncthreads();
+  RunState* rs = sr.rs;
+  if (*(volatile int32_t*)&rs->done) return;
+  const int k = *(volatile int32_t*)&rs->n_segments;
+  switch (sr.md.kind) {
+    case SMC_MODEL_LG: step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last); break;
+    case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last); break;
+    case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last); break;
+    default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last); break;
   }
 }
 
@@ -295,46 +295,9 @@ __global__ void finalize_kernel(StateView S, int N, int n_real, int n_int, int c
   }
 }
 
-}  // namespace smc
-
-using namespace smc;
-
 // ------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------
-struct smc_model_s {
-  smc_model_desc desc;
-  ModelDev md;
-  int32_t n_real, n_int, stack_cap, n_segments_known;
-  void* dev_blob = nullptr;  // observations / tree arrays
-  void* ws = nullptr;        // cached workspace
-  size_t ws_bytes = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  std::vector<cudaEvent_t> ev_seg;  // per-launch timing pairs (time_kernels)
-};
-
-namespace {
-
-#define SMC_ARG(...) __VA_ARGS__
-constexpr int kTPB = 256;
-constexpr int kMaxAncRows = 4096;
-constexpr int kMaxSegments = 1 << 24;
-
-struct Layout {
-  size_t real[2], ints[2], stack[2], logw, E[2], tM, ts, talive, tc, tinvc, tO, tq, rs, anc, incr,
-      fin_real, fin_int, fin_stack, total;
-  int n_tiles, tile, anc_rows, max_segments;
-};
-
-// Particles per tile: one wave of equally loaded CTAs when N is small enough,
-// full TPB-particle tiles otherwise.
-int tile_size(int64_t N, int ctas_per_sm, int n_sms) {
-  const int64_t slots = (int64_t)std::max(1, ctas_per_sm) * std::max(1, n_sms);
-  int64_t t = (N + slots - 1) / slots;
-  if (t < 32) t = std::min<int64_t>(32, N);
-  if (t > kTPB) t = kTPB;
-  return (int)std::max<int64_t>(1, t);
-}
 
 int model_fields(int kind, int* n_real, int* n_int) {
   switch (kind) {
@@ -346,17 +309,29 @@ int model_fields(int kind, int* n_real, int* n_int) {
   return -1;
 }
 
-Layout make_layout(const smc_model_s* m, const smc_run_cfg* c, int ctas_per_sm, int n_sms) {
+int tile_for(int64_t N) {
+  int64_t t = (N + kTileSlots - 1) / kTileSlots;
+  t = std::max<int64_t>(t, 32);
+  t = std::min<int64_t>(t, 256);
+  t = std::min<int64_t>(t, N);
+  return (int)std::max<int64_t>(t, 1);
+}
+
+int bucket_for(int tile) { return tile <= 32 ? 0 : tile <= 64 ? 1 : tile <= 128 ? 2 : 3; }
+
+Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
   Layout L{};
   const size_t N = (size_t)c->n_particles;
   const size_t rb = c->precision == SMC_PREC_FP32 ? 4 : 8;
-  L.tile = tile_size((int64_t)N, ctas_per_sm, n_sms);
+  L.tile = tile_for((int64_t)N);
   L.n_tiles = (int)((N + L.tile - 1) / L.tile);
   L.max_segments = c->max_segments > 0 ? c->max_segments
-                   : (m->n_segments_known > 0 ? m->n_segments_known : (1 << 20));
+                   : (m->n_segments_known > 0 ? m->n_segments_known : kUnboundedSegments);
   const int max_res = std::max(1, L.max_segments - 1);
   // unknown-length models keep at most kMaxAncRows recorded resamplings
-  L.anc_rows = c->record_all_ancestors ? (m->n_segments_known > 0 ? max_res : std::min(max_res, kMaxAncRows)) : 1;
+  L.anc_rows = c->record_all_ancestors
+                   ? (m->n_segments_known > 0 ? max_res : std::min(max_res, kMaxAncRows))
+                   : 1;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -388,52 +363,148 @@ Layout make_layout(const smc_model_s* m, const smc_run_cfg* c, int ctas_per_sm, 
   return L;
 }
 
-template <class M>
-cudaError_t launch_segment(const StepArgs& A, int k, cudaStream_t st) {
-  step_kernel<M, kTPB><<<A.n_tiles, kTPB, 0, st>>>(A, k);
+RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws) {
+  RunDev A;
+  std::memset(&A, 0, sizeof(A));
+  A.md = m->md;
+  for (int b = 0; b < 2; ++b) {
+    A.state[b].real = ws + Ly.real[b];
+    A.state[b].ints = (int32_t*)(ws + Ly.ints[b]);
+    A.state[b].stack = ws + Ly.stack[b];
+    A.E[b] = (double*)(ws + Ly.E[b]);
+  }
+  A.logw = (double*)(ws + Ly.logw);
+  A.tile_M = (double*)(ws + Ly.tM);
+  A.tile_s = (double*)(ws + Ly.ts);
+  A.tile_alive = (int32_t*)(ws + Ly.talive);
+  A.tile_c = (double*)(ws + Ly.tc);
+  A.tile_invc = (double*)(ws + Ly.tinvc);
+  A.tile_O = (double*)(ws + Ly.tO);
+  A.tile_q = (double*)(ws + Ly.tq);
+  A.anc = (int32_t*)(ws + Ly.anc);
+  A.incr = (double*)(ws + Ly.incr);
+  A.rs = (RunState*)(ws + Ly.rs);
+  A.N = (int)c->n_particles;
+  A.n_tiles = Ly.n_tiles;
+  A.tile = Ly.tile;
+  A.max_segments = Ly.max_segments;
+  A.record_all = c->record_all_ancestors ? 1 : 0;
+  A.anc_rows = Ly.anc_rows;
+  A.k0 = (uint32_t)(c->seed & 0xffffffffu);
+  A.k1 = (uint32_t)(c->seed >> 32) ^ c->run_id;
+  return A;
+}
+
+template <typename R>
+cudaError_t launch_bucket(int b, const RunDev* runs, const int2* map, int n, cudaStream_t st) {
+  switch (b) {
+    case 0: wave_kernel<R, 32><<<n, 32, 0, st>>>(runs, map); break;
+    case 1: wave_kernel<R, 64><<<n, 64, 0, st>>>(runs, map); break;
+    case 2: wave_kernel<R, 128><<<n, 128, 0, st>>>(runs, map); break;
+    default: wave_kernel<R, 256><<<n, 256, 0, st>>>(runs, map); break;
+  }
   return cudaGetLastError();
 }
 
-template <class M>
-int occupancy() {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<M, kTPB>, kTPB, 0) != cudaSuccess)
-    return 1;
-  return std::max(1, n);
+cudaError_t launch_wave(const WavePlan& W, int precision, cudaStream_t st) {
+  for (int b = 0; b < 4; ++b) {
+    if (!W.n_ctas[b]) continue;
+    cudaError_t e = precision == SMC_PREC_FP32
+                        ? launch_bucket<float>(b, W.runs, W.maps[b], W.n_ctas[b], st)
+                        : launch_bucket<double>(b, W.runs, W.maps[b], W.n_ctas[b], st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
-typedef cudaError_t (*seg_fn)(const StepArgs&, int, cudaStream_t);
-struct SegKernel {
-  seg_fn launch;
-  int (*occ)();
-};
-
-SegKernel pick_segment(int kind, int prec) {
-  const bool f32 = prec == SMC_PREC_FP32;
-#define SMC_SEG(M) SegKernel{launch_segment<M>, occupancy<M>}
-  switch (kind) {
-    case SMC_MODEL_LG: return f32 ? SMC_SEG(LgModel<float>) : SMC_SEG(LgModel<double>);
-    case SMC_MODEL_CRBD:
-      return f32 ? SMC_SEG(SMC_ARG(TreeModel<float, false>)) : SMC_SEG(SMC_ARG(TreeModel<double, false>));
-    case SMC_MODEL_RATESHIFT:
-      return f32 ? SMC_SEG(SMC_ARG(TreeModel<float, true>)) : SMC_SEG(SMC_ARG(TreeModel<double, true>));
-    case SMC_MODEL_GEOMETRIC: return f32 ? SMC_SEG(GeoModel<float>) : SMC_SEG(GeoModel<double>);
-  }
-#undef SMC_SEG
-  return SegKernel{nullptr, nullptr};
+size_t wave_meta_bytes(const std::vector<RunDev>& runs) {
+  size_t n_ctas = 0;
+  for (const RunDev& r : runs) n_ctas += (size_t)r.n_tiles;
+  return align_up(sizeof(RunDev) * runs.size(), 256) + align_up(sizeof(int2) * n_ctas, 256) + 4 * 256;
 }
 
-// device properties of the current device, cached per device
-int sm_count() {
-  static int cached[64] = {0};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-  if (!cached[dev]) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-    cached[dev] = n;
+// Copies the run table and the per-bucket CTA maps to `meta` (device) and
+// fills W with their device addresses.
+smc_status upload_wave(const std::vector<RunDev>& runs, void* meta, cudaStream_t st, WavePlan* W,
+                       std::vector<char>* staging) {
+  const size_t run_bytes = align_up(sizeof(RunDev) * runs.size(), 256);
+  std::vector<int2> maps[4];
+  for (size_t r = 0; r < runs.size(); ++r) {
+    const int b = bucket_for(runs[r].tile);
+    for (int t = 0; t < runs[r].n_tiles; ++t) maps[b].push_back(make_int2((int)r, t));
   }
-  return cached[dev];
+  staging->assign(wave_meta_bytes(runs), 0);
+  std::memcpy(staging->data(), runs.data(), sizeof(RunDev) * runs.size());
+  size_t off = run_bytes;
+  W->runs = (const RunDev*)meta;
+  for (int b = 0; b < 4; ++b) {
+    W->n_ctas[b] = (int)maps[b].size();
+    W->maps[b] = (const int2*)((char*)meta + off);
+    if (!maps[b].empty()) std::memcpy(staging->data() + off, maps[b].data(), sizeof(int2) * maps[b].size());
+    off = align_up(off + sizeof(int2) * maps[b].size(), 256);
+  }
+  SMC_CUDA_TRY(cudaMemcpyAsync(meta, staging->data(), off, cudaMemcpyHostToDevice, st));
+  // the source is pageable host memory: wait for the copy before it can change
+  SMC_CUDA_TRY(cudaStreamSynchronize(st));
+  return SMC_OK;
+}
+
+namespace {
+
+// Runs waves until every run is done or `max_waves` waves ran.  Known-length
+// batches launch exactly max_waves waves without reading anything back;
+// otherwise the run states are polled every 16 waves.
+smc_status drive_waves(const WavePlan& W, int precision, const std::vector<RunState*>& states,
+                       int max_waves, bool known, cudaStream_t st, std::vector<cudaEvent_t>* evs,
+                       bool timed, int* launched, double* kernel_ms) {
+  *launched = 0;
+  *kernel_ms = 0.0;
+  timed = timed && evs;
+  auto one = [&]() -> smc_status {
+    if (timed) {
+      while ((int)evs->size() < 2 * (*launched + 1)) {
+        cudaEvent_t e;
+        SMC_CUDA_TRY(cudaEventCreate(&e));
+        evs->push_back(e);
+      }
+      SMC_CUDA_TRY(cudaEventRecord((*evs)[2 * *launched], st));
+    }
+    SMC_CUDA_TRY(launch_wave(W, precision, st));
+    if (timed) SMC_CUDA_TRY(cudaEventRecord((*evs)[2 * *launched + 1], st));
+    ++*launched;
+    return SMC_OK;
+  };
+  if (known) {
+    for (int k = 0; k < max_waves; ++k) {
+      smc_status s = one();
+      if (s) return s;
+    }
+  } else {
+    const int chunk = 16;
+    const size_t n_runs = states.size();
+    std::vector<RunState> h(n_runs);
+    for (int k0 = 0; k0 < max_waves; k0 += chunk) {
+      const int k1 = std::min(max_waves, k0 + chunk);
+      for (int k = k0; k < k1; ++k) {
+        smc_status s = one();
+        if (s) return s;
+      }
+      for (size_t r = 0; r < n_runs; ++r)
+        SMC_CUDA_TRY(cudaMemcpyAsync(&h[r], states[r], sizeof(RunState), cudaMemcpyDeviceToHost, st));
+      SMC_CUDA_TRY(cudaStreamSynchronize(st));
+      bool all = true;
+      for (size_t r = 0; r < n_runs; ++r) all = all && h[r].done;
+      if (all) break;
+    }
+  }
+  if (timed) {
+    SMC_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int q = 0; q < *launched; ++q) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, (*evs)[2 * q], (*evs)[2 * q + 1]) == cudaSuccess) *kernel_ms += t;
+    }
+  }
+  return SMC_OK;
 }
 
 smc_status check_tree(const smc_model_desc* d) {
@@ -478,6 +549,81 @@ smc_status check_tree(const smc_model_desc* d) {
 }
 
 }  // namespace
+
+// Copies one finished run's outputs into its smc_result and fills its counters.
+smc_status collect_run(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws,
+                       const RunDev& A, const RunState& hrs, smc_result* r, cudaStream_t cs) {
+  const int N = A.N;
+  const int fb = (hrs.n_segments - 1) & 1;
+  const bool host = r->where == SMC_MEM_HOST;
+  double* fin_real = host ? (double*)(ws + Ly.fin_real) : r->real_fields;
+  int32_t* fin_int = host ? (int32_t*)(ws + Ly.fin_int) : r->int_fields;
+  double* fin_stack = host ? (double*)(ws + Ly.fin_stack) : r->stack;
+  if (hrs.n_segments > 0 && (r->real_fields || r->int_fields || r->stack)) {
+    const int blocks = (N + 255) / 256;
+    if (c->precision == SMC_PREC_FP32)
+      finalize_kernel<float><<<blocks, 256, 0, cs>>>(A.state[fb], N, m->n_real, m->n_int, m->stack_cap,
+                                                     r->real_fields ? fin_real : nullptr,
+                                                     r->int_fields ? fin_int : nullptr,
+                                                     r->stack ? fin_stack : nullptr);
+    else
+      finalize_kernel<double><<<blocks, 256, 0, cs>>>(A.state[fb], N, m->n_real, m->n_int, m->stack_cap,
+                                                      r->real_fields ? fin_real : nullptr,
+                                                      r->int_fields ? fin_int : nullptr,
+                                                      r->stack ? fin_stack : nullptr);
+    SMC_CUDA_TRY(cudaGetLastError());
+  }
+  const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (r->log_z) SMC_CUDA_TRY(cudaMemcpyAsync(r->log_z, &A.rs->log_z, 8, kind, cs));
+  if (r->final_logw) SMC_CUDA_TRY(cudaMemcpyAsync(r->final_logw, A.logw, 8 * (size_t)N, kind, cs));
+  if (host) {
+    if (r->real_fields && m->n_real)
+      SMC_CUDA_TRY(cudaMemcpyAsync(r->real_fields, fin_real, 8 * (size_t)N * m->n_real, kind, cs));
+    if (r->int_fields && m->n_int)
+      SMC_CUDA_TRY(cudaMemcpyAsync(r->int_fields, fin_int, 4 * (size_t)N * m->n_int, kind, cs));
+    if (r->stack && m->stack_cap)
+      SMC_CUDA_TRY(cudaMemcpyAsync(r->stack, fin_stack, 8 * (size_t)N * m->stack_cap, kind, cs));
+  }
+  if (r->ancestors) {
+    const int n_res = std::max(0, hrs.n_segments - 1);
+    const int rows = c->record_all_ancestors ? std::min(std::min(n_res, r->ancestors_rows), Ly.anc_rows)
+                                             : (n_res > 0 ? 1 : 0);
+    if (rows > 0) SMC_CUDA_TRY(cudaMemcpyAsync(r->ancestors, A.anc, 4 * (size_t)N * rows, kind, cs));
+  }
+  smc_counters& ct = r->counters;
+  ct.n_segments = hrs.n_segments;
+  ct.n_resamples = std::max(0, hrs.n_segments - 1);
+  ct.n_near_boundary = (int64_t)hrs.n_near;
+  ct.n_overflow = (int64_t)hrs.n_overflow;
+  ct.n_limit = (int64_t)hrs.n_limit;
+  int st = hrs.status;
+  if (st == 0 && !hrs.done) st = SMC_ESTEPLIMIT;
+  if (st == 0 && (hrs.n_overflow || hrs.n_limit)) st = SMC_WKILLED;
+  ct.status = st;
+  return SMC_OK;
+}
+
+smc_status check_cfg(const smc_model_s* m, const smc_run_cfg* c) {
+  if (!m || !c) return set_error(SMC_EINVAL, "NULL argument");
+  if (c->n_particles < 1 || c->n_particles > kMaxParticles)
+    return set_error(SMC_EINVAL, "n_particles must be in 1..%lld", (long long)kMaxParticles);
+  if (c->precision != SMC_PREC_FP64 && c->precision != SMC_PREC_FP32)
+    return set_error(SMC_EINVAL, "unknown precision");
+  if (c->max_segments < 0 || c->max_segments > kMaxSegments)
+    return set_error(SMC_EINVAL, "max_segments must be in 0..2^24");
+  return SMC_OK;
+}
+
+smc_status check_result(const smc_result* r) {
+  if (!r) return set_error(SMC_EINVAL, "NULL result");
+  if (r->where != SMC_MEM_HOST && r->where != SMC_MEM_DEVICE)
+    return set_error(SMC_EINVAL, "result.where must be SMC_MEM_HOST or SMC_MEM_DEVICE");
+  return SMC_OK;
+}
+
+}  // namespace smc
+
+using namespace smc;
 
 extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* out) {
   if (!d || !out) return set_error(SMC_EINVAL, "NULL argument");
@@ -596,180 +742,151 @@ extern "C" smc_status smc_model_info(smc_model_t m, int32_t* n_real, int32_t* n_
   return SMC_OK;
 }
 
-static smc_status check_cfg(const smc_model_s* m, const smc_run_cfg* c) {
-  if (!m || !c) return set_error(SMC_EINVAL, "NULL argument");
-  if (c->n_particles < 1 || c->n_particles > (int64_t)0x7fffffff - kTPB)
-    return set_error(SMC_EINVAL, "n_particles must be in 1..2^31-257");
-  if (c->precision != SMC_PREC_FP64 && c->precision != SMC_PREC_FP32)
-    return set_error(SMC_EINVAL, "unknown precision");
-  if (c->max_segments < 0 || c->max_segments > kMaxSegments)
-    return set_error(SMC_EINVAL, "max_segments must be in 0..2^24");
-  return SMC_OK;
-}
-
 extern "C" smc_status smc_workspace_bytes(smc_model_t m, const smc_run_cfg* c, size_t* bytes) {
   smc_status st = check_cfg(m, c);
   if (st) return st;
   if (!bytes) return set_error(SMC_EINVAL, "NULL bytes");
-  const SegKernel sk = pick_segment(m->desc.kind, c->precision);
-  *bytes = make_layout(m, c, sk.occ(), sm_count()).total;
+  const Layout Ly = make_layout(m, c);
+  std::vector<RunDev> one(1);
+  one[0].n_tiles = Ly.n_tiles;
+  *bytes = align_up(Ly.total, 256) + wave_meta_bytes(one);
   return SMC_OK;
 }
 
 extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r, void* stream) {
   smc_status st = check_cfg(m, c);
   if (st) return st;
-  if (!r) return set_error(SMC_EINVAL, "NULL result");
-  if (r->where != SMC_MEM_HOST && r->where != SMC_MEM_DEVICE)
-    return set_error(SMC_EINVAL, "result.where must be SMC_MEM_HOST or SMC_MEM_DEVICE");
+  if ((st = check_result(r))) return st;
   cudaStream_t cs = (cudaStream_t)stream;
-  const SegKernel sk = pick_segment(m->desc.kind, c->precision);
-  const Layout Ly = make_layout(m, c, sk.occ(), sm_count());
+  const Layout Ly = make_layout(m, c);
+  const size_t meta_off = align_up(Ly.total, 256);
+  std::vector<RunDev> runs(1);
+  runs[0].n_tiles = Ly.n_tiles;
+  const size_t need = meta_off + wave_meta_bytes(runs);
   char* ws;
   if (c->workspace) {
-    if (c->workspace_bytes < Ly.total)
-      return set_error(SMC_EINVAL, "workspace too small (%zu < %zu)", c->workspace_bytes, Ly.total);
+    if (c->workspace_bytes < need)
+      return set_error(SMC_EINVAL, "workspace too small (%zu < %zu)", c->workspace_bytes, need);
     ws = (char*)c->workspace;
   } else {
-    if (m->ws_bytes < Ly.total) {
+    if (m->ws_bytes < need) {
       if (m->ws) cudaFree(m->ws);
       m->ws = nullptr;
       m->ws_bytes = 0;
-      cudaError_t e = cudaMalloc(&m->ws, Ly.total);
-      if (e != cudaSuccess) return set_error(SMC_ENOMEM, "workspace cudaMalloc(%zu): %s", Ly.total, cudaGetErrorString(e));
-      m->ws_bytes = Ly.total;
+      cudaError_t e = cudaMalloc(&m->ws, need);
+      if (e != cudaSuccess)
+        return set_error(SMC_ENOMEM, "workspace cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+      m->ws_bytes = need;
     }
     ws = (char*)m->ws;
   }
-  const int N = (int)c->n_particles;
-  StepArgs A;
-  std::memset(&A, 0, sizeof(A));
-  A.md = m->md;
-  for (int b = 0; b < 2; ++b) {
-    A.state[b].real = ws + Ly.real[b];
-    A.state[b].ints = (int32_t*)(ws + Ly.ints[b]);
-    A.state[b].stack = ws + Ly.stack[b];
-    A.E[b] = (double*)(ws + Ly.E[b]);
-  }
-  A.logw = (double*)(ws + Ly.logw);
-  A.tile_M = (double*)(ws + Ly.tM);
-  A.tile_s = (double*)(ws + Ly.ts);
-  A.tile_alive = (int32_t*)(ws + Ly.talive);
-  A.tile_c = (double*)(ws + Ly.tc);
-  A.tile_invc = (double*)(ws + Ly.tinvc);
-  A.tile_O = (double*)(ws + Ly.tO);
-  A.tile_q = (double*)(ws + Ly.tq);
-  A.anc = (int32_t*)(ws + Ly.anc);
-  A.incr = (double*)(ws + Ly.incr);
-  A.rs = (RunState*)(ws + Ly.rs);
-  A.N = N;
-  A.n_tiles = Ly.n_tiles;
-  A.tile = Ly.tile;
-  A.max_segments = Ly.max_segments;
-  A.record_all = c->record_all_ancestors ? 1 : 0;
-  A.anc_rows = Ly.anc_rows;
-  A.k0 = (uint32_t)(c->seed & 0xffffffffu);
-  A.k1 = (uint32_t)(c->seed >> 32) ^ c->run_id;
-  seg_fn fn = sk.launch;
-  SMC_CUDA_TRY(cudaMemsetAsync(A.rs, 0, sizeof(RunState), cs));
+  runs[0] = make_rundev(m, c, Ly, ws);
+  WavePlan W;
+  SMC_CUDA_TRY(cudaMemsetAsync(runs[0].rs, 0, sizeof(RunState), cs));
+  if ((st = upload_wave(runs, ws + meta_off, cs, &W, &m->staging))) return st;
   SMC_CUDA_TRY(cudaEventRecord(m->ev0, cs));
-  RunState hrs;
+  const bool known = m->n_segments_known > 0 && Ly.max_segments >= m->n_segments_known;
   int launched = 0;
-  const bool timed = c->time_kernels != 0;
-  // one kernel per segment; with time_kernels an event pair brackets each launch
-  auto launch = [&](int k) -> smc_status {
-    if (timed) {
-      while ((int)m->ev_seg.size() < 2 * (launched + 1)) {
-        cudaEvent_t e;
-        SMC_CUDA_TRY(cudaEventCreate(&e));
-        m->ev_seg.push_back(e);
-      }
-      SMC_CUDA_TRY(cudaEventRecord(m->ev_seg[2 * launched], cs));
-    }
-    SMC_CUDA_TRY(fn(A, k, cs));
-    if (timed) SMC_CUDA_TRY(cudaEventRecord(m->ev_seg[2 * launched + 1], cs));
-    ++launched;
-    return SMC_OK;
-  };
-  if (m->n_segments_known > 0 && Ly.max_segments >= m->n_segments_known) {
-    for (int k = 0; k < m->n_segments_known; ++k) {
-      smc_status ls = launch(k);
-      if (ls) return ls;
-    }
-  } else {
-    // segment count unknown (or capped): poll the device termination flag
-    const int chunk = 16;
-    for (int k0 = 0; k0 < Ly.max_segments; k0 += chunk) {
-      const int k1 = std::min(Ly.max_segments, k0 + chunk);
-      for (int k = k0; k < k1; ++k) {
-        smc_status ls = launch(k);
-        if (ls) return ls;
-      }
-      SMC_CUDA_TRY(cudaMemcpyAsync(&hrs, A.rs, sizeof(RunState), cudaMemcpyDeviceToHost, cs));
-      SMC_CUDA_TRY(cudaStreamSynchronize(cs));
-      if (hrs.done) break;
-    }
-  }
+  double kms = 0.0;
+  std::vector<RunState*> states{runs[0].rs};
+  st = drive_waves(W, c->precision, states, known ? m->n_segments_known : Ly.max_segments, known, cs,
+                   &m->ev_seg, c->time_kernels != 0, &launched, &kms);
+  if (st) return st;
   SMC_CUDA_TRY(cudaEventRecord(m->ev1, cs));
-  SMC_CUDA_TRY(cudaMemcpyAsync(&hrs, A.rs, sizeof(RunState), cudaMemcpyDeviceToHost, cs));
+  RunState hrs;
+  SMC_CUDA_TRY(cudaMemcpyAsync(&hrs, runs[0].rs, sizeof(RunState), cudaMemcpyDeviceToHost, cs));
   SMC_CUDA_TRY(cudaStreamSynchronize(cs));
-  if (!hrs.done && hrs.status == 0) hrs.status = SMC_ESTEPLIMIT;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, m->ev0, m->ev1);
-  // outputs
-  const int fb = (hrs.n_segments - 1) & 1;
-  const bool host = r->where == SMC_MEM_HOST;
-  double* fin_real = host ? (double*)(ws + Ly.fin_real) : r->real_fields;
-  int32_t* fin_int = host ? (int32_t*)(ws + Ly.fin_int) : r->int_fields;
-  double* fin_stack = host ? (double*)(ws + Ly.fin_stack) : r->stack;
-  if (hrs.n_segments > 0 && (r->real_fields || r->int_fields || r->stack)) {
-    const int blocks = (N + 255) / 256;
-    if (c->precision == SMC_PREC_FP32)
-      finalize_kernel<float><<<blocks, 256, 0, cs>>>(A.state[fb], N, m->n_real, m->n_int, m->stack_cap,
-                                                     r->real_fields ? fin_real : nullptr,
-                                                     r->int_fields ? fin_int : nullptr,
-                                                     r->stack ? fin_stack : nullptr);
-    else
-      finalize_kernel<double><<<blocks, 256, 0, cs>>>(A.state[fb], N, m->n_real, m->n_int, m->stack_cap,
-                                                      r->real_fields ? fin_real : nullptr,
-                                                      r->int_fields ? fin_int : nullptr,
-                                                      r->stack ? fin_stack : nullptr);
-    SMC_CUDA_TRY(cudaGetLastError());
+  if ((st = collect_run(m, c, Ly, ws, runs[0], hrs, r, cs))) return st;
+  SMC_CUDA_TRY(cudaStreamSynchronize(cs));
+  r->counters.device_ms = ms;
+  r->counters.kernel_launches = launched;
+  r->counters.kernel_ms = kms;
+  const int rs_status = r->counters.status;
+  if (rs_status == SMC_EDEGENERATE) return set_error(SMC_EDEGENERATE, "all particle weights are zero");
+  if (rs_status == SMC_ESTEPLIMIT) return set_error(SMC_ESTEPLIMIT, "max_segments reached");
+  return rs_status;
+}
+
+extern "C" smc_status smc_run_batch(const smc_model_t* ms, const smc_run_cfg* cfgs, smc_result* res,
+                                    int32_t n_runs, void* stream) {
+  if (!ms || !cfgs || !res || n_runs < 1) return set_error(SMC_EINVAL, "bad batch arguments");
+  smc_status st;
+  const int prec = cfgs[0].precision;
+  for (int q = 0; q < n_runs; ++q) {
+    if ((st = check_cfg(ms[q], &cfgs[q]))) return st;
+    if ((st = check_result(&res[q]))) return st;
+    if (cfgs[q].precision != prec) return set_error(SMC_EINVAL, "a batch must use one precision");
   }
-  const cudaMemcpyKind kind = host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (r->log_z) SMC_CUDA_TRY(cudaMemcpyAsync(r->log_z, &A.rs->log_z, 8, kind, cs));
-  if (r->final_logw) SMC_CUDA_TRY(cudaMemcpyAsync(r->final_logw, A.logw, 8 * (size_t)N, kind, cs));
-  if (host) {
-    if (r->real_fields && m->n_real)
-      SMC_CUDA_TRY(cudaMemcpyAsync(r->real_fields, fin_real, 8 * (size_t)N * m->n_real, kind, cs));
-    if (r->int_fields && m->n_int)
-      SMC_CUDA_TRY(cudaMemcpyAsync(r->int_fields, fin_int, 4 * (size_t)N * m->n_int, kind, cs));
-    if (r->stack && m->stack_cap)
-      SMC_CUDA_TRY(cudaMemcpyAsync(r->stack, fin_stack, 8 * (size_t)N * m->stack_cap, kind, cs));
+  cudaStream_t cs = (cudaStream_t)stream;
+  std::vector<Layout> lys(n_runs);
+  std::vector<size_t> offs(n_runs);
+  std::vector<RunDev> runs(n_runs);
+  size_t total = 0;
+  int max_waves = 0;
+  bool known = true;
+  for (int q = 0; q < n_runs; ++q) {
+    lys[q] = make_layout(ms[q], &cfgs[q]);
+    offs[q] = total;
+    total = align_up(total + lys[q].total, 256);
+    const bool kq = ms[q]->n_segments_known > 0 && lys[q].max_segments >= ms[q]->n_segments_known;
+    known = known && kq;
+    max_waves = std::max(max_waves, kq ? ms[q]->n_segments_known : lys[q].max_segments);
+    runs[q].n_tiles = lys[q].n_tiles;
   }
-  if (r->ancestors && hrs.n_resamples >= 0) {
-    const int n_res = std::max(0, hrs.n_segments - 1);
-    const int rows = c->record_all_ancestors ? std::min(std::min(n_res, r->ancestors_rows), Ly.anc_rows)
-                                             : (n_res > 0 ? 1 : 0);
-    if (rows > 0) SMC_CUDA_TRY(cudaMemcpyAsync(r->ancestors, A.anc, 4 * (size_t)N * rows, kind, cs));
+  const size_t meta_off = total;
+  total += wave_meta_bytes(runs);
+  void* ws = nullptr;
+  {
+    cudaError_t e = cudaMallocAsync(&ws, total, cs);
+    if (e != cudaSuccess)
+      return set_error(SMC_ENOMEM, "batch workspace cudaMallocAsync(%zu): %s", total, cudaGetErrorString(e));
+  }
+  struct Free {
+    void* p;
+    cudaStream_t s;
+    ~Free() {
+      if (p) cudaFreeAsync(p, s);
+    }
+  } guard{ws, cs};
+  std::vector<RunState*> states(n_runs);
+  for (int q = 0; q < n_runs; ++q) {
+    runs[q] = make_rundev(ms[q], &cfgs[q], lys[q], (char*)ws + offs[q]);
+    states[q] = runs[q].rs;
+    SMC_CUDA_TRY(cudaMemsetAsync(runs[q].rs, 0, sizeof(RunState), cs));
+  }
+  WavePlan W;
+  std::vector<char> staging;
+  if ((st = upload_wave(runs, (char*)ws + meta_off, cs, &W, &staging))) return st;
+  cudaEvent_t e0, e1;
+  SMC_CUDA_TRY(cudaEventCreate(&e0));
+  SMC_CUDA_TRY(cudaEventCreate(&e1));
+  SMC_CUDA_TRY(cudaEventRecord(e0, cs));
+  int launched = 0;
+  double kms = 0.0;
+  st = drive_waves(W, prec, states, max_waves, known, cs, nullptr, false, &launched, &kms);
+  if (st) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+  }
+  SMC_CUDA_TRY(cudaEventRecord(e1, cs));
+  std::vector<RunState> h(n_runs);
+  for (int q = 0; q < n_runs; ++q)
+    SMC_CUDA_TRY(cudaMemcpyAsync(&h[q], states[q], sizeof(RunState), cudaMemcpyDeviceToHost, cs));
+  SMC_CUDA_TRY(cudaStreamSynchronize(cs));
+  float msec = 0.f;
+  cudaEventElapsedTime(&msec, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int q = 0; q < n_runs; ++q) {
+    if ((st = collect_run(ms[q], &cfgs[q], lys[q], (char*)ws + offs[q], runs[q], h[q], &res[q], cs)))
+      return st;
+    res[q].counters.device_ms = msec;
+    res[q].counters.kernel_launches = launched;
+    res[q].counters.kernel_ms = 0.0;
   }
   SMC_CUDA_TRY(cudaStreamSynchronize(cs));
-  smc_counters& ct = r->counters;
-  ct.n_segments = hrs.n_segments;
-  ct.n_resamples = std::max(0, hrs.n_segments - 1);
-  ct.n_near_boundary = (int64_t)hrs.n_near;
-  ct.n_overflow = (int64_t)hrs.n_overflow;
-  ct.n_limit = (int64_t)hrs.n_limit;
-  ct.device_ms = ms;
-  ct.kernel_launches = launched;
-  ct.kernel_ms = 0.0;
-  if (timed)
-    for (int q = 0; q < launched; ++q) {
-      float t = 0.f;
-      if (cudaEventElapsedTime(&t, m->ev_seg[2 * q], m->ev_seg[2 * q + 1]) == cudaSuccess) ct.kernel_ms += t;
-    }
-  if (hrs.status == SMC_EDEGENERATE) return set_error(SMC_EDEGENERATE, "all particle weights are zero");
-  if (hrs.status == SMC_ESTEPLIMIT) return set_error(SMC_ESTEPLIMIT, "max_segments reached");
-  if (hrs.n_overflow || hrs.n_limit) return SMC_WKILLED;
   return SMC_OK;
 }

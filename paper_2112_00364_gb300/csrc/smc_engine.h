@@ -1,0 +1,91 @@
+// smc_engine.h -- structures shared by the run, batch and server paths.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/smc.h"
+#include "smc_models.cuh"
+
+namespace smc {
+
+constexpr int kMaxAncRows = 4096;
+constexpr int kMaxSegments = 1 << 24;
+constexpr int kUnboundedSegments = 1 << 20;
+constexpr int64_t kMaxParticles = (int64_t)0x7fffffff - 256;
+constexpr int64_t kTileSlots = 456;  // tile = ceil(N / 456): 152 SMs x 3 resident CTAs
+
+// Per-run device state (one struct per run, in the run's workspace).
+struct RunState {
+  double log_z, m, S, r, u, inv_r;
+  unsigned long long n_near, n_overflow, n_limit;
+  int32_t done, status, n_segments, n_resamples;
+  uint32_t arrive;
+  int32_t pad_[3];
+};
+
+// Everything a CTA needs about its run (copied to shared memory per CTA).
+struct RunDev {
+  ModelDev md;
+  StateView state[2];
+  double* logw;       // [N] log-weights of the latest segment (f64; FP32 values widened)
+  double* E[2];       // [N] tile-local inclusive scans, double-buffered by segment parity
+  double* tile_M;     // [n_tiles]
+  double* tile_s;     // [n_tiles]
+  int32_t* tile_alive;
+  double* tile_c;     // [n_tiles] written by the combine: exp(M_t - m)
+  double* tile_invc;  // [n_tiles] 1 / c_t (0 where c_t = 0)
+  double* tile_O;     // [n_tiles + 1] monotone exclusive offsets, O_T >= S
+  double* tile_q;     // [n_tiles + 1] O_t * r
+  int32_t* anc;       // ancestor rows
+  double* incr;       // [max_segments] per-segment log-Z increments
+  RunState* rs;
+  int N, n_tiles, tile, max_segments, record_all, anc_rows;
+  uint32_t k0, k1;
+};
+
+struct Layout {
+  size_t real[2], ints[2], stack[2], logw, E[2], tM, ts, talive, tc, tinvc, tO, tq, rs, anc, incr,
+      fin_real, fin_int, fin_stack, total;
+  int n_tiles, tile, anc_rows, max_segments;
+};
+
+// Device addresses of one wave's run table and per-bucket CTA maps.
+struct WavePlan {
+  const RunDev* runs = nullptr;
+  const int2* maps[4] = {nullptr, nullptr, nullptr, nullptr};
+  int n_ctas[4] = {0, 0, 0, 0};
+};
+
+}  // namespace smc
+
+struct smc_model_s {
+  smc_model_desc desc;
+  smc::ModelDev md;
+  int32_t n_real, n_int, stack_cap, n_segments_known;
+  void* dev_blob = nullptr;  // observations / tree arrays
+  void* ws = nullptr;        // cached workspace of smc_run
+  size_t ws_bytes = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> ev_seg;  // per-launch timing pairs (time_kernels)
+  std::vector<char> staging;        // host staging of the run table
+};
+
+namespace smc {
+
+int model_fields(int kind, int* n_real, int* n_int);
+int tile_for(int64_t N);
+int bucket_for(int tile);
+Layout make_layout(const smc_model_s* m, const smc_run_cfg* c);
+RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws);
+size_t wave_meta_bytes(const std::vector<RunDev>& runs);
+smc_status upload_wave(const std::vector<RunDev>& runs, void* meta, cudaStream_t st, WavePlan* W,
+                       std::vector<char>* staging);
+cudaError_t launch_wave(const WavePlan& W, int precision, cudaStream_t st);
+smc_status collect_run(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws,
+                       const RunDev& A, const RunState& hrs, smc_result* r, cudaStream_t cs);
+smc_status check_cfg(const smc_model_s* m, const smc_run_cfg* c);
+smc_status check_result(const smc_result* r);
+
+}  // namespace smc

@@ -68,7 +68,7 @@ class Counters(C.Structure):
     _fields_ = [("n_segments", C.c_int32), ("n_resamples", C.c_int32),
                 ("n_near_boundary", C.c_int64), ("n_overflow", C.c_int64),
                 ("n_limit", C.c_int64), ("device_ms", C.c_double), ("kernel_ms", C.c_double),
-                ("kernel_launches", C.c_int32), ("pad_", C.c_int32)]
+                ("kernel_launches", C.c_int32), ("status", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -101,6 +101,8 @@ def lib():
         L.smc_workspace_bytes.restype = C.c_int32
         L.smc_run.argtypes = [_vp, C.POINTER(RunCfg), C.POINTER(Result), _vp]
         L.smc_run.restype = C.c_int32
+        L.smc_run_batch.argtypes = [_vp, _vp, _vp, C.c_int32, _vp]
+        L.smc_run_batch.restype = C.c_int32
         L.smc_resample_workspace_bytes.argtypes = [C.c_int64]
         L.smc_resample_workspace_bytes.restype = C.c_size_t
         L.smc_resample.argtypes = [_vp, C.c_int64, C.c_double, _vp, _vp, _vp, _vp, C.c_size_t, _vp]
@@ -214,6 +216,58 @@ def _cfg(N, seed, run_id, precision, max_segments, record_all, workspace, time_k
     return c
 
 
+def _alloc_outputs(model: Model, N: int, rows: int, where: str, outputs: dict | None) -> dict:
+    shapes = _output_shapes(model, N, rows)
+    out = dict(outputs or {})
+    if where == "host":
+        for k, (shp, dt) in shapes.items():
+            if k not in out and _wanted(model, k):
+                out[k] = np.zeros(shp, dtype=dt)
+    else:
+        import torch
+
+        tmap = {"f8": torch.float64, "i4": torch.int32}
+        for k, (shp, dt) in shapes.items():
+            if k not in out and _wanted(model, k):
+                out[k] = torch.zeros(shp, dtype=tmap[dt], device="cuda")
+    return out
+
+
+def _output_shapes(model: Model, N: int, rows: int) -> dict:
+    return dict(log_z=((1,), "f8"), final_logw=((N,), "f8"), ancestors=((rows, N), "i4"),
+                real_fields=((model.n_real, N), "f8"), int_fields=((model.n_int, N), "i4"),
+                stack=((model.stack_cap, N), "f8"))
+
+
+def _wanted(model: Model, key: str) -> bool:
+    return (key != "stack" or model.stack_cap) and (key != "real_fields" or model.n_real)
+
+
+def _rows(model: Model, max_segments: int, record_all: bool) -> int:
+    return max(1, (max_segments or model.n_segments or 4096) - 1) if record_all else 1
+
+
+def _result_struct(out: dict, where: str, rows: int) -> Result:
+    r = Result()
+    r.where = MEM_HOST if where == "host" else MEM_DEVICE
+    r.ancestors_rows = rows
+    for k in ("log_z", "final_logw", "ancestors", "real_fields", "int_fields", "stack"):
+        setattr(r, k, _ptr(out.get(k)))
+    return r
+
+
+def _result_dict(st: int, r: Result, out: dict, where: str, record_all: bool) -> dict:
+    c = r.counters
+    res = dict(status=st, run_status=c.status, n_segments=c.n_segments,
+               n_resamples=c.n_resamples, n_near_boundary=c.n_near_boundary,
+               n_overflow=c.n_overflow, n_limit=c.n_limit, device_ms=c.device_ms,
+               kernel_ms=c.kernel_ms, kernel_launches=c.kernel_launches, **out)
+    res["log_z_value"] = float(out["log_z"][0]) if where == "host" else None
+    if record_all and "ancestors" in out:
+        res["ancestors"] = out["ancestors"][: c.n_resamples]
+    return res
+
+
 def run(model: Model, N: int, seed: int, run_id: int = 0, precision: str = "fp64",
         max_segments: int = 0, record_all_ancestors: bool = False, where: str = "host",
         stream=None, workspace=None, outputs: dict | None = None,
@@ -222,41 +276,37 @@ def run(model: Model, N: int, seed: int, run_id: int = 0, precision: str = "fp64
     torch CUDA tensors (allocated here unless passed in `outputs`)."""
     cfg = _cfg(N, seed, run_id, precision, max_segments, record_all_ancestors, workspace,
                time_kernels)
-    rows = 1
-    if record_all_ancestors:
-        rows = max(1, (max_segments or model.n_segments or 4096) - 1)
-    shapes = dict(log_z=((1,), "f8"), final_logw=((N,), "f8"), ancestors=((rows, N), "i4"),
-                  real_fields=((model.n_real, N), "f8"), int_fields=((model.n_int, N), "i4"),
-                  stack=((model.stack_cap, N), "f8"))
-    out = dict(outputs or {})
-    if where == "host":
-        for k, (shp, dt) in shapes.items():
-            if k not in out and (k != "stack" or model.stack_cap) and (k != "real_fields" or model.n_real):
-                out[k] = np.zeros(shp, dtype=dt)
-    else:
-        import torch
-
-        tmap = {"f8": torch.float64, "i4": torch.int32}
-        for k, (shp, dt) in shapes.items():
-            if k not in out and (k != "stack" or model.stack_cap) and (k != "real_fields" or model.n_real):
-                out[k] = torch.zeros(shp, dtype=tmap[dt], device="cuda")
-    r = Result()
-    r.where = MEM_HOST if where == "host" else MEM_DEVICE
-    r.ancestors_rows = rows
-    for k in shapes:
-        setattr(r, k, _ptr(out.get(k)))
+    rows = _rows(model, max_segments, record_all_ancestors)
+    out = _alloc_outputs(model, N, rows, where, outputs)
+    r = _result_struct(out, where, rows)
     st = lib().smc_run(model.handle, C.byref(cfg), C.byref(r), _stream(stream))
     if st < 0 and st not in (EDEGENERATE, ESTEPLIMIT):
         _check(st)
-    c = r.counters
-    res = dict(status=st, n_segments=c.n_segments, n_resamples=c.n_resamples,
-               n_near_boundary=c.n_near_boundary, n_overflow=c.n_overflow, n_limit=c.n_limit,
-               device_ms=c.device_ms, kernel_ms=c.kernel_ms,
-               kernel_launches=c.kernel_launches, **out)
-    res["log_z_value"] = float(out["log_z"][0]) if where == "host" else None
-    if record_all_ancestors and "ancestors" in out:
-        res["ancestors"] = out["ancestors"][: c.n_resamples]
-    return res
+    return _result_dict(st, r, out, where, record_all_ancestors)
+
+
+def run_batch(models: list, specs: list, precision: str = "fp64", where: str = "host",
+              record_all_ancestors: bool = False, stream=None) -> list:
+    """smc_run_batch.  specs[q] = dict(N=..., seed=..., run_id=0, max_segments=0);
+    returns one result dict per run (same keys as run())."""
+    n = len(models)
+    cfgs = (RunCfg * n)()
+    ress = (Result * n)()
+    outs, rows_l = [], []
+    for q, (m, sp) in enumerate(zip(models, specs)):
+        c = _cfg(sp["N"], sp["seed"], sp.get("run_id", 0), precision, sp.get("max_segments", 0),
+                 record_all_ancestors, None)
+        cfgs[q] = c
+        rows = _rows(m, sp.get("max_segments", 0), record_all_ancestors)
+        out = _alloc_outputs(m, sp["N"], rows, where, sp.get("outputs"))
+        ress[q] = _result_struct(out, where, rows)
+        outs.append(out)
+        rows_l.append(rows)
+    handles = (_vp * n)(*[m.handle for m in models])
+    st = lib().smc_run_batch(handles, cfgs, ress, n, _stream(stream))
+    _check(st)
+    return [_result_dict(ress[q].counters.status, ress[q], outs[q], where, record_all_ancestors)
+            for q in range(n)]
 
 
 def resample_workspace_bytes(N: int) -> int:
