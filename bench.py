@@ -1,30 +1,34 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 particle-SMC path: SMC particle-steps/s.
 
-One step = one complete SMC run of the workload (every checkpoint segment:
-propagation, FP64 normaliser and scan, systematic resampling, gather, and
-the outputs log Z / final log-weights / last ancestors / final states).
-A particle-step is one particle advancing one checkpoint segment,
-including its share of resampling.
+A particle-step is one particle advancing one checkpoint segment, including
+its share of resampling.  One benchmark step is one complete piece of work:
 
-Default workload (one GPU): the constant-rate birth-death model of
-Listing 1 on a seeded 64-tip Yule tree of height 1, Gamma(1,1) /
-Gamma(1,0.5) priors, N = 2^16 particles, FP64, 127 checkpoints.
+  crbd64        one SMC run of the constant-rate birth-death model (Listing 1)
+                on a seeded 64-tip Yule tree of height 1, Gamma(1,1) /
+                Gamma(1,0.5) priors, N = 2^16, FP64, 127 checkpoints (default);
+  lg            one run of the linear-Gaussian model, T = 50, N = 1024, FP64;
+  rateshift256  one run of the rate-shift model on a 256-tip tree, N = 2^20,
+                FP32 particles with FP64 reductions;
+  batch512      one batched launch sequence of 512 independent runs (half
+                linear-Gaussian with T log-uniform in 20..500, half CRBD with
+                tips log-uniform in 16..256, N log-uniform in 256..65536),
+                FP32 particles with FP64 reductions; the line also carries the
+                same 512 runs timed one run per launch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload crbd64|lg|rateshift256]
+                    [--workload crbd64|lg|rateshift256|batch512]
 
 With N > 1 (launched by torch.distributed.run) every rank runs its own
-independent replica with a rank-specific seed (runs do not exchange data,
-so there is no collective on the data path; scaling is weak).  Rank 0 prints
-one JSON line.  `--impl reference` times the CPU oracle on the host cores.
+independent replica with rank-specific seeds (runs exchange no data, so there
+is no collective on the data path; scaling is weak).  Rank 0 prints one JSON
+line.  `--impl reference` times the CPU oracle on the host cores.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -44,23 +48,20 @@ METRIC = "SMC particle-steps/s at fixed log-Z error vs plain GPU path; p50/p99 l
 UNIT = "particle-steps/s"
 
 WORKLOADS = {
-    # Listing 1 CRBD, 64-tip Yule tree (seed 2), N = 2^16, FP64
     "crbd64": dict(kind="crbd", tips=64, tree_seed=2, N=1 << 16, precision="fp64"),
-    # linear-Gaussian, T = 50 observations (seed 1), N = 1024, FP64
     "lg": dict(kind="lg", T=50, obs_seed=1, N=1024, precision="fp64"),
-    # rate-shift, 256-tip Yule tree (seed 3), N = 2^20, FP32 particles / FP64 reductions
     "rateshift256": dict(kind="rateshift", tips=256, tree_seed=3, N=1 << 20, precision="fp32",
                          sigma=0.3),
+    "batch512": dict(kind="batch", n_runs=512, spec_seed=4, precision="fp32"),
 }
 
 # FP64 operations the step kernel executes per particle-step (2 x DFMA + DADD +
-# DMUL from one ncu capture of the crbd64 workload; see the profiles folder).
-FP64_FLOP_PER_PSTEP = {"crbd64": None}
-# Per-launch DRAM traffic of the step kernel from the same capture, valid only
-# for the kernel sources with this digest.
-NCU_TRAFFIC = {"crbd64": dict(bytes_per_launch=None, src_digest=None)}
+# DMUL) and its DRAM traffic per launch, from one ncu capture of the workload
+# (profiles folder); the traffic holds only for the kernel sources with the
+# recorded digest.
+NCU = {"crbd64": dict(fp64_flop_per_pstep=None, bytes_per_launch=None, src_digest=None)}
 
-# 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA) = the 1.25 TFLOP/s FP64 rate of GB300
+# 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
 
 
@@ -69,24 +70,6 @@ def src_digest() -> str:
     for p in sorted((ROOT / "paper_2112_00364_gb300" / "csrc").glob("*")):
         h.update(p.read_bytes())
     return h.hexdigest()[:16]
-
-
-def setup_inputs(w: dict):
-    if w["kind"] == "lg":
-        obs = inputs.lg_observations(w["T"], seed=w["obs_seed"])
-        return dict(obs=obs), w["T"]
-    tree = inputs.yule_tree(w["tips"], seed=w["tree_seed"])
-    p = dict(tree=tree)
-    if w["kind"] == "rateshift":
-        p.update(sigma=w["sigma"], lam_stack_cap=tree.max_pending_right() + 1)
-    return p, tree.n_nodes
-
-
-def input_bytes(params: dict) -> int:
-    if "obs" in params:
-        return params["obs"].nbytes
-    t = params["tree"]
-    return 4 * 4 * t.n_nodes + 8 * t.n_nodes
 
 
 class ClockSampler:
@@ -146,76 +129,125 @@ class ClockSampler:
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def oracle_throughput(w: dict, params: dict, n_seg: int, budget_s: float, n_particles: int,
-                      max_runs: int = 50):
-    """Time the CPU oracle on the host: full runs with seeds 1, 2, ... until
-    `budget_s` seconds of work (at least one run)."""
+# ------------------------------------------------------------------ workloads
+class Work:
+    """One workload: a list of runs (kind, params, N, seed, run_id)."""
+
+    def __init__(self, name: str, seed_base: int):
+        w = WORKLOADS[name]
+        self.name, self.w, self.precision = name, w, w["precision"]
+        self.runs = []
+        if w["kind"] == "batch":
+            for q, sp in enumerate(inputs.batch_specs(w["n_runs"], seed=w["spec_seed"])):
+                if sp.kind == "lg":
+                    p = dict(obs=inputs.lg_observations(sp.T, seed=sp.obs_seed))
+                else:
+                    p = dict(tree=inputs.yule_tree(sp.tips, seed=sp.tree_seed))
+                self.runs.append(dict(kind=sp.kind, params=p, N=sp.n_particles,
+                                      seed=seed_base + sp.seed, run_id=q,
+                                      segments=sp.n_segments()))
+        else:
+            if w["kind"] == "lg":
+                p = dict(obs=inputs.lg_observations(w["T"], seed=w["obs_seed"]))
+                seg = w["T"]
+            else:
+                tree = inputs.yule_tree(w["tips"], seed=w["tree_seed"])
+                p = dict(tree=tree)
+                if w["kind"] == "rateshift":
+                    p.update(sigma=w["sigma"], lam_stack_cap=tree.max_pending_right() + 1)
+                seg = tree.n_nodes
+            self.runs.append(dict(kind=w["kind"], params=p, N=w["N"], seed=seed_base, run_id=0,
+                                  segments=seg))
+        self.units = sum(r["N"] * r["segments"] for r in self.runs)
+
+    def config(self) -> dict:
+        w = self.w
+        cfg = {"workload": self.name, "precision": self.precision,
+               "l2": "flushed between timed steps (512 MiB write)",
+               "parallelism": "replicas (one independent workload per GPU)",
+               "particle_steps_per_step": self.units}
+        if w["kind"] == "batch":
+            cfg.update(runs=w["n_runs"], n_particles_total=sum(r["N"] for r in self.runs),
+                       mix="half linear-Gaussian (T log-uniform 20..500), half CRBD (tips "
+                           "log-uniform 16..256), N log-uniform 256..65536, seeded (spec seed 4)")
+        elif w["kind"] == "lg":
+            cfg.update(model="linear-Gaussian SSM x_t=0.9x+N(0,1), y~N(x,0.5^2)",
+                       n_particles=w["N"], checkpoints=w["T"],
+                       observations=f"T={w['T']} simulated, seed {w['obs_seed']}")
+        else:
+            cfg.update(model="CRBD (Listing 1), priors Gamma(1,1), Gamma(1,0.5), rho=1"
+                       if w["kind"] == "crbd" else "rate-shift CRBD, lognormal multipliers sigma=0.3",
+                       n_particles=w["N"], checkpoints=self.runs[0]["segments"],
+                       tree=f"Yule {w['tips']} tips seed {w['tree_seed']}, height 1.0")
+        return cfg
+
+    def input_bytes(self) -> int:
+        tot = 0
+        for r in self.runs:
+            p = r["params"]
+            tot += p["obs"].nbytes if "obs" in p else 24 * p["tree"].n_nodes
+        return tot
+
+
+def oracle_throughput(work: Work, budget_s: float, max_runs: int, n_particles=None):
+    """Time the CPU oracle on the host: the workload's runs in order (cycling),
+    until `budget_s` seconds of work (at least one run)."""
     import oracle
 
-    prec = oracle.FP64 if w["precision"] == "fp64" else oracle.FP32
-    runs, t_tot = 0, 0.0
+    prec = oracle.FP64 if work.precision == "fp64" else oracle.FP32
+    runs, t_tot, units = 0, 0.0, 0
     while runs < max_runs and (runs == 0 or t_tot < budget_s):
+        r = work.runs[runs % len(work.runs)]
+        N = n_particles or r["N"]
         t0 = time.perf_counter()
-        r = oracle.smc_run(w["kind"], n_particles, seed=runs + 1, precision=prec, **params)
+        o = oracle.smc_run(r["kind"], N, seed=r["seed"] + runs // len(work.runs), run_id=r["run_id"],
+                           precision=prec, **r["params"])
         t_tot += time.perf_counter() - t0
-        if r["status"] < 0:
-            raise RuntimeError(f"oracle status {r['status']}")
+        if o["status"] < 0:
+            raise RuntimeError(f"oracle status {o['status']}")
+        units += N * r["segments"]
         runs += 1
-    return runs * n_particles * n_seg / t_tot, runs, t_tot
+    return units / t_tot, runs, t_tot, units
 
 
-def run_reference(args, w, params, n_seg):
+def run_reference(args, work: Work):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    n_sample = min(w["N"], 1 << 14)
-    import oracle
-
-    prec = oracle.FP64 if w["precision"] == "fp64" else oracle.FP32
-    for s in range(args.warmup):
-        oracle.smc_run(w["kind"], n_sample, seed=1000 + s, precision=prec, **params)
-    times = []
-    for s in range(args.steps):
-        t0 = time.perf_counter()
-        r = oracle.smc_run(w["kind"], n_sample, seed=1 + s, precision=prec, **params)
-        times.append(time.perf_counter() - t0)
-        assert r["status"] >= 0
+    batch = work.w["kind"] == "batch"
+    n_sample = None if batch else min(work.runs[0]["N"], 1 << 14)
+    max_runs = 32 if batch else 1
+    for _ in range(args.warmup):
+        oracle_throughput(work, 0.0, 1, n_sample)
+    times, units = [], 0
+    for _ in range(args.steps):
+        v, runs, secs, u = oracle_throughput(work, 0.0 if not batch else 1e9, max_runs, n_sample)
+        times.append(secs)
+        units += u
     total = sum(times)
-    value = args.steps * n_sample * n_seg / total
-    sample = (f"{args.steps} oracle runs of the {args.workload} workload with N={n_sample} "
-              f"particles (of {w['N']}), {n_seg} checkpoints each, single-threaded")
+    value = units / total
+    if batch:
+        sample = (f"each step: the first {max_runs} of the 512 runs of the batch, run one after "
+                  f"another by the single-threaded oracle")
+    else:
+        sample = (f"each step: one oracle run of the {args.workload} workload with N={n_sample} "
+                  f"particles (of {work.runs[0]['N']}), single-threaded")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if w["precision"] == "fp64" else "f32+f64", "data": "synthetic",
-        "config": workload_config(args.workload, w, n_seg),
+        "dtype": "f64" if work.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": work.config(),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
-
-
-def workload_config(name: str, w: dict, n_seg: int) -> dict:
-    cfg = {"workload": name, "n_particles": w["N"], "checkpoints": n_seg,
-           "precision": w["precision"], "l2": "flushed between timed steps (512 MiB write)",
-           "parallelism": "replicas (one independent run per GPU)"}
-    if w["kind"] == "lg":
-        cfg.update(model="linear-Gaussian SSM x_t=0.9x+N(0,1), y~N(x,0.5^2)",
-                   observations=f"T={w['T']} simulated, seed {w['obs_seed']}")
-    else:
-        cfg.update(model="CRBD (Listing 1), priors Gamma(1,1), Gamma(1,0.5), rho=1"
-                   if w["kind"] == "crbd" else "rate-shift CRBD, lognormal multipliers sigma=0.3",
-                   tree=f"Yule {w['tips']} tips seed {w['tree_seed']}, height 1.0")
-    return cfg
 
 
 def main() -> int:
@@ -227,16 +259,15 @@ def main() -> int:
     ap.add_argument("--workload", default="crbd64", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
-    params, n_seg = setup_inputs(w)
+    ws, rank, local = dist_env()
+    work = Work(args.workload, seed_base=1 + 100000 * rank)
     if args.impl == "reference":
-        return run_reference(args, w, params, n_seg)
+        return run_reference(args, work)
 
     import torch
 
     from paper_2112_00364_gb300 import smc
 
-    ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
 
@@ -246,28 +277,38 @@ def main() -> int:
         dist = None
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    N = w["N"]
     stream = torch.cuda.Stream()
-    model = smc.Model(w["kind"], **params)
-    outs = {
-        "log_z": torch.zeros(1, dtype=torch.float64, device=dev),
-        "final_logw": torch.zeros(N, dtype=torch.float64, device=dev),
-        "ancestors": torch.zeros((1, N), dtype=torch.int32, device=dev),
-        "int_fields": torch.zeros((model.n_int, N), dtype=torch.int32, device=dev),
-    }
-    if model.n_real:
-        outs["real_fields"] = torch.zeros((model.n_real, N), dtype=torch.float64, device=dev)
-    if model.stack_cap:
-        outs["stack"] = torch.zeros((model.stack_cap, N), dtype=torch.float64, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    seed0 = 1 + 100000 * rank
+    batch = work.w["kind"] == "batch"
+    models = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
 
-    def one(seed, timed_kernels):
-        return smc.run(model, N, seed=seed, precision=w["precision"], where="device",
-                       stream=stream, outputs=outs, time_kernels=timed_kernels)
+    def dev_outputs(m, N):
+        o = {"log_z": torch.zeros(1, dtype=torch.float64, device=dev),
+             "final_logw": torch.zeros(N, dtype=torch.float64, device=dev),
+             "ancestors": torch.zeros((1, N), dtype=torch.int32, device=dev),
+             "int_fields": torch.zeros((m.n_int, N), dtype=torch.int32, device=dev)}
+        if m.n_real:
+            o["real_fields"] = torch.zeros((m.n_real, N), dtype=torch.float64, device=dev)
+        if m.stack_cap:
+            o["stack"] = torch.zeros((m.stack_cap, N), dtype=torch.float64, device=dev)
+        return o
+
+    outs = [dev_outputs(m, r["N"]) for m, r in zip(models, work.runs)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def device_step(seed_off: int, timed: bool):
+        """One step with inputs resident on the device; returns per-run results."""
+        if batch:
+            specs = [dict(N=r["N"], seed=r["seed"] + seed_off, run_id=r["run_id"], outputs=o)
+                     for r, o in zip(work.runs, outs)]
+            return smc.run_batch(models, specs, precision=work.precision, where="device",
+                                 stream=stream)
+        r = work.runs[0]
+        return [smc.run(models[0], r["N"], seed=r["seed"] + seed_off, run_id=r["run_id"],
+                        precision=work.precision, where="device", stream=stream, outputs=outs[0],
+                        time_kernels=timed)]
 
     for s in range(args.warmup):
-        one(seed0 + 50000 + s, False)
+        device_step(50000 + s, False)
     torch.cuda.synchronize()
     gpu_index = local
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -282,22 +323,21 @@ def main() -> int:
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, kern_ms, kern_launches, logz = [], 0.0, 0, []
-    statuses = []
+    step_ms, kern_ms, kern_launches, logz, statuses = [], 0.0, 0, [], set()
     for s in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        r = one(seed0 + s, True)
+        res = device_step(s, True)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        kern_ms += r["kernel_ms"]
-        kern_launches += r["kernel_launches"]
-        statuses.append(r["status"])
-        logz.append(float(outs["log_z"].cpu()[0]))
+        kern_ms += sum(r["kernel_ms"] for r in res)
+        kern_launches += res[0]["kernel_launches"]
+        statuses.update(r["status"] for r in res)
+        logz.append(float(outs[0]["log_z"].cpu()[0]))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -307,79 +347,109 @@ def main() -> int:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    units_per_step = N * n_seg
-    value = args.steps * units_per_step * ws / (total_ms * 1e-3)
-    ms_per_step = total_ms / args.steps
+    value = args.steps * work.units * ws / (total_ms * 1e-3)
+
+    # the same runs one run per launch (plain path), timed once
+    plain = None
+    if batch:
+        torch.cuda.synchronize()
+        t_plain = 0.0
+        for m, r, o in zip(models, work.runs, outs):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            smc.run(m, r["N"], seed=r["seed"], run_id=r["run_id"], precision=work.precision,
+                    where="device", stream=stream, outputs=o)
+            e1.record(stream)
+            e1.synchronize()
+            t_plain += e0.elapsed_time(e1)
+        plain = {"value": work.units / (t_plain * 1e-3), "unit": UNIT,
+                 "what": "the same 512 runs through smc_run, one run after another"}
 
     # end to end through the public API: host inputs in, host results out
-    h2d = input_bytes(params)
-    pinned = {
-        "log_z": torch.zeros(1, dtype=torch.float64).pin_memory(),
-        "final_logw": torch.zeros(N, dtype=torch.float64).pin_memory(),
-        "ancestors": torch.zeros((1, N), dtype=torch.int32).pin_memory(),
-        "int_fields": torch.zeros((model.n_int, N), dtype=torch.int32).pin_memory(),
-    }
-    if model.n_real:
-        pinned["real_fields"] = torch.zeros((model.n_real, N), dtype=torch.float64).pin_memory()
-    if model.stack_cap:
-        pinned["stack"] = torch.zeros((model.stack_cap, N), dtype=torch.float64).pin_memory()
-    d2h = sum(t.numel() * t.element_size() for t in pinned.values())
-    e2e_s = []
-    for s in range(args.steps):
+    pinned = []
+    for m, r in zip(models, work.runs):
+        N = r["N"]
+        o = {"log_z": torch.zeros(1, dtype=torch.float64).pin_memory(),
+             "final_logw": torch.zeros(N, dtype=torch.float64).pin_memory(),
+             "ancestors": torch.zeros((1, N), dtype=torch.int32).pin_memory(),
+             "int_fields": torch.zeros((m.n_int, N), dtype=torch.int32).pin_memory()}
+        if m.n_real:
+            o["real_fields"] = torch.zeros((m.n_real, N), dtype=torch.float64).pin_memory()
+        if m.stack_cap:
+            o["stack"] = torch.zeros((m.stack_cap, N), dtype=torch.float64).pin_memory()
+        pinned.append(o)
+    d2h = sum(t.numel() * t.element_size() for o in pinned for t in o.values())
+    e2e_steps = args.steps if not batch else max(1, min(args.steps, 3))
+    e2e_total = 0.0
+    for s in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        m2 = smc.Model(w["kind"], **params)
-        smc.run(m2, N, seed=seed0 + s, precision=w["precision"], where="host", stream=stream,
-                outputs=pinned)
-        m2.close()
-        e2e_s.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_s)
+        ms2 = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
+        if batch:
+            specs = [dict(N=r["N"], seed=r["seed"] + s, run_id=r["run_id"], outputs=o)
+                     for r, o in zip(work.runs, pinned)]
+            smc.run_batch(ms2, specs, precision=work.precision, where="host", stream=stream)
+        else:
+            r = work.runs[0]
+            smc.run(ms2[0], r["N"], seed=r["seed"] + s, run_id=r["run_id"],
+                    precision=work.precision, where="host", stream=stream, outputs=pinned[0])
+        for m2 in ms2:
+            m2.close()
+        e2e_total += time.perf_counter() - t0
     if dist:
         t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
-    e2e_value = args.steps * units_per_step * ws / e2e_total
+    e2e_value = e2e_steps * work.units * ws / e2e_total
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
 
-    avg_launch_s = (kern_ms / kern_launches) * 1e-3 if kern_launches else None
-    flop = FP64_FLOP_PER_PSTEP.get(args.workload)
     roof = None
-    if avg_launch_s and flop:
-        achieved = flop * N / avg_launch_s
-        tr = NCU_TRAFFIC.get(args.workload, {})
-        traffic = tr.get("bytes_per_launch") if tr.get("src_digest") == src_digest() else None
+    info = NCU.get(args.workload)
+    if info and info["fp64_flop_per_pstep"] and kern_launches and not batch:
+        avg_launch_s = kern_ms / kern_launches * 1e-3
+        achieved = info["fp64_flop_per_pstep"] * work.runs[0]["N"] / avg_launch_s
+        traffic = info["bytes_per_launch"] if info["src_digest"] == src_digest() else None
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
-                "kernel": "step_kernel (fused segment kernel)",
+                "kernel": "wave_kernel (fused segment kernel)",
                 "avg_launch_us": avg_launch_s * 1e6, "launches": kern_launches,
                 "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM"}
     cpu = None
     if ws == 1:
-        v, runs, secs = oracle_throughput(w, params, n_seg, args.cpu_seconds, N)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{runs} full oracle runs of the workload (N={N}, seeds 1..{runs}), "
-                         f"{secs:.1f} s single-threaded"}
+        if batch:
+            v, runs, secs, _ = oracle_throughput(work, 1e9, 32)
+            sample = (f"the first {runs} of the 512 runs of the batch, run one after another "
+                      f"({secs:.1f} s single-threaded)")
+        else:
+            v, runs, secs, _ = oracle_throughput(work, args.cpu_seconds, 50)
+            sample = (f"{runs} full oracle runs of the workload (seeds from {work.runs[0]['seed']}), "
+                      f"{secs:.1f} s single-threaded")
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     lat = sorted(step_ms)
+    launches_per_step = (kern_launches // max(1, args.steps)) + len(work.runs)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if w["precision"] == "fp64" else "f32+f64", "data": "synthetic",
-        "config": workload_config(args.workload, w, n_seg),
+        "dtype": "f64" if work.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": work.config(),
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "log_z": {"mean": float(np.mean(logz)), "sd": float(np.std(logz))},
-        "status": sorted(set(statuses)),
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "log_z_run0": {"mean": float(np.mean(logz)), "sd": float(np.std(logz))},
+        "status": sorted(statuses),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": work.input_bytes(),
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (n_seg + 1),
+        "gpu_launches": args.steps * launches_per_step,
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": clk,
     }
+    if plain:
+        line["plain_one_run_per_launch"] = plain
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

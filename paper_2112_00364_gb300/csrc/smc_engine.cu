@@ -460,18 +460,22 @@ smc_status drive_waves(const WavePlan& W, int precision, const std::vector<RunSt
   *launched = 0;
   *kernel_ms = 0.0;
   timed = timed && evs;
+  int kernels_per_wave = 0;
+  for (int b = 0; b < 4; ++b) kernels_per_wave += W.n_ctas[b] ? 1 : 0;
+  int waves = 0;
   auto one = [&]() -> smc_status {
     if (timed) {
-      while ((int)evs->size() < 2 * (*launched + 1)) {
+      while ((int)evs->size() < 2 * (waves + 1)) {
         cudaEvent_t e;
         SMC_CUDA_TRY(cudaEventCreate(&e));
         evs->push_back(e);
       }
-      SMC_CUDA_TRY(cudaEventRecord((*evs)[2 * *launched], st));
+      SMC_CUDA_TRY(cudaEventRecord((*evs)[2 * waves], st));
     }
     SMC_CUDA_TRY(launch_wave(W, precision, st));
-    if (timed) SMC_CUDA_TRY(cudaEventRecord((*evs)[2 * *launched + 1], st));
-    ++*launched;
+    if (timed) SMC_CUDA_TRY(cudaEventRecord((*evs)[2 * waves + 1], st));
+    ++waves;
+    *launched += kernels_per_wave;
     return SMC_OK;
   };
   if (known) {
@@ -499,7 +503,7 @@ smc_status drive_waves(const WavePlan& W, int precision, const std::vector<RunSt
   }
   if (timed) {
     SMC_CUDA_TRY(cudaStreamSynchronize(st));
-    for (int q = 0; q < *launched; ++q) {
+    for (int q = 0; q < waves; ++q) {
       float t = 0.f;
       if (cudaEventElapsedTime(&t, (*evs)[2 * q], (*evs)[2 * q + 1]) == cudaSuccess) *kernel_ms += t;
     }
