@@ -44,7 +44,8 @@ typedef int32_t smc_status;
 #define SMC_EDEGENERATE (-4)  /* every particle weight became zero; log Z = -inf */
 #define SMC_ESTEPLIMIT (-5)   /* max_segments reached before every particle hit b_stop */
 #define SMC_ETIMEOUT (-6)     /* a bounded wait gave up (server wait, device barrier) */
-#define SMC_EBUSY (-7)        /* resource temporarily unavailable (server full) */
+#define SMC_EBUSY (-7)        /* resource temporarily unavailable (server shutting down) */
+#define SMC_ECANCELLED (-8)   /* the request was cancelled before it finished */
 #define SMC_WKILLED 1         /* success; some particles were killed by the recursion-depth
                                  cap, the per-segment call limit or the stack capacity */
 
@@ -190,6 +191,60 @@ smc_status smc_run(smc_model_t m, const smc_run_cfg *c, smc_result *r, void *str
  * (SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA) with no results. */
 smc_status smc_run_batch(const smc_model_t *ms, const smc_run_cfg *cfgs, smc_result *res,
                          int32_t n_runs, void *stream);
+
+/* ---------------- continuous batching (serving) ----------------
+ * A server owns a CUDA stream and a worker thread.  Requests (a model, a run
+ * configuration and caller-owned result buffers) are queued by smc_server_submit
+ * from any thread; the worker admits queued requests into the set of resident
+ * runs whenever the resident-run cap and the device-memory budget allow, and
+ * advances every resident run by one segment per wave (the same wave kernels as
+ * smc_run_batch), so requests that arrive while others are on the GPU join the
+ * running waves instead of waiting for them to finish.  Each run's population
+ * stays in device memory across its checkpoints.  A finished run's outputs are
+ * copied into its result buffers (stream-ordered; pinned host or device buffers
+ * keep the worker from blocking) and its ticket completes.  A request's results
+ * are identical to what smc_run gives for the same model and configuration.
+ * The model handle and the result buffers must stay valid until the ticket is
+ * done.  The paper runs one SMC at a time; this layer is the build's serving form
+ * of the Section 3.3 engine. */
+typedef struct smc_server_s *smc_server_t;
+
+typedef struct {
+  int32_t precision;          /* SMC_PREC_*: every request of a server uses it */
+  int32_t max_resident_runs;  /* cap on runs resident at once (0 = 4096) */
+  int32_t poll_waves;         /* waves between looks at the finished runs (0 = 1) */
+  int32_t pad_;
+} smc_server_cfg;
+
+typedef struct {
+  int64_t waves;           /* waves launched */
+  int64_t completed;       /* requests finished */
+  int64_t particle_steps;  /* particle-steps of finished requests */
+  int32_t resident;        /* runs resident now */
+  int32_t queued;          /* requests waiting for admission */
+  smc_status worker_status;/* 0, or the error that stopped the worker */
+  int32_t pad_;
+} smc_server_stats_t;
+
+/* Create a server on the current device with a device-memory budget (bytes) for
+ * resident runs' workspaces.  Errors: SMC_EINVAL, SMC_ENOMEM, SMC_ECUDA. */
+smc_status smc_server_create(size_t device_mem_budget, const smc_server_cfg *cfg,
+                             smc_server_t *out);
+/* Queue one request; *ticket identifies it.  Errors: SMC_EINVAL (bad arguments or a
+ * precision other than the server's), SMC_ENOMEM (the request alone exceeds the
+ * budget), SMC_EBUSY (server shutting down).  Never blocks on the GPU. */
+smc_status smc_server_submit(smc_server_t s, smc_model_t m, const smc_run_cfg *c, smc_result *r,
+                             uint64_t *ticket);
+/* *done = 1 once the ticket finished; then returns the run's status. */
+smc_status smc_server_poll(smc_server_t s, uint64_t ticket, int32_t *done);
+/* Wait at most timeout_s seconds for the ticket (SMC_ETIMEOUT if it is not done);
+ * returns the run's status and, if latency_s != NULL, submit-to-done seconds. */
+smc_status smc_server_wait(smc_server_t s, uint64_t ticket, double timeout_s, double *latency_s);
+/* Cancel a queued or resident request (it completes with SMC_ECANCELLED). */
+smc_status smc_server_cancel(smc_server_t s, uint64_t ticket);
+smc_status smc_server_stats(smc_server_t s, smc_server_stats_t *out);
+/* Finish every queued and resident request, then stop the worker and free everything. */
+void smc_server_destroy(smc_server_t s);
 
 /* ---------------- resampling primitives on caller device buffers ----------------
  * These are the normaliser / scan / systematic search / gather of Section 3.3 as

@@ -18,7 +18,7 @@ CSRC = PKG / "csrc"
 INCLUDE = PKG.parent / "include"
 BUILD = PKG / "_build"
 LIB = PKG / "libsmc.so"
-SOURCES = ["smc_engine.cu", "smc_prims.cu"]
+SOURCES = ["smc_engine.cu", "smc_prims.cu", "smc_server.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

@@ -17,6 +17,7 @@ _PKG = Path(__file__).resolve().parent
 LIB_PATH = _PKG / "libsmc.so"
 
 OK, EINVAL, ENOMEM, ECUDA, EDEGENERATE, ESTEPLIMIT, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
+ECANCELLED = -8
 WKILLED = 1
 MODEL_LG, MODEL_CRBD, MODEL_RATESHIFT, MODEL_GEOMETRIC = 1, 2, 3, 4
 KINDS = {"lg": MODEL_LG, "crbd": MODEL_CRBD, "rateshift": MODEL_RATESHIFT,
@@ -77,6 +78,17 @@ class Result(C.Structure):
                 ("int_fields", _vp), ("stack", _vp), ("counters", Counters)]
 
 
+class ServerCfg(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_resident_runs", C.c_int32),
+                ("poll_waves", C.c_int32), ("pad_", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("waves", C.c_int64), ("completed", C.c_int64), ("particle_steps", C.c_int64),
+                ("resident", C.c_int32), ("queued", C.c_int32), ("worker_status", C.c_int32),
+                ("pad_", C.c_int32)]
+
+
 _lib = None
 
 
@@ -103,6 +115,21 @@ def lib():
         L.smc_run.restype = C.c_int32
         L.smc_run_batch.argtypes = [_vp, _vp, _vp, C.c_int32, _vp]
         L.smc_run_batch.restype = C.c_int32
+        L.smc_server_create.argtypes = [C.c_size_t, C.POINTER(ServerCfg), C.POINTER(_vp)]
+        L.smc_server_create.restype = C.c_int32
+        L.smc_server_submit.argtypes = [_vp, _vp, C.POINTER(RunCfg), C.POINTER(Result),
+                                        C.POINTER(C.c_uint64)]
+        L.smc_server_submit.restype = C.c_int32
+        L.smc_server_poll.argtypes = [_vp, C.c_uint64, C.POINTER(C.c_int32)]
+        L.smc_server_poll.restype = C.c_int32
+        L.smc_server_wait.argtypes = [_vp, C.c_uint64, C.c_double, C.POINTER(C.c_double)]
+        L.smc_server_wait.restype = C.c_int32
+        L.smc_server_cancel.argtypes = [_vp, C.c_uint64]
+        L.smc_server_cancel.restype = C.c_int32
+        L.smc_server_stats.argtypes = [_vp, C.POINTER(ServerStats)]
+        L.smc_server_stats.restype = C.c_int32
+        L.smc_server_destroy.argtypes = [_vp]
+        L.smc_server_destroy.restype = None
         L.smc_resample_workspace_bytes.argtypes = [C.c_int64]
         L.smc_resample_workspace_bytes.restype = C.c_size_t
         L.smc_resample.argtypes = [_vp, C.c_int64, C.c_double, _vp, _vp, _vp, _vp, C.c_size_t, _vp]
@@ -307,6 +334,69 @@ def run_batch(models: list, specs: list, precision: str = "fp64", where: str = "
     _check(st)
     return [_result_dict(ress[q].counters.status, ress[q], outs[q], where, record_all_ancestors)
             for q in range(n)]
+
+
+class Server:
+    """Continuous-batching server (smc_server_*): submit requests from any thread;
+    the library's worker admits them into the running waves as memory frees up."""
+
+    def __init__(self, budget_bytes: int, precision: str = "fp64", max_resident_runs: int = 0,
+                 poll_waves: int = 0):
+        cfg = ServerCfg()
+        cfg.precision, cfg.max_resident_runs, cfg.poll_waves = (PRECISIONS[precision],
+                                                                max_resident_runs, poll_waves)
+        h = _vp()
+        _check(lib().smc_server_create(budget_bytes, C.byref(cfg), C.byref(h)))
+        self.handle, self.precision = h, precision
+        self._live = {}
+
+    def submit(self, model: Model, N: int, seed: int, run_id: int = 0, max_segments: int = 0,
+               record_all_ancestors: bool = False, where: str = "host",
+               outputs: dict | None = None) -> int:
+        cfg = _cfg(N, seed, run_id, self.precision, max_segments, record_all_ancestors, None)
+        rows = _rows(model, max_segments, record_all_ancestors)
+        out = _alloc_outputs(model, N, rows, where, outputs)
+        r = _result_struct(out, where, rows)
+        t = C.c_uint64()
+        _check(lib().smc_server_submit(self.handle, model.handle, C.byref(cfg), C.byref(r),
+                                       C.byref(t)))
+        self._live[t.value] = (cfg, r, out, where, record_all_ancestors, model)
+        return t.value
+
+    def poll(self, ticket: int):
+        done = C.c_int32()
+        st = lib().smc_server_poll(self.handle, ticket, C.byref(done))
+        return bool(done.value), st
+
+    def wait(self, ticket: int, timeout: float = 120.0) -> dict:
+        lat = C.c_double()
+        st = lib().smc_server_wait(self.handle, ticket, timeout, C.byref(lat))
+        if st == ETIMEOUT:
+            raise SmcError(st, lib().smc_last_error().decode())
+        cfg, r, out, where, rec, _ = self._live.pop(ticket)
+        res = _result_dict(st, r, out, where, rec)
+        res["latency_s"] = lat.value
+        return res
+
+    def cancel(self, ticket: int):
+        _check(lib().smc_server_cancel(self.handle, ticket))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().smc_server_stats(self.handle, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_ if k != "pad_"}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().smc_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def resample_workspace_bytes(N: int) -> int:

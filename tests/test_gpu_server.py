@@ -1,0 +1,98 @@
+"""Continuous batching (smc_server_*) on the GPU.
+
+Requests submitted while others run are admitted into the running waves; every
+result must be identical to what the same request gives alone through smc_run.
+Failure paths are exercised on the host: cancellation, a bounded wait that runs
+out, a request larger than the memory budget.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(n=16, seed=5):
+    from paper_2112_00364_gb300 import smc
+
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for q in range(n):
+        kind = ["lg", "crbd"][q % 2]
+        if kind == "lg":
+            p = dict(obs=inputs.lg_observations(int(rng.integers(10, 200)), seed=300 + q))
+        else:
+            p = dict(tree=inputs.yule_tree(int(rng.integers(4, 64)), seed=400 + q))
+        reqs.append((smc.Model(kind, **p), int(rng.integers(100, 20000)), 700 + q, q))
+    return reqs
+
+
+def _same(a, b):
+    assert a["run_status"] == b["run_status"]
+    assert a["log_z_value"] == b["log_z_value"]
+    np.testing.assert_array_equal(a["final_logw"], b["final_logw"])
+    np.testing.assert_array_equal(a["int_fields"], b["int_fields"])
+    np.testing.assert_array_equal(a["real_fields"], b["real_fields"])
+    np.testing.assert_array_equal(a["ancestors"], b["ancestors"])
+
+
+@pytest.mark.parametrize("budget_mb,precision", [(4096, "fp64"), (24, "fp64"), (4096, "fp32")])
+def test_server_results_equal_standalone_runs(budget_mb, precision):
+    from paper_2112_00364_gb300 import smc
+
+    reqs = _requests()
+    srv = smc.Server(budget_mb << 20, precision=precision)
+    tickets = []
+    for m, N, seed, rid in reqs:
+        tickets.append(srv.submit(m, N, seed, run_id=rid))
+        time.sleep(0.002)  # arrivals overlap with resident runs
+    got = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["worker_status"] == 0
+    for (m, N, seed, rid), g in zip(reqs, got):
+        a = smc.run(m, N, seed, run_id=rid, precision=precision)
+        _same(g, a)
+        assert g["latency_s"] > 0
+
+
+def test_server_device_outputs_and_record_all():
+    import torch
+    from paper_2112_00364_gb300 import smc
+
+    reqs = _requests(4, seed=9)
+    srv = smc.Server(1 << 30)
+    ts = [srv.submit(m, N, seed, run_id=rid, record_all_ancestors=True, where="device")
+          for m, N, seed, rid in reqs]
+    got = [srv.wait(t) for t in ts]
+    srv.close()
+    torch.cuda.synchronize()
+    for (m, N, seed, rid), g in zip(reqs, got):
+        a = smc.run(m, N, seed, run_id=rid, record_all_ancestors=True)
+        assert float(g["log_z"].cpu()[0]) == a["log_z_value"]
+        np.testing.assert_array_equal(g["ancestors"].cpu().numpy(), a["ancestors"])
+
+
+def test_server_cancel_timeout_and_oversize():
+    from paper_2112_00364_gb300 import smc
+
+    tree = inputs.yule_tree(64, seed=2)
+    m = smc.Model("crbd", tree=tree)
+    srv = smc.Server(64 << 20, max_resident_runs=1)
+    t1 = srv.submit(m, 1 << 16, 1)
+    t2 = srv.submit(m, 1 << 16, 2)  # waits behind t1 (one resident run at most)
+    srv.cancel(t2)
+    with pytest.raises(smc.SmcError) as e:
+        srv.wait(t1, timeout=0.0)
+    assert e.value.status == smc.ETIMEOUT
+    r1 = srv.wait(t1)
+    assert r1["status"] == 0
+    r2 = srv.wait(t2)
+    assert r2["status"] == smc.ECANCELLED
+    with pytest.raises(smc.SmcError) as e:
+        srv.submit(m, 1 << 24, 3)  # workspace larger than the whole budget
+    assert e.value.status == smc.ENOMEM
+    srv.close()
