@@ -14,10 +14,15 @@ its share of resampling.  One benchmark step is one complete piece of work:
                 linear-Gaussian with T log-uniform in 20..500, half CRBD with
                 tips log-uniform in 16..256, N log-uniform in 256..65536),
                 FP32 particles with FP64 reductions; the line also carries the
-                same 512 runs timed one run per launch.
+                same 512 runs timed one run per launch;
+  serve2000     one second of a Poisson request stream (mean 2000 requests/s,
+                request sizes drawn from the batch512 mix) served by the
+                continuous-batching server, from the first submission to the
+                last result on the host; p50/p99 request latency, beside the
+                first requests of the stream served one run per launch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload crbd64|lg|rateshift256|batch512]
+                    [--workload crbd64|lg|rateshift256|batch512|serve2000]
 
 With N > 1 (launched by torch.distributed.run) every rank runs its own
 independent replica with rank-specific seeds (runs exchange no data, so there
@@ -53,6 +58,8 @@ WORKLOADS = {
     "rateshift256": dict(kind="rateshift", tips=256, tree_seed=3, N=1 << 20, precision="fp32",
                          sigma=0.3),
     "batch512": dict(kind="batch", n_runs=512, spec_seed=4, precision="fp32"),
+    "serve2000": dict(kind="serve", n_runs=512, spec_seed=4, precision="fp32", rate=2000.0,
+                      seconds_per_step=1.0, arrival_seed=5),
 }
 
 # FP64 operations the step kernel executes per particle-step (2 x DFMA + DADD +
@@ -141,7 +148,7 @@ class Work:
         w = WORKLOADS[name]
         self.name, self.w, self.precision = name, w, w["precision"]
         self.runs = []
-        if w["kind"] == "batch":
+        if w["kind"] in ("batch", "serve"):
             for q, sp in enumerate(inputs.batch_specs(w["n_runs"], seed=w["spec_seed"])):
                 if sp.kind == "lg":
                     p = dict(obs=inputs.lg_observations(sp.T, seed=sp.obs_seed))
@@ -170,7 +177,12 @@ class Work:
                "l2": "flushed between timed steps (512 MiB write)",
                "parallelism": "replicas (one independent workload per GPU)",
                "particle_steps_per_step": self.units}
-        if w["kind"] == "batch":
+        if w["kind"] == "serve":
+            cfg.update(arrivals=f"Poisson, mean {w['rate']:.0f} requests/s, seed {w['arrival_seed']}+step",
+                       stream_seconds_per_step=w["seconds_per_step"],
+                       mix="request sizes drawn from the batch512 runs (spec seed 4)")
+            cfg.pop("particle_steps_per_step")
+        elif w["kind"] == "batch":
             cfg.update(runs=w["n_runs"], n_particles_total=sum(r["N"] for r in self.runs),
                        mix="half linear-Gaussian (T log-uniform 20..500), half CRBD (tips "
                            "log-uniform 16..256), N log-uniform 256..65536, seeded (spec seed 4)")
@@ -218,7 +230,7 @@ def run_reference(args, work: Work):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    batch = work.w["kind"] == "batch"
+    batch = work.w["kind"] in ("batch", "serve")
     n_sample = None if batch else min(work.runs[0]["N"], 1 << 14)
     max_runs = 32 if batch else 1
     for _ in range(args.warmup):
@@ -250,6 +262,105 @@ def run_reference(args, work: Work):
     return 0
 
 
+def run_serve(args, work: Work, smc, torch, dist, ws: int, rank: int, local: int) -> int:
+    """Serve Poisson request streams through the continuous-batching server."""
+    w = work.w
+    models = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
+    srv = smc.Server(96 << 30, precision=work.precision)
+    pool: dict[int, list] = {}
+
+    def take(q: int) -> dict:
+        lst = pool.setdefault(q, [])
+        if lst:
+            return lst.pop()
+        m, N = models[q], work.runs[q]["N"]
+        o = {"log_z": torch.zeros(1, dtype=torch.float64).pin_memory(),
+             "final_logw": torch.zeros(N, dtype=torch.float64).pin_memory(),
+             "ancestors": torch.zeros((1, N), dtype=torch.int32).pin_memory(),
+             "int_fields": torch.zeros((m.n_int, N), dtype=torch.int32).pin_memory()}
+        if m.n_real:
+            o["real_fields"] = torch.zeros((m.n_real, N), dtype=torch.float64).pin_memory()
+        return o
+
+    def stream_step(step: int, seconds: float):
+        arr = inputs.poisson_arrivals(w["rate"], seconds, seed=w["arrival_seed"] + step)
+        rng = np.random.Generator(np.random.PCG64(1000 + step))
+        picks = rng.integers(0, len(work.runs), len(arr))
+        tickets, used, units, d2h = [], [], 0, 0
+        t0 = time.perf_counter()
+        for a, q in zip(arr, picks):
+            dt = t0 + a - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            r = work.runs[q]
+            o = take(int(q))
+            tickets.append(srv.submit(models[q], r["N"], seed=r["seed"] + 7919 * step,
+                                      run_id=r["run_id"], outputs=o))
+            used.append((int(q), o))
+            units += r["N"] * r["segments"]
+            d2h += sum(t.numel() * t.element_size() for t in o.values())
+        lat = [srv.wait(t, timeout=600.0)["latency_s"] for t in tickets]
+        span = time.perf_counter() - t0
+        for q, o in used:
+            pool.setdefault(q, []).append(o)
+        return units, span, lat, len(arr), d2h
+
+    stream_step(10_000, 0.2)  # warm-up
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    units, span, lats, nreq, d2h = 0, 0.0, [], 0, 0
+    for s in range(args.steps):
+        u, sp, la, n, b = stream_step(s, w["seconds_per_step"])
+        units, span, lats, nreq, d2h = units + u, span + sp, lats + la, nreq + n, d2h + b
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    value = units * ws / span
+    # the first requests of the stream, served one run per launch in arrival order
+    arr = inputs.poisson_arrivals(w["rate"], w["seconds_per_step"], seed=w["arrival_seed"])
+    rng = np.random.Generator(np.random.PCG64(1000))
+    picks = rng.integers(0, len(work.runs), len(arr))
+    n_plain = min(300, len(arr))
+    t_free, p_units, p_lat = 0.0, 0, []
+    for a, q in list(zip(arr, picks))[:n_plain]:
+        r = work.runs[q]
+        t_start = max(t_free, a)
+        c0 = time.perf_counter()
+        smc.run(models[q], r["N"], seed=r["seed"], run_id=r["run_id"], precision=work.precision,
+                outputs=take(int(q)))
+        t_free = t_start + (time.perf_counter() - c0)
+        p_lat.append(t_free - a)
+        p_units += r["N"] * r["segments"]
+    plain = {"value": p_units / t_free, "unit": UNIT,
+             "latency_ms": {"p50": 1e3 * float(np.percentile(p_lat, 50)),
+                            "p99": 1e3 * float(np.percentile(p_lat, 99))},
+             "what": f"the first {n_plain} requests of the stream, smc_run one after another in "
+                     f"arrival order"}
+    cpu = None
+    if ws == 1:
+        v, runs, secs, _ = oracle_throughput(work, 1e9, 32)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the first {runs} of the 512 request sizes, run one after another "
+                         f"({secs:.1f} s single-threaded)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": 1, "ms_per_step": 1e3 * span / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": work.config(), "requests": nreq,
+        "latency_ms": {"p50": 1e3 * float(np.percentile(lats, 50)),
+                       "p99": 1e3 * float(np.percentile(lats, 99))},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": int(st["waves"]), "server": st, "roofline": None, "cpu_baseline": cpu,
+        "clocks": clk, "plain_one_run_per_launch": plain,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -277,6 +388,8 @@ def main() -> int:
         dist = None
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
+    if work.w["kind"] == "serve":
+        return run_serve(args, work, smc, torch, dist, ws, rank, local)
     stream = torch.cuda.Stream()
     batch = work.w["kind"] == "batch"
     models = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
@@ -426,8 +539,10 @@ def main() -> int:
             sample = (f"the first {runs} of the 512 runs of the batch, run one after another "
                       f"({secs:.1f} s single-threaded)")
         else:
-            v, runs, secs, _ = oracle_throughput(work, args.cpu_seconds, 50)
-            sample = (f"{runs} full oracle runs of the workload (seeds from {work.runs[0]['seed']}), "
+            n_s = min(work.runs[0]["N"], 1 << 16)
+            v, runs, secs, _ = oracle_throughput(work, args.cpu_seconds, 50, n_particles=n_s)
+            sample = (f"{runs} oracle runs of the workload with N={n_s} particles "
+                      f"(of {work.runs[0]['N']}), seeds from {work.runs[0]['seed']}, "
                       f"{secs:.1f} s single-threaded")
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     lat = sorted(step_ms)
