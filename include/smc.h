@@ -254,12 +254,14 @@ void smc_server_destroy(smc_server_t s);
 size_t smc_resample_workspace_bytes(int64_t N);
 
 /* Systematic resampling of one population (Section 3.3, parallel systematic
- * resampling): m = max logw, S = sum exp(logw - m), P_j = running sum,
- * ancestors[i] = min{ j : P_j * (N / S) > i + u } (N - 1 if none).
- * logw [N] f64 in, ancestors [N] int32 out, out3 [3] f64 out = {m, S, m + (log S - log N)},
- * n_near [1] int64 out (offsets within 1e-12 N of a boundary).  u in (0,1).
- * Errors: SMC_EINVAL (N < 1, u outside (0,1), NULL pointer, workspace too small),
- * SMC_ECUDA.  An all -inf population gives ancestors = identity and out3 = {-inf, 0, -inf}. */
+ * resampling): with the power-of-two reference m = k ln 2, k = ceil(max logw / ln 2),
+ * S = sum exp(logw - m) and P_j the running sum, ancestors[i] = min{ j : P_j (N / S)
+ * > i + u } (N - 1 if none); the log-Z increment is m + (log S - log N).  All sums
+ * are FP64.  logw [N] f64 in (16-byte aligned), ancestors [N] int32 out, out3 [3]
+ * f64 out = {m, S, m + (log S - log N)}, n_near [1] int64 out (offsets within
+ * 1e-12 N of a boundary).  u in (0,1).  Errors: SMC_EINVAL (N < 1, u outside (0,1),
+ * NULL pointer, workspace too small), SMC_ECUDA.  An all -inf population gives
+ * ancestors = identity and out3 = {-inf, 0, -inf}. */
 smc_status smc_resample(const double *logw, int64_t N, double u, int32_t *ancestors,
                         double *out3, int64_t *n_near, void *workspace, size_t workspace_bytes,
                         void *stream);

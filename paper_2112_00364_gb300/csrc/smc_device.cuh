@@ -23,6 +23,19 @@ constexpr float kLn2f = 0.693147182f;
 constexpr double kTwoPi = 6.28318530717958647692;
 constexpr float kTwoPif = 6.28318548f;
 constexpr double kBoundaryEps = 1e-12;
+constexpr double kInvLn2 = 1.44269504088896340736;
+constexpr int kDeadTile = -2147483647 - 1;  // tile whose weights are all zero
+
+// Exact 2^n for n in [-1022, 1023] assembled from bits; 0 below.
+__device__ __forceinline__ double pow2i(int n) {
+  if (n < -1022) return 0.0;
+  return __longlong_as_double((long long)(n + 1023) << 52);
+}
+
+// Power-of-two reference of a tile: k = ceil(M / ln 2) (M finite), so that the
+// tile's weights exp(logw - k ln 2) are at most ~1 and tiles are rescaled by the
+// exact factors 2^(k_t - k_max) instead of exponentials.
+__device__ __forceinline__ int tile_exponent(double M) { return (int)ceil(M * kInvLn2); }
 
 struct Block4 {
   uint32_t w0, w1, w2, w3;
@@ -270,6 +283,20 @@ __device__ __forceinline__ double block_incl_scan(double v, double* sh) {
   }
   __syncthreads();
   return wid > 0 ? sh[wid] + v : v;
+}
+
+// Block max of an int over TPB threads; every thread gets the result.
+template <int TPB>
+__device__ __forceinline__ int block_max_int(int v, int* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = __reduce_max_sync(0xffffffffu, v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  int r = sh[0];
+#pragma unroll
+  for (int w = 1; w < TPB / 32; ++w) r = max(r, sh[w]);
+  return r;
 }
 
 // Block inclusive prefix max over TPB threads.  `sh` >= TPB/32 doubles.

@@ -13,12 +13,15 @@
 //             stack pointer;
 //   segment   blocks run until the next checkpoint with per-warp PC-sorted
 //             dispatch (smc_models.cuh); draws from Philox counters;
-//   epilogue  the tile's FP64 max M_t, e_j = exp(logw_j - M_t), its inclusive
-//             scan E_j (kept for the next segment's search) and total s_t; the
-//             run's last CTA to finish combines the run's tiles: m = max M_t,
-//             c_t = exp(M_t - m), monotone exclusive offsets O_t of c_t s_t,
-//             S = total, log Z += m + (log S - log N), the resampling uniform u_k
-//             and r = N / S.
+//   epilogue  the tile's FP64 max M_t and its power-of-two reference
+//             k_t = ceil(M_t / ln 2); weights e_j = exp(logw_j - k_t ln 2) (FP64;
+//             in FP32 mode the difference is formed in FP64 and its exponential
+//             in FP32), their FP64 inclusive scan E_j (kept for the next segment's
+//             search) and total s_t; the run's last CTA to finish combines the
+//             run's tiles: k = max k_t, c_t = 2^(k_t - k) (exact, no exponential),
+//             monotone exclusive offsets O_t of c_t s_t, S = total,
+//             log Z += k ln 2 + (log S - log N), the resampling uniform u_k and
+//             r = N / S.
 // The running sum the next search uses is P_j = min(O_t + c_t E_j, O_{t+1}) and
 // its scaled boundary q_j = P_j r.  A run stops after the segment in which every
 // particle reached b_stop (no resampling after it); its later CTAs return at once.
@@ -65,7 +68,8 @@ __device__ __forceinline__ double q_at(int j, const RunDev& A, const double* __r
 // inside the tile the threshold e* = (y / r - O_t) / c_t on E locates the
 // candidate, and the exact q_j then fixes it up if rounding moved it.  If no
 // element of tile t qualifies, the first element of tile t+1 does.  Flags the
-// offset when it lies within 1e-12 N of q_a or q_{a-1}.
+// offset when it lies within 1e-12 N of q_a or q_{a-1}; the boundaries the
+// fix-up formed are reused for the flag.
 __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const double* E, double r,
                                                  double inv_r, double u, bool* near) {
   const int N = A.N, T = A.n_tiles;
@@ -80,8 +84,11 @@ __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const d
       hi = mid - 1;
   }
   int a;
+  double qa, qa1;  // q_a and q_{a-1} (unused when a = 0)
   if (lo >= T) {
     a = N - 1;
+    qa = q_at(a, A, E, r);
+    qa1 = a > 0 ? q_at(a - 1, A, E, r) : 0.0;
   } else {
     const int t = lo;
     const int j0 = t * A.tile, j1 = min(N, j0 + A.tile);
@@ -95,14 +102,29 @@ __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const d
         l = mid + 1;
     }
     int j = l;
-    while (j < j1 && dbits(q_at(j, A, E, r)) <= yb) ++j;
-    while (j > j0 && dbits(q_at(j - 1, A, E, r)) > yb) --j;
-    a = j < j1 ? j : (j1 < N ? j1 : N - 1);
+    double q_hi = j < j1 ? q_at(j, A, E, r) : INFINITY;  // q_j
+    while (j < j1 && dbits(q_hi) <= yb) {
+      ++j;
+      q_hi = j < j1 ? q_at(j, A, E, r) : INFINITY;
+    }
+    double q_lo = j > j0 ? q_at(j - 1, A, E, r) : -1.0;  // q_{j-1}; -1 below every offset
+    while (j > j0 && dbits(q_lo) > yb) {
+      --j;
+      q_hi = q_lo;
+      q_lo = j > j0 ? q_at(j - 1, A, E, r) : -1.0;
+    }
+    if (j < j1) {
+      a = j;
+      qa = q_hi;
+      qa1 = j > j0 ? q_lo : (a > 0 ? q_at(a - 1, A, E, r) : 0.0);
+    } else {
+      a = j1 < N ? j1 : N - 1;
+      qa = q_at(a, A, E, r);
+      qa1 = a > 0 ? q_at(a - 1, A, E, r) : 0.0;
+    }
   }
   const double tol = kBoundaryEps * (double)N;
-  bool f = fabs(q_at(a, A, E, r) - y) < tol;
-  if (a > 0 && fabs(q_at(a - 1, A, E, r) - y) < tol) f = true;
-  *near = f;
+  *near = fabs(qa - y) < tol || (a > 0 && fabs(qa1 - y) < tol);
   return a;
 }
 
@@ -113,18 +135,18 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
   RunState* rs = A.rs;
   const int nt = A.n_tiles;
   double* shx = sh + TPB / 32 + 1;
-  double mloc = -INFINITY;
+  int kloc = kDeadTile;
   int alive = 0;
   for (int t = threadIdx.x; t < nt; t += TPB) {
-    mloc = fmax(mloc, __ldcg(A.tile_M + t));
+    kloc = max(kloc, __ldcg(A.tile_k + t));
     alive |= __ldcg(A.tile_alive + t);
   }
-  const double m = block_max<TPB>(mloc, sh);
+  const int kmax = block_max_int<TPB>(kloc, reinterpret_cast<int*>(sh));
   alive = __syncthreads_or(alive);
-  if (m == -INFINITY) {
+  if (kmax == kDeadTile) {
     if (threadIdx.x == 0) {
       rs->log_z = -INFINITY;
-      rs->m = m;
+      rs->m = -INFINITY;
       rs->S = 0.0;
       A.incr[k] = -INFINITY;
       rs->status = SMC_EDEGENERATE;
@@ -138,11 +160,14 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
   double carry = 0.0, omax = 0.0;
   for (int base = 0; base < nt; base += TPB) {
     const int t = base + threadIdx.x;
-    double c = 0.0, v = 0.0;
+    double c = 0.0, invc = 0.0, v = 0.0;
     if (t < nt) {
-      const double Mt = __ldcg(A.tile_M + t);
-      c = (Mt == -INFINITY) ? 0.0 : exp(Mt - m);
-      v = __ldcg(A.tile_s + t) * c;
+      const int kt = __ldcg(A.tile_k + t);
+      if (kt != kDeadTile && kt - kmax >= -1022) {
+        c = pow2i(kt - kmax);
+        invc = pow2i(kmax - kt);
+      }
+      v = __ldcg(A.tile_s + t) * c;  // exact: c is a power of two
     }
     const double incl = block_incl_scan<TPB>(v, sh);
     __syncthreads();
@@ -153,7 +178,7 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
     const double O = block_incl_max<TPB>(fmax(carry + excl, omax), sh);
     if (t < nt) {
       A.tile_c[t] = c;
-      A.tile_invc[t] = c > 0.0 ? 1.0 / c : 0.0;
+      A.tile_invc[t] = invc;
       A.tile_O[t] = O;
     }
     __syncthreads();
@@ -169,6 +194,7 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
   __syncthreads();
   for (int t = threadIdx.x; t <= nt; t += TPB) A.tile_q[t] = A.tile_O[t] * r;
   if (threadIdx.x == 0) {
+    const double m = (double)kmax * kLn2;
     const double inc = m + (log(S) - log((double)A.N));
     rs->log_z = rs->log_z + inc;
     A.incr[k] = inc;
@@ -194,6 +220,7 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
 template <class M, int TPB>
 __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const int k, double* sh,
                                           int* sh_last) {
+  using R = typename M::R;
   RunState* rs = A.rs;
   const int N = A.N;
   const int i = t * A.tile + threadIdx.x;
@@ -228,14 +255,27 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   }
   warp_add_u64(&rs->n_overflow, active ? (unsigned long long)L.overflow : 0ull);
   warp_add_u64(&rs->n_limit, active ? (unsigned long long)L.limited : 0ull);
-  // tile reduction (FP64)
+  // tile reduction: FP64 max, power-of-two reference, weights, FP64 scan
   const double Mt = block_max<TPB>(lw, sh);
-  const double e = (valid && Mt != -INFINITY) ? exp(lw - Mt) : 0.0;
+  if (threadIdx.x == 0) {
+    const int kt = Mt == -INFINITY ? kDeadTile : tile_exponent(Mt);
+    *sh_last = kt;
+  }
+  __syncthreads();
+  const int kt = *sh_last;
+  double e = 0.0;
+  if (valid && kt != kDeadTile) {
+    const double d = lw - (double)kt * kLn2;
+    if constexpr (sizeof(R) == 4)
+      e = (double)expf((float)d);  // FP32 log-weights: FP32 exponential of an FP64 difference
+    else
+      e = exp(d);
+  }
   const double E = block_incl_scan<TPB>(e, sh);
   if (valid) A.E[nb][i] = E;
   alive = __syncthreads_or(alive);
   if (threadIdx.x == TPB - 1) {
-    A.tile_M[t] = Mt;
+    A.tile_k[t] = kt;
     A.tile_s[t] = E;
   }
   if (threadIdx.x == 0) A.tile_alive[t] = alive;
@@ -374,7 +414,7 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
     A.E[b] = (double*)(ws + Ly.E[b]);
   }
   A.logw = (double*)(ws + Ly.logw);
-  A.tile_M = (double*)(ws + Ly.tM);
+  A.tile_k = (int32_t*)(ws + Ly.tM);
   A.tile_s = (double*)(ws + Ly.ts);
   A.tile_alive = (int32_t*)(ws + Ly.talive);
   A.tile_c = (double*)(ws + Ly.tc);

@@ -31,11 +31,11 @@ struct RunDev {
   StateView state[2];
   double* logw;       // [N] log-weights of the latest segment (f64; FP32 values widened)
   double* E[2];       // [N] tile-local inclusive scans, double-buffered by segment parity
-  double* tile_M;     // [n_tiles]
+  int32_t* tile_k;    // [n_tiles] power-of-two reference exponent k_t (kDeadTile: all zero)
   double* tile_s;     // [n_tiles]
   int32_t* tile_alive;
-  double* tile_c;     // [n_tiles] written by the combine: exp(M_t - m)
-  double* tile_invc;  // [n_tiles] 1 / c_t (0 where c_t = 0)
+  double* tile_c;     // [n_tiles] written by the combine: 2^(k_t - k_max) (exact)
+  double* tile_invc;  // [n_tiles] 2^(k_max - k_t) (0 where c_t = 0)
   double* tile_O;     // [n_tiles + 1] monotone exclusive offsets, O_T >= S
   double* tile_q;     // [n_tiles + 1] O_t * r
   int32_t* anc;       // ancestor rows

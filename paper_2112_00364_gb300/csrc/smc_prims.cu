@@ -3,10 +3,12 @@
 // parity hooks, and the library's error plumbing.
 //
 // smc_resample (parallel systematic resampling, three launches):
-//   1. rs_tile_reduce: per tile of TPB*IT weights, M_t = max, s_t = sum exp(x - M_t)
-//   2. rs_combine (one CTA): m = max M_t, c_t = exp(M_t - m), O_t = exclusive
-//      prefix of c_t s_t (O_{T} = S), out3 = {m, S, m + (log S - log N)}, r = N / S
-//   3. rs_ancestors: per tile, E_j = inclusive scan of exp(x_j - M_t),
+//   1. rs_tile_reduce: per tile of TPB*IT weights, M_t = max, its power-of-two
+//      reference k_t = ceil(M_t / ln 2) and s_t = sum exp(x - k_t ln 2)
+//   2. rs_combine (one CTA): k = max k_t, c_t = 2^(k_t - k) (exact), O_t =
+//      exclusive prefix of c_t s_t (O_{T} = S), out3 = {k ln 2, S,
+//      k ln 2 + (log S - log N)}, r = N / S; no exponential per tile
+//   3. rs_ancestors: per tile, E_j = inclusive scan of exp(x_j - k_t ln 2),
 //      q_j = (O_t + c_t E_j) r clamped to the tile's [O_t r, O_{t+1} r); element
 //      j owns the offsets i with q_{j-1} <= i + u < q_j and writes a_i = j for
 //      them (the last element owns everything above), so every i is written
@@ -56,7 +58,7 @@ __device__ __forceinline__ void load_tile(const double* __restrict__ x, int64_t 
 }
 
 __global__ void __launch_bounds__(RS_TPB) rs_tile_reduce(const double* __restrict__ x, int64_t N,
-                                                         double* __restrict__ tM,
+                                                         int32_t* __restrict__ tk,
                                                          double* __restrict__ ts) {
   __shared__ double sh[RS_TPB / 32 + 1];
   double v[RS_IT];
@@ -65,29 +67,31 @@ __global__ void __launch_bounds__(RS_TPB) rs_tile_reduce(const double* __restric
 #pragma unroll
   for (int q = 0; q < RS_IT; ++q) mx = fmax(mx, v[q]);
   const double Mt = block_max<RS_TPB>(mx, sh);
+  const int kt = Mt == -INFINITY ? kDeadTile : tile_exponent(Mt);
   double s = 0.0;
-  if (Mt != -INFINITY) {
+  if (kt != kDeadTile) {
+    const double R = (double)kt * kLn2;
 #pragma unroll
-    for (int q = 0; q < RS_IT; ++q) s = s + exp(v[q] - Mt);
+    for (int q = 0; q < RS_IT; ++q) s = s + exp(v[q] - R);
   }
   const double tot = block_incl_scan<RS_TPB>(s, sh);
   if (threadIdx.x == RS_TPB - 1) {
-    tM[blockIdx.x] = Mt;
+    tk[blockIdx.x] = kt;
     ts[blockIdx.x] = tot;
   }
 }
 
 // Single CTA: combine nt tile results.  tO has nt + 1 entries (tO[nt] = S).
-__global__ void __launch_bounds__(RS_TPB) rs_combine(const double* __restrict__ tM,
+__global__ void __launch_bounds__(RS_TPB) rs_combine(const int32_t* __restrict__ tk,
                                                      const double* __restrict__ ts, int nt,
                                                      int64_t N, double* __restrict__ tc,
                                                      double* __restrict__ tO, double* out3,
                                                      double* r_out) {
   __shared__ double sh[RS_TPB / 32 + 2 + RS_TPB];
-  double mloc = -INFINITY;
-  for (int t = threadIdx.x; t < nt; t += RS_TPB) mloc = fmax(mloc, tM[t]);
-  const double m = block_max<RS_TPB>(mloc, sh);
-  if (m == -INFINITY) {
+  int kloc = kDeadTile;
+  for (int t = threadIdx.x; t < nt; t += RS_TPB) kloc = max(kloc, tk[t]);
+  const int kmax = block_max_int<RS_TPB>(kloc, reinterpret_cast<int*>(sh));
+  if (kmax == kDeadTile) {
     if (threadIdx.x == 0) {
       out3[0] = -INFINITY;
       out3[1] = 0.0;
@@ -101,9 +105,9 @@ __global__ void __launch_bounds__(RS_TPB) rs_combine(const double* __restrict__ 
     const int t = base + threadIdx.x;
     double c = 0.0, v = 0.0;
     if (t < nt) {
-      const double Mt = tM[t];
-      c = (Mt == -INFINITY) ? 0.0 : exp(Mt - m);
-      v = ts[t] * c;
+      const int kt = tk[t];
+      c = (kt == kDeadTile) ? 0.0 : pow2i(kt - kmax);
+      v = ts[t] * c;  // exact: c is a power of two
     }
     const double incl = block_incl_scan<RS_TPB>(v, sh);
     __syncthreads();
@@ -117,6 +121,7 @@ __global__ void __launch_bounds__(RS_TPB) rs_combine(const double* __restrict__ 
     carry = carry + sh[RS_TPB / 32 + RS_TPB];
   }
   if (threadIdx.x == 0) {
+    const double m = (double)kmax * kLn2;
     tO[nt] = carry;
     out3[0] = m;
     out3[1] = carry;
@@ -137,7 +142,7 @@ __device__ __forceinline__ int64_t first_at_or_above(double bound, double u, int
 }
 
 __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
-    const double* __restrict__ x, int64_t N, double u, const double* __restrict__ tM,
+    const double* __restrict__ x, int64_t N, double u, const int32_t* __restrict__ tk,
     const double* __restrict__ tc, const double* __restrict__ tO, const double* __restrict__ out3,
     const double* __restrict__ r_p, int32_t* __restrict__ anc, unsigned long long* n_near) {
   __shared__ double sh[RS_TPB / 32 + 1];
@@ -152,12 +157,14 @@ __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
   }
   double v[RS_IT];
   load_tile(x, N, base, v);
-  const double Mt = tM[t], c = tc[t], O = tO[t], r = *r_p;
+  const int kt = tk[t];
+  const double c = tc[t], O = tO[t], r = *r_p;
+  const double R = kt == kDeadTile ? 0.0 : (double)kt * kLn2;
   const double lo_tile = O * r, hi_tile = tO[t + 1] * r;
   double loc = 0.0;
 #pragma unroll
   for (int q = 0; q < RS_IT; ++q) {
-    const double e = (Mt == -INFINITY) ? 0.0 : exp(v[q] - Mt);
+    const double e = (kt == kDeadTile) ? 0.0 : exp(v[q] - R);
     loc = loc + e;
     v[q] = loc;  // thread-local inclusive prefix
   }
@@ -298,7 +305,7 @@ extern "C" smc_status smc_resample(const double* logw, int64_t N, double u, int3
   cudaStream_t cs = (cudaStream_t)stream;
   const int nt = (int)((N + RS_TILE - 1) / RS_TILE);
   char* w = (char*)workspace;
-  double* tM = (double*)w;
+  int32_t* tM = (int32_t*)w;
   double* ts = (double*)(w + align_up(8 * (size_t)nt, 256));
   double* tc = (double*)(w + 2 * align_up(8 * (size_t)nt, 256));
   double* tO = (double*)(w + 3 * align_up(8 * (size_t)nt, 256));
@@ -368,7 +375,7 @@ extern "C" smc_status smc_resample_static(const double* logw, int64_t N, double 
   if (st) return st;
   cudaStream_t cs = (cudaStream_t)stream;
   const int nt = (int)((N + RS_TILE - 1) / RS_TILE);
-  double* tM = base;
+  int32_t* tM = reinterpret_cast<int32_t*>(base);
   double* ts = base + kStaticTiles;
   double* tc = base + 2 * kStaticTiles;
   double* tO = base + 3 * kStaticTiles;            // nt + 1 entries
