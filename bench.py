@@ -66,7 +66,8 @@ WORKLOADS = {
 # DMUL) and its DRAM traffic per launch, from one ncu capture of the workload
 # (profiles folder); the traffic holds only for the kernel sources with the
 # recorded digest.
-NCU = {"crbd64": dict(fp64_flop_per_pstep=None, bytes_per_launch=None, src_digest=None)}
+NCU = {"crbd64": dict(fp64_flop_per_pstep=160.0, bytes_per_launch=2.70e6,
+                     src_digest="9fbf1c76f21ae126")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
