@@ -444,14 +444,21 @@ def main() -> int:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = device_step(s, True)
+        res = device_step(s, False)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        kern_ms += sum(r["kernel_ms"] for r in res)
-        kern_launches += res[0]["kernel_launches"]
         statuses.update(r["status"] for r in res)
         logz.append(float(outs[0]["log_z"].cpu()[0]))
+    # Launch durations of the segment kernel: the same steps again with a CUDA
+    # event pair around every launch (an event between launches costs ~3 us of
+    # its own, so these steps are kept out of the value above).
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        res = device_step(s, True)
+        kern_ms += sum(r["kernel_ms"] for r in res)
+        kern_launches += res[0]["kernel_launches"]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

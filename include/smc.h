@@ -307,6 +307,12 @@ smc_status smc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, i
 smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uint64_t seed,
                       uint32_t run_id, int64_t n, double *out, int32_t *blocks, void *stream);
 
+/* Device math parity hook: y[i] = f(x[i]) on the GPU for fn 0 = the table-driven
+ * FP64 logarithm the samplers use, 1 = the table-driven FP64 exponential, 2 = the
+ * CUDA library log, 3 = the CUDA library exp.  x, y [n] f64 device pointers.
+ * Errors: SMC_EINVAL, SMC_ECUDA. */
+smc_status smc_math_eval(int32_t fn, const double *x, double *y, int64_t n, void *stream);
+
 /* Thread-local description of the calling thread's last error ("" if none). */
 const char *smc_last_error(void);
 

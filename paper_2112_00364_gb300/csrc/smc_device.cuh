@@ -72,9 +72,87 @@ __host__ __device__ __forceinline__ Block4 philox(uint32_t c0, uint32_t c1, uint
   return Block4{c0, c1, c2, c3};
 }
 
-// A particle's draw stream for one segment: counter (n, k, d, tag), d counts blocks.
+// ---- table-driven FP64 logarithm and exponential ----
+// GB300 executes FP64 at 2 DFMA/clk/SM with ~64 cycles of dependent latency, so
+// the length of a dependency chain, not its op count alone, decides how long a
+// straggling particle takes.  These follow Tang's table-driven method (ACM TOMS
+// 15(2) 1989 for exp, 16(4) 1990 for log): reduce the argument with a small
+// table so that a short Taylor polynomial, evaluated in Estrin form, finishes
+// the job in ~8 dependent operations.  Both are within ~2 ulp of the correctly
+// rounded result; special and extreme arguments go to the library functions.
+struct MathTab {
+  double log_f[192];    // log(j/128), j = 90..181 used
+  double inv_f[192];    // 128 / j, j = 90..181 used
+  double exp2_j[32];    // 2^(j/32)
+  double inv_int[256];  // 1 / k (entry 0 unused)
+};
+
+constexpr double kLn2Hi = 0x1.62e42fefa3800p-1;   // ln 2 to 42 bits: e * kLn2Hi exact, |e| < 2^11
+constexpr double kLn2Lo = 0x1.ef35793c76730p-45;  // ln 2 - kLn2Hi
+constexpr double kLn2by32Hi = 0x1.62e42fefa0000p-6;   // ln 2 / 32 to 37 bits
+constexpr double kLn2by32Lo = 0x1.cf79abc9e3b3ap-45;  // ln 2 / 32 - kLn2by32Hi
+constexpr double kInvLn2x32 = 0x1.71547652b82fep+5;   // 32 / ln 2
+
+// log x = e ln 2 + log F + log1p(u) with x = 2^e m, m in [sqrt(2)/2, sqrt(2))
+// (so that e = 0 around 1), F = j/128 the table point nearest to m (j = 91..181,
+// so F = 1 near 1 and log F and log1p(u) never cancel by more than a bit),
+// u = (m - F) / F in (-1/180, 1/180); log1p(u) = u - u^2 q(u) with the Taylor
+// series of q to degree 6 (truncation < 1e-18 relative).
+__device__ __forceinline__ double tang_log(double x, const MathTab* __restrict__ T) {
+  if (!(x >= 0x1p-1022 && x < INFINITY)) return log(x);
+  const long long b = __double_as_longlong(x);
+  int e = (int)(b >> 52) - 1023;
+  double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+  if (m >= 1.4142135623730951) {
+    m = 0.5 * m;  // exact
+    e += 1;
+  }
+  const int j = (int)(m * 128.0 + 0.5);     // nearest table point (both steps exact)
+  const double F = (double)j * 0x1p-7;      // exact
+  const double u = (m - F) * __ldg(&T->inv_f[j]);  // m - F is exact
+  const double u2 = u * u;
+  const double u4 = u2 * u2;
+  const double qa = fma(u, -1.0 / 3.0, 0.5);
+  const double qb = fma(u, -0.2, 0.25);
+  const double qc = fma(u, -1.0 / 7.0, 1.0 / 6.0);
+  const double q = fma(fma(u2, 0.125, qc), u4, fma(qb, u2, qa));
+  const double p = fma(-u2, q, u);
+  const double de = (double)e;
+  const double hi = fma(de, kLn2Hi, __ldg(&T->log_f[j]));
+  return hi + fma(de, kLn2Lo, p);
+}
+
+// exp x = 2^k 2^(j/32) e^r with n = 32 k + j = round(32 x / ln 2) and
+// |r| <= ln 2 / 64; e^r - 1 = r + r^2 (1/2 + r/6 + r^2/24 + r^3/120 + r^4/720).
+__device__ __forceinline__ double tang_exp(double x, const MathTab* __restrict__ T) {
+  if (!(x > -708.0 && x < 709.0)) return exp(x);
+  const double shift = 0x1.8p52;  // adding it leaves round(32 x / ln 2) in the low bits
+  const double t = fma(x, kInvLn2x32, shift);
+  const int n = (int)(unsigned)__double2loint(t);
+  const double nd = t - shift;
+  double r = fma(-nd, kLn2by32Hi, x);
+  r = fma(-nd, kLn2by32Lo, r);
+  const double r2 = r * r;
+  const double pa = fma(r, 1.0 / 6.0, 0.5);
+  const double pb = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  const double pq = fma(fma(r2, 1.0 / 720.0, pb), r2, pa);
+  const double p = fma(r2, pq, r);
+  const double s = __ldg(&T->exp2_j[n & 31]);
+  return fma(s, p, s) * pow2i(n >> 5);
+}
+
+// x / y from a precomputed y_inv ~ 1/y: one residual correction of x * y_inv
+// (within an ulp of the correctly rounded quotient).
+__device__ __forceinline__ double div_by(double x, double y, double y_inv) {
+  const double q = x * y_inv;
+  return fma(fma(-q, y, x), y_inv, q);
+}
+
+// A particle's draw stream for one segment: counter (n, k, d, tag), d counts
+// blocks; `tab` is the device's math table.
 struct Stream {
   uint32_t k0, k1, n, k, d, tag;
+  const MathTab* tab;
   __device__ __forceinline__ Block4 next() {
     Block4 b = philox(n, k, d, tag, k0, k1);
     d += 1;
@@ -131,6 +209,13 @@ __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_fabs(double x) { return fabs(x); }
 __device__ __forceinline__ float m_fabs(float x) { return fabsf(x); }
 
+// Logarithm / exponential used by the samplers: FP64 through the tables,
+// FP32 through the IEEE single-precision library.
+__device__ __forceinline__ double lg(double x, const Stream& s) { return tang_log(x, s.tab); }
+__device__ __forceinline__ float lg(float x, const Stream&) { return logf(x); }
+__device__ __forceinline__ double ex(double x, const Stream& s) { return tang_exp(x, s.tab); }
+__device__ __forceinline__ float ex(float x, const Stream&) { return expf(x); }
+
 template <typename R>
 struct C;
 template <>
@@ -159,7 +244,7 @@ __device__ __forceinline__ R normal01(Stream& s) {
   const Block4 b = s.next();
   const R u1 = Unif<R>::first(b);
   const R u2 = Unif<R>::second(b);
-  const R rad = m_sqrt((R)-2.0 * m_log(u1));
+  const R rad = m_sqrt((R)-2.0 * lg(u1, s));
   return rad * m_cos(C<R>::two_pi * u2);
 }
 
@@ -167,14 +252,24 @@ __device__ __forceinline__ R normal01(Stream& s) {
 template <typename R>
 __device__ __forceinline__ R exponential(Stream& s, R rate) {
   const R u = uniform01<R>(s);
-  return -m_log(u) / rate;
+  return -lg(u, s) / rate;
+}
+
+// Exponential(rate) with a precomputed 1/rate (rate > 0)
+__device__ __forceinline__ double exponential_inv(Stream& s, double rate, double inv_rate) {
+  const double u = uniform01<double>(s);
+  return div_by(-lg(u, s), rate, inv_rate);
+}
+__device__ __forceinline__ float exponential_inv(Stream& s, float rate, float) {
+  const float u = uniform01<float>(s);
+  return -logf(u) / rate;
 }
 
 // Gamma(shape 1, scale theta): theta * (-ln u)
 template <typename R>
 __device__ __forceinline__ R gamma1(Stream& s, R theta) {
   const R u = uniform01<R>(s);
-  return theta * -m_log(u);
+  return theta * -lg(u, s);
 }
 
 // Uniform(lo, hi): fma(hi - lo, u, lo)
@@ -197,11 +292,14 @@ __device__ __noinline__ int poisson(Stream& s, R mean) {
   if (mean < (R)10.0) {
     const R u = uniform01<R>(s);
     int k = 0;
-    R p = m_exp(-mean);
+    R p = ex(-mean, s);
     R acc = p;
     while (u > acc && k < 200) {
       k += 1;
-      p = p * mean / (R)k;
+      if constexpr (sizeof(R) == 8)
+        p = div_by(p * mean, (double)k, __ldg(&s.tab->inv_int[k]));
+      else
+        p = p * mean / (R)k;
       acc = acc + p;
     }
     return k;
@@ -230,7 +328,7 @@ __device__ __noinline__ int poisson(Stream& s, R mean) {
 // LogNormal(0, sigma) = exp(sigma * N(0,1))
 template <typename R>
 __device__ __forceinline__ R lognormal(Stream& s, R sigma) {
-  return m_exp(sigma * normal01<R>(s));
+  return ex(sigma * normal01<R>(s), s);
 }
 
 // ---- FP64 warp / block primitives (deterministic association order) ----

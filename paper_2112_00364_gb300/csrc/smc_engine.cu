@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -188,28 +189,34 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
     carry = carry + chunk_total;
     __syncthreads();
   }
+  // The independent scalar work of the tail runs on different warps at once:
+  // every thread forms r = N / S for the tile boundaries, thread 0 the log-Z
+  // increment (table logarithm), a thread of warp 1 the next resampling uniform.
   const double S = carry;
-  const double r = (double)A.N / S;
+  const double r = (double)A.N * (1.0 / S);
+  const bool go_on = alive && k + 1 < A.max_segments;
   if (threadIdx.x == 0) A.tile_O[nt] = fmax(S, omax);
   __syncthreads();
   for (int t = threadIdx.x; t <= nt; t += TPB) A.tile_q[t] = A.tile_O[t] * r;
+  if (threadIdx.x == (TPB > 32 ? 32 : 0) && go_on) {
+    const Block4 b = philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1);
+    rs->u = Unif<double>::first(b);
+  }
   if (threadIdx.x == 0) {
     const double m = (double)kmax * kLn2;
-    const double inc = m + (log(S) - log((double)A.N));
+    const double inc = m + (tang_log(S, A.md.tab) - A.log_n);
     rs->log_z = rs->log_z + inc;
     A.incr[k] = inc;
     rs->m = m;
     rs->S = S;
     if (!alive) {
       rs->done = 1;
-    } else if (k + 1 >= A.max_segments) {
+    } else if (!go_on) {
       rs->status = SMC_ESTEPLIMIT;
       rs->done = 1;
     } else {
-      const Block4 b = philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1);
-      rs->u = Unif<double>::first(b);
       rs->r = r;
-      rs->inv_r = S / (double)A.N;
+      rs->inv_r = S * A.inv_n;
     }
     rs->n_segments = k + 1;
     rs->arrive = 0;
@@ -242,7 +249,7 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
     }
   }
   if (k > 0) warp_add_u64(&rs->n_near, near ? 1ull : 0ull);
-  Stream s{A.k0, A.k1, (uint32_t)i, (uint32_t)k, 0u, 0u};
+  Stream s{A.k0, A.k1, (uint32_t)i, (uint32_t)k, 0u, 0u, A.md.tab};
   const bool active = valid && L.pc != PC_STOP;
   run_segment<M>(L, s, A.md, Sn, i, k, N, active);
   double lw = -INFINITY;
@@ -269,7 +276,7 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
     if constexpr (sizeof(R) == 4)
       e = (double)expf((float)d);  // FP32 log-weights: FP32 exponential of an FP64 difference
     else
-      e = exp(d);
+      e = tang_exp(d, A.md.tab);
   }
   const double E = block_incl_scan<TPB>(e, sh);
   if (valid) A.E[nb][i] = E;
@@ -339,6 +346,38 @@ __global__ void finalize_kernel(StateView S, int N, int n_real, int n_int, int c
 // host side
 // ------------------------------------------------------------------------
 
+__device__ MathTab g_math_tab;
+
+namespace {
+std::mutex g_tab_mu;
+const MathTab* g_tab_ptr[128] = {nullptr};
+}  // namespace
+
+// The table entries are computed on the host in double (glibc log1p / exp2,
+// correctly rounded division) and copied once to each device that uses them.
+smc_status math_table(const MathTab** out) {
+  int dev = -1;
+  SMC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return set_error(SMC_EINVAL, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_tab_mu);
+  if (!g_tab_ptr[dev]) {
+    MathTab h;
+    for (int j = 0; j < 192; ++j) {
+      h.log_f[j] = j ? std::log((double)j / 128.0) : 0.0;
+      h.inv_f[j] = j ? 128.0 / (double)j : 0.0;
+    }
+    for (int j = 0; j < 32; ++j) h.exp2_j[j] = std::exp2((double)j / 32.0);
+    h.inv_int[0] = 0.0;
+    for (int k = 1; k < 256; ++k) h.inv_int[k] = 1.0 / (double)k;
+    SMC_CUDA_TRY(cudaMemcpyToSymbol(g_math_tab, &h, sizeof(MathTab)));
+    void* p = nullptr;
+    SMC_CUDA_TRY(cudaGetSymbolAddress(&p, g_math_tab));
+    g_tab_ptr[dev] = (const MathTab*)p;
+  }
+  *out = g_tab_ptr[dev];
+  return SMC_OK;
+}
+
 int model_fields(int kind, int* n_real, int* n_int) {
   switch (kind) {
     case SMC_MODEL_LG: *n_real = 1; *n_int = 1; return 0;
@@ -358,6 +397,12 @@ int tile_for(int64_t N) {
 }
 
 int bucket_for(int tile) { return tile <= 32 ? 0 : tile <= 64 ? 1 : tile <= 128 ? 2 : 3; }
+
+int real_state_fields(int kind) {
+  int n_real, n_int;
+  model_fields(kind, &n_real, &n_int);
+  return kind == SMC_MODEL_CRBD ? 3 : n_real;  // CRBD keeps log(lambda) internally
+}
 
 Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
   Layout L{};
@@ -379,7 +424,7 @@ Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
     return o;
   };
   for (int b = 0; b < 2; ++b) {
-    L.real[b] = take(rb * N * (size_t)m->n_real);
+    L.real[b] = take(rb * N * (size_t)m->n_real_state);
     L.ints[b] = take(4 * N * (size_t)m->n_int);
     L.stack[b] = take(rb * N * (size_t)m->stack_cap);
   }
@@ -425,6 +470,8 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
   A.incr = (double*)(ws + Ly.incr);
   A.rs = (RunState*)(ws + Ly.rs);
   A.N = (int)c->n_particles;
+  A.log_n = std::log((double)c->n_particles);
+  A.inv_n = 1.0 / (double)c->n_particles;
   A.n_tiles = Ly.n_tiles;
   A.tile = Ly.tile;
   A.max_segments = Ly.max_segments;
@@ -691,6 +738,7 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
   if (!m) return set_error(SMC_ENOMEM, "host allocation failed");
   m->desc = *d;
   m->n_real = n_real;
+  m->n_real_state = real_state_fields(d->kind);
   m->n_int = n_int;
   m->stack_cap = d->kind == SMC_MODEL_RATESHIFT ? d->lam_stack_cap : 0;
   ModelDev& md = m->md;
@@ -716,6 +764,16 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
   md.sigma = d->sigma;
   md.geo_p = d->geo_p;
   md.geo_logw = d->geo_logw;
+  md.log_rho = d->rho > 0.0 ? std::log(d->rho) : 0.0;
+  {
+    const MathTab* tab = nullptr;
+    smc_status ts = math_table(&tab);
+    if (ts) {
+      delete m;
+      return ts;
+    }
+    md.tab = tab;
+  }
   m->n_segments_known = 0;
   if (d->kind == SMC_MODEL_LG) {
     md.lg_lc = std::log(d->r_sd) + 0.91893853320467274178;

@@ -41,6 +41,7 @@ struct RunDev {
   int32_t* anc;       // ancestor rows
   double* incr;       // [max_segments] per-segment log-Z increments
   RunState* rs;
+  double log_n, inv_n;  // log N and 1 / N, computed on the host
   int N, n_tiles, tile, max_segments, record_all, anc_rows;
   uint32_t k0, k1;
 };
@@ -64,6 +65,7 @@ struct smc_model_s {
   smc_model_desc desc;
   smc::ModelDev md;
   int32_t n_real, n_int, stack_cap, n_segments_known;
+  int32_t n_real_state;  // real fields kept in PSTATE (>= n_real; extra ones are internal)
   void* dev_blob = nullptr;  // observations / tree arrays
   void* ws = nullptr;        // cached workspace of smc_run
   size_t ws_bytes = 0;
@@ -75,6 +77,8 @@ struct smc_model_s {
 namespace smc {
 
 int model_fields(int kind, int* n_real, int* n_int);
+// This device's log / exp tables (filled on first use per device).
+smc_status math_table(const MathTab** out);
 int tile_for(int64_t N);
 int bucket_for(int tile);
 Layout make_layout(const smc_model_s* m, const smc_run_cfg* c);

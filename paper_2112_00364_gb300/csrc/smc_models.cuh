@@ -19,6 +19,8 @@ namespace smc {
 // the tree are shared global constants, not per-particle state).
 struct ModelDev {
   int kind, T, n_nodes, fixed_rates, depth_cap, call_limit, lam_stack_cap, pad_;
+  const MathTab* tab;  // this device's log / exp tables
+  double log_rho;      // log(rho), computed on the host
   const double* obs;
   const int* parent;
   const int* left;
@@ -181,6 +183,8 @@ struct GeoModel {
 template <typename Real, bool RS>
 struct TreeModel {
   using R = Real;
+  // CRBD keeps log(lambda) as a third, internal real field (computed once at the
+  // prior block instead of once per internal-node branch); it is not an output.
   static constexpr int NB = 6, N_REAL = 2, N_INT = RS ? 2 : 1;
   static constexpr bool HAS_STACK = RS;
   enum { PRIOR = 0, BRANCH = 1, SIMBRANCH = 2, UNDET = 3, ITER = 4, END = 5 };
@@ -188,7 +192,7 @@ struct TreeModel {
     int pc, sp, v, n_top, fsp, calls;
     bool ckpt;
     int overflow, limited;
-    R lam, mu, logw;
+    R lam, mu, logw, loglam, inv_mu;
     R lam_b, start, stop, lnp1, lnp2, lnp3, cur_t;
     R fr_t[SMC_MAX_DEPTH], fr_bl[SMC_MAX_DEPTH];
     int fr_rem[SMC_MAX_DEPTH];
@@ -196,13 +200,14 @@ struct TreeModel {
   __device__ static void init(Lane& L) {
     L.pc = PRIOR;
     L.sp = 0;
-    L.lam = L.mu = (R)0;
+    L.lam = L.mu = L.loglam = (R)0;
     L.logw = (R)0;
   }
   __device__ static void gather(Lane& L, const StateView& Sc, const StateView& Sn, int a, int i,
                                 int N, const ModelDev&) {
     L.lam = Sc.rf<R>(0, a, N);
     L.mu = Sc.rf<R>(1, a, N);
+    if (!RS) L.loglam = Sc.rf<R>(2, a, N);
     L.pc = Sc.inf_(0, a, N);
     L.logw = (R)0;
     if (RS) {
@@ -214,6 +219,7 @@ struct TreeModel {
   __device__ static void store(const Lane& L, const StateView& Sn, int i, int N) {
     Sn.rf<R>(0, i, N) = L.lam;
     Sn.rf<R>(1, i, N) = L.mu;
+    if (!RS) Sn.rf<R>(2, i, N) = L.loglam;
     Sn.inf_(0, i, N) = L.pc;
     if (RS) Sn.inf_(1, i, N) = L.sp;
   }
@@ -245,6 +251,8 @@ struct TreeModel {
         if (RS) {
           S.st<R>(0, i, N) = L.lam;  // the root's rate, pending for its children
           L.sp = 1;
+        } else {
+          L.loglam = lg(L.lam, s);
         }
         L.logw = L.logw + (R)md.corr;
         L.pc = BRANCH;
@@ -270,7 +278,7 @@ struct TreeModel {
           if (md.fixed_mult) {
             mult = (R)md.fixed_mult[v];
           } else {
-            Stream sm{s.k0, s.k1, s.n, s.k, 0u, 2u};
+            Stream sm{s.k0, s.k1, s.n, s.k, 0u, 2u, s.tab};
             mult = lognormal<R>(sm, (R)md.sigma);
           }
           lam = lam_p * mult;
@@ -280,8 +288,9 @@ struct TreeModel {
         L.stop = (R)md.age[v];
         const R dt = L.start - L.stop;
         L.lnp1 = -L.mu * dt;
-        L.lnp2 = (md.left[v] >= 0) ? m_log(lam) : m_log((R)md.rho);
+        L.lnp2 = (md.left[v] >= 0) ? (RS ? lg(lam, s) : L.loglam) : (R)md.log_rho;
         L.n_top = poisson<R>(s, lam * dt);
+        if (L.n_top > 0 && L.mu > (R)0) L.inv_mu = (R)1 / L.mu;
         L.lnp3 = (R)0;
         L.fsp = 0;
         L.calls = 0;
@@ -313,7 +322,7 @@ struct TreeModel {
           return;
         }
         const R t = L.cur_t;
-        const R dur = exponential<R>(s, L.mu);
+        const R dur = L.mu > (R)0 ? exponential_inv(s, L.mu, L.inv_mu) : exponential<R>(s, L.mu);
         if (dur > t) {
           if (bernoulli<R>(s, (R)md.rho)) {
             L.lnp3 = neg_inf<R>();

@@ -22,6 +22,7 @@
 #include <mutex>
 
 #include "smc_device.cuh"
+#include "smc_engine.h"
 #include "smc_internal.h"
 
 namespace smc {
@@ -258,10 +259,11 @@ __global__ void philox_kernel(const uint32_t* __restrict__ ctr, const uint32_t* 
 
 template <typename R>
 __global__ void sample_kernel(int dist, R p1, R p2, uint32_t k0, uint32_t k1, int64_t n,
-                              double* __restrict__ out, int32_t* __restrict__ blocks) {
+                              double* __restrict__ out, int32_t* __restrict__ blocks,
+                              const MathTab* tab) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  Stream s{k0, k1, (uint32_t)i, 0u, 0u, 0u};
+  Stream s{k0, k1, (uint32_t)i, 0u, 0u, 0u, tab};
   double v = 0.0;
   switch (dist) {
     case 0: v = (double)uniform01<R>(s); break;
@@ -277,9 +279,28 @@ __global__ void sample_kernel(int dist, R p1, R p2, uint32_t k0, uint32_t k1, in
   if (blocks) blocks[i] = (int32_t)s.d;
 }
 
+__global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* __restrict__ y,
+                                 int64_t n, const MathTab* tab) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  y[i] = fn == 0 ? tang_log(v, tab) : fn == 1 ? tang_exp(v, tab) : fn == 2 ? log(v) : exp(v);
+}
+
 }  // namespace smc
 
 using namespace smc;
+
+extern "C" smc_status smc_math_eval(int32_t fn, const double* x, double* y, int64_t n, void* stream) {
+  if (!x || !y || n < 0 || fn < 0 || fn > 3) return set_error(SMC_EINVAL, "bad argument");
+  if (n == 0) return SMC_OK;
+  const MathTab* tab = nullptr;
+  smc_status ts = math_table(&tab);
+  if (ts) return ts;
+  math_eval_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(fn, x, y, n, tab);
+  SMC_CUDA_TRY(cudaGetLastError());
+  return SMC_OK;
+}
 
 extern "C" const char* smc_last_error(void) { return g_err; }
 
@@ -428,10 +449,13 @@ extern "C" smc_status smc_sample(int32_t dist, int32_t precision, double p1, dou
   const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32) ^ run_id;
   const unsigned g = (unsigned)((n + 255) / 256);
   cudaStream_t cs = (cudaStream_t)stream;
+  const MathTab* tab = nullptr;
+  smc_status ts = math_table(&tab);
+  if (ts) return ts;
   if (precision == SMC_PREC_FP64)
-    sample_kernel<double><<<g, 256, 0, cs>>>(dist, p1, p2, k0, k1, n, out, blocks);
+    sample_kernel<double><<<g, 256, 0, cs>>>(dist, p1, p2, k0, k1, n, out, blocks, tab);
   else if (precision == SMC_PREC_FP32)
-    sample_kernel<float><<<g, 256, 0, cs>>>(dist, (float)p1, (float)p2, k0, k1, n, out, blocks);
+    sample_kernel<float><<<g, 256, 0, cs>>>(dist, (float)p1, (float)p2, k0, k1, n, out, blocks, tab);
   else
     return set_error(SMC_EINVAL, "unknown precision");
   SMC_CUDA_TRY(cudaGetLastError());

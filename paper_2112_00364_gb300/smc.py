@@ -143,6 +143,8 @@ def lib():
         L.smc_sample.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint64,
                                  C.c_uint32, C.c_int64, _vp, _vp, _vp]
         L.smc_sample.restype = C.c_int32
+        L.smc_math_eval.argtypes = [C.c_int32, _vp, _vp, C.c_int64, _vp]
+        L.smc_math_eval.restype = C.c_int32
         L.smc_last_error.argtypes = []
         L.smc_last_error.restype = C.c_char_p
         L.smc_version.argtypes = []
@@ -464,6 +466,17 @@ def sample(dist: str, n: int, p1: float = 0.0, p2: float = 0.0, seed: int = 1, r
     _check(lib().smc_sample(DIST[dist], PRECISIONS[precision], p1, p2, seed, run_id, n,
                             _ptr(out), _ptr(blocks), _stream(stream)))
     return out, blocks
+
+
+def math_eval(fn: str, x):
+    """Device math parity hook: fn in table_log / table_exp / lib_log / lib_exp."""
+    import torch
+
+    code = {"table_log": 0, "table_exp": 1, "lib_log": 2, "lib_exp": 3}[fn]
+    xd = torch.as_tensor(x, dtype=torch.float64).cuda()
+    y = torch.empty_like(xd)
+    _check(lib().smc_math_eval(code, _ptr(xd), _ptr(y), xd.numel(), None))
+    return y.cpu().numpy()
 
 
 def version() -> str:

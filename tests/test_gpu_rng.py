@@ -66,3 +66,31 @@ def test_variates_fp32(dist, p1, p2):
         # CUDA's single-precision logf/cosf/expf are within 1-2 ulp of glibc's
         scale = max(abs(p1), abs(p2), 1.0)
         np.testing.assert_allclose(g, o, rtol=2e-6, atol=1e-6 * scale)
+
+
+def _ulp_diff(a, b):
+    ia = a.view(np.int64)
+    ib = b.view(np.int64)
+    return np.abs(ia - ib)
+
+
+@pytest.mark.parametrize("fn", ["log", "exp"])
+def test_table_math_within_two_ulp(fn):
+    """The table-driven FP64 log / exp used by the samplers (Tang's method) stay
+    within 2 ulp of CUDA's library functions and of numpy's (glibc) results."""
+    from paper_2112_00364_gb300 import smc
+
+    rng = np.random.default_rng(5)
+    if fn == "log":
+        x = np.concatenate([rng.random(400_000), np.exp(rng.uniform(-700, 700, 400_000)),
+                            1.0 + rng.uniform(-1e-3, 1e-3, 100_000), [1.0, 2.0, 0.5, 1e-300]])
+        ref = np.log(x)
+    else:
+        x = np.concatenate([rng.uniform(-700, 700, 400_000), rng.uniform(-40, 0, 400_000),
+                            rng.uniform(-1e-3, 1e-3, 100_000), [0.0, -1.0, 1.0]])
+        ref = np.exp(x)
+    tab = smc.math_eval("table_" + fn, x)
+    lib = smc.math_eval("lib_" + fn, x)
+    assert _ulp_diff(tab, lib).max() <= 2
+    ok = np.isfinite(ref) & (ref != 0)
+    assert _ulp_diff(tab[ok], ref[ok]).max() <= 2
