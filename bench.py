@@ -66,8 +66,8 @@ WORKLOADS = {
 # DMUL) and its DRAM traffic per launch, from one ncu capture of the workload
 # (profiles folder); the traffic holds only for the kernel sources with the
 # recorded digest.
-NCU = {"crbd64": dict(fp64_flop_per_pstep=160.0, bytes_per_launch=2.70e6,
-                     src_digest="9fbf1c76f21ae126")}
+NCU = {"crbd64": dict(fp64_flop_per_pstep=95.4, bytes_per_launch=3.24e6,
+                     fp64_pipe_elapsed=0.342, src_digest="d37df0c0b5fbd72e")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
@@ -539,6 +539,7 @@ def main() -> int:
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
                 "kernel": "wave_kernel (fused segment kernel)",
                 "avg_launch_us": avg_launch_s * 1e6, "launches": kern_launches,
+                "fp64_pipe_active_of_elapsed_ncu": info["fp64_pipe_elapsed"],
                 "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM"}
     cpu = None
     if ws == 1:

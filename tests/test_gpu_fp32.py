@@ -1,0 +1,129 @@
+"""FP32-particle / FP64-reduction mode against the oracle (GPU).
+
+In FP32 mode the particle arithmetic and log-weights are single precision while
+the normaliser, scan and log Z stay FP64.  CUDA's and glibc's single-precision
+log / exp / cos differ in the last place, so ancestors can differ near
+cumulative-weight boundaries far more often than in FP64; the oracle therefore
+runs in follow mode (it adopts every GPU ancestor) and the two runs are compared
+to FP32 rounding, with the number of differing ancestors reported and bounded.
+The statistical checks compare FP32 estimates with exact likelihoods and with
+the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import closed_forms as cf
+import inputs
+import oracle
+from parity import run_pair
+
+pytestmark = pytest.mark.gpu
+
+# FP32 tolerances: log Z accumulates one FP32-accurate increment per checkpoint
+LOGZ_ABS_PER_SEGMENT_FP32 = 2e-5
+STATE_RTOL_FP32 = 2e-5
+
+
+def _close_frac(a, b, rtol, atol):
+    """Fraction of elements of a and b that differ by more than atol + rtol |b|.
+
+    A particle whose control flow took a different branch on a last-place
+    difference of a single-precision library function (a Bernoulli draw, a
+    survival test) differs by more than rounding; such particles must stay rare."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    same_inf = (a == b)
+    with np.errstate(invalid="ignore"):
+        bad = ~same_inf & ~(np.abs(a - b) <= atol + rtol * np.abs(b))
+    return float(bad.mean()) if bad.size else 0.0
+
+
+def _check_fp32(g, o, max_mismatch_frac=2e-3, max_bad_frac=2e-3):
+    assert g["n_segments"] == o["n_segments"]
+    n_off = max(1, o["n_resamples"] * len(g["final_logw"]))
+    assert (o["n_hard_mismatch"] + o["n_flag_mismatch"]) / n_off < max_mismatch_frac
+    tol = LOGZ_ABS_PER_SEGMENT_FP32 * g["n_segments"] * max(1.0, abs(o["log_z"]) / g["n_segments"])
+    assert abs(g["log_z_value"] - o["log_z"]) <= tol, (g["log_z_value"], o["log_z"], tol)
+    assert _close_frac(g["final_logw"], o["final_logw"], STATE_RTOL_FP32, 1e-5) <= max_bad_frac
+    assert _close_frac(g["real_fields"], o["real_fields"], STATE_RTOL_FP32, 1e-6) <= max_bad_frac
+    np.testing.assert_array_equal(g["int_fields"][0], o["int_fields"][0])
+
+
+@pytest.mark.parametrize("N,seed", [(1000, 1), (5000, 2)])
+def test_lg_fp32_follows_oracle(N, seed):
+    y = inputs.lg_observations(50, seed=1)
+    g, o = run_pair("lg", N, seed, precision="fp32", obs=y)
+    _check_fp32(g, o)
+
+
+@pytest.mark.parametrize("kind", ["crbd", "rateshift"])
+def test_tree_fp32_follows_oracle(kind):
+    tree = inputs.yule_tree(32, seed=3)
+    p = dict(tree=tree)
+    if kind == "rateshift":
+        p.update(sigma=0.3, lam_stack_cap=tree.max_pending_right() + 1)
+    g, o = run_pair(kind, 4000, 5, precision="fp32", **p)
+    _check_fp32(g, o)
+
+
+def test_rateshift_fp32_unbiased_fixed_multipliers():
+    from paper_2112_00364_gb300 import smc
+
+    tree = inputs.yule_tree(24, seed=6)
+    cap = tree.max_pending_right() + 1
+    rng = np.random.default_rng(1)
+    mult = np.exp(0.3 * rng.standard_normal(tree.n_nodes))
+    lam0, mu = 2.0, 0.6
+    lam_b = np.empty(tree.n_nodes)
+    lam_b[0] = lam0
+    for v in tree.preorder[1:]:
+        lam_b[v] = lam_b[tree.parent[v]] * mult[v]
+    m = smc.Model("rateshift", tree=tree, rates=(lam0, mu), fixed_mult=mult, lam_stack_cap=cap)
+    lz = [smc.run(m, 1 << 14, seed=s, precision="fp32")["log_z_value"] for s in range(1, 101)]
+    ok, mean, se = cf.unbiased_check(np.array(lz), cf.crbd_log_z_rates(tree, lam_b, mu))
+    assert ok, (mean, se)
+
+
+def test_crbd_fp32_unbiased_fixed_rates_64_tips():
+    from paper_2112_00364_gb300 import smc
+
+    tree = inputs.yule_tree(64, seed=2)
+    m = smc.Model("crbd", tree=tree, rates=(4.0, 1.0))
+    lz = [smc.run(m, 1 << 16, seed=s, precision="fp32")["log_z_value"] for s in range(1, 101)]
+    ok, mean, se = cf.unbiased_check(np.array(lz), cf.crbd_log_z(tree, 4.0, 1.0))
+    assert ok, (mean, se)
+
+
+def test_rateshift_fp32_matches_fp64_oracle_in_distribution():
+    """The log-Z error of FP32 particles against the FP64 oracle (north-star
+    precision statement): over 24 seeds the two means of log Zhat agree within
+    3 combined standard errors, and the mean difference is reported."""
+    from paper_2112_00364_gb300 import smc
+
+    tree = inputs.yule_tree(48, seed=3)
+    p = dict(tree=tree, sigma=0.3, lam_stack_cap=tree.max_pending_right() + 1)
+    m = smc.Model("rateshift", **p)
+    g = np.array([smc.run(m, 4096, seed=s, precision="fp32")["log_z_value"] for s in range(1, 25)])
+    o = np.array([oracle.smc_run("rateshift", 4096, seed=100 + s, **p)["log_z"]
+                  for s in range(1, 25)])
+    se = math.sqrt(g.var(ddof=1) / len(g) + o.var(ddof=1) / len(o))
+    assert abs(g.mean() - o.mean()) <= 3 * se, (g.mean(), o.mean(), se)
+
+
+def test_rateshift_full_config_properties():
+    """C3 at full size (256-tip tree, N = 2^20, FP32 particles): every particle
+    ends at b_stop with an empty pending-rate stack, log Z is finite, the
+    recorded last ancestors are a valid systematic resampling (non-decreasing,
+    in range), and no particle hit the stack or depth caps."""
+    from paper_2112_00364_gb300 import smc
+
+    tree = inputs.yule_tree(256, seed=3)
+    m = smc.Model("rateshift", tree=tree, sigma=0.3, lam_stack_cap=tree.max_pending_right() + 1)
+    r = smc.run(m, 1 << 20, seed=1, precision="fp32")
+    assert r["status"] == 0 and r["n_segments"] == 511
+    assert np.isfinite(r["log_z_value"])
+    assert np.all(r["int_fields"][0] == -1) and np.all(r["int_fields"][1] == 0)
+    a = r["ancestors"][0]
+    assert a.min() >= 0 and a.max() < (1 << 20) and np.all(np.diff(a) >= 0)
+    assert r["n_overflow"] == 0 and r["n_limit"] == 0
