@@ -141,6 +141,20 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def job_rate(units_per_rank: float, seconds: float, dist=None, device="cpu") -> tuple:
+    """Whole-job rate of independent replicas: every rank processed
+    `units_per_rank` units; the job took as long as its slowest rank.  Returns
+    (units of all ranks / slowest time, slowest time)."""
+    ws = 1
+    if dist is not None:
+        import torch
+
+        t = torch.tensor([seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds, ws = float(t.item()), dist.get_world_size()
+    return units_per_rank * ws / seconds, seconds
+
+
 # ------------------------------------------------------------------ workloads
 class Work:
     """One workload: a list of runs (kind, params, N, seed, run_id)."""
@@ -311,14 +325,19 @@ def run_serve(args, work: Work, smc, torch, dist, ws: int, rank: int, local: int
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    if dist:
+        dist.barrier()
     units, span, lats, nreq, d2h = 0, 0.0, [], 0, 0
     for s in range(args.steps):
         u, sp, la, n, b = stream_step(s, w["seconds_per_step"])
         units, span, lats, nreq, d2h = units + u, span + sp, lats + la, nreq + n, d2h + b
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     clk = clocks.stop()
     st = srv.stats()
     srv.close()
-    value = units * ws / span
+    value, span = job_rate(units, span, dist, torch.device("cuda", local))
     # the first requests of the stream, served one run per launch in arrival order
     arr = inputs.poisson_arrivals(w["rate"], w["seconds_per_step"], seed=w["arrival_seed"])
     rng = np.random.Generator(np.random.PCG64(1000))
@@ -463,12 +482,8 @@ def main() -> int:
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = args.steps * work.units * ws / (total_ms * 1e-3)
+    value, total_s = job_rate(args.steps * work.units, sum(step_ms) * 1e-3, dist, dev)
+    total_ms = total_s * 1e3
 
     # the same runs one run per launch (plain path), timed once
     plain = None
@@ -518,11 +533,7 @@ def main() -> int:
         for m2 in ms2:
             m2.close()
         e2e_total += time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = e2e_steps * work.units * ws / e2e_total
+    e2e_value, e2e_total = job_rate(e2e_steps * work.units, e2e_total, dist, dev)
 
     if rank != 0:
         if dist:
