@@ -413,4 +413,126 @@ __device__ __forceinline__ double block_incl_max(double v, double* sh) {
   return v;
 }
 
+// Block inclusive prefix max of int64 keys over TPB threads.  `sh` >= TPB/32
+// long longs.  Non-negative doubles order like their bit patterns, so this is
+// also the prefix max of such doubles, on the integer pipes.
+template <int TPB>
+__device__ __forceinline__ long long block_incl_max_i64(long long v, long long* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = max(v, t);
+  }
+  if (TPB > 32) {
+    __syncthreads();
+    if (lane == 31) sh[wid] = v;
+    __syncthreads();
+    for (int w = 0; w < wid; ++w) v = max(v, sh[w]);
+  }
+  return v;
+}
+
+// Order-preserving int64 key of a double (not NaN): for x >= 0 its bits, for
+// x < 0 its bits with the magnitude bits flipped; max of keys = key of max.
+__device__ __forceinline__ long long order_key(double x) {
+  long long b = __double_as_longlong(x);
+  if ((b & 0x7FFFFFFFFFFFFFFFll) > 0x7FF0000000000000ll) b = (long long)0xFFF0000000000000ull;  // NaN as -inf
+  return b >= 0 ? b : b ^ 0x7FFFFFFFFFFFFFFFll;
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+  return __longlong_as_double(k >= 0 ? k : k ^ 0x7FFFFFFFFFFFFFFFll);
+}
+
+// Warp max of doubles through their order keys (integer shuffles only).
+__device__ __forceinline__ double warp_max_key(double x) {
+  long long v = order_key(x);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return from_order_key(v);
+}
+
+// ---- fixed-point weights: w * 2^54 as int64 (tile-local scans) ----
+// Weights relative to a tile's power-of-two reference lie in [0, 1], and a
+// tile holds at most 256 particles, so its running sums stay below 2^62.
+// Integer sums are exact and associative: every order of summation gives the
+// same bits, and the running sums are non-decreasing by construction.
+constexpr int kFixBits = 54;
+
+// round(x * 2^54) for finite 0 <= x < 2^9 (integer operations only; below
+// 2^-55 the result is 0).
+__device__ __forceinline__ long long to_fix54(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)(b >> 52);  // biased exponent; 0 for zero and subnormals
+  if (b <= 0 || e == 0) return 0;
+  const long long m = (b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll;  // x = m 2^(e-1075)
+  const int sh = e - (1075 - kFixBits);                                     // x 2^54 = m 2^sh
+  if (sh >= 0) return m << sh;
+  const int rs = -sh;
+  if (rs > 54) return 0;
+  return (m + (1ll << (rs - 1))) >> rs;
+}
+
+// floor(x * 2^54) for any x: -1 below zero, LLONG_MAX from 2^9 up (above every
+// tile sum), integer operations only.
+__device__ __forceinline__ long long floor_fix54(double x) {
+  const long long b = __double_as_longlong(x);
+  if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return 0;  // +-0
+  if (b < 0) return -1;
+  const int e = (int)(b >> 52);
+  if (e == 0) return 0;
+  if (e >= 1023 + 9) return 0x7FFFFFFFFFFFFFFFll;
+  const long long m = (b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll;
+  const int sh = e - (1075 - kFixBits);
+  if (sh >= 0) return m << sh;
+  const int rs = -sh;
+  return rs >= 63 ? 0 : (m >> rs);
+}
+
+// Block inclusive scan of int64 over TPB threads (exact).  `sh` >= TPB/32 long longs.
+template <int TPB>
+__device__ __forceinline__ long long block_incl_scan_i64(long long v, long long* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (TPB == 32) return v;
+  __syncthreads();
+  if (lane == 31) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    long long t = lane < TPB / 32 ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < TPB / 32; o <<= 1) {
+      const long long q = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += q;
+    }
+    const long long ex = __shfl_up_sync(0xffffffffu, t, 1);
+    if (lane < TPB / 32) sh[lane] = lane ? ex : 0;
+  }
+  __syncthreads();
+  return wid > 0 ? sh[wid] + v : v;
+}
+
+// Block max of doubles (no NaN) through their order keys: integer shuffles
+// and compares only.  Every thread gets the result.  `sh` >= TPB/32 long longs.
+template <int TPB>
+__device__ __forceinline__ double block_max_key(double x, long long* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long v = order_key(x);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (TPB > 32) {
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    v = sh[0];
+#pragma unroll
+    for (int w = 1; w < TPB / 32; ++w) v = max(v, sh[w]);
+  }
+  return from_order_key(v);
+}
+
 }  // namespace smc

@@ -13,17 +13,19 @@
 //             stack pointer;
 //   segment   blocks run until the next checkpoint with per-warp PC-sorted
 //             dispatch (smc_models.cuh); draws from Philox counters;
-//   epilogue  the tile's FP64 max M_t and its power-of-two reference
-//             k_t = ceil(M_t / ln 2); weights e_j = exp(logw_j - k_t ln 2) (FP64;
-//             in FP32 mode the difference is formed in FP64 and its exponential
-//             in FP32), their FP64 inclusive scan E_j (kept for the next segment's
-//             search) and total s_t; the run's last CTA to finish combines the
-//             run's tiles: k = max k_t, c_t = 2^(k_t - k) (exact, no exponential),
-//             monotone exclusive offsets O_t of c_t s_t, S = total,
-//             log Z += k ln 2 + (log S - log N), the resampling uniform u_k and
-//             r = N / S.
-// The running sum the next search uses is P_j = min(O_t + c_t E_j, O_{t+1}) and
-// its scaled boundary q_j = P_j r.  A run stops after the segment in which every
+//   epilogue  per warp, as soon as its particles are done: the warp's max M_w,
+//             its power-of-two reference k_w = ceil(M_w / ln 2), the weights
+//             e_j = exp(logw_j - k_w ln 2) (FP64; in FP32 mode the difference is
+//             formed in FP64 and its exponential in FP32) rounded to integers
+//             e_j 2^54; after the tile barrier the tile reference k_t = max k_w,
+//             each weight shifted exactly to it, and the tile's integer running
+//             sum E_j (kept for the next segment's search) and total s_t; the
+//             run's last CTA to finish combines the run's tiles: k = max k_t,
+//             c_t = 2^(k_t - k) (exact, no exponential), non-decreasing offsets
+//             O_t of c_t s_t, S = total, log Z += k ln 2 + (log S - log N), the
+//             resampling uniform u_k and r = N / S.
+// The running sum the next search uses is P_j = O_t + c_t E_j 2^-54 and its
+// scaled boundary q_j = P_j r.  A run stops after the segment in which every
 // particle reached b_stop (no resampling after it); its later CTAs return at once.
 //
 // A run's tile size depends only on its N (tile = ceil(N / 456) clamped to
@@ -53,25 +55,22 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned l
 }
 
 // Non-negative doubles order like their bit patterns read as int64, so the
-// searches below compare bits on the integer pipes and spend FP64 work only on
-// the few boundary values they actually form.
+// tile search compares bits on the integer pipes.
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
-// q_j = min(O_t + c_t E_j, O_{t+1}) * r for j in tile t.
-__device__ __forceinline__ double q_at(int j, const RunDev& A, const double* __restrict__ E,
-                                       double r) {
-  const int t = j / A.tile;
-  const double P = fmin(A.tile_O[t] + A.tile_c[t] * E[j], A.tile_O[t + 1]);
-  return P * r;
+// a_i = min{ j : q_j > y }, y = i + u, with q_j = (O_t + c_t E_j) r for j in
+// tile t and E_j the tile's fixed-point running sum (units of 2^-54 of the
+// tile's reference).  The tile is t = max{ t : O_t r <= y } (N - 1 if y lies
+// above every boundary); inside it q_j > y <=> E_j > e* = (y / r - O_t) / c_t,
+// and since E_j is an integer, <=> E_j > floor(e* 2^54): one threshold per
+// particle, then integer compares only.  If no element of tile t qualifies, the
+// first element of tile t+1 does.  The offset is flagged when it lies within
+// 1e-12 N of q_a or q_{a-1}, measured in the same units.
+__device__ __forceinline__ long long e_threshold(double y, const RunDev& A, int t, double inv_r) {
+  return floor_fix54(fma(y, inv_r, -A.tile_O[t]) * A.tile_invc[t]);
 }
 
-// a_i = min{ j : q_j > i + u } (N - 1 if none).  Tile first: t = max{t : O_t r <= y};
-// inside the tile the threshold e* = (y / r - O_t) / c_t on E locates the
-// candidate, and the exact q_j then fixes it up if rounding moved it.  If no
-// element of tile t qualifies, the first element of tile t+1 does.  Flags the
-// offset when it lies within 1e-12 N of q_a or q_{a-1}; the boundaries the
-// fix-up formed are reused for the flag.
-__device__ __forceinline__ int systematic_search(int i, const RunDev& A, const double* E, double r,
+__device__ __forceinline__ int systematic_search(int i, const RunDev& A, const long long* E,
                                                  double inv_r, double u, bool* near) {
   const int N = A.N, T = A.n_tiles;
   const double y = (double)i + u;
@@ -84,61 +83,73 @@ __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const d
     else
       hi = mid - 1;
   }
-  int a;
-  double qa, qa1;  // q_a and q_{a-1} (unused when a = 0)
-  if (lo >= T) {
-    a = N - 1;
-    qa = q_at(a, A, E, r);
-    qa1 = a > 0 ? q_at(a - 1, A, E, r) : 0.0;
-  } else {
-    const int t = lo;
-    const int j0 = t * A.tile, j1 = min(N, j0 + A.tile);
-    const long long eb = dbits((y * inv_r - A.tile_O[t]) * A.tile_invc[t]);
-    int l = j0, h = j1;  // first j in [j0, j1) with E_j > e*
-    while (l < h) {
-      const int mid = (l + h) >> 1;
-      if (dbits(E[mid]) > eb)
-        h = mid;
-      else
-        l = mid + 1;
-    }
-    int j = l;
-    double q_hi = j < j1 ? q_at(j, A, E, r) : INFINITY;  // q_j
-    while (j < j1 && dbits(q_hi) <= yb) {
-      ++j;
-      q_hi = j < j1 ? q_at(j, A, E, r) : INFINITY;
-    }
-    double q_lo = j > j0 ? q_at(j - 1, A, E, r) : -1.0;  // q_{j-1}; -1 below every offset
-    while (j > j0 && dbits(q_lo) > yb) {
-      --j;
-      q_hi = q_lo;
-      q_lo = j > j0 ? q_at(j - 1, A, E, r) : -1.0;
-    }
-    if (j < j1) {
-      a = j;
-      qa = q_hi;
-      qa1 = j > j0 ? q_lo : (a > 0 ? q_at(a - 1, A, E, r) : 0.0);
-    } else {
-      a = j1 < N ? j1 : N - 1;
-      qa = q_at(a, A, E, r);
-      qa1 = a > 0 ? q_at(a - 1, A, E, r) : 0.0;
-    }
+  const double tolE = kBoundaryEps * (double)N * inv_r;  // 1e-12 N on the q scale, in E units x c_t
+  if (lo >= T) {  // above the last boundary (rounding at the top)
+    *near = fabs(A.tile_q[T] - y) < kBoundaryEps * (double)N;
+    return N - 1;
   }
-  const double tol = kBoundaryEps * (double)N;
-  *near = fabs(qa - y) < tol || (a > 0 && fabs(qa1 - y) < tol);
+  const int t = lo;
+  const int j0 = t * A.tile, j1 = min(N, j0 + A.tile);
+  const long long F = e_threshold(y, A, t, inv_r);
+  const long long tolF = to_fix54(fmin(tolE * A.tile_invc[t], 256.0));
+  int l = j0, h = j1;  // first j in [j0, j1) with E_j > F
+  while (l < h) {
+    const int mid = (l + h) >> 1;
+    if (E[mid] > F)
+      h = mid;
+    else
+      l = mid + 1;
+  }
+  const long long Eb = l > j0 ? E[l - 1] : 0;  // E_{a-1} in tile t
+  bool nr = F - Eb < tolF;
+  int a;
+  if (l < j1) {
+    a = l;
+    nr = nr || E[l] - F <= tolF;
+  } else if (j1 < N) {  // the first element of the next tile
+    a = j1;
+    const long long F1 = e_threshold(y, A, t + 1, inv_r);
+    const long long tol1 = to_fix54(fmin(tolE * A.tile_invc[t + 1], 256.0));
+    nr = nr || E[j1] - F1 <= tol1;
+  } else {
+    a = N - 1;
+  }
+  *near = nr;
   return a;
 }
 
 // The run's last CTA of a segment: combine the tile reductions (all FP64).
-// `sh` holds >= TPB/32 + TPB + 2 doubles.
+// Thread p owns the kCombineP consecutive tiles p*P.. of each chunk of TPB*P
+// tiles: it forms their c_t v_t and offsets by sequential additions (so they
+// are non-decreasing within the thread), one block scan of the thread totals
+// places the threads, and an integer prefix max over the offsets' bit patterns
+// keeps them non-decreasing across thread seams.  `sh` holds >= TPB + 2 doubles.
+constexpr int kCombineP = 4;
+
 template <int TPB>
 __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
+  constexpr int P = kCombineP;
   RunState* rs = A.rs;
   const int nt = A.n_tiles;
-  double* shx = sh + TPB / 32 + 1;
+  long long* shl = reinterpret_cast<long long*>(sh);
+  // first chunk's tile values stay in registers
+  int kt0[P];
+  double s0[P];
   int kloc = kDeadTile;
   int alive = 0;
-  for (int t = threadIdx.x; t < nt; t += TPB) {
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const int t = threadIdx.x * P + q;
+    kt0[q] = kDeadTile;
+    s0[q] = 0.0;
+    if (t < nt) {
+      kt0[q] = __ldcg(A.tile_k + t);
+      s0[q] = __ldcg(A.tile_s + t);
+      alive |= __ldcg(A.tile_alive + t);
+    }
+    kloc = max(kloc, kt0[q]);
+  }
+  for (int t = TPB * P + threadIdx.x; t < nt; t += TPB) {
     kloc = max(kloc, __ldcg(A.tile_k + t));
     alive |= __ldcg(A.tile_alive + t);
   }
@@ -157,35 +168,66 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
     }
     return;
   }
-  // exclusive offsets O_t of v_t = c_t s_t, made monotone by a running max
-  double carry = 0.0, omax = 0.0;
-  for (int base = 0; base < nt; base += TPB) {
-    const int t = base + threadIdx.x;
-    double c = 0.0, invc = 0.0, v = 0.0;
-    if (t < nt) {
-      const int kt = __ldcg(A.tile_k + t);
+  double carry = 0.0;  // offset of the chunk (the same in every thread)
+  long long omax = 0;  // bits of the largest offset of earlier chunks
+  double O0[P];        // first chunk's offsets, kept for tile_q
+  for (int base = 0; base < nt; base += TPB * P) {
+    double v[P];
+    double tot = 0.0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int t = base + threadIdx.x * P + q;
+      int kt = kDeadTile;
+      double st = 0.0;
+      if (base == 0) {
+        kt = kt0[q];
+        st = s0[q];
+      } else if (t < nt) {
+        kt = __ldcg(A.tile_k + t);
+        st = __ldcg(A.tile_s + t);
+      }
+      double c = 0.0, invc = 0.0;
       if (kt != kDeadTile && kt - kmax >= -1022) {
         c = pow2i(kt - kmax);
         invc = pow2i(kmax - kt);
       }
-      v = __ldcg(A.tile_s + t) * c;  // exact: c is a power of two
+      if (t < nt) {
+        A.tile_c[t] = c;
+        A.tile_invc[t] = invc;
+      }
+      v[q] = st * c;  // exact: c is a power of two
+      tot = tot + v[q];
     }
-    const double incl = block_incl_scan<TPB>(v, sh);
+    const double incl = block_incl_scan<TPB>(tot, sh);
     __syncthreads();
-    shx[threadIdx.x + 1] = incl;
+    sh[threadIdx.x + 1] = incl;
     __syncthreads();
-    const double excl = threadIdx.x ? shx[threadIdx.x] : 0.0;
-    const double chunk_total = shx[TPB];
-    const double O = block_incl_max<TPB>(fmax(carry + excl, omax), sh);
-    if (t < nt) {
-      A.tile_c[t] = c;
-      A.tile_invc[t] = invc;
-      A.tile_O[t] = O;
+    double O = carry + (threadIdx.x ? sh[threadIdx.x] : 0.0);
+    const double chunk_total = sh[TPB];
+    double Oq[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      Oq[q] = O;
+      O = O + v[q];
     }
+    // seams: every offset at least the largest offset before it
     __syncthreads();
-    if (threadIdx.x == TPB - 1) shx[0] = O;
+    const long long last = max(__double_as_longlong(Oq[P - 1]), omax);
+    const long long incl_m = block_incl_max_i64<TPB>(last, shl);
     __syncthreads();
-    omax = shx[0];
+    shl[threadIdx.x + 1] = incl_m;
+    if (threadIdx.x == 0) shl[0] = omax;
+    __syncthreads();
+    const long long prev = shl[threadIdx.x];
+    const long long chunk_max = shl[TPB];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      Oq[q] = __longlong_as_double(max(__double_as_longlong(Oq[q]), prev));
+      const int t = base + threadIdx.x * P + q;
+      if (t < nt) A.tile_O[t] = Oq[q];
+      if (base == 0) O0[q] = Oq[q];
+    }
+    omax = chunk_max;
     carry = carry + chunk_total;
     __syncthreads();
   }
@@ -195,9 +237,20 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
   const double S = carry;
   const double r = (double)A.N * (1.0 / S);
   const bool go_on = alive && k + 1 < A.max_segments;
-  if (threadIdx.x == 0) A.tile_O[nt] = fmax(S, omax);
-  __syncthreads();
-  for (int t = threadIdx.x; t <= nt; t += TPB) A.tile_q[t] = A.tile_O[t] * r;
+  const double O_end = fmax(S, __longlong_as_double(omax));
+  if (nt <= TPB * P) {
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int t = threadIdx.x * P + q;
+      if (t < nt) A.tile_q[t] = O0[q] * r;
+    }
+  } else {
+    for (int t = threadIdx.x; t < nt; t += TPB) A.tile_q[t] = A.tile_O[t] * r;
+  }
+  if (threadIdx.x == 0) {
+    A.tile_O[nt] = O_end;
+    A.tile_q[nt] = O_end * r;
+  }
   if (threadIdx.x == (TPB > 32 ? 32 : 0) && go_on) {
     const Block4 b = philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1);
     rs->u = Unif<double>::first(b);
@@ -226,7 +279,7 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
 // One tile of one run for segment k (the whole per-CTA body of a wave).
 template <class M, int TPB>
 __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const int k, double* sh,
-                                          int* sh_last) {
+                                          int* sh_last, int* sh_kw) {
   using R = typename M::R;
   RunState* rs = A.rs;
   const int N = A.N;
@@ -241,8 +294,8 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
     if (k == 0) {
       M::init(L);
     } else {
-      const double r = rs->r, u = rs->u, inv_r = rs->inv_r;
-      const int a = systematic_search(i, A, A.E[cb], r, inv_r, u, &near);
+      const double u = rs->u, inv_r = rs->inv_r;
+      const int a = systematic_search(i, A, A.E[cb], inv_r, u, &near);
       const int row = A.record_all ? k - 1 : 0;
       if (row < A.anc_rows) A.anc[(size_t)row * N + i] = a;
       M::gather(L, Sc, Sn, a, i, N, A.md);
@@ -262,28 +315,43 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   }
   warp_add_u64(&rs->n_overflow, active ? (unsigned long long)L.overflow : 0ull);
   warp_add_u64(&rs->n_limit, active ? (unsigned long long)L.limited : 0ull);
-  // tile reduction: FP64 max, power-of-two reference, weights, FP64 scan
-  const double Mt = block_max<TPB>(lw, sh);
-  if (threadIdx.x == 0) {
-    const int kt = Mt == -INFINITY ? kDeadTile : tile_exponent(Mt);
-    *sh_last = kt;
-  }
-  __syncthreads();
-  const int kt = *sh_last;
-  double e = 0.0;
-  if (valid && kt != kDeadTile) {
-    const double d = lw - (double)kt * kLn2;
-    if constexpr (sizeof(R) == 4)
-      e = (double)expf((float)d);  // FP32 log-weights: FP32 exponential of an FP64 difference
-    else
-      e = tang_exp(d, A.md.tab);
-  }
-  const double E = block_incl_scan<TPB>(e, sh);
-  if (valid) A.E[nb][i] = E;
-  alive = __syncthreads_or(alive);
-  if (threadIdx.x == TPB - 1) {
-    A.tile_k[t] = kt;
-    A.tile_s[t] = E;
+  // Weights, first per warp as soon as the warp's particles reached the
+  // checkpoint (overlapping the tile's slower warps): the warp's max M_w, its
+  // power-of-two reference k_w = ceil(M_w / ln 2), e_j = exp(logw_j - k_w ln 2)
+  // and e_j 2^54 rounded to an integer.  Then, after the tile barrier, the tile
+  // reference k_t = max k_w, the exact shift of each weight to it, and the
+  // tile's integer running sum E_j (the next segment's search keys).
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long ef = 0;
+  {
+    const double Mw = warp_max_key(lw);
+    const int kw = Mw == -INFINITY ? kDeadTile : tile_exponent(Mw);
+    if (valid && kw != kDeadTile) {
+      const double d = lw - (double)kw * kLn2;
+      double e;
+      if constexpr (sizeof(R) == 4)
+        e = (double)expf((float)d);  // FP32 log-weights: FP32 exponential of an FP64 difference
+      else
+        e = tang_exp(d, A.md.tab);
+      ef = to_fix54(e);
+    }
+    if (lane == 0) sh_kw[wid] = kw;
+    // shift from the warp's reference to the tile's (after the barrier)
+    alive = __syncthreads_or(alive);
+    int kt = sh_kw[0];
+#pragma unroll
+    for (int w = 1; w < TPB / 32; ++w) kt = max(kt, sh_kw[w]);
+    const int shift = kw == kDeadTile ? 64 : kt - kw;
+    if (shift >= 63)
+      ef = 0;
+    else if (shift > 0)
+      ef = (ef + (1ll << (shift - 1))) >> shift;
+    const long long E = block_incl_scan_i64<TPB>(ef, reinterpret_cast<long long*>(sh));
+    if (valid) A.E[nb][i] = E;
+    if (threadIdx.x == TPB - 1) {
+      A.tile_k[t] = kt;
+      A.tile_s[t] = (double)E * 0x1p-54;  // below 2^62: one rounding
+    }
   }
   if (threadIdx.x == 0) A.tile_alive[t] = alive;
   __threadfence();
@@ -306,6 +374,7 @@ __global__ void __launch_bounds__(TPB) wave_kernel(const RunDev* __restrict__ ru
   __shared__ __align__(16) RunDev sr;
   __shared__ double sh[TPB / 32 + 2 + TPB + 1];
   __shared__ int sh_last;
+  __shared__ int sh_kw[TPB / 32];
   const int2 rt = cta_map[blockIdx.x];
   {
     const int* src = reinterpret_cast<const int*>(runs + rt.x);
@@ -313,14 +382,20 @@ __global__ void __launch_bounds__(TPB) wave_kernel(const RunDev* __restrict__ ru
     for (int w = threadIdx.x; w < (int)(sizeof(RunDev) / 4); w += TPB) dst[w] = src[w];
   }
   __syncthreads();
+  // Waves are launched with programmatic stream serialisation: the next wave's
+  // CTAs may start (and copy their run table, which no kernel writes) while
+  // this wave's last CTAs still run; everything below reads what the previous
+  // wave wrote, so it waits for that wave's completion first.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   RunState* rs = sr.rs;
   if (*(volatile int32_t*)&rs->done) return;
   const int k = *(volatile int32_t*)&rs->n_segments;
   switch (sr.md.kind) {
-    case SMC_MODEL_LG: step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last); break;
-    case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last); break;
-    case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last); break;
-    default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last); break;
+    case SMC_MODEL_LG: step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw); break;
+    case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw); break;
+    case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw); break;
+    default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw); break;
   }
 }
 
@@ -456,7 +531,7 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
     A.state[b].real = ws + Ly.real[b];
     A.state[b].ints = (int32_t*)(ws + Ly.ints[b]);
     A.state[b].stack = ws + Ly.stack[b];
-    A.E[b] = (double*)(ws + Ly.E[b]);
+    A.E[b] = (long long*)(ws + Ly.E[b]);
   }
   A.logw = (double*)(ws + Ly.logw);
   A.tile_k = (int32_t*)(ws + Ly.tM);
@@ -482,15 +557,31 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
   return A;
 }
 
+// One bucket of a wave, launched so that it may begin before the kernel ahead
+// of it in the stream has finished (wave_kernel waits for it where it must).
+template <typename R, int TPB>
+cudaError_t launch_pdl(const RunDev* runs, const int2* map, int n, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)n);
+  cfg.blockDim = dim3(TPB);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, wave_kernel<R, TPB>, runs, map);
+}
+
 template <typename R>
 cudaError_t launch_bucket(int b, const RunDev* runs, const int2* map, int n, cudaStream_t st) {
   switch (b) {
-    case 0: wave_kernel<R, 32><<<n, 32, 0, st>>>(runs, map); break;
-    case 1: wave_kernel<R, 64><<<n, 64, 0, st>>>(runs, map); break;
-    case 2: wave_kernel<R, 128><<<n, 128, 0, st>>>(runs, map); break;
-    default: wave_kernel<R, 256><<<n, 256, 0, st>>>(runs, map); break;
+    case 0: return launch_pdl<R, 32>(runs, map, n, st);
+    case 1: return launch_pdl<R, 64>(runs, map, n, st);
+    case 2: return launch_pdl<R, 128>(runs, map, n, st);
+    default: return launch_pdl<R, 256>(runs, map, n, st);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_wave(const WavePlan& W, int precision, cudaStream_t st) {

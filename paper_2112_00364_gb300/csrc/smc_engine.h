@@ -30,7 +30,7 @@ struct RunDev {
   ModelDev md;
   StateView state[2];
   double* logw;       // [N] log-weights of the latest segment (f64; FP32 values widened)
-  double* E[2];       // [N] tile-local inclusive scans, double-buffered by segment parity
+  long long* E[2];    // [N] tile-local running sums of the weights x 2^54 (int64), double-buffered by segment parity
   int32_t* tile_k;    // [n_tiles] power-of-two reference exponent k_t (kDeadTile: all zero)
   double* tile_s;     // [n_tiles]
   int32_t* tile_alive;
