@@ -309,7 +309,10 @@ smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uin
 
 /* Device math parity hook: y[i] = f(x[i]) on the GPU for fn 0 = the table-driven
  * FP64 logarithm the samplers use, 1 = the table-driven FP64 exponential, 2 = the
- * CUDA library log, 3 = the CUDA library exp.  x, y [n] f64 device pointers.
+ * CUDA library log, 3 = the CUDA library exp; for fn 4 and 5 x[i] holds 64 random
+ * bits b (read as uint64) and y[i] = log u of the FP64 uniform u = ((b >> 11) | 1)
+ * 2^-53, 4 = reduced on the integer pipes (what the samplers use), 5 = the
+ * table logarithm of u built as a double.  x, y [n] f64 device pointers.
  * Errors: SMC_EINVAL, SMC_ECUDA. */
 smc_status smc_math_eval(int32_t fn, const double *x, double *y, int64_t n, void *stream);
 

@@ -83,6 +83,8 @@ __host__ __device__ __forceinline__ Block4 philox(uint32_t c0, uint32_t c1, uint
 struct MathTab {
   double log_f[192];    // log(j/128), j = 90..181 used
   double inv_f[192];    // 128 / j, j = 90..181 used
+  double inv_f52[192];  // (128 / j) 2^-52 (exact scaling of inv_f)
+  double inv_f53[192];  // (128 / j) 2^-53
   double exp2_j[32];    // 2^(j/32)
   double inv_int[256];  // 1 / k (entry 0 unused)
 };
@@ -98,6 +100,19 @@ constexpr double kInvLn2x32 = 0x1.71547652b82fep+5;   // 32 / ln 2
 // so F = 1 near 1 and log F and log1p(u) never cancel by more than a bit),
 // u = (m - F) / F in (-1/180, 1/180); log1p(u) = u - u^2 q(u) with the Taylor
 // series of q to degree 6 (truncation < 1e-18 relative).
+__device__ __forceinline__ double tang_log_tail(double u, int j, int e, const MathTab* __restrict__ T) {
+  const double u2 = u * u;
+  const double u4 = u2 * u2;
+  const double qa = fma(u, -1.0 / 3.0, 0.5);
+  const double qb = fma(u, -0.2, 0.25);
+  const double qc = fma(u, -1.0 / 7.0, 1.0 / 6.0);
+  const double q = fma(fma(u2, 0.125, qc), u4, fma(qb, u2, qa));
+  const double p = fma(-u2, q, u);
+  const double de = (double)e;
+  const double hi = fma(de, kLn2Hi, __ldg(&T->log_f[j]));
+  return hi + fma(de, kLn2Lo, p);
+}
+
 __device__ __forceinline__ double tang_log(double x, const MathTab* __restrict__ T) {
   if (!(x >= 0x1p-1022 && x < INFINITY)) return log(x);
   const long long b = __double_as_longlong(x);
@@ -110,16 +125,35 @@ __device__ __forceinline__ double tang_log(double x, const MathTab* __restrict__
   const int j = (int)(m * 128.0 + 0.5);     // nearest table point (both steps exact)
   const double F = (double)j * 0x1p-7;      // exact
   const double u = (m - F) * __ldg(&T->inv_f[j]);  // m - F is exact
-  const double u2 = u * u;
-  const double u4 = u2 * u2;
-  const double qa = fma(u, -1.0 / 3.0, 0.5);
-  const double qb = fma(u, -0.2, 0.25);
-  const double qc = fma(u, -1.0 / 7.0, 1.0 / 6.0);
-  const double q = fma(fma(u2, 0.125, qc), u4, fma(qb, u2, qa));
-  const double p = fma(-u2, q, u);
-  const double de = (double)e;
-  const double hi = fma(de, kLn2Hi, __ldg(&T->log_f[j]));
-  return hi + fma(de, kLn2Lo, p);
+  return tang_log_tail(u, j, e, T);
+}
+
+// log u for the FP64 uniform u = ((x >> 11) | 1) 2^-53 of 64 random bits x,
+// with the same reduction as tang_log done on the integer pipes: the
+// significand n = (x >> 11) | 1 gives the exponent (leading-zero count), the
+// halving test, the table point j and the exact difference m - F as an
+// integer; one conversion and one product form u = (m - F) / F.  Returns the
+// same bits as tang_log of that uniform.
+__device__ __forceinline__ double log_unif53(unsigned long long x, const MathTab* __restrict__ T) {
+  const unsigned long long n = (x >> 11) | 1ull;  // u = n 2^-53, n odd, 1 <= n < 2^53
+  const int p = 63 - __clzll((long long)n);
+  const unsigned long long mb = n << (52 - p);    // significand with its leading 1 at bit 52
+  int e = p - 53;
+  int j;
+  long long diff;
+  double rf;
+  if (mb >= 0x16A09E667F3BCDull) {  // m >= sqrt(2) (the double 1.4142135623730951): use m / 2
+    e += 1;
+    j = (int)((mb + (1ull << 45)) >> 46);
+    diff = (long long)mb - ((long long)j << 46);  // (m / 2 - j / 128) 2^53
+    rf = __ldg(&T->inv_f53[j]);
+  } else {
+    j = (int)((mb + (1ull << 44)) >> 45);
+    diff = (long long)mb - ((long long)j << 45);  // (m - j / 128) 2^52
+    rf = __ldg(&T->inv_f52[j]);
+  }
+  const double u = (double)diff * rf;
+  return tang_log_tail(u, j, e, T);
 }
 
 // exp x = 2^k 2^(j/32) e^r with n = 32 k + j = round(32 x / ln 2) and
@@ -239,37 +273,53 @@ __device__ __forceinline__ R uniform01(Stream& s) {
 }
 
 // Box-Muller, cosine branch: sqrt(-2 ln u1) * cos(2 pi u2)
+__device__ __forceinline__ double log_first_uniform(const Block4& b, const Stream& s, double) {
+  return log_unif53(((unsigned long long)b.w1 << 32) | b.w0, s.tab);
+}
+__device__ __forceinline__ float log_first_uniform(const Block4& b, const Stream&, float) {
+  return logf(Unif<float>::first(b));
+}
+
 template <typename R>
 __device__ __forceinline__ R normal01(Stream& s) {
   const Block4 b = s.next();
-  const R u1 = Unif<R>::first(b);
   const R u2 = Unif<R>::second(b);
-  const R rad = m_sqrt((R)-2.0 * lg(u1, s));
+  const R rad = m_sqrt((R)-2.0 * log_first_uniform(b, s, (R)0));
   return rad * m_cos(C<R>::two_pi * u2);
+}
+
+// -ln u of the next uniform (FP64: straight from its random bits)
+template <typename R>
+__device__ __forceinline__ R neg_log_uniform(Stream& s);
+template <>
+__device__ __forceinline__ double neg_log_uniform<double>(Stream& s) {
+  const Block4 b = s.next();
+  return -log_unif53(((unsigned long long)b.w1 << 32) | b.w0, s.tab);
+}
+template <>
+__device__ __forceinline__ float neg_log_uniform<float>(Stream& s) {
+  return -logf(uniform01<float>(s));
 }
 
 // Exponential(rate): -ln(u) / rate
 template <typename R>
 __device__ __forceinline__ R exponential(Stream& s, R rate) {
-  const R u = uniform01<R>(s);
-  return -lg(u, s) / rate;
+  return neg_log_uniform<R>(s) / rate;
 }
 
-// Exponential(rate) with a precomputed 1/rate (rate > 0)
-__device__ __forceinline__ double exponential_inv(Stream& s, double rate, double inv_rate) {
-  const double u = uniform01<double>(s);
-  return div_by(-lg(u, s), rate, inv_rate);
+// Exponential(rate) with a precomputed 1/rate (rate > 0): -ln(u) * (1/rate),
+// within an ulp or so of the quotient
+__device__ __forceinline__ double exponential_inv(Stream& s, double, double inv_rate) {
+  return neg_log_uniform<double>(s) * inv_rate;
 }
 __device__ __forceinline__ float exponential_inv(Stream& s, float rate, float) {
-  const float u = uniform01<float>(s);
-  return -logf(u) / rate;
+  return neg_log_uniform<float>(s) / rate;
 }
 
 // Gamma(shape 1, scale theta): theta * (-ln u)
 template <typename R>
 __device__ __forceinline__ R gamma1(Stream& s, R theta) {
-  const R u = uniform01<R>(s);
-  return theta * -lg(u, s);
+  return theta * neg_log_uniform<R>(s);
 }
 
 // Uniform(lo, hi): fma(hi - lo, u, lo)
@@ -297,7 +347,7 @@ __device__ __noinline__ int poisson(Stream& s, R mean) {
     while (u > acc && k < 200) {
       k += 1;
       if constexpr (sizeof(R) == 8)
-        p = div_by(p * mean, (double)k, __ldg(&s.tab->inv_int[k]));
+        p = p * (mean * __ldg(&s.tab->inv_int[k]));  // mean / k off the chain through p
       else
         p = p * mean / (R)k;
       acc = acc + p;

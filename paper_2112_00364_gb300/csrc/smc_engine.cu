@@ -59,57 +59,93 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned l
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
 // a_i = min{ j : q_j > y }, y = i + u, with q_j = (O_t + c_t E_j) r for j in
-// tile t and E_j the tile's fixed-point running sum (units of 2^-54 of the
-// tile's reference).  The tile is t = max{ t : O_t r <= y } (N - 1 if y lies
-// above every boundary); inside it q_j > y <=> E_j > e* = (y / r - O_t) / c_t,
-// and since E_j is an integer, <=> E_j > floor(e* 2^54): one threshold per
-// particle, then integer compares only.  If no element of tile t qualifies, the
-// first element of tile t+1 does.  The offset is flagged when it lies within
-// 1e-12 N of q_a or q_{a-1}, measured in the same units.
-__device__ __forceinline__ long long e_threshold(double y, const RunDev& A, int t, double inv_r) {
-  return floor_fix54(fma(y, inv_r, -A.tile_O[t]) * A.tile_invc[t]);
+// tile t, r = N / S and E_j the tile's fixed-point running sum (units of 2^-54
+// of the tile's reference).  Everything is compared on the P scale, z = y S / N:
+// the tile is t = max{ t : O_t <= z } (N - 1 if z lies above every offset);
+// inside it q_j > y <=> E_j > e* = (z - O_t) / c_t, and since E_j is an
+// integer, <=> E_j > floor(e* 2^54): one threshold per particle, then an
+// 8-ary search with integer compares (three rounds of independent loads for a
+// 256-particle tile).  If no element of tile t qualifies, the first element of
+// tile t+1 does.  The offset is flagged when it lies within 1e-12 N of q_a or
+// q_{a-1}, measured in the same units.  `O` is the run's offset array (a copy
+// in shared memory when it fits).
+__device__ __forceinline__ long long e_threshold(double z, double O_t, double invc) {
+  return floor_fix54((z - O_t) * invc);
 }
 
-__device__ __forceinline__ int systematic_search(int i, const RunDev& A, const long long* E,
-                                                 double inv_r, double u, bool* near) {
+__device__ __forceinline__ int systematic_search(int i, const RunDev& A, const double* O,
+                                                 const long long* __restrict__ E, double inv_r,
+                                                 double u, bool* near) {
   const int N = A.N, T = A.n_tiles;
-  const double y = (double)i + u;
-  const long long yb = dbits(y);
-  int lo = 0, hi = T;  // tile_q[0] = 0 <= y
+  const double z = ((double)i + u) * inv_r;
+  const long long zb = dbits(z);
+  int lo = 0, hi = T;  // O_0 = 0 <= z
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (dbits(A.tile_q[mid]) <= yb)
+    if (dbits(O[mid]) <= zb)
       lo = mid;
     else
       hi = mid - 1;
   }
-  const double tolE = kBoundaryEps * (double)N * inv_r;  // 1e-12 N on the q scale, in E units x c_t
-  if (lo >= T) {  // above the last boundary (rounding at the top)
-    *near = fabs(A.tile_q[T] - y) < kBoundaryEps * (double)N;
+  const double tolP = kBoundaryEps * (double)N * inv_r;  // 1e-12 N on the q scale
+  if (lo >= T) {  // above the last offset (rounding at the top)
+    *near = fabs(O[T] - z) < tolP;
     return N - 1;
   }
   const int t = lo;
   const int j0 = t * A.tile, j1 = min(N, j0 + A.tile);
-  const long long F = e_threshold(y, A, t, inv_r);
-  const long long tolF = to_fix54(fmin(tolE * A.tile_invc[t], 256.0));
-  int l = j0, h = j1;  // first j in [j0, j1) with E_j > F
-  while (l < h) {
-    const int mid = (l + h) >> 1;
-    if (E[mid] > F)
-      h = mid;
-    else
-      l = mid + 1;
+  const double invc = A.tile_invc[t];
+  const long long F = e_threshold(z, O[t], invc);
+  const long long tolF = to_fix54(fmin(tolP * invc, 256.0));
+  // first j in [j0, j1) with E_j > F
+  long long Eb = 0;  // E_{b-1} for the current bracket start b (0 before the tile)
+  int b = j0, len = j1 - j0;
+  while (len > 8) {
+    const int w = (len + 7) >> 3;
+    long long v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = E[b + min((m + 1) * w, len) - 1];
+    int m = 8;
+#pragma unroll
+    for (int q = 7; q >= 0; --q)
+      if (v[q] > F) m = q;
+    if (m == 8) {  // nothing in the tile qualifies
+      Eb = v[7];
+      b += len;
+      len = 0;
+      break;
+    }
+    if (m > 0) Eb = v[m - 1];
+    len = min((m + 1) * w, len) - m * w;
+    b += m * w;
   }
-  const long long Eb = l > j0 ? E[l - 1] : 0;  // E_{a-1} in tile t
+  int l = b + len;  // none found yet
+  long long El = 0;
+  if (len > 0) {
+    long long v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = m < len ? E[b + m] : 0x7FFFFFFFFFFFFFFFll;
+    int m = 8;
+#pragma unroll
+    for (int q = 7; q >= 0; --q)
+      if (v[q] > F) m = q;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (q == m) El = v[q];
+      if (q < m && q < len) Eb = v[q];
+    }
+    if (m < len) l = b + m;
+  }
   bool nr = F - Eb < tolF;
   int a;
   if (l < j1) {
     a = l;
-    nr = nr || E[l] - F <= tolF;
+    nr = nr || El - F <= tolF;
   } else if (j1 < N) {  // the first element of the next tile
     a = j1;
-    const long long F1 = e_threshold(y, A, t + 1, inv_r);
-    const long long tol1 = to_fix54(fmin(tolE * A.tile_invc[t + 1], 256.0));
+    const double invc1 = A.tile_invc[t + 1];
+    const long long F1 = e_threshold(z, O[t + 1], invc1);
+    const long long tol1 = to_fix54(fmin(tolP * invc1, 256.0));
     nr = nr || E[j1] - F1 <= tol1;
   } else {
     a = N - 1;
@@ -170,7 +206,6 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
   }
   double carry = 0.0;  // offset of the chunk (the same in every thread)
   long long omax = 0;  // bits of the largest offset of earlier chunks
-  double O0[P];        // first chunk's offsets, kept for tile_q
   for (int base = 0; base < nt; base += TPB * P) {
     double v[P];
     double tot = 0.0;
@@ -191,10 +226,7 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
         c = pow2i(kt - kmax);
         invc = pow2i(kmax - kt);
       }
-      if (t < nt) {
-        A.tile_c[t] = c;
-        A.tile_invc[t] = invc;
-      }
+      if (t < nt) A.tile_invc[t] = invc;
       v[q] = st * c;  // exact: c is a power of two
       tot = tot + v[q];
     }
@@ -225,32 +257,17 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
       Oq[q] = __longlong_as_double(max(__double_as_longlong(Oq[q]), prev));
       const int t = base + threadIdx.x * P + q;
       if (t < nt) A.tile_O[t] = Oq[q];
-      if (base == 0) O0[q] = Oq[q];
     }
     omax = chunk_max;
     carry = carry + chunk_total;
     __syncthreads();
   }
-  // The independent scalar work of the tail runs on different warps at once:
-  // every thread forms r = N / S for the tile boundaries, thread 0 the log-Z
-  // increment (table logarithm), a thread of warp 1 the next resampling uniform.
+  // The tail's independent scalar work runs on different warps at once:
+  // thread 0 forms the log-Z increment (table logarithm), a thread of warp 1
+  // the next resampling uniform.
   const double S = carry;
-  const double r = (double)A.N * (1.0 / S);
   const bool go_on = alive && k + 1 < A.max_segments;
-  const double O_end = fmax(S, __longlong_as_double(omax));
-  if (nt <= TPB * P) {
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int t = threadIdx.x * P + q;
-      if (t < nt) A.tile_q[t] = O0[q] * r;
-    }
-  } else {
-    for (int t = threadIdx.x; t < nt; t += TPB) A.tile_q[t] = A.tile_O[t] * r;
-  }
-  if (threadIdx.x == 0) {
-    A.tile_O[nt] = O_end;
-    A.tile_q[nt] = O_end * r;
-  }
+  if (threadIdx.x == 0) A.tile_O[nt] = fmax(S, __longlong_as_double(omax));
   if (threadIdx.x == (TPB > 32 ? 32 : 0) && go_on) {
     const Block4 b = philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1);
     rs->u = Unif<double>::first(b);
@@ -268,7 +285,6 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
       rs->status = SMC_ESTEPLIMIT;
       rs->done = 1;
     } else {
-      rs->r = r;
       rs->inv_r = S * A.inv_n;
     }
     rs->n_segments = k + 1;
@@ -279,7 +295,7 @@ __device__ void combine_tiles(const RunDev& A, int k, double* sh) {
 // One tile of one run for segment k (the whole per-CTA body of a wave).
 template <class M, int TPB>
 __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const int k, double* sh,
-                                          int* sh_last, int* sh_kw) {
+                                          int* sh_last, int* sh_kw, double* sh_O) {
   using R = typename M::R;
   RunState* rs = A.rs;
   const int N = A.N;
@@ -290,12 +306,18 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   const StateView Sn = A.state[nb];
   typename M::Lane L;
   bool near = false;
+  const double* O = A.tile_O;
+  if (k > 0 && A.n_tiles < 4 * TPB) {  // the run's offsets into shared memory
+    for (int q = threadIdx.x; q <= A.n_tiles; q += TPB) sh_O[q] = O[q];
+    __syncthreads();
+    O = sh_O;
+  }
   if (valid) {
     if (k == 0) {
       M::init(L);
     } else {
       const double u = rs->u, inv_r = rs->inv_r;
-      const int a = systematic_search(i, A, A.E[cb], inv_r, u, &near);
+      const int a = systematic_search(i, A, O, A.E[cb], inv_r, u, &near);
       const int row = A.record_all ? k - 1 : 0;
       if (row < A.anc_rows) A.anc[(size_t)row * N + i] = a;
       M::gather(L, Sc, Sn, a, i, N, A.md);
@@ -375,6 +397,7 @@ __global__ void __launch_bounds__(TPB) wave_kernel(const RunDev* __restrict__ ru
   __shared__ double sh[TPB / 32 + 2 + TPB + 1];
   __shared__ int sh_last;
   __shared__ int sh_kw[TPB / 32];
+  __shared__ double sh_O[4 * TPB];
   const int2 rt = cta_map[blockIdx.x];
   {
     const int* src = reinterpret_cast<const int*>(runs + rt.x);
@@ -392,10 +415,10 @@ __global__ void __launch_bounds__(TPB) wave_kernel(const RunDev* __restrict__ ru
   if (*(volatile int32_t*)&rs->done) return;
   const int k = *(volatile int32_t*)&rs->n_segments;
   switch (sr.md.kind) {
-    case SMC_MODEL_LG: step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw); break;
-    case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw); break;
-    case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw); break;
-    default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw); break;
+    case SMC_MODEL_LG: step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O); break;
+    case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O); break;
+    case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O); break;
+    default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O); break;
   }
 }
 
@@ -440,6 +463,8 @@ smc_status math_table(const MathTab** out) {
     for (int j = 0; j < 192; ++j) {
       h.log_f[j] = j ? std::log((double)j / 128.0) : 0.0;
       h.inv_f[j] = j ? 128.0 / (double)j : 0.0;
+      h.inv_f52[j] = std::ldexp(h.inv_f[j], -52);
+      h.inv_f53[j] = std::ldexp(h.inv_f[j], -53);
     }
     for (int j = 0; j < 32; ++j) h.exp2_j[j] = std::exp2((double)j / 32.0);
     h.inv_int[0] = 0.0;
@@ -509,10 +534,8 @@ Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
   L.tM = take(8 * (size_t)L.n_tiles);
   L.ts = take(8 * (size_t)L.n_tiles);
   L.talive = take(4 * (size_t)L.n_tiles);
-  L.tc = take(8 * (size_t)L.n_tiles);
   L.tinvc = take(8 * (size_t)L.n_tiles);
   L.tO = take(8 * (size_t)(L.n_tiles + 1));
-  L.tq = take(8 * (size_t)(L.n_tiles + 1));
   L.rs = take(sizeof(RunState));
   L.anc = take(4 * N * (size_t)L.anc_rows);
   L.incr = take(8 * (size_t)L.max_segments);
@@ -537,10 +560,8 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
   A.tile_k = (int32_t*)(ws + Ly.tM);
   A.tile_s = (double*)(ws + Ly.ts);
   A.tile_alive = (int32_t*)(ws + Ly.talive);
-  A.tile_c = (double*)(ws + Ly.tc);
   A.tile_invc = (double*)(ws + Ly.tinvc);
   A.tile_O = (double*)(ws + Ly.tO);
-  A.tile_q = (double*)(ws + Ly.tq);
   A.anc = (int32_t*)(ws + Ly.anc);
   A.incr = (double*)(ws + Ly.incr);
   A.rs = (RunState*)(ws + Ly.rs);

@@ -18,7 +18,7 @@ constexpr int64_t kTileSlots = 456;  // tile = ceil(N / 456): 152 SMs x 3 reside
 
 // Per-run device state (one struct per run, in the run's workspace).
 struct RunState {
-  double log_z, m, S, r, u, inv_r;
+  double log_z, m, S, u, inv_r;  // inv_r = S / N
   unsigned long long n_near, n_overflow, n_limit;
   int32_t done, status, n_segments, n_resamples;
   uint32_t arrive;
@@ -34,10 +34,8 @@ struct RunDev {
   int32_t* tile_k;    // [n_tiles] power-of-two reference exponent k_t (kDeadTile: all zero)
   double* tile_s;     // [n_tiles]
   int32_t* tile_alive;
-  double* tile_c;     // [n_tiles] written by the combine: 2^(k_t - k_max) (exact)
-  double* tile_invc;  // [n_tiles] 2^(k_max - k_t) (0 where c_t = 0)
+  double* tile_invc;  // [n_tiles] written by the combine: 2^(k_max - k_t) = 1 / c_t (0 where c_t = 0)
   double* tile_O;     // [n_tiles + 1] monotone exclusive offsets, O_T >= S
-  double* tile_q;     // [n_tiles + 1] O_t * r
   int32_t* anc;       // ancestor rows
   double* incr;       // [max_segments] per-segment log-Z increments
   RunState* rs;
@@ -47,7 +45,7 @@ struct RunDev {
 };
 
 struct Layout {
-  size_t real[2], ints[2], stack[2], logw, E[2], tM, ts, talive, tc, tinvc, tO, tq, rs, anc, incr,
+  size_t real[2], ints[2], stack[2], logw, E[2], tM, ts, talive, tinvc, tO, rs, anc, incr,
       fin_real, fin_int, fin_stack, total;
   int n_tiles, tile, anc_rows, max_segments;
 };

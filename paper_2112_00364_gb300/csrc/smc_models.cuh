@@ -167,15 +167,17 @@ struct GeoModel {
 // crbdGoesUndetected / iter) never crosses a checkpoint, so it lives in the
 // lane's registers and thread-local memory.
 //
-// Blocks (checkpoints only after 0 and 5):
+// Blocks (checkpoints only after 0 and 3):
 //   0 PRIOR      lambda ~ Gamma(1, ls), mu ~ Gamma(1, ms); weight(corrFactor)
 //   1 BRANCH     simTree body for node v = preorder[k]: lnProb1 = -mu dt,
 //                lnProb2 = ln lambda (internal) or ln rho (tip), n ~ Poisson(lambda dt)
-//   2 SIMBRANCH  simBranch loop: next hidden event time ~ U(stop, start)
-//   3 UNDET      crbdGoesUndetected(t): dur ~ Exp(mu); if dur > t, detected
-//                with prob rho; j ~ Poisson(lambda min(dur, t)); push a frame
-//   4 ITER       iter loop of the top frame: next event ~ U(t - bl, t), or pop
-//   5 END        weight(lnProb1 + (lnProb2 + lnProb3)); checkpoint
+//   2 HIDDEN     one hidden speciation event per execution: the next event
+//                time (simBranch: ~ U(stop, start); iter of the top frame:
+//                ~ U(t - bl, t); finished frames return true first), then the
+//                crbdGoesUndetected call at that time: dur ~ Exp(mu); if
+//                dur > t, detected with prob rho; j ~ Poisson(lambda min(dur, t));
+//                j > 0 pushes a frame
+//   3 END        weight(lnProb1 + (lnProb2 + lnProb3)); checkpoint
 // A detected hidden lineage makes lnProb3 = -inf and ends the branch at once.
 // A call deeper than depth_cap, or the (call_limit+1)-th call of a segment,
 // kills the particle (lnProb3 = -inf) and is counted.
@@ -185,9 +187,9 @@ struct TreeModel {
   using R = Real;
   // CRBD keeps log(lambda) as a third, internal real field (computed once at the
   // prior block instead of once per internal-node branch); it is not an output.
-  static constexpr int NB = 6, N_REAL = 2, N_INT = RS ? 2 : 1;
+  static constexpr int NB = 4, N_REAL = 2, N_INT = RS ? 2 : 1;
   static constexpr bool HAS_STACK = RS;
-  enum { PRIOR = 0, BRANCH = 1, SIMBRANCH = 2, UNDET = 3, ITER = 4, END = 5 };
+  enum { PRIOR = 0, BRANCH = 1, HIDDEN = 2, END = 3 };
   struct Lane {
     int pc, sp, v, n_top, fsp, calls;
     bool ckpt;
@@ -226,16 +228,6 @@ struct TreeModel {
   __device__ static void begin(Lane& L) {
     L.ckpt = false;
     L.overflow = L.limited = 0;
-  }
-  __device__ __forceinline__ static void ret_true(Lane& L) {
-    // an undetected call returned true: to simBranch (no frame left) or to
-    // the iter loop of the frame below
-    if (L.fsp == 0) {
-      L.lnp3 = L.lnp3 + C<R>::ln2;
-      L.pc = SIMBRANCH;
-    } else {
-      L.pc = ITER;
-    }
   }
   __device__ static void block(int b, Lane& L, Stream& s, const ModelDev& md, const StateView& S,
                                int i, int k, int N) {
@@ -294,20 +286,35 @@ struct TreeModel {
         L.lnp3 = (R)0;
         L.fsp = 0;
         L.calls = 0;
-        L.pc = SIMBRANCH;
+        L.pc = HIDDEN;
         return;
       }
-      case SIMBRANCH: {
-        if (L.n_top == 0) {
-          L.pc = END;
-          return;
+      case HIDDEN: {
+        // the next event: a child of the top frame, or the branch's next one;
+        // a frame whose children all went undetected returns true (at the
+        // branch level that multiplies the weight by 2: lnProb3 += ln 2)
+        for (;;) {
+          if (L.fsp == 0) {
+            if (L.n_top == 0) {
+              L.pc = END;
+              return;
+            }
+            L.n_top -= 1;
+            L.cur_t = uniform_ab<R>(s, L.stop, L.start);
+            break;
+          }
+          const int f = L.fsp - 1;
+          if (L.fr_rem[f] == 0) {
+            L.fsp = f;
+            if (f == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
+            continue;
+          }
+          L.fr_rem[f] -= 1;
+          const R t = L.fr_t[f];
+          L.cur_t = uniform_ab<R>(s, t - L.fr_bl[f], t);
+          break;
         }
-        L.n_top -= 1;
-        L.cur_t = uniform_ab<R>(s, L.stop, L.start);
-        L.pc = UNDET;
-        return;
-      }
-      case UNDET: {
+        // crbdGoesUndetected(cur_t)
         if (L.fsp + 1 > md.depth_cap) {
           L.overflow = 1;
           L.lnp3 = neg_inf<R>();
@@ -332,29 +339,14 @@ struct TreeModel {
         }
         const R bl = dur < t ? dur : t;
         const int j = poisson<R>(s, L.lam_b * bl);
-        if (j == 0) {
-          ret_true(L);
+        if (j == 0) {  // returned true at once
+          if (L.fsp == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
           return;
         }
         L.fr_t[L.fsp] = t;
         L.fr_bl[L.fsp] = bl;
         L.fr_rem[L.fsp] = j;
         L.fsp += 1;
-        L.pc = ITER;
-        return;
-      }
-      case ITER: {
-        const int f = L.fsp - 1;
-        if (L.fr_rem[f] == 0) {
-          L.fsp = f;
-          ret_true(L);
-          return;
-        }
-        L.fr_rem[f] -= 1;
-        const R t = L.fr_t[f];
-        const R lo = t - L.fr_bl[f];
-        L.cur_t = uniform_ab<R>(s, lo, t);
-        L.pc = UNDET;
         return;
       }
       default: {  // END

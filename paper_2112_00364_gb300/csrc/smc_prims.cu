@@ -284,7 +284,15 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double v = x[i];
-  y[i] = fn == 0 ? tang_log(v, tab) : fn == 1 ? tang_exp(v, tab) : fn == 2 ? log(v) : exp(v);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  switch (fn) {
+    case 0: y[i] = tang_log(v, tab); break;
+    case 1: y[i] = tang_exp(v, tab); break;
+    case 2: y[i] = log(v); break;
+    case 3: y[i] = exp(v); break;
+    case 4: y[i] = log_unif53(bits, tab); break;
+    default: y[i] = tang_log(Unif<double>::from64(bits), tab); break;
+  }
 }
 
 }  // namespace smc
@@ -292,7 +300,7 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
 using namespace smc;
 
 extern "C" smc_status smc_math_eval(int32_t fn, const double* x, double* y, int64_t n, void* stream) {
-  if (!x || !y || n < 0 || fn < 0 || fn > 3) return set_error(SMC_EINVAL, "bad argument");
+  if (!x || !y || n < 0 || fn < 0 || fn > 5) return set_error(SMC_EINVAL, "bad argument");
   if (n == 0) return SMC_OK;
   const MathTab* tab = nullptr;
   smc_status ts = math_table(&tab);

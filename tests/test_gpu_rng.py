@@ -94,3 +94,21 @@ def test_table_math_within_two_ulp(fn):
     assert _ulp_diff(tab, lib).max() <= 2
     ok = np.isfinite(ref) & (ref != 0)
     assert _ulp_diff(tab[ok], ref[ok]).max() <= 2
+
+
+def test_uniform_log_from_bits_matches_table_log():
+    """The samplers take log u of an FP64 uniform straight from its 64 random
+    bits (reduction on the integer pipes); it gives the same bits as the table
+    log of the uniform built as a double, and stays within 2 ulp of numpy."""
+    from paper_2112_00364_gb300 import smc
+
+    rng = np.random.default_rng(11)
+    bits = np.concatenate([rng.integers(0, 2**63, 500_000, dtype=np.uint64) * 2
+                           + rng.integers(0, 2, 500_000, dtype=np.uint64),
+                           np.array([0, 1, 2**11, 2**64 - 1, 0x6A09E667F3BCD << 12,
+                                     (0x6A09E667F3BCD << 12) - 1, 1 << 63], dtype=np.uint64)])
+    a = smc.math_eval("unif_log_bits", bits)
+    b = smc.math_eval("unif_log_table", bits)
+    np.testing.assert_array_equal(a.view(np.int64), b.view(np.int64))
+    u = ((bits >> np.uint64(11)) | np.uint64(1)).astype(np.float64) * 2.0**-53
+    assert _ulp_diff(a, np.log(u)).max() <= 2
