@@ -54,49 +54,232 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned l
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
 }
 
-// Non-negative doubles order like their bit patterns read as int64, so the
-// tile search compares bits on the integer pipes.
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// A tile record written by another CTA of the previous segment (one 16-byte
+// load at L2, past the L1).
+__device__ __forceinline__ TileRec load_rec(const TileRec* p) {
+  const longlong2 v = __ldcg(reinterpret_cast<const longlong2*>(p));
+  TileRec r;
+  r.s = v.x;
+  r.k = (int32_t)(v.y & 0xffffffffll);
+  r.alive = (int32_t)(v.y >> 32);
+  return r;
+}
 
-// a_i = min{ j : q_j > y }, y = i + u, with q_j = (O_t + c_t E_j) r for j in
-// tile t, r = N / S and E_j the tile's fixed-point running sum (units of 2^-54
-// of the tile's reference).  Everything is compared on the P scale, z = y S / N:
-// the tile is t = max{ t : O_t <= z } (N - 1 if z lies above every offset);
-// inside it q_j > y <=> E_j > e* = (z - O_t) / c_t, and since E_j is an
-// integer, <=> E_j > floor(e* 2^54): one threshold per particle, then an
+// ---------------------------------------------------------------------------
+// Offsets.  A tile's record holds its exact running-sum total s_t in units of
+// 2^-54 of its reference 2^k_t.  The combine of a segment brings every total
+// to the run's reference 2^k_max and one common unit U = 2^(k_max - 54 + G):
+// v_t = round(s_t / 2^(k_max - k_t + G)), with the coarsening G >= 0 the
+// smallest that keeps the sum below 2^62 (from a bound on it: each tile's
+// total is below 2^(62 - (k_max - k_t))).  The offsets O_t = sum_{t' < t} v_t'
+// and S = O_T are then exact integers, non-decreasing by construction, and the
+// same in whatever order they are summed.  Rounding costs at most half a unit
+// per tile, and since the tile that holds the largest weight has s >= 2^53,
+// G is at most 10 bits more than the sum needs: S is within n_tiles 2^-52 of
+// the exact sum of the weights.
+// ---------------------------------------------------------------------------
+
+// floor(x) as int64 for finite x >= 0 (LLONG_MAX from 2^63 up); -1 for x < 0.
+__device__ __forceinline__ long long floor_i64(double x) {
+  const long long b = __double_as_longlong(x);
+  if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return 0;
+  if (b < 0) return -1;
+  const int e = (int)(b >> 52);
+  if (e < 1023) return 0;
+  if (e >= 1023 + 63) return 0x7FFFFFFFFFFFFFFFll;
+  const long long m = (b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll;
+  const int sh = e - 1075;  // x = m 2^sh
+  return sh >= 0 ? (m << sh) : (m >> -sh);
+}
+
+// x << sh for x >= 0, saturating at LLONG_MAX
+__device__ __forceinline__ long long shl_sat(long long x, int sh) {
+  if (x == 0) return 0;
+  if (sh >= 63 || x > (0x7FFFFFFFFFFFFFFFll >> sh)) return 0x7FFFFFFFFFFFFFFFll;
+  return x << sh;
+}
+
+// the tile total in the run's unit U: round(s / 2^(k_max - k_t + G))
+__device__ __forceinline__ long long to_run_units(long long s, int kt, int kmax, int G) {
+  if (kt == kDeadTile) return 0;
+  const int sh = kmax - kt + G;
+  if (sh >= 63) return 0;
+  if (sh == 0) return s;
+  return (s + (1ll << (sh - 1))) >> sh;
+}
+
+// one tile's share of the bound on the sum (units of 2^52 U at G = 0)
+__device__ __forceinline__ int bound_share(int kt, int kmax) {
+  if (kt == kDeadTile) return 0;
+  const int d = kmax - kt;
+  return d > 10 ? 1 : (1 << (10 - d));
+}
+
+template <int TPB>
+__device__ __forceinline__ int block_sum_int(int v, int* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = __reduce_add_sync(0xffffffffu, v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  int r = 0;
+#pragma unroll
+  for (int w = 0; w < TPB / 32; ++w) r += sh[w];
+  return r;
+}
+
+struct Combined {
+  long long S;  // total in units U
+  int kmax, G, alive;
+};
+
+// Combine n_tiles tile records into the offsets O[0..nt] (O[nt] = S).  With
+// `ks` non-NULL the records are first staged in shared memory (k_t into ks,
+// s_t into O, which the offsets then overwrite); otherwise they are read from
+// `rec` on each pass.  Every thread of the CTA calls it; all integer work.
+template <int TPB>
+__device__ Combined combine_offsets(const TileRec* rec, int nt, long long* O, int* ks, double* sh) {
+  constexpr int P = 4;  // consecutive tiles per thread per chunk
+  int* shi = reinterpret_cast<int*>(sh);
+  long long* shl = reinterpret_cast<long long*>(sh);
+  int kl = kDeadTile, al = 0;
+  for (int q = threadIdx.x; q < nt; q += TPB) {
+    const TileRec r = load_rec(rec + q);
+    if (ks) {
+      ks[q] = r.k;
+      O[q] = r.s;
+    }
+    kl = max(kl, r.k);
+    al |= r.alive;
+  }
+  Combined c;
+  c.kmax = block_max_int<TPB>(kl, shi);
+  c.alive = __syncthreads_or(al);
+  c.G = 0;
+  c.S = 0;
+  if (c.kmax == kDeadTile) return c;
+  int bl = 0;
+  for (int q = threadIdx.x; q < nt; q += TPB) bl += bound_share(ks ? ks[q] : load_rec(rec + q).k, c.kmax);
+  const int b = block_sum_int<TPB>(bl, shi);  // >= 1024: the tile of the largest weight
+  c.G = max(0, (32 - __clz(b - 1)) - 10);
+  long long carry = 0;
+  for (int base = 0; base < nt; base += TPB * P) {
+    long long v[P];
+    long long tot = 0;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int t = base + threadIdx.x * P + q;
+      v[q] = 0;
+      if (t < nt) {
+        long long st;
+        int kt;
+        if (ks) {
+          st = O[t];
+          kt = ks[t];
+        } else {
+          const TileRec r = load_rec(rec + t);
+          st = r.s;
+          kt = r.k;
+        }
+        v[q] = to_run_units(st, kt, c.kmax, c.G);
+      }
+      tot += v[q];
+    }
+    const long long incl = block_incl_scan_i64<TPB>(tot, shl);
+    long long off = carry + (incl - tot);
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int t = base + threadIdx.x * P + q;
+      if (t < nt) O[t] = off;
+      off += v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == TPB - 1) shl[0] = incl;
+    __syncthreads();
+    carry += shl[0];
+    __syncthreads();
+  }
+  c.S = carry;
+  if (threadIdx.x == 0) O[nt] = carry;
+  __syncthreads();
+  return c;
+}
+
+// Finish segment k-1 of the run from its combined offsets (one thread):
+// log Z += k_max ln 2 + (log S - log N) with S = S_units U, the increment
+// record, and the end of the run.  Returns whether segment k runs.
+__device__ __forceinline__ bool finish_segment(const RunDev& A, int k, const Combined& c) {
+  RunState* rs = A.rs;
+  if (c.kmax == kDeadTile) {
+    rs->log_z = -INFINITY;
+    rs->m = -INFINITY;
+    rs->S = 0.0;
+    A.incr[k - 1] = -INFINITY;
+    rs->status = SMC_EDEGENERATE;
+    rs->done = 1;
+    rs->n_segments = k;
+    return false;
+  }
+  const double Sd = (double)c.S;
+  const double inc = (double)(c.kmax - 54 + c.G) * kLn2 + (tang_log(Sd, A.md.tab) - A.log_n);
+  rs->log_z = rs->log_z + inc;
+  A.incr[k - 1] = inc;
+  rs->m = (double)c.kmax * kLn2;
+  rs->S = Sd * pow2i(c.G - 54);
+  rs->n_segments = k;
+  const bool go_on = c.alive && k < A.max_segments;
+  if (!c.alive) {
+    rs->done = 1;
+  } else if (!go_on) {
+    rs->status = SMC_ESTEPLIMIT;
+    rs->done = 1;
+  }
+  return go_on;
+}
+
+// What the search of segment k needs about segment k-1's weights.
+struct SearchCtx {
+  const long long* O;  // offsets in units U, O[T] = S
+  const int* ks;       // tile reference exponents (shared memory), or NULL: read the records
+  const TileRec* rec;
+  int kmax, G;
+  double inv_r;        // S / N in units U
+  double u;            // the resampling uniform
+  long long tolZ;      // 1e-12 N on the q scale, in units U
+};
+
+// a_i = min{ j : q_j > y } for y = i + u, with q_j = P_j N / S and P_j the
+// running sum of the weights; on the P scale in units U, z = y S / N.  The tile
+// is t = max{ t : O_t <= z } (N - 1 if z lies above every offset); inside it
+// P_j = O_t + E_j 2^-(k_max - k_t + G), so P_j > z <=> E_j > floor((z - O_t)
+// 2^(k_max - k_t + G)) (E_j is an integer): one threshold per particle, then an
 // 8-ary search with integer compares (three rounds of independent loads for a
 // 256-particle tile).  If no element of tile t qualifies, the first element of
 // tile t+1 does.  The offset is flagged when it lies within 1e-12 N of q_a or
-// q_{a-1}, measured in the same units.  `O` is the run's offset array (a copy
-// in shared memory when it fits).
-__device__ __forceinline__ long long e_threshold(double z, double O_t, double invc) {
-  return floor_fix54((z - O_t) * invc);
-}
-
-__device__ __forceinline__ int systematic_search(int i, const RunDev& A, const double* O,
-                                                 const long long* __restrict__ E, double inv_r,
-                                                 double u, bool* near) {
+// q_{a-1}, measured in the same units.
+__device__ __forceinline__ int systematic_search(int i, const RunDev& A, const SearchCtx& X,
+                                                 const long long* __restrict__ E, bool* near) {
   const int N = A.N, T = A.n_tiles;
-  const double z = ((double)i + u) * inv_r;
-  const long long zb = dbits(z);
+  const double z = ((double)i + X.u) * X.inv_r;
+  const long long Z = floor_i64(z);
   int lo = 0, hi = T;  // O_0 = 0 <= z
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (dbits(O[mid]) <= zb)
+    if (X.O[mid] <= Z)
       lo = mid;
     else
       hi = mid - 1;
   }
-  const double tolP = kBoundaryEps * (double)N * inv_r;  // 1e-12 N on the q scale
   if (lo >= T) {  // above the last offset (rounding at the top)
-    *near = fabs(O[T] - z) < tolP;
+    *near = Z - X.O[T] < X.tolZ;
     return N - 1;
   }
   const int t = lo;
   const int j0 = t * A.tile, j1 = min(N, j0 + A.tile);
-  const double invc = A.tile_invc[t];
-  const long long F = e_threshold(z, O[t], invc);
-  const long long tolF = to_fix54(fmin(tolP * invc, 256.0));
+  const int kt = X.ks ? X.ks[t] : load_rec(X.rec + t).k;
+  const int sh = X.kmax - kt + X.G;
+  const long long F = floor_i64((z - (double)X.O[t]) * pow2i(min(sh, 1000)));
+  const long long tolF = shl_sat(X.tolZ, sh);
   // first j in [j0, j1) with E_j > F
   long long Eb = 0;  // E_{b-1} for the current bracket start b (0 before the tile)
   int b = j0, len = j1 - j0;
@@ -143,10 +326,7 @@ __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const d
     nr = nr || El - F <= tolF;
   } else if (j1 < N) {  // the first element of the next tile
     a = j1;
-    const double invc1 = A.tile_invc[t + 1];
-    const long long F1 = e_threshold(z, O[t + 1], invc1);
-    const long long tol1 = to_fix54(fmin(tolP * invc1, 256.0));
-    nr = nr || E[j1] - F1 <= tol1;
+    nr = nr || X.O[t + 1] - Z <= X.tolZ;
   } else {
     a = N - 1;
   }
@@ -154,148 +334,10 @@ __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const d
   return a;
 }
 
-// The run's last CTA of a segment: combine the tile reductions (all FP64).
-// Thread p owns the kCombineP consecutive tiles p*P.. of each chunk of TPB*P
-// tiles: it forms their c_t v_t and offsets by sequential additions (so they
-// are non-decreasing within the thread), one block scan of the thread totals
-// places the threads, and an integer prefix max over the offsets' bit patterns
-// keeps them non-decreasing across thread seams.  `sh` holds >= TPB + 2 doubles.
-constexpr int kCombineP = 4;
-
-template <int TPB>
-__device__ void combine_tiles(const RunDev& A, int k, double* sh) {
-  constexpr int P = kCombineP;
-  RunState* rs = A.rs;
-  const int nt = A.n_tiles;
-  long long* shl = reinterpret_cast<long long*>(sh);
-  // first chunk's tile values stay in registers
-  int kt0[P];
-  double s0[P];
-  int kloc = kDeadTile;
-  int alive = 0;
-#pragma unroll
-  for (int q = 0; q < P; ++q) {
-    const int t = threadIdx.x * P + q;
-    kt0[q] = kDeadTile;
-    s0[q] = 0.0;
-    if (t < nt) {
-      kt0[q] = __ldcg(A.tile_k + t);
-      s0[q] = __ldcg(A.tile_s + t);
-      alive |= __ldcg(A.tile_alive + t);
-    }
-    kloc = max(kloc, kt0[q]);
-  }
-  for (int t = TPB * P + threadIdx.x; t < nt; t += TPB) {
-    kloc = max(kloc, __ldcg(A.tile_k + t));
-    alive |= __ldcg(A.tile_alive + t);
-  }
-  const int kmax = block_max_int<TPB>(kloc, reinterpret_cast<int*>(sh));
-  alive = __syncthreads_or(alive);
-  if (kmax == kDeadTile) {
-    if (threadIdx.x == 0) {
-      rs->log_z = -INFINITY;
-      rs->m = -INFINITY;
-      rs->S = 0.0;
-      A.incr[k] = -INFINITY;
-      rs->status = SMC_EDEGENERATE;
-      rs->n_segments = k + 1;
-      rs->done = 1;
-      rs->arrive = 0;
-    }
-    return;
-  }
-  double carry = 0.0;  // offset of the chunk (the same in every thread)
-  long long omax = 0;  // bits of the largest offset of earlier chunks
-  for (int base = 0; base < nt; base += TPB * P) {
-    double v[P];
-    double tot = 0.0;
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int t = base + threadIdx.x * P + q;
-      int kt = kDeadTile;
-      double st = 0.0;
-      if (base == 0) {
-        kt = kt0[q];
-        st = s0[q];
-      } else if (t < nt) {
-        kt = __ldcg(A.tile_k + t);
-        st = __ldcg(A.tile_s + t);
-      }
-      double c = 0.0, invc = 0.0;
-      if (kt != kDeadTile && kt - kmax >= -1022) {
-        c = pow2i(kt - kmax);
-        invc = pow2i(kmax - kt);
-      }
-      if (t < nt) A.tile_invc[t] = invc;
-      v[q] = st * c;  // exact: c is a power of two
-      tot = tot + v[q];
-    }
-    const double incl = block_incl_scan<TPB>(tot, sh);
-    __syncthreads();
-    sh[threadIdx.x + 1] = incl;
-    __syncthreads();
-    double O = carry + (threadIdx.x ? sh[threadIdx.x] : 0.0);
-    const double chunk_total = sh[TPB];
-    double Oq[P];
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      Oq[q] = O;
-      O = O + v[q];
-    }
-    // seams: every offset at least the largest offset before it
-    __syncthreads();
-    const long long last = max(__double_as_longlong(Oq[P - 1]), omax);
-    const long long incl_m = block_incl_max_i64<TPB>(last, shl);
-    __syncthreads();
-    shl[threadIdx.x + 1] = incl_m;
-    if (threadIdx.x == 0) shl[0] = omax;
-    __syncthreads();
-    const long long prev = shl[threadIdx.x];
-    const long long chunk_max = shl[TPB];
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      Oq[q] = __longlong_as_double(max(__double_as_longlong(Oq[q]), prev));
-      const int t = base + threadIdx.x * P + q;
-      if (t < nt) A.tile_O[t] = Oq[q];
-    }
-    omax = chunk_max;
-    carry = carry + chunk_total;
-    __syncthreads();
-  }
-  // The tail's independent scalar work runs on different warps at once:
-  // thread 0 forms the log-Z increment (table logarithm), a thread of warp 1
-  // the next resampling uniform.
-  const double S = carry;
-  const bool go_on = alive && k + 1 < A.max_segments;
-  if (threadIdx.x == 0) A.tile_O[nt] = fmax(S, __longlong_as_double(omax));
-  if (threadIdx.x == (TPB > 32 ? 32 : 0) && go_on) {
-    const Block4 b = philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1);
-    rs->u = Unif<double>::first(b);
-  }
-  if (threadIdx.x == 0) {
-    const double m = (double)kmax * kLn2;
-    const double inc = m + (tang_log(S, A.md.tab) - A.log_n);
-    rs->log_z = rs->log_z + inc;
-    A.incr[k] = inc;
-    rs->m = m;
-    rs->S = S;
-    if (!alive) {
-      rs->done = 1;
-    } else if (!go_on) {
-      rs->status = SMC_ESTEPLIMIT;
-      rs->done = 1;
-    } else {
-      rs->inv_r = S * A.inv_n;
-    }
-    rs->n_segments = k + 1;
-    rs->arrive = 0;
-  }
-}
-
 // One tile of one run for segment k (the whole per-CTA body of a wave).
 template <class M, int TPB>
 __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const int k, double* sh,
-                                          int* sh_last, int* sh_kw, double* sh_O) {
+                                          int* sh_last, int* sh_kw, long long* sh_O, int* sh_ks) {
   using R = typename M::R;
   RunState* rs = A.rs;
   const int N = A.N;
@@ -304,26 +346,52 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   const int nb = k & 1, cb = nb ^ 1;
   const StateView Sc = A.state[cb];
   const StateView Sn = A.state[nb];
+  const bool redundant = A.n_tiles < redundant_cap(TPB);
   typename M::Lane L;
   bool near = false;
-  const double* O = A.tile_O;
-  if (k > 0 && A.n_tiles < 4 * TPB) {  // the run's offsets into shared memory
-    for (int q = threadIdx.x; q <= A.n_tiles; q += TPB) sh_O[q] = O[q];
-    __syncthreads();
-    O = sh_O;
-  }
-  if (valid) {
-    if (k == 0) {
-      M::init(L);
+  if (k > 0) {
+    SearchCtx X;
+    X.rec = A.rec[cb];
+    if (redundant) {
+      const Combined c = combine_offsets<TPB>(A.rec[cb], A.n_tiles, sh_O, sh_ks, sh);
+      const bool go_on = c.kmax != kDeadTile && c.alive && k < A.max_segments;
+      if (t == 0 && threadIdx.x == 0) finish_segment(A, k, c);
+      if (!go_on) return;
+      // the run's scalars by one warp (FP64 work costs the whole SM's FP64 pipe)
+      double* shx = sh + TPB / 32 + 1;
+      if (threadIdx.x == 0) {
+        const double Sd = (double)c.S;
+        shx[0] = Sd * A.inv_n;
+        shx[1] = Unif<double>::first(philox(0u, (uint32_t)(k - 1), 0u, 1u, A.k0, A.k1));
+        reinterpret_cast<long long*>(shx)[2] = floor_i64(kBoundaryEps * Sd);
+      }
+      __syncthreads();
+      X.O = sh_O;
+      X.ks = sh_ks;
+      X.kmax = c.kmax;
+      X.G = c.G;
+      X.inv_r = shx[0];
+      X.u = shx[1];
+      X.tolZ = reinterpret_cast<long long*>(shx)[2];
     } else {
-      const double u = rs->u, inv_r = rs->inv_r;
-      const int a = systematic_search(i, A, O, A.E[cb], inv_r, u, &near);
+      X.O = A.tile_O;
+      X.ks = nullptr;
+      X.kmax = rs->kmax;
+      X.G = rs->G;
+      X.inv_r = rs->inv_r;
+      X.u = rs->u;
+      X.tolZ = rs->tolZ;
+    }
+    if (valid) {
+      const int a = systematic_search(i, A, X, A.E[cb], &near);
       const int row = A.record_all ? k - 1 : 0;
       if (row < A.anc_rows) A.anc[(size_t)row * N + i] = a;
       M::gather(L, Sc, Sn, a, i, N, A.md);
     }
+    warp_add_u64(&rs->n_near, near ? 1ull : 0ull);
+  } else if (valid) {
+    M::init(L);
   }
-  if (k > 0) warp_add_u64(&rs->n_near, near ? 1ull : 0ull);
   Stream s{A.k0, A.k1, (uint32_t)i, (uint32_t)k, 0u, 0u, A.md.tab};
   const bool active = valid && L.pc != PC_STOP;
   run_segment<M>(L, s, A.md, Sn, i, k, N, active);
@@ -345,37 +413,37 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   // tile's integer running sum E_j (the next segment's search keys).
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long long ef = 0;
-  {
-    const double Mw = warp_max_key(lw);
-    const int kw = Mw == -INFINITY ? kDeadTile : tile_exponent(Mw);
-    if (valid && kw != kDeadTile) {
-      const double d = lw - (double)kw * kLn2;
-      double e;
-      if constexpr (sizeof(R) == 4)
-        e = (double)expf((float)d);  // FP32 log-weights: FP32 exponential of an FP64 difference
-      else
-        e = tang_exp(d, A.md.tab);
-      ef = to_fix54(e);
-    }
-    if (lane == 0) sh_kw[wid] = kw;
-    // shift from the warp's reference to the tile's (after the barrier)
-    alive = __syncthreads_or(alive);
-    int kt = sh_kw[0];
-#pragma unroll
-    for (int w = 1; w < TPB / 32; ++w) kt = max(kt, sh_kw[w]);
-    const int shift = kw == kDeadTile ? 64 : kt - kw;
-    if (shift >= 63)
-      ef = 0;
-    else if (shift > 0)
-      ef = (ef + (1ll << (shift - 1))) >> shift;
-    const long long E = block_incl_scan_i64<TPB>(ef, reinterpret_cast<long long*>(sh));
-    if (valid) A.E[nb][i] = E;
-    if (threadIdx.x == TPB - 1) {
-      A.tile_k[t] = kt;
-      A.tile_s[t] = (double)E * 0x1p-54;  // below 2^62: one rounding
-    }
+  const double Mw = warp_max_key(lw);
+  const int kw = Mw == -INFINITY ? kDeadTile : tile_exponent(Mw);
+  if (valid && kw != kDeadTile) {
+    const double d = lw - (double)kw * kLn2;
+    double e;
+    if constexpr (sizeof(R) == 4)
+      e = (double)expf((float)d);  // FP32 log-weights: FP32 exponential of an FP64 difference
+    else
+      e = tang_exp(d, A.md.tab);
+    ef = to_fix54(e);
   }
-  if (threadIdx.x == 0) A.tile_alive[t] = alive;
+  if (lane == 0) sh_kw[wid] = kw;
+  alive = __syncthreads_or(alive);
+  int kt = sh_kw[0];
+#pragma unroll
+  for (int w = 1; w < TPB / 32; ++w) kt = max(kt, sh_kw[w]);
+  const int shift = kw == kDeadTile ? 64 : kt - kw;
+  if (shift >= 63)
+    ef = 0;
+  else if (shift > 0)
+    ef = (ef + (1ll << (shift - 1))) >> shift;
+  const long long E = block_incl_scan_i64<TPB>(ef, reinterpret_cast<long long*>(sh));
+  if (valid) A.E[nb][i] = E;
+  if (threadIdx.x == TPB - 1) {
+    TileRec r;
+    r.s = E;
+    r.k = kt;
+    r.alive = alive;
+    A.rec[nb][t] = r;
+  }
+  if (redundant) return;  // the next wave combines
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -383,21 +451,34 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
     *sh_last = (prev == (unsigned)A.n_tiles - 1u);
   }
   __syncthreads();
-  if (*sh_last) {
+  if (*sh_last) {  // the run's last tile of segment k: combine for the next wave
     __threadfence();
-    combine_tiles<TPB>(A, k, sh);
+    const Combined c = combine_offsets<TPB>(A.rec[nb], A.n_tiles, A.tile_O, nullptr, sh);
+    if (threadIdx.x == 0) {
+      if (finish_segment(A, k + 1, c)) {
+        const double Sd = (double)c.S;
+        rs->kmax = c.kmax;
+        rs->G = c.G;
+        rs->inv_r = Sd * A.inv_n;
+        rs->tolZ = floor_i64(kBoundaryEps * Sd);
+        rs->u = Unif<double>::first(philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1));
+      }
+      rs->arrive = 0;
+    }
   }
 }
 
-// One wave: CTA b runs tile cta_map[b].y of run cta_map[b].x.
+// One wave: CTA b runs tile cta_map[b].y of run cta_map[b].x, segment
+// k = wave - start_wave of that run.
 template <typename R, int TPB>
 __global__ void __launch_bounds__(TPB) wave_kernel(const RunDev* __restrict__ runs,
-                                                   const int2* __restrict__ cta_map) {
+                                                   const int2* __restrict__ cta_map, unsigned wave) {
   __shared__ __align__(16) RunDev sr;
   __shared__ double sh[TPB / 32 + 2 + TPB + 1];
   __shared__ int sh_last;
   __shared__ int sh_kw[TPB / 32];
-  __shared__ double sh_O[4 * TPB];
+  __shared__ long long sh_O[redundant_cap(TPB)];
+  __shared__ int sh_ks[redundant_cap(TPB)];
   const int2 rt = cta_map[blockIdx.x];
   {
     const int* src = reinterpret_cast<const int*>(runs + rt.x);
@@ -413,12 +494,13 @@ __global__ void __launch_bounds__(TPB) wave_kernel(const RunDev* __restrict__ ru
   asm volatile("griddepcontrol.wait;" ::: "memory");
   RunState* rs = sr.rs;
   if (*(volatile int32_t*)&rs->done) return;
-  const int k = *(volatile int32_t*)&rs->n_segments;
+  const int k = (int)(wave - sr.start_wave);  // wraps correctly past 2^32 waves
+  if (k < 0) return;
   switch (sr.md.kind) {
-    case SMC_MODEL_LG: step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O); break;
-    case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O); break;
-    case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O); break;
-    default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O); break;
+    case SMC_MODEL_LG: step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
   }
 }
 
@@ -531,10 +613,8 @@ Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
   L.logw = take(8 * N);
   L.E[0] = take(8 * N);
   L.E[1] = take(8 * N);
-  L.tM = take(8 * (size_t)L.n_tiles);
-  L.ts = take(8 * (size_t)L.n_tiles);
-  L.talive = take(4 * (size_t)L.n_tiles);
-  L.tinvc = take(8 * (size_t)L.n_tiles);
+  L.rec[0] = take(sizeof(TileRec) * (size_t)L.n_tiles);
+  L.rec[1] = take(sizeof(TileRec) * (size_t)L.n_tiles);
   L.tO = take(8 * (size_t)(L.n_tiles + 1));
   L.rs = take(sizeof(RunState));
   L.anc = take(4 * N * (size_t)L.anc_rows);
@@ -557,11 +637,9 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
     A.E[b] = (long long*)(ws + Ly.E[b]);
   }
   A.logw = (double*)(ws + Ly.logw);
-  A.tile_k = (int32_t*)(ws + Ly.tM);
-  A.tile_s = (double*)(ws + Ly.ts);
-  A.tile_alive = (int32_t*)(ws + Ly.talive);
-  A.tile_invc = (double*)(ws + Ly.tinvc);
-  A.tile_O = (double*)(ws + Ly.tO);
+  A.rec[0] = (TileRec*)(ws + Ly.rec[0]);
+  A.rec[1] = (TileRec*)(ws + Ly.rec[1]);
+  A.tile_O = (long long*)(ws + Ly.tO);
   A.anc = (int32_t*)(ws + Ly.anc);
   A.incr = (double*)(ws + Ly.incr);
   A.rs = (RunState*)(ws + Ly.rs);
@@ -581,7 +659,7 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
 // One bucket of a wave, launched so that it may begin before the kernel ahead
 // of it in the stream has finished (wave_kernel waits for it where it must).
 template <typename R, int TPB>
-cudaError_t launch_pdl(const RunDev* runs, const int2* map, int n, cudaStream_t st) {
+cudaError_t launch_pdl(const RunDev* runs, const int2* map, int n, cudaStream_t st, unsigned wave) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)n);
   cfg.blockDim = dim3(TPB);
@@ -592,25 +670,26 @@ cudaError_t launch_pdl(const RunDev* runs, const int2* map, int n, cudaStream_t 
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, wave_kernel<R, TPB>, runs, map);
+  return cudaLaunchKernelEx(&cfg, wave_kernel<R, TPB>, runs, map, wave);
 }
 
 template <typename R>
-cudaError_t launch_bucket(int b, const RunDev* runs, const int2* map, int n, cudaStream_t st) {
+cudaError_t launch_bucket(int b, const RunDev* runs, const int2* map, int n, cudaStream_t st,
+                          unsigned wave) {
   switch (b) {
-    case 0: return launch_pdl<R, 32>(runs, map, n, st);
-    case 1: return launch_pdl<R, 64>(runs, map, n, st);
-    case 2: return launch_pdl<R, 128>(runs, map, n, st);
-    default: return launch_pdl<R, 256>(runs, map, n, st);
+    case 0: return launch_pdl<R, 32>(runs, map, n, st, wave);
+    case 1: return launch_pdl<R, 64>(runs, map, n, st, wave);
+    case 2: return launch_pdl<R, 128>(runs, map, n, st, wave);
+    default: return launch_pdl<R, 256>(runs, map, n, st, wave);
   }
 }
 
-cudaError_t launch_wave(const WavePlan& W, int precision, cudaStream_t st) {
+cudaError_t launch_wave(const WavePlan& W, int precision, cudaStream_t st, unsigned wave) {
   for (int b = 0; b < 4; ++b) {
     if (!W.n_ctas[b]) continue;
     cudaError_t e = precision == SMC_PREC_FP32
-                        ? launch_bucket<float>(b, W.runs, W.maps[b], W.n_ctas[b], st)
-                        : launch_bucket<double>(b, W.runs, W.maps[b], W.n_ctas[b], st);
+                        ? launch_bucket<float>(b, W.runs, W.maps[b], W.n_ctas[b], st, wave)
+                        : launch_bucket<double>(b, W.runs, W.maps[b], W.n_ctas[b], st, wave);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -652,7 +731,8 @@ namespace {
 
 // Runs waves until every run is done or `max_waves` waves ran.  Known-length
 // batches launch exactly max_waves waves without reading anything back;
-// otherwise the run states are polled every 16 waves.
+// otherwise the run states are polled every 16 waves.  A run of S segments
+// needs S + 1 waves: the wave after its last segment combines that segment.
 smc_status drive_waves(const WavePlan& W, int precision, const std::vector<RunState*>& states,
                        int max_waves, bool known, cudaStream_t st, std::vector<cudaEvent_t>* evs,
                        bool timed, int* launched, double* kernel_ms) {
@@ -671,7 +751,7 @@ smc_status drive_waves(const WavePlan& W, int precision, const std::vector<RunSt
       }
       SMC_CUDA_TRY(cudaEventRecord((*evs)[2 * waves], st));
     }
-    SMC_CUDA_TRY(launch_wave(W, precision, st));
+    SMC_CUDA_TRY(launch_wave(W, precision, st, (unsigned)waves));
     if (timed) SMC_CUDA_TRY(cudaEventRecord((*evs)[2 * waves + 1], st));
     ++waves;
     *launched += kernels_per_wave;
@@ -1003,7 +1083,7 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
   int launched = 0;
   double kms = 0.0;
   std::vector<RunState*> states{runs[0].rs};
-  st = drive_waves(W, c->precision, states, known ? m->n_segments_known : Ly.max_segments, known, cs,
+  st = drive_waves(W, c->precision, states, (known ? m->n_segments_known : Ly.max_segments) + 1, known, cs,
                    &m->ev_seg, c->time_kernels != 0, &launched, &kms);
   if (st) return st;
   SMC_CUDA_TRY(cudaEventRecord(m->ev1, cs));
@@ -1079,7 +1159,7 @@ extern "C" smc_status smc_run_batch(const smc_model_t* ms, const smc_run_cfg* cf
   SMC_CUDA_TRY(cudaEventRecord(e0, cs));
   int launched = 0;
   double kms = 0.0;
-  st = drive_waves(W, prec, states, max_waves, known, cs, nullptr, false, &launched, &kms);
+  st = drive_waves(W, prec, states, max_waves + 1, known, cs, nullptr, false, &launched, &kms);
   if (st) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -16,13 +16,28 @@ constexpr int kUnboundedSegments = 1 << 20;
 constexpr int64_t kMaxParticles = (int64_t)0x7fffffff - 256;
 constexpr int64_t kTileSlots = 456;  // tile = ceil(N / 456): 152 SMs x 3 resident CTAs
 
+// One tile's reduction of a segment: its running-sum total, the reference
+// exponent k (kDeadTile: every weight zero) and
+// whether any of its particles is still short of b_stop.  One 16-byte store.
+struct __align__(16) TileRec {
+  long long s;  // exact, units of 2^-54 of 2^k
+  int32_t k, alive;
+};
+
+// Runs of fewer tiles than this combine a segment's tiles in every CTA of the
+// next wave (the offsets then live in shared memory); larger runs combine in
+// the last CTA of the segment.
+__host__ __device__ constexpr int redundant_cap(int tpb) { return 4 * tpb > 512 ? 4 * tpb : 512; }
+
 // Per-run device state (one struct per run, in the run's workspace).
 struct RunState {
-  double log_z, m, S, u, inv_r;  // inv_r = S / N
+  double log_z, m, S;
+  double u, inv_r;        // the next resampling's uniform and S / N in units U (one-CTA combine)
+  long long tolZ;         // boundary tolerance in units U (one-CTA combine)
   unsigned long long n_near, n_overflow, n_limit;
   int32_t done, status, n_segments, n_resamples;
   uint32_t arrive;
-  int32_t pad_[3];
+  int32_t kmax, G, pad_;  // the run's reference exponent and coarsening (one-CTA combine)
 };
 
 // Everything a CTA needs about its run (copied to shared memory per CTA).
@@ -31,21 +46,19 @@ struct RunDev {
   StateView state[2];
   double* logw;       // [N] log-weights of the latest segment (f64; FP32 values widened)
   long long* E[2];    // [N] tile-local running sums of the weights x 2^54 (int64), double-buffered by segment parity
-  int32_t* tile_k;    // [n_tiles] power-of-two reference exponent k_t (kDeadTile: all zero)
-  double* tile_s;     // [n_tiles]
-  int32_t* tile_alive;
-  double* tile_invc;  // [n_tiles] written by the combine: 2^(k_max - k_t) = 1 / c_t (0 where c_t = 0)
-  double* tile_O;     // [n_tiles + 1] monotone exclusive offsets, O_T >= S
+  TileRec* rec[2];    // [n_tiles] tile reductions, double-buffered by segment parity
+  long long* tile_O;  // [n_tiles + 1] offsets in the run's unit, O_T = S (runs combined in one CTA)
   int32_t* anc;       // ancestor rows
   double* incr;       // [max_segments] per-segment log-Z increments
   RunState* rs;
   double log_n, inv_n;  // log N and 1 / N, computed on the host
   int N, n_tiles, tile, max_segments, record_all, anc_rows;
+  unsigned start_wave;  // wave index of the run's segment 0 (segment k runs in wave start_wave + k)
   uint32_t k0, k1;
 };
 
 struct Layout {
-  size_t real[2], ints[2], stack[2], logw, E[2], tM, ts, talive, tinvc, tO, rs, anc, incr,
+  size_t real[2], ints[2], stack[2], logw, E[2], rec[2], tO, rs, anc, incr,
       fin_real, fin_int, fin_stack, total;
   int n_tiles, tile, anc_rows, max_segments;
 };
@@ -84,7 +97,7 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
 size_t wave_meta_bytes(const std::vector<RunDev>& runs);
 smc_status upload_wave(const std::vector<RunDev>& runs, void* meta, cudaStream_t st, WavePlan* W,
                        std::vector<char>* staging);
-cudaError_t launch_wave(const WavePlan& W, int precision, cudaStream_t st);
+cudaError_t launch_wave(const WavePlan& W, int precision, cudaStream_t st, unsigned wave);
 smc_status collect_run(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws,
                        const RunDev& A, const RunState& hrs, smc_result* r, cudaStream_t cs);
 smc_status check_cfg(const smc_model_s* m, const smc_run_cfg* c);

@@ -212,6 +212,7 @@ int admit(Server* S, smc_status* err) {
     }
     q->ws = (char*)p;
     q->dev = make_rundev(q->model, &q->cfg, q->ly, q->ws);
+    q->dev.start_wave = (unsigned)S->waves.load();  // its segment 0 runs in the next wave
     e = cudaMemsetAsync(q->dev.rs, 0, sizeof(RunState), S->stream);
     if (e != cudaSuccess) {
       *err = cuda_fail(e, "cudaMemsetAsync(run state)");
@@ -303,7 +304,7 @@ void worker_main(Server* S) {
     if (S->table_dirty && (err = upload_table(S))) break;
     const int per_poll = std::max(1, S->cfg.poll_waves);
     for (int w = 0; w < per_poll && !err; ++w) {
-      cudaError_t e = launch_wave(S->plan, S->cfg.precision, S->stream);
+      cudaError_t e = launch_wave(S->plan, S->cfg.precision, S->stream, (unsigned)S->waves.load());
       if (e != cudaSuccess) err = cuda_fail(e, "wave launch");
       S->waves += 1;
     }

@@ -51,6 +51,17 @@ def test_crbd_full_config_parity():
     assert g["n_segments"] == 127 and g["n_resamples"] == 126
 
 
+@pytest.mark.parametrize("kind", ["lg", "crbd"])
+def test_large_population_parity(kind):
+    """N = 300,001: 1,172 tiles of 256, more than a CTA combines for itself, so
+    the run's last tile of each segment forms the offsets for the next wave."""
+    if kind == "lg":
+        g, o = run_pair("lg", 300_001, seed=5, obs=inputs.lg_observations(12, seed=3))
+    else:
+        g, o = run_pair("crbd", 300_001, seed=5, tree=inputs.yule_tree(6, seed=4))
+    assert_parity_fp64(g, o)
+
+
 def test_crbd_kill_rules_parity():
     tree = inputs.yule_tree(8, seed=8)
     g, o = run_pair("crbd", 2000, seed=3, tree=tree, rates=(6.0, 5.0), depth_cap=2)
