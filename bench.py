@@ -66,17 +66,22 @@ WORKLOADS = {
 # DMUL) and its DRAM traffic per launch, from one ncu capture of the workload
 # (profiles folder); the traffic holds only for the kernel sources with the
 # recorded digest.
-NCU = {"crbd64": dict(fp64_flop_per_pstep=95.4, bytes_per_launch=3.24e6,
-                     fp64_pipe_elapsed=0.342, src_digest="d37df0c0b5fbd72e")}
+NCU = {"crbd64": dict(fp64_flop_per_pstep=43.4, bytes_per_launch=3.36e6,
+                     fp64_pipe_elapsed=0.236, src_digest="751e81baf78ce64b")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
 
 
+# the segment kernel's sources (the standalone resampling kernels are not among them)
+KERNEL_SOURCES = ("smc_engine.cu", "smc_engine.h", "smc_models.cuh", "smc_device.cuh",
+                  "smc_combine.cuh")
+
+
 def src_digest() -> str:
     h = hashlib.sha256()
-    for p in sorted((ROOT / "paper_2112_00364_gb300" / "csrc").glob("*")):
-        h.update(p.read_bytes())
+    for name in KERNEL_SOURCES:
+        h.update((ROOT / "paper_2112_00364_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
 
