@@ -256,11 +256,14 @@ size_t smc_resample_workspace_bytes(int64_t N);
 /* Systematic resampling of one population (Section 3.3, parallel systematic
  * resampling): with the power-of-two reference m = k ln 2, k = ceil(max logw / ln 2),
  * S = sum exp(logw - m) and P_j the running sum, ancestors[i] = min{ j : P_j (N / S)
- * > i + u } (N - 1 if none); the log-Z increment is m + (log S - log N).  All sums
- * are FP64.  logw [N] f64 in (16-byte aligned), ancestors [N] int32 out, out3 [3]
- * f64 out = {m, S, m + (log S - log N)}, n_near [1] int64 out (offsets within
- * 1e-12 N of a boundary).  u in (0,1).  Errors: SMC_EINVAL (N < 1, u outside (0,1),
- * NULL pointer, workspace too small), SMC_ECUDA.  An all -inf population gives
+ * > i + u } (N - 1 if none); the log-Z increment is m + (log S - log N).  The sums
+ * are exact integer sums of the weights rounded to 2^-54 of their tile's
+ * power-of-two reference (within n_tiles 2^-52 of the FP64 sum).  logw [N] f64 in
+ * (16-byte aligned), ancestors [N] int32 out, out3 [3] f64 out = {m, S, m + (log S
+ * - log N)}, n_near [1] int64 out (offsets within 1e-12 N of a boundary).  u in
+ * (0,1).  workspace: device memory of smc_resample_workspace_bytes(N) bytes,
+ * 256-byte aligned.  Errors: SMC_EINVAL (N < 1, u outside (0,1), NULL pointer,
+ * workspace too small or misaligned), SMC_ECUDA.  An all -inf population gives
  * ancestors = identity and out3 = {-inf, 0, -inf}. */
 smc_status smc_resample(const double *logw, int64_t N, double u, int32_t *ancestors,
                         double *out3, int64_t *n_near, void *workspace, size_t workspace_bytes,
@@ -312,7 +315,10 @@ smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uin
  * CUDA library log, 3 = the CUDA library exp; for fn 4 and 5 x[i] holds 64 random
  * bits b (read as uint64) and y[i] = log u of the FP64 uniform u = ((b >> 11) | 1)
  * 2^-53, 4 = reduced on the integer pipes (what the samplers use), 5 = the
- * table logarithm of u built as a double.  x, y [n] f64 device pointers.
+ * table logarithm of u built as a double; for fn 6 and 7 y[i] holds (as int64
+ * bits) the fixed-point weight round(e^x[i] 2^54) for x[i] <= 0, 6 = computed
+ * on the integer pipes (what the segment kernel uses), 7 = the table exponential
+ * rounded to the same grid.  x, y [n] f64 device pointers.
  * Errors: SMC_EINVAL, SMC_ECUDA. */
 smc_status smc_math_eval(int32_t fn, const double *x, double *y, int64_t n, void *stream);
 

@@ -85,6 +85,7 @@ struct MathTab {
   double inv_f[192];    // 128 / j, j = 90..181 used
   double inv_f52[192];  // (128 / j) 2^-52 (exact scaling of inv_f)
   double inv_f53[192];  // (128 / j) 2^-53
+  unsigned long long exp2_neg_q63[128];  // round(2^(-j/128) 2^63)
   double exp2_j[32];    // 2^(j/32)
   double inv_int[256];  // 1 / k (entry 0 unused)
 };
@@ -173,6 +174,57 @@ __device__ __forceinline__ double tang_exp(double x, const MathTab* __restrict__
   const double p = fma(r2, pq, r);
   const double s = __ldg(&T->exp2_j[n & 31]);
   return fma(s, p, s) * pow2i(n >> 5);
+}
+
+// ---- integer exponential of fixed-point weights ----
+// round(e^d 2^B) for d <= 0 (B = 54 for the segment kernel's tiles of at most
+// 256 weights, 50 for the standalone resampler's tiles of 4096, so that a
+// tile's sum stays below 2^62), the weight of a particle relative to a
+// power-of-two reference as a 2^-B fixed-point integer, on the integer pipes
+// (only the argument split is FP64).  e^d = 2^-y with y = -d / ln 2 = n + j/128
+// + r, r < 2^-7: e^d = 2^-n 2^(-j/128) e^(-r ln 2), the last factor by its
+// Taylor series to degree 6 (Horner; all partial sums positive), in 2^-63 fixed
+// point with 64-bit multiply-high products.  Within one unit of the exact
+// rounding; below e^-38.5 (less than half a unit) it returns 0.  A d slightly
+// above 0 (rounding of the reference) is taken as 0.
+constexpr unsigned long long kInvLn2Q63 = 0xb8aa3b295c17f0bcull;  // round(2^63 / ln 2)
+constexpr unsigned long long kLn2Q64 = 0xb17217f7d1cf79acull;     // round(ln 2 2^64)
+
+__device__ __forceinline__ unsigned long long mulhi64(unsigned long long a, unsigned long long b) {
+  return __umul64hi(a, b);
+}
+
+template <int B>
+__device__ __forceinline__ long long exp_fix(double d, const MathTab* __restrict__ T) {
+  static_assert(B >= 40 && B <= 54, "fixed-point bits");
+  if (!(d > -38.5)) return 0;
+  const long long b = __double_as_longlong(-d);
+  if (b <= 0) return 1ll << B;  // d >= 0
+  const int e = (int)(b >> 52);
+  if (e == 0) return 1ll << B;  // |d| below 2^-1022
+  const unsigned long long m = (unsigned long long)((b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll);
+  const int sh = e - 1017;  // X = -d 2^58 (below 2^64 since -d < 2^6)
+  const unsigned long long X = sh >= 0 ? (m << sh) : (-sh < 64 ? (m >> -sh) : 0ull);
+  // Y = X / ln 2 in units of 2^-58: floor(X kInvLn2Q63 / 2^63)
+  const unsigned long long Y = (mulhi64(X, kInvLn2Q63) << 1) | ((X * kInvLn2Q63) >> 63);
+  const int n = (int)(Y >> 58);
+  if (n >= B + 1) return 0;  // at most half a unit
+  const int j = (int)((Y >> 51) & 127);
+  const unsigned long long r = Y & ((1ull << 51) - 1);  // r 2^58, r < 2^-7
+  const unsigned long long t2 = mulhi64(r << 5, kLn2Q64) << 1;  // 2 t 2^63 with t = r ln 2
+  unsigned long long p = 0x2d82d82d82d82eull;                   // 2^63 / 720
+  p = 0x111111111111111ull - mulhi64(t2, p);                     // 2^63 / 120 - t p
+  p = 0x555555555555555ull - mulhi64(t2, p);                     // 2^63 / 24
+  p = 0x1555555555555555ull - mulhi64(t2, p);                    // 2^63 / 6
+  p = 0x4000000000000000ull - mulhi64(t2, p);                    // 2^63 / 2
+  p = 0x8000000000000000ull - mulhi64(t2, p);                    // 2^63
+  p = 0x8000000000000000ull - mulhi64(t2, p);                    // e^-t 2^63
+  const unsigned long long q = mulhi64(p, __ldg(&T->exp2_neg_q63[j])) << 1;  // e^-(j/128 + r) ln 2 2^63
+  const int s = 63 - B + n;  // to 2^-B units and the factor 2^-n
+  return (long long)((q + (1ull << (s - 1))) >> s);
+}
+__device__ __forceinline__ long long exp_fix54(double d, const MathTab* __restrict__ T) {
+  return exp_fix<54>(d, T);
 }
 
 // x / y from a precomputed y_inv ~ 1/y: one residual correction of x * y_inv

@@ -54,157 +54,6 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned l
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
 }
 
-// A tile record written by another CTA of the previous segment (one 16-byte
-// load at L2, past the L1).
-__device__ __forceinline__ TileRec load_rec(const TileRec* p) {
-  const longlong2 v = __ldcg(reinterpret_cast<const longlong2*>(p));
-  TileRec r;
-  r.s = v.x;
-  r.k = (int32_t)(v.y & 0xffffffffll);
-  r.alive = (int32_t)(v.y >> 32);
-  return r;
-}
-
-// ---------------------------------------------------------------------------
-// Offsets.  A tile's record holds its exact running-sum total s_t in units of
-// 2^-54 of its reference 2^k_t.  The combine of a segment brings every total
-// to the run's reference 2^k_max and one common unit U = 2^(k_max - 54 + G):
-// v_t = round(s_t / 2^(k_max - k_t + G)), with the coarsening G >= 0 the
-// smallest that keeps the sum below 2^62 (from a bound on it: each tile's
-// total is below 2^(62 - (k_max - k_t))).  The offsets O_t = sum_{t' < t} v_t'
-// and S = O_T are then exact integers, non-decreasing by construction, and the
-// same in whatever order they are summed.  Rounding costs at most half a unit
-// per tile, and since the tile that holds the largest weight has s >= 2^53,
-// G is at most 10 bits more than the sum needs: S is within n_tiles 2^-52 of
-// the exact sum of the weights.
-// ---------------------------------------------------------------------------
-
-// floor(x) as int64 for finite x >= 0 (LLONG_MAX from 2^63 up); -1 for x < 0.
-__device__ __forceinline__ long long floor_i64(double x) {
-  const long long b = __double_as_longlong(x);
-  if ((b & 0x7FFFFFFFFFFFFFFFll) == 0) return 0;
-  if (b < 0) return -1;
-  const int e = (int)(b >> 52);
-  if (e < 1023) return 0;
-  if (e >= 1023 + 63) return 0x7FFFFFFFFFFFFFFFll;
-  const long long m = (b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll;
-  const int sh = e - 1075;  // x = m 2^sh
-  return sh >= 0 ? (m << sh) : (m >> -sh);
-}
-
-// x << sh for x >= 0, saturating at LLONG_MAX
-__device__ __forceinline__ long long shl_sat(long long x, int sh) {
-  if (x == 0) return 0;
-  if (sh >= 63 || x > (0x7FFFFFFFFFFFFFFFll >> sh)) return 0x7FFFFFFFFFFFFFFFll;
-  return x << sh;
-}
-
-// the tile total in the run's unit U: round(s / 2^(k_max - k_t + G))
-__device__ __forceinline__ long long to_run_units(long long s, int kt, int kmax, int G) {
-  if (kt == kDeadTile) return 0;
-  const int sh = kmax - kt + G;
-  if (sh >= 63) return 0;
-  if (sh == 0) return s;
-  return (s + (1ll << (sh - 1))) >> sh;
-}
-
-// one tile's share of the bound on the sum (units of 2^52 U at G = 0)
-__device__ __forceinline__ int bound_share(int kt, int kmax) {
-  if (kt == kDeadTile) return 0;
-  const int d = kmax - kt;
-  return d > 10 ? 1 : (1 << (10 - d));
-}
-
-template <int TPB>
-__device__ __forceinline__ int block_sum_int(int v, int* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = __reduce_add_sync(0xffffffffu, v);
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  int r = 0;
-#pragma unroll
-  for (int w = 0; w < TPB / 32; ++w) r += sh[w];
-  return r;
-}
-
-struct Combined {
-  long long S;  // total in units U
-  int kmax, G, alive;
-};
-
-// Combine n_tiles tile records into the offsets O[0..nt] (O[nt] = S).  With
-// `ks` non-NULL the records are first staged in shared memory (k_t into ks,
-// s_t into O, which the offsets then overwrite); otherwise they are read from
-// `rec` on each pass.  Every thread of the CTA calls it; all integer work.
-template <int TPB>
-__device__ Combined combine_offsets(const TileRec* rec, int nt, long long* O, int* ks, double* sh) {
-  constexpr int P = 4;  // consecutive tiles per thread per chunk
-  int* shi = reinterpret_cast<int*>(sh);
-  long long* shl = reinterpret_cast<long long*>(sh);
-  int kl = kDeadTile, al = 0;
-  for (int q = threadIdx.x; q < nt; q += TPB) {
-    const TileRec r = load_rec(rec + q);
-    if (ks) {
-      ks[q] = r.k;
-      O[q] = r.s;
-    }
-    kl = max(kl, r.k);
-    al |= r.alive;
-  }
-  Combined c;
-  c.kmax = block_max_int<TPB>(kl, shi);
-  c.alive = __syncthreads_or(al);
-  c.G = 0;
-  c.S = 0;
-  if (c.kmax == kDeadTile) return c;
-  int bl = 0;
-  for (int q = threadIdx.x; q < nt; q += TPB) bl += bound_share(ks ? ks[q] : load_rec(rec + q).k, c.kmax);
-  const int b = block_sum_int<TPB>(bl, shi);  // >= 1024: the tile of the largest weight
-  c.G = max(0, (32 - __clz(b - 1)) - 10);
-  long long carry = 0;
-  for (int base = 0; base < nt; base += TPB * P) {
-    long long v[P];
-    long long tot = 0;
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int t = base + threadIdx.x * P + q;
-      v[q] = 0;
-      if (t < nt) {
-        long long st;
-        int kt;
-        if (ks) {
-          st = O[t];
-          kt = ks[t];
-        } else {
-          const TileRec r = load_rec(rec + t);
-          st = r.s;
-          kt = r.k;
-        }
-        v[q] = to_run_units(st, kt, c.kmax, c.G);
-      }
-      tot += v[q];
-    }
-    const long long incl = block_incl_scan_i64<TPB>(tot, shl);
-    long long off = carry + (incl - tot);
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int t = base + threadIdx.x * P + q;
-      if (t < nt) O[t] = off;
-      off += v[q];
-    }
-    __syncthreads();
-    if (threadIdx.x == TPB - 1) shl[0] = incl;
-    __syncthreads();
-    carry += shl[0];
-    __syncthreads();
-  }
-  c.S = carry;
-  if (threadIdx.x == 0) O[nt] = carry;
-  __syncthreads();
-  return c;
-}
-
 // Finish segment k-1 of the run from its combined offsets (one thread):
 // log Z += k_max ln 2 + (log S - log N) with S = S_units U, the increment
 // record, and the end of the run.  Returns whether segment k runs.
@@ -243,25 +92,33 @@ struct SearchCtx {
   const int* ks;       // tile reference exponents (shared memory), or NULL: read the records
   const TileRec* rec;
   int kmax, G;
-  double inv_r;        // S / N in units U
-  double u;            // the resampling uniform
+  Q64 d, z0;           // S / N and u S / N in 64.64 (units U)
   long long tolZ;      // 1e-12 N on the q scale, in units U
 };
 
+// The run's search scalars from its combined total (one thread).
+__device__ __forceinline__ void search_scalars(const Combined& c, int N, double u, Q64* d, Q64* z0,
+                                               long long* tolZ) {
+  *d = q_ratio((unsigned long long)c.S, (unsigned long long)N);
+  *z0 = q_scale(frac64(u), *d);
+  *tolZ = floor_i64(kBoundaryEps * (double)c.S);
+}
+
 // a_i = min{ j : q_j > y } for y = i + u, with q_j = P_j N / S and P_j the
-// running sum of the weights; on the P scale in units U, z = y S / N.  The tile
-// is t = max{ t : O_t <= z } (N - 1 if z lies above every offset); inside it
-// P_j = O_t + E_j 2^-(k_max - k_t + G), so P_j > z <=> E_j > floor((z - O_t)
+// running sum of the weights; on the P scale in units U the offset is
+// z_i = z_0 + i S / N (64.64 fixed point, exact and non-decreasing in i).  The
+// tile is t = max{ t : O_t <= z } (N - 1 if z lies above every offset); inside
+// it P_j = O_t + E_j 2^-(k_max - k_t + G), so P_j > z <=> E_j > floor((z - O_t)
 // 2^(k_max - k_t + G)) (E_j is an integer): one threshold per particle, then an
 // 8-ary search with integer compares (three rounds of independent loads for a
 // 256-particle tile).  If no element of tile t qualifies, the first element of
 // tile t+1 does.  The offset is flagged when it lies within 1e-12 N of q_a or
-// q_{a-1}, measured in the same units.
+// q_{a-1}, measured in the same units.  Integer arithmetic only.
 __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const SearchCtx& X,
                                                  const long long* __restrict__ E, bool* near) {
   const int N = A.N, T = A.n_tiles;
-  const double z = ((double)i + X.u) * X.inv_r;
-  const long long Z = floor_i64(z);
+  const Q64 z = q_add(X.z0, q_mul_u32((unsigned)i, X.d));
+  const long long Z = (long long)z.hi;
   int lo = 0, hi = T;  // O_0 = 0 <= z
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -278,7 +135,7 @@ __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const S
   const int j0 = t * A.tile, j1 = min(N, j0 + A.tile);
   const int kt = X.ks ? X.ks[t] : load_rec(X.rec + t).k;
   const int sh = X.kmax - kt + X.G;
-  const long long F = floor_i64((z - (double)X.O[t]) * pow2i(min(sh, 1000)));
+  const long long F = q_threshold(z, X.O[t], sh);
   const long long tolF = shl_sat(X.tolZ, sh);
   // first j in [j0, j1) with E_j > F
   long long Eb = 0;  // E_{b-1} for the current bracket start b (0 before the tile)
@@ -357,29 +214,34 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
       const bool go_on = c.kmax != kDeadTile && c.alive && k < A.max_segments;
       if (t == 0 && threadIdx.x == 0) finish_segment(A, k, c);
       if (!go_on) return;
-      // the run's scalars by one warp (FP64 work costs the whole SM's FP64 pipe)
-      double* shx = sh + TPB / 32 + 1;
+      // the run's search scalars by one thread, shared through shared memory
+      unsigned long long* shq = reinterpret_cast<unsigned long long*>(sh + TPB / 32 + 1);
       if (threadIdx.x == 0) {
-        const double Sd = (double)c.S;
-        shx[0] = Sd * A.inv_n;
-        shx[1] = Unif<double>::first(philox(0u, (uint32_t)(k - 1), 0u, 1u, A.k0, A.k1));
-        reinterpret_cast<long long*>(shx)[2] = floor_i64(kBoundaryEps * Sd);
+        Q64 d, z0;
+        long long tolZ;
+        search_scalars(c, N, Unif<double>::first(philox(0u, (uint32_t)(k - 1), 0u, 1u, A.k0, A.k1)),
+                       &d, &z0, &tolZ);
+        shq[0] = d.hi;
+        shq[1] = d.lo;
+        shq[2] = z0.hi;
+        shq[3] = z0.lo;
+        shq[4] = (unsigned long long)tolZ;
       }
       __syncthreads();
       X.O = sh_O;
       X.ks = sh_ks;
       X.kmax = c.kmax;
       X.G = c.G;
-      X.inv_r = shx[0];
-      X.u = shx[1];
-      X.tolZ = reinterpret_cast<long long*>(shx)[2];
+      X.d = Q64{shq[0], shq[1]};
+      X.z0 = Q64{shq[2], shq[3]};
+      X.tolZ = (long long)shq[4];
     } else {
       X.O = A.tile_O;
       X.ks = nullptr;
       X.kmax = rs->kmax;
       X.G = rs->G;
-      X.inv_r = rs->inv_r;
-      X.u = rs->u;
+      X.d = Q64{rs->d_hi, rs->d_lo};
+      X.z0 = Q64{rs->z0_hi, rs->z0_lo};
       X.tolZ = rs->tolZ;
     }
     if (valid) {
@@ -407,8 +269,8 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   warp_add_u64(&rs->n_limit, active ? (unsigned long long)L.limited : 0ull);
   // Weights, first per warp as soon as the warp's particles reached the
   // checkpoint (overlapping the tile's slower warps): the warp's max M_w, its
-  // power-of-two reference k_w = ceil(M_w / ln 2), e_j = exp(logw_j - k_w ln 2)
-  // and e_j 2^54 rounded to an integer.  Then, after the tile barrier, the tile
+  // power-of-two reference k_w = ceil(M_w / ln 2), and e_j = exp(logw_j - k_w
+  // ln 2) 2^54 rounded to an integer (FP64 mode: on the integer pipes).  Then, after the tile barrier, the tile
   // reference k_t = max k_w, the exact shift of each weight to it, and the
   // tile's integer running sum E_j (the next segment's search keys).
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -416,13 +278,14 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   const double Mw = warp_max_key(lw);
   const int kw = Mw == -INFINITY ? kDeadTile : tile_exponent(Mw);
   if (valid && kw != kDeadTile) {
-    const double d = lw - (double)kw * kLn2;
-    double e;
-    if constexpr (sizeof(R) == 4)
-      e = (double)expf((float)d);  // FP32 log-weights: FP32 exponential of an FP64 difference
-    else
-      e = tang_exp(d, A.md.tab);
-    ef = to_fix54(e);
+    if constexpr (sizeof(R) == 4) {
+      // FP32 log-weights: FP32 exponential of an FP64 difference
+      ef = to_fix54((double)expf((float)(lw - (double)kw * kLn2)));
+    } else {
+      const double kd = (double)kw;
+      const double d = fma(-kd, kLn2Lo, fma(-kd, kLn2Hi, lw));  // lw - kw ln 2, two-part ln 2
+      ef = exp_fix54(d, A.md.tab);
+    }
   }
   if (lane == 0) sh_kw[wid] = kw;
   alive = __syncthreads_or(alive);
@@ -456,12 +319,17 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
     const Combined c = combine_offsets<TPB>(A.rec[nb], A.n_tiles, A.tile_O, nullptr, sh);
     if (threadIdx.x == 0) {
       if (finish_segment(A, k + 1, c)) {
-        const double Sd = (double)c.S;
+        Q64 d, z0;
+        long long tolZ;
+        search_scalars(c, N, Unif<double>::first(philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1)), &d,
+                       &z0, &tolZ);
         rs->kmax = c.kmax;
         rs->G = c.G;
-        rs->inv_r = Sd * A.inv_n;
-        rs->tolZ = floor_i64(kBoundaryEps * Sd);
-        rs->u = Unif<double>::first(philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1));
+        rs->d_hi = d.hi;
+        rs->d_lo = d.lo;
+        rs->z0_hi = z0.hi;
+        rs->z0_lo = z0.lo;
+        rs->tolZ = tolZ;
       }
       rs->arrive = 0;
     }
@@ -549,6 +417,9 @@ smc_status math_table(const MathTab** out) {
       h.inv_f53[j] = std::ldexp(h.inv_f[j], -53);
     }
     for (int j = 0; j < 32; ++j) h.exp2_j[j] = std::exp2((double)j / 32.0);
+    for (int j = 0; j < 128; ++j)
+      h.exp2_neg_q63[j] = (unsigned long long)std::llroundl(
+          std::ldexp(std::exp2l(-(long double)j / 128.0L), 63));
     h.inv_int[0] = 0.0;
     for (int k = 1; k < 256; ++k) h.inv_int[k] = 1.0 / (double)k;
     SMC_CUDA_TRY(cudaMemcpyToSymbol(g_math_tab, &h, sizeof(MathTab)));

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/smc.h"
+#include "smc_combine.cuh"
 #include "smc_models.cuh"
 
 namespace smc {
@@ -16,24 +17,13 @@ constexpr int kUnboundedSegments = 1 << 20;
 constexpr int64_t kMaxParticles = (int64_t)0x7fffffff - 256;
 constexpr int64_t kTileSlots = 456;  // tile = ceil(N / 456): 152 SMs x 3 resident CTAs
 
-// One tile's reduction of a segment: its running-sum total, the reference
-// exponent k (kDeadTile: every weight zero) and
-// whether any of its particles is still short of b_stop.  One 16-byte store.
-struct __align__(16) TileRec {
-  long long s;  // exact, units of 2^-54 of 2^k
-  int32_t k, alive;
-};
-
-// Runs of fewer tiles than this combine a segment's tiles in every CTA of the
-// next wave (the offsets then live in shared memory); larger runs combine in
-// the last CTA of the segment.
-__host__ __device__ constexpr int redundant_cap(int tpb) { return 4 * tpb > 512 ? 4 * tpb : 512; }
-
 // Per-run device state (one struct per run, in the run's workspace).
 struct RunState {
   double log_z, m, S;
-  double u, inv_r;        // the next resampling's uniform and S / N in units U (one-CTA combine)
-  long long tolZ;         // boundary tolerance in units U (one-CTA combine)
+  // the next search's scalars when the run combines in one CTA: S / N and
+  // u S / N in 64.64 fixed point, and the boundary tolerance (units U)
+  unsigned long long d_hi, d_lo, z0_hi, z0_lo;
+  long long tolZ;
   unsigned long long n_near, n_overflow, n_limit;
   int32_t done, status, n_segments, n_resamples;
   uint32_t arrive;

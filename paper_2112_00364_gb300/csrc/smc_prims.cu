@@ -2,17 +2,21 @@
 // HBM-streaming kernels, the particle-duplication gather, the random-number
 // parity hooks, and the library's error plumbing.
 //
-// smc_resample (parallel systematic resampling, three launches):
+// smc_resample (parallel systematic resampling, three launches), in the
+// segment kernel's integer arithmetic (smc_combine.cuh):
 //   1. rs_tile_reduce: per tile of TPB*IT weights, M_t = max, its power-of-two
-//      reference k_t = ceil(M_t / ln 2) and s_t = sum exp(x - k_t ln 2)
-//   2. rs_combine (one CTA): k = max k_t, c_t = 2^(k_t - k) (exact), O_t =
-//      exclusive prefix of c_t s_t (O_{T} = S), out3 = {k ln 2, S,
-//      k ln 2 + (log S - log N)}, r = N / S; no exponential per tile
-//   3. rs_ancestors: per tile, E_j = inclusive scan of exp(x_j - k_t ln 2),
-//      q_j = (O_t + c_t E_j) r clamped to the tile's [O_t r, O_{t+1} r); element
-//      j owns the offsets i with q_{j-1} <= i + u < q_j and writes a_i = j for
-//      them (the last element owns everything above), so every i is written
-//      exactly once and a_i = min{ j : q_j > i + u } up to rounding at tile seams.
+//      reference k_t = ceil(M_t / ln 2), the weights round(exp(x - k_t ln 2)
+//      2^50) on the integer pipes and their exact total s_t
+//   2. rs_combine (one CTA): k = max k_t, integer offsets O_t of the totals in
+//      the common unit U, S = O_T, out3 = {k ln 2, S U 2^-k, log-Z increment},
+//      and the 64.64 fixed-point offsets' scale S / N and start u S / N
+//   3. rs_ancestors: per tile, the weights again and their integer running sum
+//      E_j; element j owns the offsets z_i = (i + u) S / N in [B_{j-1}, B_j),
+//      B_j = min(O_t + E_j 2^-(k - k_t + G), O_{t+1}) (the first element of a
+//      tile from the previous tile's last boundary, the last element of the
+//      population everything above), and writes a_i = j for them: every i is
+//      written exactly once, a_i = min{ j : P_j > z_i } as in the segment
+//      kernel's search, and the z_i are walked with integer additions.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,6 +25,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "smc_combine.cuh"
 #include "smc_device.cuh"
 #include "smc_engine.h"
 #include "smc_internal.h"
@@ -58,152 +63,188 @@ __device__ __forceinline__ void load_tile(const double* __restrict__ x, int64_t 
   }
 }
 
+// The search scalars of a population, written by rs_combine.
+struct RsScalars {
+  unsigned long long d_hi, d_lo, z0_hi, z0_lo;  // S / N and u S / N in 64.64 (units U)
+  long long tolZ;                                // 1e-12 N on the q scale, in units U
+  double inv_d;                                  // N / S
+  int32_t kmax, G, degenerate, pad_;
+};
+
+// Weights as 2^-50 fixed-point integers: a tile of 4096 sums below 2^62.
+constexpr int kRsBits = 50;
+
+// The tile's weights round(exp(x - k_t ln 2) 2^50) (k_t from the tile max).
+__device__ __forceinline__ void tile_weights(const double (&v)[RS_IT], int kt, const MathTab* tab,
+                                             long long (&ef)[RS_IT]) {
+  const double kd = (double)kt;
+#pragma unroll
+  for (int q = 0; q < RS_IT; ++q) {
+    ef[q] = 0;
+    if (kt != kDeadTile) ef[q] = exp_fix<kRsBits>(fma(-kd, kLn2Lo, fma(-kd, kLn2Hi, v[q])), tab);
+  }
+}
+
 __global__ void __launch_bounds__(RS_TPB) rs_tile_reduce(const double* __restrict__ x, int64_t N,
-                                                         int32_t* __restrict__ tk,
-                                                         double* __restrict__ ts) {
-  __shared__ double sh[RS_TPB / 32 + 1];
+                                                         TileRec* __restrict__ rec,
+                                                         const MathTab* tab) {
+  __shared__ long long sh[RS_TPB / 32 + 1];
+  __shared__ int sh_k;
   double v[RS_IT];
   load_tile(x, N, (int64_t)blockIdx.x * RS_TILE, v);
   double mx = -INFINITY;
 #pragma unroll
   for (int q = 0; q < RS_IT; ++q) mx = fmax(mx, v[q]);
-  const double Mt = block_max<RS_TPB>(mx, sh);
-  const int kt = Mt == -INFINITY ? kDeadTile : tile_exponent(Mt);
-  double s = 0.0;
-  if (kt != kDeadTile) {
-    const double R = (double)kt * kLn2;
+  const double Mt = block_max_key<RS_TPB>(mx, sh);
+  if (threadIdx.x == 0) sh_k = Mt == -INFINITY ? kDeadTile : tile_exponent(Mt);
+  __syncthreads();
+  const int kt = sh_k;
+  long long ef[RS_IT];
+  tile_weights(v, kt, tab, ef);
+  long long tot = 0;
 #pragma unroll
-    for (int q = 0; q < RS_IT; ++q) s = s + exp(v[q] - R);
-  }
-  const double tot = block_incl_scan<RS_TPB>(s, sh);
+  for (int q = 0; q < RS_IT; ++q) tot += ef[q];
+  const long long incl = block_incl_scan_i64<RS_TPB>(tot, sh);
   if (threadIdx.x == RS_TPB - 1) {
-    tk[blockIdx.x] = kt;
-    ts[blockIdx.x] = tot;
+    TileRec r;
+    r.s = incl;
+    r.k = kt;
+    r.alive = 0;
+    rec[blockIdx.x] = r;
   }
 }
 
-// Single CTA: combine nt tile results.  tO has nt + 1 entries (tO[nt] = S).
-__global__ void __launch_bounds__(RS_TPB) rs_combine(const int32_t* __restrict__ tk,
-                                                     const double* __restrict__ ts, int nt,
-                                                     int64_t N, double* __restrict__ tc,
-                                                     double* __restrict__ tO, double* out3,
-                                                     double* r_out) {
-  __shared__ double sh[RS_TPB / 32 + 2 + RS_TPB];
-  int kloc = kDeadTile;
-  for (int t = threadIdx.x; t < nt; t += RS_TPB) kloc = max(kloc, tk[t]);
-  const int kmax = block_max_int<RS_TPB>(kloc, reinterpret_cast<int*>(sh));
-  if (kmax == kDeadTile) {
-    if (threadIdx.x == 0) {
-      out3[0] = -INFINITY;
-      out3[1] = 0.0;
-      out3[2] = -INFINITY;
-      *r_out = 0.0;
-    }
+// Single CTA: combine nt tile records.  O has nt + 1 entries (O[nt] = S).
+__global__ void __launch_bounds__(RS_TPB) rs_combine(const TileRec* __restrict__ rec, int nt,
+                                                     int64_t N, double log_n, double u,
+                                                     long long* __restrict__ O, RsScalars* sc,
+                                                     double* out3, const MathTab* tab) {
+  __shared__ double sh[RS_TPB / 32 + 2 + RS_TPB + 1];
+  const Combined c = combine_offsets<RS_TPB>(rec, nt, O, nullptr, sh);
+  if (threadIdx.x != 0) return;
+  RsScalars s;
+  std::memset(&s, 0, sizeof(s));
+  if (c.kmax == kDeadTile) {
+    out3[0] = -INFINITY;
+    out3[1] = 0.0;
+    out3[2] = -INFINITY;
+    s.degenerate = 1;
+    *sc = s;
     return;
   }
-  double carry = 0.0;
-  for (int base = 0; base < nt; base += RS_TPB) {
-    const int t = base + threadIdx.x;
-    double c = 0.0, v = 0.0;
-    if (t < nt) {
-      const int kt = tk[t];
-      c = (kt == kDeadTile) ? 0.0 : pow2i(kt - kmax);
-      v = ts[t] * c;  // exact: c is a power of two
-    }
-    const double incl = block_incl_scan<RS_TPB>(v, sh);
-    __syncthreads();
-    sh[RS_TPB / 32 + 1 + threadIdx.x] = incl;
-    __syncthreads();
-    const double excl = threadIdx.x ? sh[RS_TPB / 32 + threadIdx.x] : 0.0;
-    if (t < nt) {
-      tc[t] = c;
-      tO[t] = carry + excl;
-    }
-    carry = carry + sh[RS_TPB / 32 + RS_TPB];
-  }
-  if (threadIdx.x == 0) {
-    const double m = (double)kmax * kLn2;
-    tO[nt] = carry;
-    out3[0] = m;
-    out3[1] = carry;
-    out3[2] = m + (log(carry) - log((double)N));
-    *r_out = (double)N / carry;
-  }
+  const double Sd = (double)c.S;
+  out3[0] = (double)c.kmax * kLn2;
+  out3[1] = Sd * pow2i(c.G - kRsBits);
+  out3[2] = (double)(c.kmax - kRsBits + c.G) * kLn2 + (tang_log(Sd, tab) - log_n);
+  const Q64 d = q_ratio((unsigned long long)c.S, (unsigned long long)N);
+  const Q64 z0 = q_scale(frac64(u), d);
+  s.d_hi = d.hi;
+  s.d_lo = d.lo;
+  s.z0_hi = z0.hi;
+  s.z0_lo = z0.lo;
+  s.tolZ = floor_i64(kBoundaryEps * Sd);
+  s.inv_d = (double)N / Sd;
+  s.kmax = c.kmax;
+  s.G = c.G;
+  *sc = s;
 }
 
-// first offset index c in [0, N] with fl(c + u) >= bound (bound finite, >= 0)
-__device__ __forceinline__ int64_t first_at_or_above(double bound, double u, int64_t N) {
-  if (!(bound < (double)N + 1.0)) return N;
-  double g = ceil(bound - u);
-  int64_t c = g < 0.0 ? 0 : (int64_t)g;
-  if (c > N) c = N;
-  while (c > 0 && (double)(c - 1) + u >= bound) --c;
-  while (c < N && (double)c + u < bound) ++c;
+// O_t + E 2^-sh in 64.64 (E >= 0 a tile running sum), capped at cap
+__device__ __forceinline__ Q64 boundary(long long O_t, long long E, int sh, long long cap) {
+  Q64 b;
+  if (sh <= 0) {  // the run's unit is finer than the tile's: exact
+    b.hi = (unsigned long long)(O_t + (E << -sh));
+    b.lo = 0;
+  } else if (sh < 64) {
+    b.hi = (unsigned long long)(O_t + (E >> sh));
+    b.lo = (unsigned long long)E << (64 - sh);
+  } else {
+    b.hi = (unsigned long long)O_t;
+    b.lo = sh - 64 < 63 ? ((unsigned long long)E >> (sh - 64)) : 0ull;
+  }
+  const Q64 c{(unsigned long long)cap, 0ull};
+  return q_lt(c, b) ? c : b;
+}
+
+// min{ i in [0, N] : z_i >= B } with z_i = z0 + i d: an FP64 estimate, then
+// exact integer steps
+__device__ __forceinline__ int64_t first_at_or_above(Q64 B, Q64 z0, Q64 d, double inv_d, int64_t N) {
+  const double diff = ((double)B.hi - (double)z0.hi) + ((double)B.lo - (double)z0.lo) * 0x1p-64;
+  const double est = diff * inv_d;
+  int64_t c = est <= 0.0 ? 0 : (est >= (double)N ? N : (int64_t)ceil(est));
+  while (c > 0 && !q_lt(q_add(z0, q_mul_u32((unsigned)(c - 1), d)), B)) --c;
+  while (c < N && q_lt(q_add(z0, q_mul_u32((unsigned)c, d)), B)) ++c;
   return c;
 }
 
 __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
-    const double* __restrict__ x, int64_t N, double u, const int32_t* __restrict__ tk,
-    const double* __restrict__ tc, const double* __restrict__ tO, const double* __restrict__ out3,
-    const double* __restrict__ r_p, int32_t* __restrict__ anc, unsigned long long* n_near) {
-  __shared__ double sh[RS_TPB / 32 + 1];
-  __shared__ double sh_last[RS_TPB];
+    const double* __restrict__ x, int64_t N, const TileRec* __restrict__ rec,
+    const long long* __restrict__ O, const RsScalars* __restrict__ scp, int32_t* __restrict__ anc,
+    unsigned long long* n_near, const MathTab* tab) {
+  __shared__ long long sh[RS_TPB / 32 + 1];
   const int t = blockIdx.x;
+  const int nt = (int)((N + RS_TILE - 1) / RS_TILE);
   const int64_t base = (int64_t)t * RS_TILE;
   const int64_t j0 = base + (int64_t)threadIdx.x * RS_IT;
-  if (out3[0] == -INFINITY) {  // degenerate population: identity
+  const RsScalars sc = *scp;
+  if (sc.degenerate) {  // every weight zero: identity
     for (int q = 0; q < RS_IT; ++q)
       if (j0 + q < N) anc[j0 + q] = (int32_t)(j0 + q);
     return;
   }
   double v[RS_IT];
   load_tile(x, N, base, v);
-  const int kt = tk[t];
-  const double c = tc[t], O = tO[t], r = *r_p;
-  const double R = kt == kDeadTile ? 0.0 : (double)kt * kLn2;
-  const double lo_tile = O * r, hi_tile = tO[t + 1] * r;
-  double loc = 0.0;
+  const TileRec r = rec[t];
+  long long ef[RS_IT];
+  tile_weights(v, r.k, tab, ef);
+  long long loc = 0;
 #pragma unroll
   for (int q = 0; q < RS_IT; ++q) {
-    const double e = (kt == kDeadTile) ? 0.0 : exp(v[q] - R);
-    loc = loc + e;
-    v[q] = loc;  // thread-local inclusive prefix
+    loc += ef[q];
+    ef[q] = loc;  // thread-local running sum
   }
-  const double incl = block_incl_scan<RS_TPB>(loc, sh);
-  const double excl = incl - loc;  // only used to offset this thread's prefixes
-  // The tile's offsets are split between threads at the running maximum of
-  // each thread's last (clamped) boundary, so that consecutive threads hand
-  // over exactly the same value even where rounding makes the per-thread
-  // prefixes disagree in the last bit.
-  double q_prev_thread_last;
-  {
-    const double Elast = excl + v[RS_IT - 1];
-    const double ql = fmin((O + c * Elast) * r, hi_tile);
-    const double pm = block_incl_max<RS_TPB>(fmax(ql, lo_tile), sh);
-    sh_last[threadIdx.x] = pm;
-    __syncthreads();
-    q_prev_thread_last = threadIdx.x ? sh_last[threadIdx.x - 1] : lo_tile;
+  const long long excl = block_incl_scan_i64<RS_TPB>(loc, sh) - loc;
+  if (j0 >= N) return;
+  const Q64 d{sc.d_hi, sc.d_lo}, z0{sc.z0_hi, sc.z0_lo};
+  const Q64 tol{(unsigned long long)sc.tolZ, 0ull};
+  const long long Ot = O[t], Ot1 = O[t + 1];
+  const int sh_t = r.k == kDeadTile ? 1 << 20 : sc.kmax - r.k + sc.G;
+  // lower boundary of this thread's first element
+  Q64 Blo;
+  if (threadIdx.x > 0) {
+    Blo = boundary(Ot, excl, sh_t, Ot1);
+  } else if (t > 0) {  // the previous tile's last boundary
+    const TileRec rp = rec[t - 1];
+    const int shp = rp.k == kDeadTile ? 1 << 20 : sc.kmax - rp.k + sc.G;
+    Blo = boundary(O[t - 1], rp.s, shp, Ot);
+  } else {
+    Blo = Q64{0ull, 0ull};
   }
-  const double tol = kBoundaryEps * (double)N;
-  double lo = q_prev_thread_last;
+  int64_t c = first_at_or_above(Blo, z0, d, sc.inv_d, N);
+  Q64 z = q_add(z0, q_mul_u32((unsigned)c, d));
   unsigned long long near = 0;
-#pragma unroll 1
   for (int q = 0; q < RS_IT; ++q) {
     const int64_t j = j0 + q;
     if (j >= N) break;
-    const double qraw = (O + c * (excl + v[q])) * r;
-    double hi = fmin(qraw, hi_tile);
-    if (hi < lo) hi = lo;
-    const int64_t i0 = first_at_or_above(lo, u, N);
-    const int64_t i1 = (j == N - 1) ? N : first_at_or_above(hi, u, N);
-    for (int64_t i = i0; i < i1; ++i) {
-      anc[i] = (int32_t)j;
-      const double y = (double)i + u;
-      if (fabs(qraw - y) < tol || fabs(lo - y) < tol) ++near;
+    const bool last = j == N - 1;
+    const Q64 Bhi = boundary(Ot, excl + ef[q], sh_t, Ot1);
+    const int64_t first = c;
+    Q64 zl = z;
+    while (c < N && (last || q_lt(z, Bhi))) {
+      anc[c] = (int32_t)j;
+      zl = z;
+      ++c;
+      z = q_add(z, d);
     }
-    lo = hi;
+    if (c > first) {  // the first offset near the lower boundary, the last near the upper
+      const Q64 zf = q_add(z0, q_mul_u32((unsigned)first, d));
+      if (q_lt(q_sub(zf, Blo), tol)) ++near;
+      if (!last && !q_lt(tol, q_sub(Bhi, zl))) ++near;
+    }
+    Blo = Bhi;
   }
-  near = __reduce_add_sync(0xffffffffu, (unsigned)near);
+  (void)nt;
+  near = __reduce_add_sync(__activemask(), (unsigned)near);
   if ((threadIdx.x & 31) == 0 && near) atomicAdd(n_near, near);
 }
 
@@ -291,7 +332,9 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
     case 2: y[i] = log(v); break;
     case 3: y[i] = exp(v); break;
     case 4: y[i] = log_unif53(bits, tab); break;
-    default: y[i] = tang_log(Unif<double>::from64(bits), tab); break;
+    case 5: y[i] = tang_log(Unif<double>::from64(bits), tab); break;
+    case 6: y[i] = __longlong_as_double(exp_fix54(v, tab)); break;
+    default: y[i] = __longlong_as_double(to_fix54(tang_exp(v, tab))); break;
   }
 }
 
@@ -300,7 +343,7 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
 using namespace smc;
 
 extern "C" smc_status smc_math_eval(int32_t fn, const double* x, double* y, int64_t n, void* stream) {
-  if (!x || !y || n < 0 || fn < 0 || fn > 5) return set_error(SMC_EINVAL, "bad argument");
+  if (!x || !y || n < 0 || fn < 0 || fn > 7) return set_error(SMC_EINVAL, "bad argument");
   if (n == 0) return SMC_OK;
   const MathTab* tab = nullptr;
   smc_status ts = math_table(&tab);
@@ -314,40 +357,77 @@ extern "C" const char* smc_last_error(void) { return g_err; }
 
 extern "C" const char* smc_version(void) { return "gb300-pcfg-smc 0.1 (sm_103a)"; }
 
+namespace smc {
+namespace {
+
+struct RsScratch {
+  TileRec* rec;  // [nt]
+  long long* O;  // [nt + 1]
+  RsScalars* sc;
+};
+
+size_t rs_scratch_bytes(int64_t nt) {
+  return align_up(sizeof(TileRec) * (size_t)nt, 256) + align_up(8 * (size_t)(nt + 1), 256) +
+         align_up(sizeof(RsScalars), 256);
+}
+
+RsScratch rs_carve(char* w, int64_t nt) {
+  RsScratch r;
+  r.rec = (TileRec*)w;
+  w += align_up(sizeof(TileRec) * (size_t)nt, 256);
+  r.O = (long long*)w;
+  w += align_up(8 * (size_t)(nt + 1), 256);
+  r.sc = (RsScalars*)w;
+  return r;
+}
+
+smc_status rs_check(const double* logw, int64_t N, double u, const int32_t* anc, const double* out3,
+                    const int64_t* n_near) {
+  if (!logw || !anc || !out3 || !n_near) return set_error(SMC_EINVAL, "NULL pointer");
+  if (N < 1 || N > 0x7fffffffLL) return set_error(SMC_EINVAL, "N must be in 1..2^31-1");
+  if (!(u > 0.0 && u < 1.0)) return set_error(SMC_EINVAL, "u must be in (0,1)");
+  if ((reinterpret_cast<uintptr_t>(logw) & 15) != 0)
+    return set_error(SMC_EINVAL, "logw must be 16-byte aligned");
+  return SMC_OK;
+}
+
+smc_status rs_launch(const double* logw, int64_t N, double u, int32_t* ancestors, double* out3,
+                     int64_t* n_near, const RsScratch& w, cudaStream_t cs) {
+  const MathTab* tab = nullptr;
+  smc_status ts = math_table(&tab);
+  if (ts) return ts;
+  const int nt = (int)((N + RS_TILE - 1) / RS_TILE);
+  SMC_CUDA_TRY(cudaMemsetAsync(n_near, 0, sizeof(int64_t), cs));
+  rs_tile_reduce<<<nt, RS_TPB, 0, cs>>>(logw, N, w.rec, tab);
+  SMC_CUDA_TRY(cudaGetLastError());
+  rs_combine<<<1, RS_TPB, 0, cs>>>(w.rec, nt, N, std::log((double)N), u, w.O, w.sc, out3, tab);
+  SMC_CUDA_TRY(cudaGetLastError());
+  rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, N, w.rec, w.O, w.sc, ancestors,
+                                      reinterpret_cast<unsigned long long*>(n_near), tab);
+  SMC_CUDA_TRY(cudaGetLastError());
+  return SMC_OK;
+}
+
+}  // namespace
+}  // namespace smc
+
 extern "C" size_t smc_resample_workspace_bytes(int64_t N) {
   if (N < 1) return 0;
-  const size_t nt = (size_t)((N + RS_TILE - 1) / RS_TILE);
-  return align_up(8 * nt, 256) * 3 + align_up(8 * (nt + 1), 256) + 256;
+  return rs_scratch_bytes((N + RS_TILE - 1) / RS_TILE);
 }
 
 extern "C" smc_status smc_resample(const double* logw, int64_t N, double u, int32_t* ancestors,
                                    double* out3, int64_t* n_near, void* workspace,
                                    size_t workspace_bytes, void* stream) {
-  if (!logw || !ancestors || !out3 || !n_near || !workspace)
-    return set_error(SMC_EINVAL, "NULL pointer");
-  if (N < 1 || N > 0x7fffffffLL) return set_error(SMC_EINVAL, "N must be in 1..2^31-1");
-  if (!(u > 0.0 && u < 1.0)) return set_error(SMC_EINVAL, "u must be in (0,1)");
+  smc_status st = rs_check(logw, N, u, ancestors, out3, n_near);
+  if (st) return st;
+  if (!workspace) return set_error(SMC_EINVAL, "NULL pointer");
   if (workspace_bytes < smc_resample_workspace_bytes(N))
     return set_error(SMC_EINVAL, "workspace too small");
-  if ((reinterpret_cast<uintptr_t>(logw) & 15) != 0)
-    return set_error(SMC_EINVAL, "logw must be 16-byte aligned");
-  cudaStream_t cs = (cudaStream_t)stream;
-  const int nt = (int)((N + RS_TILE - 1) / RS_TILE);
-  char* w = (char*)workspace;
-  int32_t* tM = (int32_t*)w;
-  double* ts = (double*)(w + align_up(8 * (size_t)nt, 256));
-  double* tc = (double*)(w + 2 * align_up(8 * (size_t)nt, 256));
-  double* tO = (double*)(w + 3 * align_up(8 * (size_t)nt, 256));
-  double* r = (double*)(w + 3 * align_up(8 * (size_t)nt, 256) + align_up(8 * (size_t)(nt + 1), 256));
-  SMC_CUDA_TRY(cudaMemsetAsync(n_near, 0, sizeof(int64_t), cs));
-  rs_tile_reduce<<<nt, RS_TPB, 0, cs>>>(logw, N, tM, ts);
-  SMC_CUDA_TRY(cudaGetLastError());
-  rs_combine<<<1, RS_TPB, 0, cs>>>(tM, ts, nt, N, tc, tO, out3, r);
-  SMC_CUDA_TRY(cudaGetLastError());
-  rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, N, u, tM, tc, tO, out3, r, ancestors,
-                                      reinterpret_cast<unsigned long long*>(n_near));
-  SMC_CUDA_TRY(cudaGetLastError());
-  return SMC_OK;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return set_error(SMC_EINVAL, "workspace must be 256-byte aligned");
+  return rs_launch(logw, N, u, ancestors, out3, n_near,
+                   rs_carve((char*)workspace, (N + RS_TILE - 1) / RS_TILE), (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -356,16 +436,19 @@ extern "C" smc_status smc_resample(const double* logw, int64_t N, double u, int3
 // Some callers cannot call cudaMalloc (code whose device memory is owned by
 // another framework's pool, paths where an allocation's implicit device-wide
 // synchronisation is not allowed, hosts that forbid allocation after start-up).
-// For them the tile scratch of the three resampling kernels lives in this
+// For them the per-tile scratch of the three resampling kernels lives in this
 // file-scope array, sized for populations of up to SMC_RESAMPLE_STATIC_MAX_N
-// particles (4096 tiles): 3 x 4096 tile values + 4097 offsets + N/S, 131,136
-// bytes that every GPU which loads the library keeps until the process exits.
-// Every call shares the array and it keeps the last call's contents; nothing in
-// it has to start at zero (each call writes every entry it later reads), but two
-// calls that overlap on the GPU race on it.
+// particles (4096 tiles): 4096 tile records, 4097 offsets and the search
+// scalars in 131,136 bytes that every GPU which loads the library keeps until
+// the process exits.  Every call shares the array and it keeps the last call's
+// contents; nothing in it has to start at zero (each call writes every entry it
+// later reads), but two calls that overlap on the GPU race on it.
 constexpr int kStaticTiles = (int)((SMC_RESAMPLE_STATIC_MAX_N + RS_TILE - 1) / RS_TILE);
 constexpr int kStaticDoubles = 3 * kStaticTiles + (kStaticTiles + 1) + 7;
 static __device__ __align__(256) double g_resample_scratch[kStaticDoubles];
+static_assert(sizeof(TileRec) * kStaticTiles % 256 == 0 && (8 * (kStaticTiles + 1) + 255) / 256 * 256 +
+                  sizeof(TileRec) * kStaticTiles + 256 <= sizeof(double) * kStaticDoubles,
+              "the static scratch holds the tile records, offsets and scalars");
 
 namespace {
 std::mutex g_static_mu;
@@ -402,22 +485,8 @@ extern "C" smc_status smc_resample_static(const double* logw, int64_t N, double 
   double* base = nullptr;
   smc_status st = static_scratch(&base);
   if (st) return st;
-  cudaStream_t cs = (cudaStream_t)stream;
-  const int nt = (int)((N + RS_TILE - 1) / RS_TILE);
-  int32_t* tM = reinterpret_cast<int32_t*>(base);
-  double* ts = base + kStaticTiles;
-  double* tc = base + 2 * kStaticTiles;
-  double* tO = base + 3 * kStaticTiles;            // nt + 1 entries
-  double* r = base + 4 * kStaticTiles + 1;
-  SMC_CUDA_TRY(cudaMemsetAsync(n_near, 0, sizeof(int64_t), cs));
-  rs_tile_reduce<<<nt, RS_TPB, 0, cs>>>(logw, N, tM, ts);
-  SMC_CUDA_TRY(cudaGetLastError());
-  rs_combine<<<1, RS_TPB, 0, cs>>>(tM, ts, nt, N, tc, tO, out3, r);
-  SMC_CUDA_TRY(cudaGetLastError());
-  rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, N, u, tM, tc, tO, out3, r, ancestors,
-                                      reinterpret_cast<unsigned long long*>(n_near));
-  SMC_CUDA_TRY(cudaGetLastError());
-  return SMC_OK;
+  return rs_launch(logw, N, u, ancestors, out3, n_near,
+                   rs_carve((char*)base, (N + RS_TILE - 1) / RS_TILE), (cudaStream_t)stream);
 }
 
 extern "C" smc_status smc_gather(const void* src, void* dst, const int32_t* anc, const int32_t* sp,

@@ -471,17 +471,20 @@ def sample(dist: str, n: int, p1: float = 0.0, p2: float = 0.0, seed: int = 1, r
 def math_eval(fn: str, x):
     """Device math parity hook: fn in table_log / table_exp / lib_log / lib_exp, or
     unif_log_bits / unif_log_table with x uint64 random bits (log of the FP64 uniform
-    they make, reduced on the integer pipes / through the table log of the double)."""
+    they make, reduced on the integer pipes / through the table log of the double), or
+    exp_fix54 / table_exp_fix54: round(e^x 2^54) as int64 for x <= 0 (integer pipes /
+    table exponential rounded to that grid)."""
     import torch
 
     code = {"table_log": 0, "table_exp": 1, "lib_log": 2, "lib_exp": 3, "unif_log_bits": 4,
-            "unif_log_table": 5}[fn]
-    if code >= 4:
+            "unif_log_table": 5, "exp_fix54": 6, "table_exp_fix54": 7}[fn]
+    if code in (4, 5):
         x = np.ascontiguousarray(x, dtype=np.uint64).view(np.float64)
     xd = torch.as_tensor(x, dtype=torch.float64).cuda()
     y = torch.empty_like(xd)
     _check(lib().smc_math_eval(code, _ptr(xd), _ptr(y), xd.numel(), None))
-    return y.cpu().numpy()
+    out = y.cpu().numpy()
+    return out.view(np.int64) if code >= 6 else out
 
 
 def version() -> str:
