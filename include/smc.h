@@ -250,7 +250,9 @@ void smc_server_destroy(smc_server_t s);
  * These are the normaliser / scan / systematic search / gather of Section 3.3 as
  * standalone HBM-streaming kernels.  All pointers are device pointers. */
 
-/* Scratch bytes smc_resample needs for a population of N. */
+/* Scratch bytes smc_resample needs for a population of N (8 bytes per particle
+ * for the tiles' running sums, kept between its first and third kernel, plus
+ * the per-tile records and offsets). */
 size_t smc_resample_workspace_bytes(int64_t N);
 
 /* Systematic resampling of one population (Section 3.3, parallel systematic

@@ -194,17 +194,10 @@ __device__ __forceinline__ unsigned long long mulhi64(unsigned long long a, unsi
   return __umul64hi(a, b);
 }
 
+// The core from X = -d 2^58 (an unsigned integer, -d < 38.5).
 template <int B>
-__device__ __forceinline__ long long exp_fix(double d, const MathTab* __restrict__ T) {
+__device__ __forceinline__ long long exp_fix_x(unsigned long long X, const MathTab* __restrict__ T) {
   static_assert(B >= 40 && B <= 54, "fixed-point bits");
-  if (!(d > -38.5)) return 0;
-  const long long b = __double_as_longlong(-d);
-  if (b <= 0) return 1ll << B;  // d >= 0
-  const int e = (int)(b >> 52);
-  if (e == 0) return 1ll << B;  // |d| below 2^-1022
-  const unsigned long long m = (unsigned long long)((b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll);
-  const int sh = e - 1017;  // X = -d 2^58 (below 2^64 since -d < 2^6)
-  const unsigned long long X = sh >= 0 ? (m << sh) : (-sh < 64 ? (m >> -sh) : 0ull);
   // Y = X / ln 2 in units of 2^-58: floor(X kInvLn2Q63 / 2^63)
   const unsigned long long Y = (mulhi64(X, kInvLn2Q63) << 1) | ((X * kInvLn2Q63) >> 63);
   const int n = (int)(Y >> 58);
@@ -223,6 +216,61 @@ __device__ __forceinline__ long long exp_fix(double d, const MathTab* __restrict
   const int s = 63 - B + n;  // to 2^-B units and the factor 2^-n
   return (long long)((q + (1ull << (s - 1))) >> s);
 }
+
+template <int B>
+__device__ __forceinline__ long long exp_fix(double d, const MathTab* __restrict__ T) {
+  if (!(d > -38.5)) return 0;
+  const long long b = __double_as_longlong(-d);
+  if (b <= 0) return 1ll << B;  // d >= 0
+  const int e = (int)(b >> 52);
+  if (e == 0) return 1ll << B;  // |d| below 2^-1022
+  const unsigned long long m = (unsigned long long)((b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll);
+  const int sh = e - 1017;  // X = -d 2^58 (below 2^64 since -d < 2^6)
+  return exp_fix_x<B>(sh >= 0 ? (m << sh) : (-sh < 64 ? (m >> -sh) : 0ull), T);
+}
+
+// ---- the argument k ln 2 - x in 2^-58 fixed point, on the integer pipes ----
+// For a power-of-two reference 2^k (|k| < 2^11) and a log-weight x <= k ln 2
+// (up to rounding): K = k ln 2 2^58 from ln 2 to 2^-116, and x 2^58 from the
+// bits of x, both in 128-bit integers, so X = K - x 2^58 is within two units
+// of (k ln 2 - x) 2^58 whatever the magnitudes of k and x.
+constexpr unsigned long long kLn2Q116Hi = 0xb17217f7d1cf7ull;               // round(ln 2 2^116) >> 64
+constexpr unsigned long long kLn2Q116Lo = 0x9abc9e3b39803f2full;           // its low 64 bits
+constexpr unsigned long long kExpCutQ58 = 0x9a00000000000000ull;           // 38.5 2^58
+
+__device__ __forceinline__ __int128 ref_q58(int k) {
+  const __int128 l = ((__int128)kLn2Q116Hi << 64) | (__int128)kLn2Q116Lo;
+  return ((__int128)k * l) >> 58;
+}
+
+// floor-toward-zero of x 2^58 as a signed 128-bit integer (|x| < 2^69)
+__device__ __forceinline__ __int128 fix_q58(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return 0;
+  const unsigned long long m = (unsigned long long)((b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll);
+  const int sh = e - 1017;
+  __int128 v;
+  if (sh >= 74)
+    v = (__int128)1 << 126;
+  else if (sh >= 0)
+    v = (__int128)m << sh;
+  else
+    v = -sh < 64 ? (__int128)(m >> -sh) : 0;
+  return b < 0 ? -v : v;
+}
+
+// round(e^(x - k ln 2) 2^B) for a log-weight x (-inf allowed) and the
+// reference K = ref_q58(k), |k| < 2^11: integer pipes only.
+template <int B>
+__device__ __forceinline__ long long weight_fix(double x, __int128 K, const MathTab* __restrict__ T) {
+  if (__double_as_longlong(x) == (long long)0xFFF0000000000000ull) return 0;  // -inf
+  __int128 X = K - fix_q58(x);
+  if (X < 0) X = 0;  // x above the reference by rounding: weight 1
+  if (X >= (__int128)kExpCutQ58) return 0;
+  return exp_fix_x<B>((unsigned long long)X, T);
+}
+
 __device__ __forceinline__ long long exp_fix54(double d, const MathTab* __restrict__ T) {
   return exp_fix<54>(d, T);
 }

@@ -281,6 +281,8 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
     if constexpr (sizeof(R) == 4) {
       // FP32 log-weights: FP32 exponential of an FP64 difference
       ef = to_fix54((double)expf((float)(lw - (double)kw * kLn2)));
+    } else if (kw > -2048 && kw < 2048) {
+      ef = weight_fix<54>(lw, ref_q58(kw), A.md.tab);  // integer pipes only
     } else {
       const double kd = (double)kw;
       const double d = fma(-kd, kLn2Lo, fma(-kd, kLn2Hi, lw));  // lw - kw ln 2, two-part ln 2

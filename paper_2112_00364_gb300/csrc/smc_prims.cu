@@ -6,17 +6,19 @@
 // segment kernel's integer arithmetic (smc_combine.cuh):
 //   1. rs_tile_reduce: per tile of TPB*IT weights, M_t = max, its power-of-two
 //      reference k_t = ceil(M_t / ln 2), the weights round(exp(x - k_t ln 2)
-//      2^50) on the integer pipes and their exact total s_t
+//      2^50) on the integer pipes, their exact tile running sums E_j and total
+//      (smc_resample keeps the E_j in its workspace for pass 3)
 //   2. rs_combine (one CTA): k = max k_t, integer offsets O_t of the totals in
 //      the common unit U, S = O_T, out3 = {k ln 2, S U 2^-k, log-Z increment},
 //      and the 64.64 fixed-point offsets' scale S / N and start u S / N
-//   3. rs_ancestors: per tile, the weights again and their integer running sum
-//      E_j; element j owns the offsets z_i = (i + u) S / N in [B_{j-1}, B_j),
-//      B_j = min(O_t + E_j 2^-(k - k_t + G), O_{t+1}) (the first element of a
-//      tile from the previous tile's last boundary, the last element of the
-//      population everything above), and writes a_i = j for them: every i is
-//      written exactly once, a_i = min{ j : P_j > z_i } as in the segment
-//      kernel's search, and the z_i are walked with integer additions.
+//   3. rs_ancestors: per tile, element j owns the offsets z_i = (i + u) S / N
+//      in [B_{j-1}, B_j), B_j = min(O_t + E_j 2^-(k - k_t + G), O_{t+1}) (the
+//      first element of a tile from the previous tile's last boundary, the last
+//      element of the population everything above): the counts c_j = #{ i :
+//      z_i < B_j } go to shared memory and the tile's offsets are spread over
+//      the threads, each writing a_i = j found by a binary search over the
+//      counts.  Every i is written exactly once and a_i = min{ j : P_j > z_i },
+//      the segment kernel's rule.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -66,8 +68,8 @@ __device__ __forceinline__ void load_tile(const double* __restrict__ x, int64_t 
 // The search scalars of a population, written by rs_combine.
 struct RsScalars {
   unsigned long long d_hi, d_lo, z0_hi, z0_lo;  // S / N and u S / N in 64.64 (units U)
+  unsigned long long inv_d;                      // floor(2^64 N / S)
   long long tolZ;                                // 1e-12 N on the q scale, in units U
-  double inv_d;                                  // N / S
   int32_t kmax, G, degenerate, pad_;
 };
 
@@ -77,37 +79,64 @@ constexpr int kRsBits = 50;
 // The tile's weights round(exp(x - k_t ln 2) 2^50) (k_t from the tile max).
 __device__ __forceinline__ void tile_weights(const double (&v)[RS_IT], int kt, const MathTab* tab,
                                              long long (&ef)[RS_IT]) {
-  const double kd = (double)kt;
+  if (kt == kDeadTile) {
 #pragma unroll
-  for (int q = 0; q < RS_IT; ++q) {
-    ef[q] = 0;
-    if (kt != kDeadTile) ef[q] = exp_fix<kRsBits>(fma(-kd, kLn2Lo, fma(-kd, kLn2Hi, v[q])), tab);
+    for (int q = 0; q < RS_IT; ++q) ef[q] = 0;
+  } else if (kt > -2048 && kt < 2048) {
+    const __int128 K = ref_q58(kt);
+#pragma unroll
+    for (int q = 0; q < RS_IT; ++q) ef[q] = weight_fix<kRsBits>(v[q], K, tab);
+  } else {
+    const double kd = (double)kt;
+#pragma unroll
+    for (int q = 0; q < RS_IT; ++q)
+      ef[q] = exp_fix<kRsBits>(fma(-kd, kLn2Lo, fma(-kd, kLn2Hi, v[q])), tab);
   }
 }
 
+// The tile's running sums E_j (tile-local, inclusive) of its weights: the
+// thread's 16 consecutive weights in sequence, the threads by a block scan.
+__device__ __forceinline__ void tile_running_sums(long long (&ef)[RS_IT], long long* sh) {
+  long long loc = 0;
+#pragma unroll
+  for (int q = 0; q < RS_IT; ++q) {
+    loc += ef[q];
+    ef[q] = loc;
+  }
+  const long long excl = block_incl_scan_i64<RS_TPB>(loc, sh) - loc;
+#pragma unroll
+  for (int q = 0; q < RS_IT; ++q) ef[q] += excl;
+}
+
+// Pass 1: tile reference, weights and running sums; the tile's record; with
+// `ecache` the running sums are kept for pass 3.
 __global__ void __launch_bounds__(RS_TPB) rs_tile_reduce(const double* __restrict__ x, int64_t N,
                                                          TileRec* __restrict__ rec,
+                                                         long long* __restrict__ ecache,
                                                          const MathTab* tab) {
   __shared__ long long sh[RS_TPB / 32 + 1];
   __shared__ int sh_k;
   double v[RS_IT];
   load_tile(x, N, (int64_t)blockIdx.x * RS_TILE, v);
-  double mx = -INFINITY;
+  long long key = order_key(v[0]);
 #pragma unroll
-  for (int q = 0; q < RS_IT; ++q) mx = fmax(mx, v[q]);
-  const double Mt = block_max_key<RS_TPB>(mx, sh);
+  for (int q = 1; q < RS_IT; ++q) key = max(key, order_key(v[q]));
+  const double Mt = block_max_key<RS_TPB>(from_order_key(key), sh);
   if (threadIdx.x == 0) sh_k = Mt == -INFINITY ? kDeadTile : tile_exponent(Mt);
   __syncthreads();
   const int kt = sh_k;
-  long long ef[RS_IT];
-  tile_weights(v, kt, tab, ef);
-  long long tot = 0;
+  long long E[RS_IT];
+  tile_weights(v, kt, tab, E);
+  tile_running_sums(E, sh);
+  if (ecache) {
+    longlong2* p = reinterpret_cast<longlong2*>(ecache + (int64_t)blockIdx.x * RS_TILE +
+                                                threadIdx.x * RS_IT);
 #pragma unroll
-  for (int q = 0; q < RS_IT; ++q) tot += ef[q];
-  const long long incl = block_incl_scan_i64<RS_TPB>(tot, sh);
+    for (int q = 0; q < RS_IT / 2; ++q) p[q] = make_longlong2(E[2 * q], E[2 * q + 1]);
+  }
   if (threadIdx.x == RS_TPB - 1) {
     TileRec r;
-    r.s = incl;
+    r.s = E[RS_IT - 1];
     r.k = kt;
     r.alive = 0;
     rec[blockIdx.x] = r;
@@ -142,8 +171,8 @@ __global__ void __launch_bounds__(RS_TPB) rs_combine(const TileRec* __restrict__
   s.d_lo = d.lo;
   s.z0_hi = z0.hi;
   s.z0_lo = z0.lo;
+  s.inv_d = (unsigned long long)(((unsigned __int128)N << 64) / (unsigned long long)c.S);
   s.tolZ = floor_i64(kBoundaryEps * Sd);
-  s.inv_d = (double)N / Sd;
   s.kmax = c.kmax;
   s.G = c.G;
   *sc = s;
@@ -166,24 +195,46 @@ __device__ __forceinline__ Q64 boundary(long long O_t, long long E, int sh, long
   return q_lt(c, b) ? c : b;
 }
 
-// min{ i in [0, N] : z_i >= B } with z_i = z0 + i d: an FP64 estimate, then
-// exact integer steps
-__device__ __forceinline__ int64_t first_at_or_above(Q64 B, Q64 z0, Q64 d, double inv_d, int64_t N) {
-  const double diff = ((double)B.hi - (double)z0.hi) + ((double)B.lo - (double)z0.lo) * 0x1p-64;
-  const double est = diff * inv_d;
-  int64_t c = est <= 0.0 ? 0 : (est >= (double)N ? N : (int64_t)ceil(est));
-  while (c > 0 && !q_lt(q_add(z0, q_mul_u32((unsigned)(c - 1), d)), B)) --c;
-  while (c < N && q_lt(q_add(z0, q_mul_u32((unsigned)c, d)), B)) ++c;
+// c = min{ i in [0, N] : z_i >= B } with z_i = z0 + i d: an estimate from the
+// 0.64 reciprocal of d, then exact integer steps.  Adds to *near the offsets
+// c - 1 and c when they lie within tol of B.
+__device__ __forceinline__ int64_t count_below(Q64 B, Q64 z0, Q64 d, unsigned long long inv_d,
+                                               int64_t N, Q64 tol, unsigned* near) {
+  if (!q_lt(z0, B)) {  // z_0 >= B
+    if (q_lt(q_sub(z0, B), tol)) ++*near;
+    return 0;
+  }
+  const Q64 diff = q_sub(B, z0);
+  int64_t c = (int64_t)min((unsigned long long)N, __umul64hi(diff.hi, inv_d));
+  Q64 zc = q_add(z0, q_mul_u32((unsigned)c, d));  // z_c
+  while (c < N && q_lt(zc, B)) {
+    ++c;
+    zc = q_add(zc, d);
+  }
+  while (c > 0 && !q_lt(q_sub(zc, d), B)) {
+    --c;
+    zc = q_sub(zc, d);
+  }
+  // here z_{c-1} < B <= z_c (when those offsets exist)
+  if (c > 0 && !q_lt(tol, q_sub(B, q_sub(zc, d)))) ++*near;
+  if (c < N && q_lt(q_sub(zc, B), tol)) ++*near;
   return c;
 }
 
+// Pass 3: every element's upper boundary B_j and offset count c_j = #{ i :
+// z_i < B_j } into shared memory, then the tile's offsets [c_lo, c_end) spread
+// over the threads, each finding its element by a binary search over the
+// counts.  Element j owns [B_{j-1}, B_j); the first element of a tile starts
+// at the previous tile's last boundary, the last element of the population
+// owns everything above.
 __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
     const double* __restrict__ x, int64_t N, const TileRec* __restrict__ rec,
-    const long long* __restrict__ O, const RsScalars* __restrict__ scp, int32_t* __restrict__ anc,
-    unsigned long long* n_near, const MathTab* tab) {
+    const long long* __restrict__ O, const RsScalars* __restrict__ scp,
+    const long long* __restrict__ ecache, int32_t* __restrict__ anc, unsigned long long* n_near,
+    const MathTab* tab) {
   __shared__ long long sh[RS_TPB / 32 + 1];
+  __shared__ int64_t sh_c[RS_TILE + 1];
   const int t = blockIdx.x;
-  const int nt = (int)((N + RS_TILE - 1) / RS_TILE);
   const int64_t base = (int64_t)t * RS_TILE;
   const int64_t j0 = base + (int64_t)threadIdx.x * RS_IT;
   const RsScalars sc = *scp;
@@ -192,60 +243,60 @@ __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
       if (j0 + q < N) anc[j0 + q] = (int32_t)(j0 + q);
     return;
   }
-  double v[RS_IT];
-  load_tile(x, N, base, v);
   const TileRec r = rec[t];
-  long long ef[RS_IT];
-  tile_weights(v, r.k, tab, ef);
-  long long loc = 0;
+  long long E[RS_IT];
+  if (ecache) {
+    const longlong2* p = reinterpret_cast<const longlong2*>(ecache + j0);
 #pragma unroll
-  for (int q = 0; q < RS_IT; ++q) {
-    loc += ef[q];
-    ef[q] = loc;  // thread-local running sum
+    for (int q = 0; q < RS_IT / 2; ++q) {
+      const longlong2 w = __ldcs(p + q);
+      E[2 * q] = w.x;
+      E[2 * q + 1] = w.y;
+    }
+  } else {
+    double v[RS_IT];
+    load_tile(x, N, base, v);
+    tile_weights(v, r.k, tab, E);
+    tile_running_sums(E, sh);
   }
-  const long long excl = block_incl_scan_i64<RS_TPB>(loc, sh) - loc;
-  if (j0 >= N) return;
   const Q64 d{sc.d_hi, sc.d_lo}, z0{sc.z0_hi, sc.z0_lo};
   const Q64 tol{(unsigned long long)sc.tolZ, 0ull};
   const long long Ot = O[t], Ot1 = O[t + 1];
   const int sh_t = r.k == kDeadTile ? 1 << 20 : sc.kmax - r.k + sc.G;
-  // lower boundary of this thread's first element
-  Q64 Blo;
-  if (threadIdx.x > 0) {
-    Blo = boundary(Ot, excl, sh_t, Ot1);
-  } else if (t > 0) {  // the previous tile's last boundary
-    const TileRec rp = rec[t - 1];
-    const int shp = rp.k == kDeadTile ? 1 << 20 : sc.kmax - rp.k + sc.G;
-    Blo = boundary(O[t - 1], rp.s, shp, Ot);
-  } else {
-    Blo = Q64{0ull, 0ull};
-  }
-  int64_t c = first_at_or_above(Blo, z0, d, sc.inv_d, N);
-  Q64 z = q_add(z0, q_mul_u32((unsigned)c, d));
-  unsigned long long near = 0;
+  unsigned near = 0;
+#pragma unroll
   for (int q = 0; q < RS_IT; ++q) {
     const int64_t j = j0 + q;
-    if (j >= N) break;
-    const bool last = j == N - 1;
-    const Q64 Bhi = boundary(Ot, excl + ef[q], sh_t, Ot1);
-    const int64_t first = c;
-    Q64 zl = z;
-    while (c < N && (last || q_lt(z, Bhi))) {
-      anc[c] = (int32_t)j;
-      zl = z;
-      ++c;
-      z = q_add(z, d);
-    }
-    if (c > first) {  // the first offset near the lower boundary, the last near the upper
-      const Q64 zf = q_add(z0, q_mul_u32((unsigned)first, d));
-      if (q_lt(q_sub(zf, Blo), tol)) ++near;
-      if (!last && !q_lt(tol, q_sub(Bhi, zl))) ++near;
-    }
-    Blo = Bhi;
+    int64_t c = N;
+    if (j < N - 1) c = count_below(boundary(Ot, E[q], sh_t, Ot1), z0, d, sc.inv_d, N, tol, &near);
+    sh_c[threadIdx.x * RS_IT + q + 1] = c;
   }
-  (void)nt;
-  near = __reduce_add_sync(__activemask(), (unsigned)near);
-  if ((threadIdx.x & 31) == 0 && near) atomicAdd(n_near, near);
+  if (threadIdx.x == 0) {
+    int64_t c0 = 0;
+    if (t > 0) {  // the previous tile's last boundary
+      const TileRec rp = rec[t - 1];
+      const int shp = rp.k == kDeadTile ? 1 << 20 : sc.kmax - rp.k + sc.G;
+      unsigned dummy = 0;
+      c0 = count_below(boundary(O[t - 1], rp.s, shp, Ot), z0, d, sc.inv_d, N, tol, &dummy);
+    }
+    sh_c[0] = c0;
+  }
+  __syncthreads();
+  const int n_el = (int)min((int64_t)RS_TILE, N - base);
+  const int64_t c_lo = sh_c[0], c_end = sh_c[n_el];
+  for (int64_t i = c_lo + threadIdx.x; i < c_end; i += RS_TPB) {
+    int lo = 1, hi = n_el;  // first idx in [1, n_el] with sh_c[idx] > i
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (sh_c[mid] > i)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    anc[i] = (int32_t)(base + lo - 1);
+  }
+  near = __reduce_add_sync(0xffffffffu, near);
+  if ((threadIdx.x & 31) == 0 && near) atomicAdd(n_near, (unsigned long long)near);
 }
 
 // Particle duplication: dst[f][i] = src[f][anc[i]], 16-byte stores of
@@ -361,23 +412,26 @@ namespace smc {
 namespace {
 
 struct RsScratch {
-  TileRec* rec;  // [nt]
-  long long* O;  // [nt + 1]
+  TileRec* rec;       // [nt]
+  long long* O;       // [nt + 1]
   RsScalars* sc;
+  long long* ecache;  // [nt * RS_TILE] running sums kept from pass 1, or NULL (recomputed)
 };
 
-size_t rs_scratch_bytes(int64_t nt) {
+size_t rs_scratch_bytes(int64_t nt, bool cache) {
   return align_up(sizeof(TileRec) * (size_t)nt, 256) + align_up(8 * (size_t)(nt + 1), 256) +
-         align_up(sizeof(RsScalars), 256);
+         align_up(sizeof(RsScalars), 256) + (cache ? 8 * (size_t)nt * RS_TILE : 0);
 }
 
-RsScratch rs_carve(char* w, int64_t nt) {
+RsScratch rs_carve(char* w, int64_t nt, bool cache) {
   RsScratch r;
   r.rec = (TileRec*)w;
   w += align_up(sizeof(TileRec) * (size_t)nt, 256);
   r.O = (long long*)w;
   w += align_up(8 * (size_t)(nt + 1), 256);
   r.sc = (RsScalars*)w;
+  w += align_up(sizeof(RsScalars), 256);
+  r.ecache = cache ? (long long*)w : nullptr;
   return r;
 }
 
@@ -398,11 +452,11 @@ smc_status rs_launch(const double* logw, int64_t N, double u, int32_t* ancestors
   if (ts) return ts;
   const int nt = (int)((N + RS_TILE - 1) / RS_TILE);
   SMC_CUDA_TRY(cudaMemsetAsync(n_near, 0, sizeof(int64_t), cs));
-  rs_tile_reduce<<<nt, RS_TPB, 0, cs>>>(logw, N, w.rec, tab);
+  rs_tile_reduce<<<nt, RS_TPB, 0, cs>>>(logw, N, w.rec, w.ecache, tab);
   SMC_CUDA_TRY(cudaGetLastError());
   rs_combine<<<1, RS_TPB, 0, cs>>>(w.rec, nt, N, std::log((double)N), u, w.O, w.sc, out3, tab);
   SMC_CUDA_TRY(cudaGetLastError());
-  rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, N, w.rec, w.O, w.sc, ancestors,
+  rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, N, w.rec, w.O, w.sc, w.ecache, ancestors,
                                       reinterpret_cast<unsigned long long*>(n_near), tab);
   SMC_CUDA_TRY(cudaGetLastError());
   return SMC_OK;
@@ -413,7 +467,7 @@ smc_status rs_launch(const double* logw, int64_t N, double u, int32_t* ancestors
 
 extern "C" size_t smc_resample_workspace_bytes(int64_t N) {
   if (N < 1) return 0;
-  return rs_scratch_bytes((N + RS_TILE - 1) / RS_TILE);
+  return rs_scratch_bytes((N + RS_TILE - 1) / RS_TILE, true);
 }
 
 extern "C" smc_status smc_resample(const double* logw, int64_t N, double u, int32_t* ancestors,
@@ -427,7 +481,7 @@ extern "C" smc_status smc_resample(const double* logw, int64_t N, double u, int3
   if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
     return set_error(SMC_EINVAL, "workspace must be 256-byte aligned");
   return rs_launch(logw, N, u, ancestors, out3, n_near,
-                   rs_carve((char*)workspace, (N + RS_TILE - 1) / RS_TILE), (cudaStream_t)stream);
+                   rs_carve((char*)workspace, (N + RS_TILE - 1) / RS_TILE, true), (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -486,7 +540,7 @@ extern "C" smc_status smc_resample_static(const double* logw, int64_t N, double 
   smc_status st = static_scratch(&base);
   if (st) return st;
   return rs_launch(logw, N, u, ancestors, out3, n_near,
-                   rs_carve((char*)base, (N + RS_TILE - 1) / RS_TILE), (cudaStream_t)stream);
+                   rs_carve((char*)base, (N + RS_TILE - 1) / RS_TILE, false), (cudaStream_t)stream);
 }
 
 extern "C" smc_status smc_gather(const void* src, void* dst, const int32_t* anc, const int32_t* sp,
