@@ -60,7 +60,14 @@ WORKLOADS = {
     "batch512": dict(kind="batch", n_runs=512, spec_seed=4, precision="fp32"),
     "serve2000": dict(kind="serve", n_runs=512, spec_seed=4, precision="fp32", rate=2000.0,
                       seconds_per_step=1.0, arrival_seed=5),
+    # the standalone resampling steps (normaliser, scan, systematic search) and
+    # the gather of a 2-field FP64 state, on a population larger than L2
+    "resample24": dict(kind="resample", N=1 << 24, fields=2, logw_seed=24, logw_scale=2.0,
+                       precision="fp64"),
 }
+
+HBM_PEAK_GBS = 6778.0  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, per particle
 
 # FP64 operations the step kernel executes per particle-step (2 x DFMA + DADD +
 # DMUL) and its DRAM traffic per launch, from one ncu capture of the workload
@@ -168,6 +175,9 @@ class Work:
         w = WORKLOADS[name]
         self.name, self.w, self.precision = name, w, w["precision"]
         self.runs = []
+        if w["kind"] == "resample":
+            self.units = w["N"]
+            return
         if w["kind"] in ("batch", "serve"):
             for q, sp in enumerate(inputs.batch_specs(w["n_runs"], seed=w["spec_seed"])):
                 if sp.kind == "lg":
@@ -197,6 +207,14 @@ class Work:
                "l2": "flushed between timed steps (512 MiB write)",
                "parallelism": "replicas (one independent workload per GPU)",
                "particle_steps_per_step": self.units}
+        if w["kind"] == "resample":
+            cfg.pop("particle_steps_per_step")
+            cfg.update(n_particles=w["N"], state_fields=w["fields"],
+                       step="smc_resample (FP64 normaliser, scan, systematic search) + smc_gather "
+                            "of a 2-field f64 state",
+                       logw=f"normal(0, {w['logw_scale']}) seed {w['logw_seed']}",
+                       l2="inputs (384 MiB) larger than L2; L2 also flushed between steps")
+            return cfg
         if w["kind"] == "serve":
             cfg.update(arrivals=f"Poisson, mean {w['rate']:.0f} requests/s, seed {w['arrival_seed']}+step",
                        stream_seconds_per_step=w["seconds_per_step"],
@@ -250,6 +268,8 @@ def run_reference(args, work: Work):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    if work.w["kind"] == "resample":
+        return run_reference_resample(args, work, ws)
     batch = work.w["kind"] in ("batch", "serve")
     n_sample = None if batch else min(work.runs[0]["N"], 1 << 14)
     max_runs = 32 if batch else 1
@@ -277,6 +297,36 @@ def run_reference(args, work: Work):
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_resample(args, work: Work, ws: int) -> int:
+    """The oracle's systematic resampling on the host, a 2^20-particle sample per step."""
+    import oracle
+
+    w = work.w
+    n_s = 1 << 20
+    lw = inputs.random_logw(w["N"], seed=w["logw_seed"], scale=w["logw_scale"])[:n_s]
+    for _ in range(args.warmup):
+        oracle.resample(lw, 0.5)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        oracle.resample(lw, (k + 0.5) / (args.steps + 1))
+    secs = time.perf_counter() - t0
+    value = args.steps * n_s / secs
+    sample = f"each step: oracle systematic resampling of {n_s} of the {w['N']} log-weights, no gather"
+    line = {
+        "impl": "reference", "metric": "standalone resample + gather throughput (particles/s)",
+        "value": value, "unit": "particles/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": work.config(),
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -386,6 +436,115 @@ def run_serve(args, work: Work, smc, torch, dist, ws: int, rank: int, local: int
     return 0
 
 
+def run_resample(args, work: Work, smc, torch, dist, ws: int, rank: int, local: int) -> int:
+    """The standalone resampling entry points on a 2^24-particle population."""
+    w = work.w
+    N = w["N"]
+    dev = torch.device("cuda", local if dist else 0)
+    lw_h = inputs.random_logw(N, seed=w["logw_seed"] + rank, scale=w["logw_scale"])
+    lw = torch.from_numpy(lw_h).to(dev)
+    wsb = torch.empty(smc.resample_workspace_bytes(N), dtype=torch.uint8, device=dev)
+    anc = torch.empty(N, dtype=torch.int32, device=dev)
+    o3 = torch.empty(3, dtype=torch.float64, device=dev)
+    nn = torch.empty(1, dtype=torch.int64, device=dev)
+    src = torch.randn(w["fields"], N, dtype=torch.float64, device=dev)
+    dst = torch.empty_like(src)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    rng = np.random.default_rng(99 + rank)
+
+    def step(u):
+        smc.resample(lw, u, anc, o3, nn, wsb, stream=stream)
+        smc.gather(src, dst, anc, stream=stream)
+
+    for _ in range(args.warmup):
+        step(float(rng.random() * 0.98 + 0.01))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    rs_ms, g_ms = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        u = float(rng.random() * 0.98 + 0.01)
+        e[0].record(stream)
+        smc.resample(lw, u, anc, o3, nn, wsb, stream=stream)
+        e[1].record(stream)
+        smc.gather(src, dst, anc, stream=stream)
+        e[2].record(stream)
+        e[2].synchronize()
+        rs_ms.append(e[0].elapsed_time(e[1]))
+        g_ms.append(e[1].elapsed_time(e[2]))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_s = (sum(rs_ms) + sum(g_ms)) * 1e-3
+    value, total_s = job_rate(args.steps * N, total_s, dist, dev)
+    # end to end: host log-weights in (pinned), ancestors and the gathered state out
+    lw_pin = torch.from_numpy(lw_h).pin_memory()
+    anc_pin = torch.empty(N, dtype=torch.int32).pin_memory()
+    dst_pin = torch.empty(w["fields"], N, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            lw.copy_(lw_pin, non_blocking=True)
+        step(float(rng.random() * 0.98 + 0.01))
+        with torch.cuda.stream(stream):
+            anc_pin.copy_(anc, non_blocking=True)
+            dst_pin.copy_(dst, non_blocking=True)
+        stream.synchronize()
+    e2e_value, _ = job_rate(e2e_steps * N, time.perf_counter() - t0, dist, dev)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    rs_s = float(np.mean(rs_ms)) * 1e-3
+    g_s = float(np.mean(g_ms)) * 1e-3
+    rs_gbs = RS_BYTES * N / rs_s / 1e9
+    g_bytes = 4 + 2 * 8 * w["fields"]
+    g_gbs = g_bytes * N / g_s / 1e9
+    roof = {"bound": "hbm", "achieved": rs_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+            "frac": rs_gbs / HBM_PEAK_GBS, "traffic": None,
+            "kernel": "smc_resample (rs_tile_reduce + rs_combine + rs_ancestors)",
+            "bytes_per_particle": RS_BYTES, "avg_call_us": rs_s * 1e6,
+            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+            "gather": {"achieved": g_gbs, "frac": g_gbs / HBM_PEAK_GBS, "avg_call_us": g_s * 1e6,
+                       "bytes_per_particle": g_bytes}}
+    cpu = None
+    if ws == 1:
+        import oracle
+
+        n_s = 1 << 21
+        t1 = time.perf_counter()
+        oracle.resample(lw_h[:n_s], 0.5)
+        secs = time.perf_counter() - t1
+        cpu = {"value": n_s / secs, "unit": "particles/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle systematic resampling of the first {n_s} log-weights "
+                         f"({secs:.2f} s single-threaded; no gather)"}
+    line = {
+        "metric": "standalone resample + gather throughput (particles/s)", "value": value,
+        "unit": "particles/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": work.config(),
+        "e2e": {"value": e2e_value, "unit": "particles/s", "h2d_bytes_per_step": 8 * N,
+                "d2h_bytes_per_step": 4 * N + 8 * w["fields"] * N},
+        "gpu_launches": 4 * args.steps, "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+        "n_near_last": int(nn.cpu()[0]),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,6 +574,8 @@ def main() -> int:
     dev = torch.device("cuda", torch.cuda.current_device())
     if work.w["kind"] == "serve":
         return run_serve(args, work, smc, torch, dist, ws, rank, local)
+    if work.w["kind"] == "resample":
+        return run_resample(args, work, smc, torch, dist, ws, rank, local)
     stream = torch.cuda.Stream()
     batch = work.w["kind"] == "batch"
     models = [smc.Model(r["kind"], **r["params"]) for r in work.runs]

@@ -17,9 +17,9 @@ struct __align__(16) TileRec {
   int32_t k, alive;
 };
 
-// Runs of fewer tiles than this combine a segment's tiles in every CTA of the
-// next wave (the offsets then live in shared memory); larger runs combine in
-// the last CTA of the segment.
+// Runs of fewer tiles than this may combine a segment's tiles in every CTA of
+// the next wave (the offsets then live in shared memory); others combine in the
+// last CTA of the segment.
 __host__ __device__ constexpr int redundant_cap(int tpb) { return 4 * tpb > 512 ? 4 * tpb : 512; }
 
 // A tile record written by another CTA of the previous segment (one 16-byte

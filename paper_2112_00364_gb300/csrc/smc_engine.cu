@@ -203,7 +203,7 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   const int nb = k & 1, cb = nb ^ 1;
   const StateView Sc = A.state[cb];
   const StateView Sn = A.state[nb];
-  const bool redundant = A.n_tiles < redundant_cap(TPB);
+  const bool redundant = A.redundant != 0;
   typename M::Lane L;
   bool near = false;
   if (k > 0) {
@@ -340,8 +340,10 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
 
 // One wave: CTA b runs tile cta_map[b].y of run cta_map[b].x, segment
 // k = wave - start_wave of that run.
+// 768 resident threads per SM (three 256-thread CTAs: the grid sizing of
+// tile_for) bounds the kernel to 85 registers per thread.
 template <typename R, int TPB>
-__global__ void __launch_bounds__(TPB) wave_kernel(const RunDev* __restrict__ runs,
+__global__ void __launch_bounds__(TPB, 768 / TPB) wave_kernel(const RunDev* __restrict__ runs,
                                                    const int2* __restrict__ cta_map, unsigned wave) {
   __shared__ __align__(16) RunDev sr;
   __shared__ double sh[TPB / 32 + 2 + TPB + 1];
@@ -452,6 +454,11 @@ int tile_for(int64_t N) {
 }
 
 int bucket_for(int tile) { return tile <= 32 ? 0 : tile <= 64 ? 1 : tile <= 128 ? 2 : 3; }
+
+int combine_in_every_cta(int tile, int n_tiles, bool single) {
+  const int tpb = 32 << bucket_for(tile);
+  return single ? (n_tiles < redundant_cap(tpb) ? 1 : 0) : (n_tiles <= tpb ? 1 : 0);
+}
 
 int real_state_fields(int kind) {
   int n_real, n_int;
@@ -948,6 +955,7 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
     ws = (char*)m->ws;
   }
   runs[0] = make_rundev(m, c, Ly, ws);
+  runs[0].redundant = combine_in_every_cta(Ly.tile, Ly.n_tiles, true);
   WavePlan W;
   SMC_CUDA_TRY(cudaMemsetAsync(runs[0].rs, 0, sizeof(RunState), cs));
   if ((st = upload_wave(runs, ws + meta_off, cs, &W, &m->staging))) return st;
@@ -1020,6 +1028,7 @@ extern "C" smc_status smc_run_batch(const smc_model_t* ms, const smc_run_cfg* cf
   std::vector<RunState*> states(n_runs);
   for (int q = 0; q < n_runs; ++q) {
     runs[q] = make_rundev(ms[q], &cfgs[q], lys[q], (char*)ws + offs[q]);
+    runs[q].redundant = combine_in_every_cta(lys[q].tile, lys[q].n_tiles, n_runs == 1);
     states[q] = runs[q].rs;
     SMC_CUDA_TRY(cudaMemsetAsync(runs[q].rs, 0, sizeof(RunState), cs));
   }

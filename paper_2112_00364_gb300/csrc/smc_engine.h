@@ -44,6 +44,7 @@ struct RunDev {
   double log_n, inv_n;  // log N and 1 / N, computed on the host
   int N, n_tiles, tile, max_segments, record_all, anc_rows;
   unsigned start_wave;  // wave index of the run's segment 0 (segment k runs in wave start_wave + k)
+  int redundant;        // combine a segment's tiles in every CTA of the next wave (else in the last CTA)
   uint32_t k0, k1;
 };
 
@@ -82,6 +83,10 @@ int model_fields(int kind, int* n_real, int* n_int);
 smc_status math_table(const MathTab** out);
 int tile_for(int64_t N);
 int bucket_for(int tile);
+// The combine placement of a run (the same results either way): in every CTA
+// of the next wave when latency matters (`single`: a run alone, up to
+// redundant_cap tiles), else only for runs of at most one tile per thread.
+int combine_in_every_cta(int tile, int n_tiles, bool single);
 Layout make_layout(const smc_model_s* m, const smc_run_cfg* c);
 RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws);
 size_t wave_meta_bytes(const std::vector<RunDev>& runs);

@@ -213,6 +213,7 @@ int admit(Server* S, smc_status* err) {
     q->ws = (char*)p;
     q->dev = make_rundev(q->model, &q->cfg, q->ly, q->ws);
     q->dev.start_wave = (unsigned)S->waves.load();  // its segment 0 runs in the next wave
+    q->dev.redundant = combine_in_every_cta(q->ly.tile, q->ly.n_tiles, false);
     e = cudaMemsetAsync(q->dev.rs, 0, sizeof(RunState), S->stream);
     if (e != cudaSuccess) {
       *err = cuda_fail(e, "cudaMemsetAsync(run state)");
