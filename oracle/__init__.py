@@ -54,16 +54,19 @@ class OrcModel(C.Structure):
 class OrcCfg(C.Structure):
     _fields_ = [("N", C.c_int64), ("seed", C.c_uint64), ("run_id", C.c_uint32),
                 ("max_segments", C.c_int32), ("follow_anc", _i32p), ("n_follow", C.c_int32),
-                ("pad_", C.c_int32)]
+                ("pad_", C.c_int32), ("ess_threshold", C.c_double), ("follow_resampled", _i32p),
+                ("n_follow_resampled", C.c_int32), ("pad2_", C.c_int32)]
 
 
 class OrcOut(C.Structure):
     _fields_ = [
         ("log_z", C.c_double), ("n_flagged", C.c_int64), ("n_flag_mismatch", C.c_int64),
         ("n_hard_mismatch", C.c_int64), ("n_overflow", C.c_int64), ("n_limit", C.c_int64),
+        ("n_ess_flagged", C.c_int64), ("n_dec_flag_mismatch", C.c_int64),
+        ("n_dec_hard_mismatch", C.c_int64),
         ("n_segments", C.c_int32), ("n_resamples", C.c_int32),
         ("final_logw", _f64p), ("real_fields", _f64p), ("int_fields", _i32p), ("stack", _f64p),
-        ("ancestors", _i32p), ("incr", _f64p), ("anc_capacity", C.c_int32),
+        ("ancestors", _i32p), ("resampled", _i32p), ("incr", _f64p), ("anc_capacity", C.c_int32),
         ("incr_capacity", C.c_int32),
     ]
 
@@ -183,11 +186,14 @@ KINDS = {"lg": LG, "crbd": CRBD, "rateshift": RATESHIFT, "geometric": GEOMETRIC}
 
 def smc_run(model: str, N: int, seed: int, run_id: int = 0, precision: int = FP64,
             max_segments: int = 1 << 20, follow=None, record_ancestors: bool = False,
-            record_incr: bool = False, **params) -> dict:
+            record_incr: bool = False, ess_threshold: float = 0.0, follow_resampled=None,
+            **params) -> dict:
     """Run the oracle SMC once.  `model` is one of lg / crbd / rateshift / geometric;
     params: obs, tree, rates=(lambda, mu), rho, sigma, fixed_mult, depth_cap,
     call_limit, lam_stack_cap, x0_mean, x0_sd, a, b, q_sd, r_sd, geo_p, geo_logw.
-    follow: int32 [n_resamples, N] ancestors from another implementation."""
+    follow: int32 [transitions, N] ancestors from another implementation (row k:
+    after checkpoint k); ess_threshold tau > 0: resample only when ESS < tau N;
+    follow_resampled: int32 [transitions] another implementation's decisions."""
     keep: list = []
     m = _model_struct(KINDS[model], precision, keep, **params)
     nr, ni, sc = C.c_int32(), C.c_int32(), C.c_int32()
@@ -199,6 +205,12 @@ def smc_run(model: str, N: int, seed: int, run_id: int = 0, precision: int = FP6
         follow = np.ascontiguousarray(follow, dtype=np.int32)
         keep.append(follow)
         cfg.follow_anc, cfg.n_follow = _p(follow, C.c_int32), follow.shape[0]
+    cfg.ess_threshold = ess_threshold
+    if follow_resampled is not None:
+        follow_resampled = np.ascontiguousarray(follow_resampled, dtype=np.int32)
+        keep.append(follow_resampled)
+        cfg.follow_resampled = _p(follow_resampled, C.c_int32)
+        cfg.n_follow_resampled = follow_resampled.shape[0]
     o = OrcOut()
     logw = np.empty(N)
     real = np.empty((max(nr, 1), N))
@@ -208,9 +220,12 @@ def smc_run(model: str, N: int, seed: int, run_id: int = 0, precision: int = FP6
     o.stack = _p(stack, C.c_double)
     cap_seg = min(max_segments, _segments_hint(model, params))
     anc = incr = None
+    resampled = np.zeros(cap_seg, dtype=np.int32)
+    o.resampled = _p(resampled, C.c_int32)
+    o.anc_capacity = cap_seg
     if record_ancestors:
         anc = np.empty((cap_seg, N), dtype=np.int32)
-        o.ancestors, o.anc_capacity = _p(anc, C.c_int32), cap_seg
+        o.ancestors = _p(anc, C.c_int32)
     if record_incr:
         incr = np.empty(cap_seg)
         o.incr, o.incr_capacity = _p(incr, C.c_double), cap_seg
@@ -218,10 +233,13 @@ def smc_run(model: str, N: int, seed: int, run_id: int = 0, precision: int = FP6
     res = dict(status=rc, log_z=o.log_z, n_segments=o.n_segments, n_resamples=o.n_resamples,
                n_flagged=o.n_flagged, n_flag_mismatch=o.n_flag_mismatch,
                n_hard_mismatch=o.n_hard_mismatch, n_overflow=o.n_overflow, n_limit=o.n_limit,
+               n_ess_flagged=o.n_ess_flagged, n_dec_flag_mismatch=o.n_dec_flag_mismatch,
+               n_dec_hard_mismatch=o.n_dec_hard_mismatch,
+               resampled=resampled[: max(0, min(o.n_segments - 1, cap_seg))],
                final_logw=logw, real_fields=real[:nr], int_fields=ints,
                stack=stack[:sc] if sc else None)
     if anc is not None:
-        res["ancestors"] = anc[: min(o.n_resamples, cap_seg)]
+        res["ancestors"] = anc[: max(0, min(o.n_segments - 1, cap_seg))]
     if incr is not None:
         res["incr"] = incr[: min(o.n_segments, cap_seg)]
     return res

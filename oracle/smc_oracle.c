@@ -15,6 +15,12 @@
  *     (b_stop,s,true).
  *   - Normalising constant: log Z accumulates log((1/N) sum_n w_n) at every
  *     checkpoint (Section 3.3, "normalizing constants").
+ *   - ESS-triggered resampling (Section 3.3, adaptive resampling based on the
+ *     effective sample size): ESS = (sum w)^2 / sum w^2; the population is
+ *     resampled only when ESS < tau N, otherwise the particles keep their
+ *     weights, which accumulate until the next resampling, and log Z then
+ *     gains log((1/N) sum_n W_n) of the accumulated weights (the paper gives
+ *     no formula; this is the standard estimator for it).
  *   - Systematic resampling (Section 3.3): one uniform u per checkpoint,
  *     a_i = min{ j : N P_j / S > i + u }, P_j the running sum of weights.
  *   - Models: the state-space model of Eq. 2 / Fig. 3 (generalised to
@@ -155,6 +161,16 @@ static int normaliser(const double *lw, int64_t N, double *m, double *S, double 
   *S = s;
   *incr = mx + (log(s) - log((double)N));
   return 0;
+}
+
+/* ESS = (sum_n w_n)^2 / sum_n w_n^2 with w_n = exp(logw_n - m), sums left to right */
+static double ess_of(const double *lw, int64_t N, double mx, double S) {
+  double q = 0.0;
+  for (int64_t i = 0; i < N; i++) {
+    const double w = exp(lw[i] - mx);
+    q = q + w * w;
+  }
+  return (S * S) / q;
 }
 
 static double resample_uniform(const uint32_t key[2], uint32_t k) {

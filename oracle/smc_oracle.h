@@ -60,6 +60,12 @@ typedef struct {
   const int32_t *follow_anc; /* [n_follow][N] ancestors from another implementation, or NULL */
   int32_t n_follow;
   int32_t pad_;
+  /* ESS-triggered resampling: resample at a checkpoint only when ESS < ess_threshold N
+   * (0: at every checkpoint) */
+  double ess_threshold;
+  const int32_t *follow_resampled; /* [n_follow_resampled] another implementation's decisions */
+  int32_t n_follow_resampled;
+  int32_t pad2_;
 } orc_cfg;
 
 typedef struct {
@@ -69,6 +75,8 @@ typedef struct {
   int64_t n_hard_mismatch;  /* follow mode: differing ancestors that were not flagged */
   int64_t n_overflow;       /* particles killed by the recursion-depth cap */
   int64_t n_limit;          /* particles killed by the per-segment call limit */
+  int64_t n_ess_flagged;    /* ESS decisions within 1e-9 of the threshold */
+  int64_t n_dec_flag_mismatch, n_dec_hard_mismatch;  /* follow mode: differing decisions */
   int32_t n_segments;
   int32_t n_resamples;
   /* caller-owned outputs (any may be NULL) */
@@ -76,7 +84,9 @@ typedef struct {
   double *real_fields;  /* [n_real][N] (FP32 values widened exactly) */
   int32_t *int_fields;  /* [n_int][N]; field 0 is the block index (pc) */
   double *stack;        /* [lam_stack_cap][N] (rate-shift) */
-  int32_t *ancestors;   /* [anc_capacity][N] */
+  int32_t *ancestors;   /* [anc_capacity][N]: row k = the ancestors after checkpoint k
+                           (the identity where the population was not resampled) */
+  int32_t *resampled;   /* [anc_capacity] 1 where the population was resampled after checkpoint k */
   double *incr;         /* [incr_capacity] per-segment log-Z increments */
   int32_t anc_capacity;
   int32_t incr_capacity;
