@@ -117,11 +117,16 @@ typedef struct {
   void *workspace;       /* optional caller-owned device workspace (>= smc_workspace_bytes);
                             NULL = the model handle allocates and caches one */
   size_t workspace_bytes;
+  double ess_threshold;  /* adaptive resampling (Section 3.3): 0 = resample after every
+                            checkpoint; tau > 0 = resample only when the effective sample
+                            size (sum w)^2 / sum w^2 < tau N, otherwise the particles keep
+                            their states and accumulated log-weights and the log-Z
+                            increment waits for the next resampling or the end */
 } smc_run_cfg;
 
 /* Counters of one run (host struct, filled by smc_run before it returns). */
 typedef struct {
-  int32_t n_segments;       /* segments executed (= log-Z increments) */
+  int32_t n_segments;       /* segments executed */
   int32_t n_resamples;      /* resampling steps executed */
   int64_t n_near_boundary;  /* resampled offsets within 1e-12 N of a cumulative-weight boundary */
   int64_t n_overflow;       /* particle-segments killed by the depth cap or stack capacity */
@@ -129,6 +134,7 @@ typedef struct {
   double device_ms;         /* GPU time of the run (CUDA events) */
   double kernel_ms;         /* time_kernels = 1: summed duration of the segment-kernel launches */
   int32_t kernel_launches;  /* segment-kernel launches of the run (one per wave and CTA size) */
+  int32_t n_ess_near;       /* ess_threshold > 0: checkpoints whose ESS lay within 1e-9 of tau N */
   smc_status status;        /* this run's own status (0, SMC_WKILLED, SMC_EDEGENERATE,
                                SMC_ESTEPLIMIT) */
 } smc_counters;
@@ -140,11 +146,14 @@ typedef struct {
   int32_t ancestors_rows;    /* capacity of `ancestors` in rows of N */
   double *log_z;             /* [1] log of the normalising-constant estimate */
   double *final_logw;        /* [N] log-weights after the last segment (not resampled) */
-  int32_t *ancestors;        /* [rows][N]: row r = ancestors of resampling r (record_all), or the
-                                last resampling's ancestors in row 0 */
+  int32_t *ancestors;        /* [rows][N]: row k = the ancestors after checkpoint k (record_all;
+                                the identity where the population was not resampled), or the
+                                last checkpoint's in row 0 */
   double *real_fields;       /* [n_real][N] final real state fields, field-major, widened to f64 */
   int32_t *int_fields;       /* [n_int][N] final int fields; field 0 is the block index */
   double *stack;             /* [stack_cap][N] final PSTATE stack (RATESHIFT), entries >= sp are 0 */
+  int32_t *resampled;        /* [rows] 1 where the population was resampled after checkpoint k
+                                (record_all; else row 0 holds the last checkpoint's) */
   smc_counters counters;     /* filled on return */
 } smc_result;
 

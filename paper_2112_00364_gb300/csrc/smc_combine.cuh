@@ -86,14 +86,18 @@ __device__ __forceinline__ long long magnitude(long long s, int kt, int kmax) {
 struct Combined {
   long long S;  // total in units U
   int kmax, G, alive;
+  double ess;   // (sum w)^2 / sum w^2 when the squared sums were given, else 0
 };
 
 // Combine n_tiles tile records into the offsets O[0..nt] (O[nt] = S).  With
 // `ks` non-NULL the records are first staged in shared memory (k_t into ks,
 // s_t into O, which the offsets then overwrite); otherwise they are read from
 // `rec` on each pass.  Every thread of the CTA calls it; all integer work.
+// With `q` (the tiles' sums of squared weights) non-NULL the effective sample
+// size is formed too, in FP64 by the first warp: sum w^2 relative to 2^(2 k_max).
 template <int TPB>
-__device__ Combined combine_offsets(const TileRec* rec, int nt, long long* O, int* ks, double* sh) {
+__device__ Combined combine_offsets(const TileRec* rec, int nt, long long* O, int* ks, double* sh,
+                                    const long long* q = nullptr) {
   constexpr int P = 4;  // consecutive tiles per thread per chunk
   int* shi = reinterpret_cast<int*>(sh);
   long long* shl = reinterpret_cast<long long*>(sh);
@@ -112,6 +116,7 @@ __device__ Combined combine_offsets(const TileRec* rec, int nt, long long* O, in
   c.alive = __syncthreads_or(al);
   c.G = 0;
   c.S = 0;
+  c.ess = 0.0;
   if (c.kmax == kDeadTile) return c;
   // G from b = sum over live tiles of (floor(s_t 2^-(k_max - k_t + 20)) + 1),
   // which lies between the exact sum T of the totals in units of 2^20 U (at
@@ -172,6 +177,25 @@ __device__ Combined combine_offsets(const TileRec* rec, int nt, long long* O, in
   }
   c.S = carry;
   if (threadIdx.x == 0) O[nt] = carry;
+  if (q) {
+    double* qs = sh + TPB / 32 + 1;
+    if (threadIdx.x < 32) {
+      double acc = 0.0;
+      for (int t = threadIdx.x; t < nt; t += 32) {
+        const int kt = ks ? ks[t] : load_rec(rec + t).k;
+        const int d2 = 2 * (c.kmax - kt);
+        if (kt != kDeadTile && d2 < 900) acc = acc + (double)__ldcg(q + t) * pow2i(-54 - d2);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o);
+      if (threadIdx.x == 0) {
+        const double s = (double)carry * pow2i(c.G - 54);
+        qs[0] = acc > 0.0 ? (s * s) / acc : 0.0;
+      }
+    }
+    __syncthreads();
+    c.ess = qs[0];
+  }
   __syncthreads();
   return c;
 }

@@ -57,7 +57,13 @@ __device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned l
 // Finish segment k-1 of the run from its combined offsets (one thread):
 // log Z += k_max ln 2 + (log S - log N) with S = S_units U, the increment
 // record, and the end of the run.  Returns whether segment k runs.
-__device__ __forceinline__ bool finish_segment(const RunDev& A, int k, const Combined& c) {
+// Whether to resample after checkpoint k-1 (the same in every CTA: c is).
+__device__ __forceinline__ bool decide_resample(const RunDev& A, const Combined& c) {
+  return !A.ess || c.ess < A.ess_target;
+}
+
+__device__ __forceinline__ bool finish_segment(const RunDev& A, int k, const Combined& c,
+                                               bool resample) {
   RunState* rs = A.rs;
   if (c.kmax == kDeadTile) {
     rs->log_z = -INFINITY;
@@ -71,12 +77,20 @@ __device__ __forceinline__ bool finish_segment(const RunDev& A, int k, const Com
   }
   const double Sd = (double)c.S;
   const double inc = (double)(c.kmax - 54 + c.G) * kLn2 + (tang_log(Sd, A.md.tab) - A.log_n);
-  rs->log_z = rs->log_z + inc;
-  A.incr[k - 1] = inc;
+  const bool go_on = c.alive && k < A.max_segments;
+  // the accumulated weights are closed into log Z when the population is
+  // resampled, at the end and at the step limit
+  const bool close = !go_on || resample;
+  if (close) rs->log_z = rs->log_z + inc;
+  A.incr[k - 1] = close ? inc : 0.0;
   rs->m = (double)c.kmax * kLn2;
   rs->S = Sd * pow2i(c.G - 54);
   rs->n_segments = k;
-  const bool go_on = c.alive && k < A.max_segments;
+  if (go_on) {
+    A.dec[k - 1] = resample ? 1 : 0;
+    rs->n_resamples += resample ? 1 : 0;
+    if (A.ess && fabs(c.ess - A.ess_target) <= 1e-9 * A.ess_target) rs->n_ess_near += 1;
+  }
   if (!c.alive) {
     rs->done = 1;
   } else if (!go_on) {
@@ -209,14 +223,17 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   if (k > 0) {
     SearchCtx X;
     X.rec = A.rec[cb];
+    bool resample;
     if (redundant) {
-      const Combined c = combine_offsets<TPB>(A.rec[cb], A.n_tiles, sh_O, sh_ks, sh);
+      const Combined c = combine_offsets<TPB>(A.rec[cb], A.n_tiles, sh_O, sh_ks, sh,
+                                              A.ess ? A.tq[cb] : nullptr);
       const bool go_on = c.kmax != kDeadTile && c.alive && k < A.max_segments;
-      if (t == 0 && threadIdx.x == 0) finish_segment(A, k, c);
+      resample = decide_resample(A, c);
+      if (t == 0 && threadIdx.x == 0) finish_segment(A, k, c, resample);
       if (!go_on) return;
       // the run's search scalars by one thread, shared through shared memory
       unsigned long long* shq = reinterpret_cast<unsigned long long*>(sh + TPB / 32 + 1);
-      if (threadIdx.x == 0) {
+      if (resample && threadIdx.x == 0) {
         Q64 d, z0;
         long long tolZ;
         search_scalars(c, N, Unif<double>::first(philox(0u, (uint32_t)(k - 1), 0u, 1u, A.k0, A.k1)),
@@ -236,6 +253,7 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
       X.z0 = Q64{shq[2], shq[3]};
       X.tolZ = (long long)shq[4];
     } else {
+      resample = rs->resample != 0;
       X.O = A.tile_O;
       X.ks = nullptr;
       X.kmax = rs->kmax;
@@ -245,10 +263,16 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
       X.tolZ = rs->tolZ;
     }
     if (valid) {
-      const int a = systematic_search(i, A, X, A.E[cb], &near);
       const int row = A.record_all ? k - 1 : 0;
-      if (row < A.anc_rows) A.anc[(size_t)row * N + i] = a;
-      M::gather(L, Sc, Sn, a, i, N, A.md);
+      if (resample) {
+        const int a = systematic_search(i, A, X, A.E[cb], &near);
+        if (row < A.anc_rows) A.anc[(size_t)row * N + i] = a;
+        M::gather(L, Sc, Sn, a, i, N, A.md);
+      } else {  // not resampled: the particle keeps its state and its accumulated weight
+        if (row < A.anc_rows) A.anc[(size_t)row * N + i] = i;
+        M::gather(L, Sc, Sn, i, i, N, A.md);
+        L.logw = (R)A.logw[i];
+      }
     }
     warp_add_u64(&rs->n_near, near ? 1ull : 0ull);
   } else if (valid) {
@@ -301,6 +325,13 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
     ef = (ef + (1ll << (shift - 1))) >> shift;
   const long long E = block_incl_scan_i64<TPB>(ef, reinterpret_cast<long long*>(sh));
   if (valid) A.E[nb][i] = E;
+  if (A.ess) {  // the tile's sum of squared weights, units 2^-54 of 2^(2 k_t)
+    const unsigned long long u = (unsigned long long)ef;
+    const long long sq = (long long)((__umul64hi(u, u) << 10) | ((u * u) >> 54));
+    __syncthreads();
+    const long long Q = block_incl_scan_i64<TPB>(sq, reinterpret_cast<long long*>(sh));
+    if (threadIdx.x == TPB - 1) A.tq[nb][t] = Q;
+  }
   if (threadIdx.x == TPB - 1) {
     TileRec r;
     r.s = E;
@@ -318,9 +349,12 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   __syncthreads();
   if (*sh_last) {  // the run's last tile of segment k: combine for the next wave
     __threadfence();
-    const Combined c = combine_offsets<TPB>(A.rec[nb], A.n_tiles, A.tile_O, nullptr, sh);
+    const Combined c = combine_offsets<TPB>(A.rec[nb], A.n_tiles, A.tile_O, nullptr, sh,
+                                            A.ess ? A.tq[nb] : nullptr);
     if (threadIdx.x == 0) {
-      if (finish_segment(A, k + 1, c)) {
+      const bool resample = decide_resample(A, c);
+      rs->resample = resample ? 1 : 0;
+      if (finish_segment(A, k + 1, c, resample) && resample) {
         Q64 d, z0;
         long long tolZ;
         search_scalars(c, N, Unif<double>::first(philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1)), &d,
@@ -495,6 +529,9 @@ Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
   L.E[1] = take(8 * N);
   L.rec[0] = take(sizeof(TileRec) * (size_t)L.n_tiles);
   L.rec[1] = take(sizeof(TileRec) * (size_t)L.n_tiles);
+  L.tq[0] = take(8 * (size_t)L.n_tiles);
+  L.tq[1] = take(8 * (size_t)L.n_tiles);
+  L.dec = take(4 * (size_t)L.max_segments);
   L.tO = take(8 * (size_t)(L.n_tiles + 1));
   L.rs = take(sizeof(RunState));
   L.anc = take(4 * N * (size_t)L.anc_rows);
@@ -519,6 +556,12 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
   A.logw = (double*)(ws + Ly.logw);
   A.rec[0] = (TileRec*)(ws + Ly.rec[0]);
   A.rec[1] = (TileRec*)(ws + Ly.rec[1]);
+  A.tq[0] = (long long*)(ws + Ly.tq[0]);
+  A.tq[1] = (long long*)(ws + Ly.tq[1]);
+  A.dec = (int32_t*)(ws + Ly.dec);
+  A.ess_tau = c->ess_threshold;
+  A.ess = c->ess_threshold > 0.0 ? 1 : 0;
+  A.ess_target = c->ess_threshold * (double)c->n_particles;
   A.tile_O = (long long*)(ws + Ly.tO);
   A.anc = (int32_t*)(ws + Ly.anc);
   A.incr = (double*)(ws + Ly.incr);
@@ -753,9 +796,16 @@ smc_status collect_run(const smc_model_s* m, const smc_run_cfg* c, const Layout&
                                              : (n_res > 0 ? 1 : 0);
     if (rows > 0) SMC_CUDA_TRY(cudaMemcpyAsync(r->ancestors, A.anc, 4 * (size_t)N * rows, kind, cs));
   }
+  if (r->resampled) {  // the decisions (record_all: one per checkpoint; else the last one)
+    const int n_tr = std::max(0, std::min(hrs.n_segments - 1, Ly.max_segments));
+    const int rows = c->record_all_ancestors ? std::min(n_tr, r->ancestors_rows) : (n_tr > 0 ? 1 : 0);
+    const int32_t* src = c->record_all_ancestors ? A.dec : A.dec + (n_tr - 1);
+    if (rows > 0) SMC_CUDA_TRY(cudaMemcpyAsync(r->resampled, src, 4 * (size_t)rows, kind, cs));
+  }
   smc_counters& ct = r->counters;
   ct.n_segments = hrs.n_segments;
-  ct.n_resamples = std::max(0, hrs.n_segments - 1);
+  ct.n_resamples = hrs.n_resamples;
+  ct.n_ess_near = hrs.n_ess_near;
   ct.n_near_boundary = (int64_t)hrs.n_near;
   ct.n_overflow = (int64_t)hrs.n_overflow;
   ct.n_limit = (int64_t)hrs.n_limit;
@@ -774,6 +824,8 @@ smc_status check_cfg(const smc_model_s* m, const smc_run_cfg* c) {
     return set_error(SMC_EINVAL, "unknown precision");
   if (c->max_segments < 0 || c->max_segments > kMaxSegments)
     return set_error(SMC_EINVAL, "max_segments must be in 0..2^24");
+  if (!(c->ess_threshold >= 0.0 && c->ess_threshold < 1e300))
+    return set_error(SMC_EINVAL, "ess_threshold must be finite and >= 0");
   return SMC_OK;
 }
 

@@ -27,7 +27,9 @@ struct RunState {
   unsigned long long n_near, n_overflow, n_limit;
   int32_t done, status, n_segments, n_resamples;
   uint32_t arrive;
-  int32_t kmax, G, pad_;  // the run's reference exponent and coarsening (one-CTA combine)
+  int32_t kmax, G;        // the run's reference exponent and coarsening (one-CTA combine)
+  int32_t resample;       // the one-CTA combine's decision for the next wave
+  int32_t n_ess_near;     // ESS decisions within 1e-9 of the threshold
 };
 
 // Everything a CTA needs about its run (copied to shared memory per CTA).
@@ -37,19 +39,24 @@ struct RunDev {
   double* logw;       // [N] log-weights of the latest segment (f64; FP32 values widened)
   long long* E[2];    // [N] tile-local running sums of the weights x 2^54 (int64), double-buffered by segment parity
   TileRec* rec[2];    // [n_tiles] tile reductions, double-buffered by segment parity
+  long long* tq[2];   // [n_tiles] ESS mode: the tiles' sums of squared weights (units 2^-54 of 2^(2 k_t))
+  int32_t* dec;       // [max_segments] 1 where the population was resampled after checkpoint k
   long long* tile_O;  // [n_tiles + 1] offsets in the run's unit, O_T = S (runs combined in one CTA)
   int32_t* anc;       // ancestor rows
   double* incr;       // [max_segments] per-segment log-Z increments
   RunState* rs;
   double log_n, inv_n;  // log N and 1 / N, computed on the host
+  double ess_tau;       // 0: resample after every checkpoint; > 0: only when ESS < ess_tau N
+  double ess_target;    // ess_tau N
   int N, n_tiles, tile, max_segments, record_all, anc_rows;
   unsigned start_wave;  // wave index of the run's segment 0 (segment k runs in wave start_wave + k)
   int redundant;        // combine a segment's tiles in every CTA of the next wave (else in the last CTA)
+  int ess;              // ess_tau > 0 (an integer flag for the kernel's branches)
   uint32_t k0, k1;
 };
 
 struct Layout {
-  size_t real[2], ints[2], stack[2], logw, E[2], rec[2], tO, rs, anc, incr,
+  size_t real[2], ints[2], stack[2], logw, E[2], rec[2], tq[2], dec, tO, rs, anc, incr,
       fin_real, fin_int, fin_stack, total;
   int n_tiles, tile, anc_rows, max_segments;
 };

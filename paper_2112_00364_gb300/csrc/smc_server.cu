@@ -36,7 +36,7 @@ namespace smc {
 // Snapshot of a run's state after a wave: everything retiring it needs.
 struct RunFlags {
   unsigned long long n_near, n_overflow, n_limit;
-  int32_t done, status, n_segments, pad;
+  int32_t done, status, n_segments, n_resamples, n_ess_near, pad;
 };
 
 __global__ void gather_flags_kernel(const RunDev* __restrict__ runs, int n, RunFlags* out) {
@@ -47,6 +47,8 @@ __global__ void gather_flags_kernel(const RunDev* __restrict__ runs, int n, RunF
   f.done = *(volatile const int32_t*)&rs->done;
   f.status = rs->status;
   f.n_segments = rs->n_segments;
+  f.n_resamples = rs->n_resamples;
+  f.n_ess_near = rs->n_ess_near;
   f.pad = 0;
   f.n_near = rs->n_near;
   f.n_overflow = rs->n_overflow;
@@ -246,6 +248,8 @@ smc_status retire(Server* S, int b) {
     hrs.done = f[i].done;
     hrs.status = f[i].status;
     hrs.n_segments = f[i].n_segments;
+    hrs.n_resamples = f[i].n_resamples;
+    hrs.n_ess_near = f[i].n_ess_near;
     hrs.n_near = f[i].n_near;
     hrs.n_overflow = f[i].n_overflow;
     hrs.n_limit = f[i].n_limit;

@@ -62,20 +62,20 @@ class RunCfg(C.Structure):
                 ("precision", C.c_int32), ("max_segments", C.c_int32),
                 ("record_all_ancestors", C.c_int32), ("time_kernels", C.c_int32),
                 ("pad_", C.c_int32), ("workspace", _vp),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("ess_threshold", C.c_double)]
 
 
 class Counters(C.Structure):
     _fields_ = [("n_segments", C.c_int32), ("n_resamples", C.c_int32),
                 ("n_near_boundary", C.c_int64), ("n_overflow", C.c_int64),
                 ("n_limit", C.c_int64), ("device_ms", C.c_double), ("kernel_ms", C.c_double),
-                ("kernel_launches", C.c_int32), ("status", C.c_int32)]
+                ("kernel_launches", C.c_int32), ("n_ess_near", C.c_int32), ("status", C.c_int32)]
 
 
 class Result(C.Structure):
     _fields_ = [("where", C.c_int32), ("ancestors_rows", C.c_int32), ("log_z", _vp),
                 ("final_logw", _vp), ("ancestors", _vp), ("real_fields", _vp),
-                ("int_fields", _vp), ("stack", _vp), ("counters", Counters)]
+                ("int_fields", _vp), ("stack", _vp), ("resampled", _vp), ("counters", Counters)]
 
 
 class ServerCfg(C.Structure):
@@ -234,9 +234,11 @@ class Model:
         return out.value
 
 
-def _cfg(N, seed, run_id, precision, max_segments, record_all, workspace, time_kernels=False):
+def _cfg(N, seed, run_id, precision, max_segments, record_all, workspace, time_kernels=False,
+         ess_threshold=0.0):
     c = RunCfg()
     c.time_kernels = int(time_kernels)
+    c.ess_threshold = float(ess_threshold)
     c.n_particles, c.seed, c.run_id = N, seed, run_id
     c.precision = PRECISIONS[precision]
     c.max_segments, c.record_all_ancestors = max_segments, int(record_all)
@@ -265,7 +267,7 @@ def _alloc_outputs(model: Model, N: int, rows: int, where: str, outputs: dict | 
 def _output_shapes(model: Model, N: int, rows: int) -> dict:
     return dict(log_z=((1,), "f8"), final_logw=((N,), "f8"), ancestors=((rows, N), "i4"),
                 real_fields=((model.n_real, N), "f8"), int_fields=((model.n_int, N), "i4"),
-                stack=((model.stack_cap, N), "f8"))
+                stack=((model.stack_cap, N), "f8"), resampled=((rows,), "i4"))
 
 
 def _wanted(model: Model, key: str) -> bool:
@@ -280,7 +282,8 @@ def _result_struct(out: dict, where: str, rows: int) -> Result:
     r = Result()
     r.where = MEM_HOST if where == "host" else MEM_DEVICE
     r.ancestors_rows = rows
-    for k in ("log_z", "final_logw", "ancestors", "real_fields", "int_fields", "stack"):
+    for k in ("log_z", "final_logw", "ancestors", "real_fields", "int_fields", "stack",
+              "resampled"):
         setattr(r, k, _ptr(out.get(k)))
     return r
 
@@ -290,21 +293,26 @@ def _result_dict(st: int, r: Result, out: dict, where: str, record_all: bool) ->
     res = dict(status=st, run_status=c.status, n_segments=c.n_segments,
                n_resamples=c.n_resamples, n_near_boundary=c.n_near_boundary,
                n_overflow=c.n_overflow, n_limit=c.n_limit, device_ms=c.device_ms,
-               kernel_ms=c.kernel_ms, kernel_launches=c.kernel_launches, **out)
+               kernel_ms=c.kernel_ms, kernel_launches=c.kernel_launches, n_ess_near=c.n_ess_near,
+               **out)
     res["log_z_value"] = float(out["log_z"][0]) if where == "host" else None
-    if record_all and "ancestors" in out:
-        res["ancestors"] = out["ancestors"][: c.n_resamples]
+    if record_all:
+        n_tr = max(0, c.n_segments - 1)  # checkpoints after which the run went on
+        for k in ("ancestors", "resampled"):
+            if k in out:
+                res[k] = out[k][:n_tr]
     return res
 
 
 def run(model: Model, N: int, seed: int, run_id: int = 0, precision: str = "fp64",
         max_segments: int = 0, record_all_ancestors: bool = False, where: str = "host",
         stream=None, workspace=None, outputs: dict | None = None,
-        time_kernels: bool = False) -> dict:
+        time_kernels: bool = False, ess_threshold: float = 0.0) -> dict:
     """smc_run.  where="host": outputs are numpy arrays; where="device": outputs are
-    torch CUDA tensors (allocated here unless passed in `outputs`)."""
+    torch CUDA tensors (allocated here unless passed in `outputs`).  ess_threshold
+    tau > 0: resample only when ESS < tau N."""
     cfg = _cfg(N, seed, run_id, precision, max_segments, record_all_ancestors, workspace,
-               time_kernels)
+               time_kernels, ess_threshold)
     rows = _rows(model, max_segments, record_all_ancestors)
     out = _alloc_outputs(model, N, rows, where, outputs)
     r = _result_struct(out, where, rows)
@@ -324,7 +332,7 @@ def run_batch(models: list, specs: list, precision: str = "fp64", where: str = "
     outs, rows_l = [], []
     for q, (m, sp) in enumerate(zip(models, specs)):
         c = _cfg(sp["N"], sp["seed"], sp.get("run_id", 0), precision, sp.get("max_segments", 0),
-                 record_all_ancestors, None)
+                 record_all_ancestors, None, False, sp.get("ess_threshold", 0.0))
         cfgs[q] = c
         rows = _rows(m, sp.get("max_segments", 0), record_all_ancestors)
         out = _alloc_outputs(m, sp["N"], rows, where, sp.get("outputs"))
@@ -354,8 +362,9 @@ class Server:
 
     def submit(self, model: Model, N: int, seed: int, run_id: int = 0, max_segments: int = 0,
                record_all_ancestors: bool = False, where: str = "host",
-               outputs: dict | None = None) -> int:
-        cfg = _cfg(N, seed, run_id, self.precision, max_segments, record_all_ancestors, None)
+               outputs: dict | None = None, ess_threshold: float = 0.0) -> int:
+        cfg = _cfg(N, seed, run_id, self.precision, max_segments, record_all_ancestors, None,
+                   False, ess_threshold)
         rows = _rows(model, max_segments, record_all_ancestors)
         out = _alloc_outputs(model, N, rows, where, outputs)
         r = _result_struct(out, where, rows)

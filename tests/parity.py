@@ -18,12 +18,15 @@ LOGZ_RTOL_FP64 = 1e-9  # log-Z tolerance at FP64 (relative)
 STATE_RTOL_FP64 = 1e-12  # final FP64 states / log-weights (relative)
 
 
-def run_pair(kind: str, N: int, seed: int, precision: str = "fp64", run_id: int = 0, **params):
+def run_pair(kind: str, N: int, seed: int, precision: str = "fp64", run_id: int = 0,
+             ess_threshold: float = 0.0, **params):
     model = smc.Model(kind, **params)
-    g = smc.run(model, N, seed, run_id=run_id, precision=precision, record_all_ancestors=True)
+    g = smc.run(model, N, seed, run_id=run_id, precision=precision, record_all_ancestors=True,
+                ess_threshold=ess_threshold)
     o = oracle.smc_run(kind, N, seed, run_id=run_id,
                        precision=oracle.FP64 if precision == "fp64" else oracle.FP32,
-                       follow=g["ancestors"], record_ancestors=True, **params)
+                       follow=g["ancestors"], record_ancestors=True, ess_threshold=ess_threshold,
+                       follow_resampled=g["resampled"] if ess_threshold > 0 else None, **params)
     model.close()
     return g, o
 
@@ -38,6 +41,7 @@ def assert_parity_fp64(g, o, logz_rtol=LOGZ_RTOL_FP64, state_rtol=STATE_RTOL_FP6
     assert g["n_segments"] == o["n_segments"]
     assert g["n_resamples"] == o["n_resamples"]
     assert o["n_hard_mismatch"] == 0, o["n_hard_mismatch"]
+    assert o["n_dec_hard_mismatch"] == 0, o["n_dec_hard_mismatch"]
     lz_g, lz_o = g["log_z_value"], o["log_z"]
     if np.isfinite(lz_o):
         assert abs(lz_g - lz_o) <= logz_rtol * max(1.0, abs(lz_o)), (lz_g, lz_o)
