@@ -223,3 +223,42 @@ def random_logw(n: int, seed: int, scale: float = 3.0, dead_frac: float = 0.0) -
     if dead_frac > 0:
         lw[rng.random(n) < dead_frac] = -np.inf
     return lw
+
+
+def seir_observations(n_days: int = 182, seed: int = 7, report_every: int = 7) -> np.ndarray:
+    """Daily report series for the vector-borne disease SEIR model (stand-in for
+    the dengue case data, which is not available): the model run forward with
+    fixed parameters (human attack 0.3, incubation 1/4.4, recovery 1/4.5,
+    mosquito attack 0.3, mosquito incubation 1/6.5, reporting 0.6; 6 infectious,
+    5 exposed, 7,370 humans, 3 mosquitoes per human) by numpy's generator.  New
+    infectious cases accumulate and a report y ~ Binomial(cases, 0.6) is made
+    every `report_every` days (days report_every - 1, 2 report_every - 1, ...);
+    other days hold -1 (no report).  Float array of length n_days."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h_lam, h_del, h_gam, m_lam, m_del, rho = 0.3, 1 / 4.4, 1 / 4.5, 0.3, 1 / 6.5, 0.6
+    n = 7370
+    hS, hE, hI, hR = n - 11, 5, 6, 0
+    mS, mE, mI, mR = 3 * n, 0, 0, 0
+    y = np.full(n_days, -1.0)
+    z = hI
+    for t in range(n_days):
+        if t > 0:
+            hN = hS + hE + hI + hR
+            tau = rng.binomial(hS, 1.0 - np.exp(-mI / hN))
+            dE = rng.binomial(tau, h_lam)
+            dI = rng.binomial(hE, h_del)
+            dR = rng.binomial(hI, h_gam)
+            m_tau = rng.binomial(mS, 1.0 - np.exp(-hI / hN))
+            mN = mS + mE + mI + mR
+            mdE = rng.binomial(m_tau, m_lam)
+            mdI = rng.binomial(mE, m_del)
+            hS, hE, hI, hR = hS - dE, hE + dE - dI, hI + dI - dR, hR + dR
+            mS, mE, mI = mS - mdE, mE + mdE - mdI, mI + mdI
+            mS, mE, mI, mR = (rng.binomial(mS, 6 / 7), rng.binomial(mE, 6 / 7),
+                              rng.binomial(mI, 6 / 7), rng.binomial(mR, 6 / 7))
+            mS += rng.binomial(mN, 1 / 7)
+            z += dI
+        if (t + 1) % report_every == 0:
+            y[t] = float(rng.binomial(z, rho))
+            z = 0
+    return y

@@ -25,7 +25,8 @@
  *     a_i = min{ j : N P_j / S > i + u }, P_j the running sum of weights.
  *   - Models: the state-space model of Eq. 2 / Fig. 3 (generalised to
  *     x_t = a x_{t-1} + b + q z), the CRBD model of Listing 1, a rate-shift
- *     variant of it, and the weighted geometric program of Fig. 2a.
+ *     variant of it, the weighted geometric program of Fig. 2a, and the SEIR
+ *     vector-borne disease model of Section 6.2 (Listing 2).
  *
  * Random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11) with
  * key (seed_lo, seed_hi XOR run_id) and counter (particle slot n,
@@ -136,6 +137,8 @@ static int model_setup(const orc_model *m, model_consts *mc) {
     double lnfact = 0.0;
     for (int32_t i = 2; i <= tips; i++) lnfact = lnfact + log((double)i);
     mc->corr = (double)(tips - 1) * LN2_D - lnfact;
+  } else if (m->kind == ORC_SEIR) {
+    if (!m->obs || m->T <= 0) return ORC_EINVAL;
   } else if (m->kind != ORC_GEOMETRIC) {
     return ORC_EINVAL;
   }
@@ -231,8 +234,31 @@ int orc_n_fields(const orc_model *m, int32_t *n_real, int32_t *n_int, int32_t *s
     case ORC_CRBD: *n_real = 2; *n_int = 1; return ORC_OK;
     case ORC_RATESHIFT: *n_real = 2; *n_int = 2; *stack_cap = m->lam_stack_cap; return ORC_OK;
     case ORC_GEOMETRIC: *n_real = 0; *n_int = 2; return ORC_OK;
+    case ORC_SEIR: *n_real = 6; *n_int = 10; return ORC_OK;
   }
   return ORC_EINVAL;
+}
+
+/* log k! : exact sums of logs below 32, Stirling's series for log Gamma(k+1)
+ * above (x = k + 1: (x - 1/2) ln x - x + ln(2 pi)/2 + 1/(12x) - 1/(360x^3) +
+ * 1/(1260x^5), truncation below 1e-13 there). */
+static double lfact_table[32];
+static int lfact_ready = 0;
+static double lfact_d(int64_t k) {
+  if (!lfact_ready) {
+    double acc = 0.0;
+    lfact_table[0] = 0.0;
+    for (int i = 1; i < 32; i++) {
+      acc = acc + log((double)i);
+      lfact_table[i] = acc;
+    }
+    lfact_ready = 1;
+  }
+  if (k < 32) return lfact_table[k];
+  const double x = (double)k + 1.0;
+  const double ix = 1.0 / x, ix2 = ix * ix;
+  const double series = ix * (1.0 / 12.0 - ix2 * (1.0 / 360.0 - ix2 * (1.0 / 1260.0)));
+  return (x - 0.5) * log(x) - x + HALF_LOG_2PI_D + series;
 }
 
 /* ------------------ precision instantiations ------------------ */
