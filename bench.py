@@ -55,6 +55,8 @@ UNIT = "particle-steps/s"
 WORKLOADS = {
     "crbd64": dict(kind="crbd", tips=64, tree_seed=2, N=1 << 16, precision="fp64"),
     "lg": dict(kind="lg", T=50, obs_seed=1, N=1024, precision="fp64"),
+    # the vector-borne disease SEIR model (Section 6.2), 26 weeks of synthetic reports
+    "seir182": dict(kind="seir", days=182, obs_seed=7, N=1 << 16, precision="fp64"),
     "rateshift256": dict(kind="rateshift", tips=256, tree_seed=3, N=1 << 20, precision="fp32",
                          sigma=0.3),
     "batch512": dict(kind="batch", n_runs=512, spec_seed=4, precision="fp32"),
@@ -191,6 +193,9 @@ class Work:
             if w["kind"] == "lg":
                 p = dict(obs=inputs.lg_observations(w["T"], seed=w["obs_seed"]))
                 seg = w["T"]
+            elif w["kind"] == "seir":
+                p = dict(obs=inputs.seir_observations(w["days"], seed=w["obs_seed"]))
+                seg = w["days"]
             else:
                 tree = inputs.yule_tree(w["tips"], seed=w["tree_seed"])
                 p = dict(tree=tree)
@@ -224,6 +229,10 @@ class Work:
             cfg.update(runs=w["n_runs"], n_particles_total=sum(r["N"] for r in self.runs),
                        mix="half linear-Gaussian (T log-uniform 20..500), half CRBD (tips "
                            "log-uniform 16..256), N log-uniform 256..65536, seeded (spec seed 4)")
+        elif w["kind"] == "seir":
+            cfg.update(model="vector-borne disease SEIR (Listing 2), 7370 humans, Beta priors",
+                       n_particles=w["N"], checkpoints=w["days"],
+                       observations=f"{w['days']} days, weekly synthetic reports, seed {w['obs_seed']}")
         elif w["kind"] == "lg":
             cfg.update(model="linear-Gaussian SSM x_t=0.9x+N(0,1), y~N(x,0.5^2)",
                        n_particles=w["N"], checkpoints=w["T"],

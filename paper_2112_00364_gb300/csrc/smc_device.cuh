@@ -86,6 +86,7 @@ struct MathTab {
   double inv_f52[192];  // (128 / j) 2^-52 (exact scaling of inv_f)
   double inv_f53[192];  // (128 / j) 2^-53
   unsigned long long exp2_neg_q63[128];  // round(2^(-j/128) 2^63)
+  double lfact[32];                      // log k!, k < 32 (sums of logs in order)
   double exp2_j[32];    // 2^(j/32)
   double inv_int[256];  // 1 / k (entry 0 unused)
 };
@@ -479,6 +480,112 @@ __device__ __noinline__ int poisson(Stream& s, R mean) {
 template <typename R>
 __device__ __forceinline__ R lognormal(Stream& s, R sigma) {
   return ex(sigma * normal01<R>(s), s);
+}
+
+// log k!: the table below 32, Stirling's series for log Gamma(k+1) above
+// (x = k + 1: (x - 1/2) ln x - x + ln(2 pi)/2 + 1/(12x) - 1/(360x^3) + 1/(1260x^5)).
+__device__ __forceinline__ double lfact(int k, const MathTab* __restrict__ T) {
+  if (k < 32) return __ldg(&T->lfact[k]);
+  const double x = (double)k + 1.0;
+  const double ix = 1.0 / x, ix2 = ix * ix;
+  const double series = ix * (1.0 / 12.0 - ix2 * (1.0 / 360.0 - ix2 * (1.0 / 1260.0)));
+  return (x - 0.5) * tang_log(x, T) - x + 0.91893853320467274178 + series;
+}
+
+// Gamma(shape, 1), shape >= 1 (Marsaglia and Tsang 2000): d = shape - 1/3,
+// c = 1/sqrt(9d); x ~ N(0,1), v = (1 + c x)^3 (rejected at once if 1 + c x <= 0),
+// u ~ U(0,1); accept d v if u < 1 - 0.0331 x^4 or ln u < x^2/2 + d (1 - v + ln v).
+template <typename R>
+__device__ __noinline__ R gamma_mt(Stream& s, R shape) {
+  const R d = shape - (R)1.0 / (R)3.0;
+  const R c = (R)1.0 / m_sqrt((R)9.0 * d);
+  for (int trial = 0; trial < 1000; ++trial) {
+    const R x = normal01<R>(s);
+    R v = (R)1.0 + c * x;
+    if (v <= (R)0.0) continue;
+    v = v * v * v;
+    const R u = uniform01<R>(s);
+    const R x2 = x * x;
+    if (u < (R)1.0 - (R)0.0331 * (x2 * x2)) return d * v;
+    if (lg(u, s) < (R)0.5 * x2 + d * ((R)1.0 - v + lg(v, s))) return d * v;
+  }
+  return d;
+}
+
+// Beta(a, b) = X / (X + Y), X ~ Gamma(a), Y ~ Gamma(b) drawn in that order.
+template <typename R>
+__device__ __forceinline__ R beta_ab(Stream& s, R a, R b) {
+  const R x = gamma_mt<R>(s, a);
+  const R y = gamma_mt<R>(s, b);
+  return x / (x + y);
+}
+
+// Binomial(n, p).  With p' = min(p, 1 - p) (the draw for p > 1/2 is n minus
+// the draw for 1 - p): n p' < 10: inversion by sequential search from 0 with
+// one uniform, f_0 = exp(n ln q), f_{k+1} = f_k (p'/q) (n - k) / (k + 1), at
+// most 200 terms; otherwise Hormann's transformed rejection with squeeze
+// (BTRS, 1993), one block per trial, acceptance in logs with log k!, at most
+// 1000 trials.
+template <typename R>
+__device__ __noinline__ int binomial(Stream& s, int n, R p) {
+  if (n <= 0 || !(p > (R)0.0)) return 0;
+  if (!(p < (R)1.0)) return n;
+  const bool flip = p > (R)0.5;
+  const R pp = flip ? (R)1.0 - p : p;
+  const R q = (R)1.0 - pp;
+  int k;
+  if ((R)n * pp < (R)10.0) {
+    const R u = uniform01<R>(s);
+    const R r = pp / q;
+    R f = ex((R)n * lg(q, s), s);
+    R acc = f;
+    k = 0;
+    while (u > acc && k < n && k < 200) {
+      f = f * r * (R)(n - k) / (R)(k + 1);
+      k += 1;
+      acc = acc + f;
+    }
+  } else {
+    const R spq = m_sqrt((R)n * pp * q);
+    const R b = (R)1.15 + (R)2.53 * spq;
+    const R a = (R)-0.0873 + (R)0.0248 * b + (R)0.01 * pp;
+    const R c = (R)n * pp + (R)0.5;
+    const R vr = (R)0.92 - (R)4.2 / b;
+    const R alpha = ((R)2.83 + (R)5.1 / b) * spq;
+    const R lpq = lg(pp / q, s);
+    const int m = (int)m_floor((R)(n + 1) * pp);
+    const R h = (R)lfact(m, s.tab) + (R)lfact(n - m, s.tab);
+    k = (int)m_floor((R)n * pp);
+    for (int trial = 0; trial < 1000; ++trial) {
+      const Block4 blk = s.next();
+      const R u = Unif<R>::first(blk) - (R)0.5;
+      R v = Unif<R>::second(blk);
+      const R us = (R)0.5 - m_fabs(u);
+      const R kr = m_floor(((R)2.0 * a / us + b) * u + c);
+      if (kr < (R)0.0 || kr > (R)n) continue;
+      const int kk = (int)kr;
+      if (us >= (R)0.07 && v <= vr) {
+        k = kk;
+        break;
+      }
+      v = lg(v * alpha / (a / (us * us) + b), s);
+      if (v <= h - (R)lfact(kk, s.tab) - (R)lfact(n - kk, s.tab) + (R)(kk - m) * lpq) {
+        k = kk;
+        break;
+      }
+    }
+  }
+  return flip ? n - k : k;
+}
+
+// log Binomial(y | z, rho) (-inf for y > z); zero counts contribute nothing.
+template <typename R>
+__device__ __forceinline__ R binomial_logpmf(int y, int z, R rho, const Stream& s) {
+  if (y > z) return neg_inf<R>();
+  R lp = (R)(lfact(z, s.tab) - lfact(y, s.tab) - lfact(z - y, s.tab));
+  if (y > 0) lp = lp + (R)y * lg(rho, s);
+  if (z - y > 0) lp = lp + (R)(z - y) * lg((R)1.0 - rho, s);
+  return lp;
 }
 
 // ---- FP64 warp / block primitives (deterministic association order) ----

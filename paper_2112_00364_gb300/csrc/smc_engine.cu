@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(TPB, 768 / TPB) wave_kernel(const RunDev* __re
   if (k < 0) return;
   switch (sr.md.kind) {
     case SMC_MODEL_LG: step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    case SMC_MODEL_SEIR: step_tile<SeirModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
     case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
     case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
     default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
@@ -458,6 +459,14 @@ smc_status math_table(const MathTab** out) {
     for (int j = 0; j < 128; ++j)
       h.exp2_neg_q63[j] = (unsigned long long)std::llroundl(
           std::ldexp(std::exp2l(-(long double)j / 128.0L), 63));
+    {
+      double acc = 0.0;
+      h.lfact[0] = 0.0;
+      for (int j = 1; j < 32; ++j) {
+        acc = acc + std::log((double)j);
+        h.lfact[j] = acc;
+      }
+    }
     h.inv_int[0] = 0.0;
     for (int k = 1; k < 256; ++k) h.inv_int[k] = 1.0 / (double)k;
     SMC_CUDA_TRY(cudaMemcpyToSymbol(g_math_tab, &h, sizeof(MathTab)));
@@ -475,6 +484,7 @@ int model_fields(int kind, int* n_real, int* n_int) {
     case SMC_MODEL_CRBD: *n_real = 2; *n_int = 1; return 0;
     case SMC_MODEL_RATESHIFT: *n_real = 2; *n_int = 2; return 0;
     case SMC_MODEL_GEOMETRIC: *n_real = 0; *n_int = 2; return 0;
+    case SMC_MODEL_SEIR: *n_real = 6; *n_int = 10; return 0;
   }
   return -1;
 }
@@ -851,6 +861,13 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
     if (!(d->r_sd > 0.0) || !(d->x0_sd >= 0.0) || !(d->q_sd >= 0.0))
       return set_error(SMC_EINVAL, "LG standard deviations must be >= 0 (r_sd > 0)");
     blob = 8 * (size_t)d->T;
+  } else if (d->kind == SMC_MODEL_SEIR) {
+    if (d->T < 1 || !d->obs) return set_error(SMC_EINVAL, "SEIR needs T >= 1 days of reports");
+    for (int t = 0; t < d->T; ++t)
+      if (!(d->obs[t] == -1.0 || (d->obs[t] >= 0.0 && d->obs[t] == std::floor(d->obs[t]) &&
+                                  d->obs[t] < 2147483647.0)))
+        return set_error(SMC_EINVAL, "SEIR reports must be counts >= 0 or -1 (day %d)", t);
+    blob = 8 * (size_t)d->T;
   } else if (d->kind == SMC_MODEL_GEOMETRIC) {
     if (!(d->geo_p >= 0.0 && d->geo_p <= 1.0)) return set_error(SMC_EINVAL, "geo_p in [0,1]");
   } else {
@@ -903,6 +920,7 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
     md.lg_lc = std::log(d->r_sd) + 0.91893853320467274178;
     m->n_segments_known = d->T;
   }
+  if (d->kind == SMC_MODEL_SEIR) m->n_segments_known = d->T;
   if (d->kind == SMC_MODEL_CRBD || d->kind == SMC_MODEL_RATESHIFT) {
     const int tips = (d->n_nodes + 1) / 2;
     double lnfact = 0.0;
@@ -925,7 +943,7 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
       return dst;
     };
     bool ok = true;
-    if (d->kind == SMC_MODEL_LG) {
+    if (d->kind == SMC_MODEL_LG || d->kind == SMC_MODEL_SEIR) {
       ok = (md.obs = (const double*)put(d->obs, 8 * (size_t)d->T)) != nullptr;
     } else {
       const size_t M = d->n_nodes;

@@ -160,6 +160,132 @@ struct GeoModel {
 };
 
 // ------------------------------------------------------------------------
+// Vector-borne disease SEIR model (Section 6.2, Listing 2): one checkpoint per
+// day (the `resample` of its `condition`).
+//   block 0 (day 0): the parameters from their Beta priors, the initial
+//     compartments (hI = 1 + Poisson(5), hE = Poisson(5), hR uniform, mosquitoes
+//     n 10^u with u ~ U(-1, 2)), then the condition of day 0;
+//   block 1 (day k): humans infected by infectious mosquitoes, exposed, turned
+//     infectious and recovered (Binomial draws in the listing's order), the same
+//     for mosquitoes, their daily survival (6/7) and births (1/7), then the
+//     condition of day k.
+// condition: new infectious humans accumulate in z; a report y_k != -1 adds
+// log Binomial(y_k | z, rho) to the weight and starts z again from 0.
+// PSTATE ints: block index, hS hE hI hR mS mE mI mR z; reals: hLambda hDelta
+// hGamma mLambda mDelta rho.  Humans n = 7370.
+// ------------------------------------------------------------------------
+template <typename Real>
+struct SeirModel {
+  using R = Real;
+  static constexpr int NB = 2, N_REAL = 6, N_INT = 10;
+  static constexpr bool HAS_STACK = false;
+  struct Lane {
+    int pc;
+    bool ckpt;
+    R logw;
+    int overflow, limited;
+    int c[9];
+    R th[6];
+  };
+  __device__ static void init(Lane& L) {
+    L.pc = 0;
+    L.logw = (R)0;
+#pragma unroll
+    for (int f = 0; f < 9; ++f) L.c[f] = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) L.th[f] = (R)0;
+  }
+  __device__ static void gather(Lane& L, const StateView& Sc, const StateView&, int a, int, int N,
+                                const ModelDev&) {
+    L.pc = Sc.inf_(0, a, N);
+#pragma unroll
+    for (int f = 0; f < 9; ++f) L.c[f] = Sc.inf_(f + 1, a, N);
+#pragma unroll
+    for (int f = 0; f < 6; ++f) L.th[f] = Sc.rf<R>(f, a, N);
+    L.logw = (R)0;
+  }
+  __device__ static void store(const Lane& L, const StateView& Sn, int i, int N) {
+    Sn.inf_(0, i, N) = L.pc;
+#pragma unroll
+    for (int f = 0; f < 9; ++f) Sn.inf_(f + 1, i, N) = L.c[f];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) Sn.rf<R>(f, i, N) = L.th[f];
+  }
+  __device__ static void begin(Lane& L) {
+    L.ckpt = false;
+    L.overflow = L.limited = 0;
+  }
+  __device__ static void block(int b, Lane& L, Stream& s, const ModelDev& md, const StateView&, int,
+                               int k, int) {
+    int* C = L.c;
+    R* th = L.th;
+    int hDeltaI;
+    if (b == 0) {
+      th[0] = beta_ab<R>(s, (R)1.0, (R)1.0);                                     // hLambda
+      th[1] = beta_ab<R>(s, (R)1.0 + (R)2.0 / (R)4.4, (R)3.0 - (R)2.0 / (R)4.4);  // hDelta
+      th[2] = beta_ab<R>(s, (R)1.0 + (R)2.0 / (R)4.5, (R)3.0 - (R)2.0 / (R)4.5);  // hGamma
+      th[3] = beta_ab<R>(s, (R)1.0, (R)1.0);                                     // mLambda
+      th[4] = beta_ab<R>(s, (R)1.0 + (R)2.0 / (R)6.5, (R)3.0 - (R)2.0 / (R)6.5);  // mDelta
+      th[5] = beta_ab<R>(s, (R)1.0, (R)1.0);                                     // rho
+      const int n = 7370;
+      const int hI = 1 + poisson<R>(s, (R)5.0);
+      const int hE = poisson<R>(s, (R)5.0);
+      const int hR = (int)m_floor(uniform_ab<R>(s, (R)0.0, (R)(n - hI - hE + 1)));
+      C[0] = n - hE - hI - hR;
+      C[1] = hE;
+      C[2] = hI;
+      C[3] = hR;
+      const R u = uniform_ab<R>(s, (R)-1.0, (R)2.0);
+      C[4] = (int)m_floor((R)n * ex(u * (R)2.302585092994045684, s));  // n 10^u
+      C[5] = C[6] = C[7] = 0;
+      C[8] = 0;
+      hDeltaI = hI;
+    } else {
+      const int hSP = C[0], hEP = C[1], hIP = C[2], hRP = C[3];
+      const int mSP = C[4], mEP = C[5], mIP = C[6], mRP = C[7];
+      // humans
+      const int hN = hSP + hEP + hIP + hRP;
+      const int hTau = binomial<R>(s, hSP, (R)1.0 - ex(-((R)mIP / (R)hN), s));
+      const int hDeltaE = binomial<R>(s, hTau, th[0]);
+      hDeltaI = binomial<R>(s, hEP, th[1]);
+      const int hDeltaR = binomial<R>(s, hIP, th[2]);
+      C[0] = hSP - hDeltaE;
+      C[1] = hEP + hDeltaE - hDeltaI;
+      C[2] = hIP + hDeltaI - hDeltaR;
+      C[3] = hRP + hDeltaR;
+      // mosquitoes
+      const int mTau = binomial<R>(s, mSP, (R)1.0 - ex(-((R)hIP / (R)hN), s));
+      const int mN = mSP + mEP + mIP + mRP;
+      const int mDeltaE = binomial<R>(s, mTau, th[3]);
+      const int mDeltaI = binomial<R>(s, mEP, th[4]);
+      const int mDeltaR = binomial<R>(s, mIP, (R)0.0);
+      int mS = mSP - mDeltaE;
+      int mE = mEP + mDeltaE - mDeltaI;
+      int mI = mIP + mDeltaI - mDeltaR;
+      int mR = mRP + mDeltaR;
+      const R mMu = (R)6.0 / (R)7.0, mNu = (R)1.0 / (R)7.0;
+      mS = binomial<R>(s, mS, mMu);
+      mE = binomial<R>(s, mE, mMu);
+      mI = binomial<R>(s, mI, mMu);
+      mR = binomial<R>(s, mR, mMu);
+      mS = mS + binomial<R>(s, mN, mNu);
+      C[4] = mS;
+      C[5] = mE;
+      C[6] = mI;
+      C[7] = mR;
+    }
+    C[8] = C[8] + hDeltaI;
+    const int y = (int)md.obs[k];
+    if (y != -1) {
+      L.logw = L.logw + binomial_logpmf<R>(y, C[8], th[5], s);
+      C[8] = 0;
+    }
+    L.pc = (k + 1 == md.T) ? PC_STOP : 1;
+    L.ckpt = true;
+  }
+};
+
+// ------------------------------------------------------------------------
 // Birth-death tree models (Listing 1).  PSTATE crossing checkpoints:
 // real 0 = lambda (RATESHIFT: the root rate lambda0), real 1 = mu, int 0 =
 // block index; RATESHIFT adds int 1 = stack pointer and the pending-rate
