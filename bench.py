@@ -75,8 +75,8 @@ RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, 
 # DMUL) and its DRAM traffic per launch, from one ncu capture of the workload
 # (profiles folder); the traffic holds only for the kernel sources with the
 # recorded digest.
-NCU = {"crbd64": dict(fp64_flop_per_pstep=43.4, bytes_per_launch=3.36e6,
-                     fp64_pipe_elapsed=0.236, src_digest="751e81baf78ce64b")}
+NCU = {"crbd64": dict(fp64_flop_per_pstep=38.5, bytes_per_launch=3.27e6,
+                     fp64_pipe_elapsed=0.268, src_digest="33f36ef9cb607f1e")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
