@@ -85,11 +85,18 @@ FP64_PEAK_FLOPS = 152 * 2070e6 * 4
 # the segment kernel's sources (the standalone resampling kernels are not among them)
 KERNEL_SOURCES = ("smc_engine.cu", "smc_engine.h", "smc_models.cuh", "smc_device.cuh",
                   "smc_combine.cuh")
+# the standalone resampling kernels' sources
+RS_SOURCES = ("smc_prims.cu", "smc_device.cuh", "smc_combine.cuh")
+
+# DRAM traffic of one smc_resample call at 2^24 (the three kernels' dram__bytes
+# read + write in one ncu capture, profiles folder), valid for the sources with
+# the recorded digest.
+RS_NCU = dict(bytes_per_call=3.535e8, src_digest="2f19134deccb975f")
 
 
-def src_digest() -> str:
+def src_digest(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in sources:
         h.update((ROOT / "paper_2112_00364_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
@@ -521,7 +528,9 @@ def run_resample(args, work: Work, smc, torch, dist, ws: int, rank: int, local: 
     g_bytes = 4 + 2 * 8 * w["fields"]
     g_gbs = g_bytes * N / g_s / 1e9
     roof = {"bound": "hbm", "achieved": rs_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-            "frac": rs_gbs / HBM_PEAK_GBS, "traffic": None,
+            "frac": rs_gbs / HBM_PEAK_GBS,
+            "traffic": RS_NCU["bytes_per_call"] if RS_NCU["src_digest"] == src_digest(RS_SOURCES)
+            else None,
             "kernel": "smc_resample (rs_tile_reduce + rs_combine + rs_ancestors)",
             "bytes_per_particle": RS_BYTES, "avg_call_us": rs_s * 1e6,
             "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",

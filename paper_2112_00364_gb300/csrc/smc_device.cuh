@@ -86,6 +86,8 @@ struct MathTab {
   double inv_f52[192];  // (128 / j) 2^-52 (exact scaling of inv_f)
   double inv_f53[192];  // (128 / j) 2^-53
   unsigned long long exp2_neg_q63[128];  // round(2^(-j/128) 2^63)
+  unsigned long long exp2_neg64_q63[64];    // round(2^(-j/64) 2^63)
+  unsigned long long exp2_neg4096_q63[64];  // round(2^(-j/4096) 2^63)
   double lfact[32];                      // log k!, k < 32 (sums of logs in order)
   double exp2_j[32];    // 2^(j/32)
   double inv_int[256];  // 1 / k (entry 0 unused)
@@ -218,6 +220,36 @@ __device__ __forceinline__ long long exp_fix_x(unsigned long long X, const MathT
   return (long long)((q + (1ull << (s - 1))) >> s);
 }
 
+// The same exponential from two 64-entry tables, T64[j] = 2^(-j/64) and
+// T4096[j] = 2^(-j/4096) in Q63 (the caller stages them, e.g. in shared
+// memory), and a degree-4 polynomial on a remainder below 2^-12.5: Y = X / ln 2
+// = n + j1/64 + j2/4096 + g, 2^-g = e^-r with r = g ln 2, and
+// e^-r = 1 - r + r^2/2 - r^3/6 + r^4/24 (truncation below 2^-69), the terms
+// past r in 32-bit products.  Four 64-bit multiply-highs instead of ten;
+// relative error below 2^-55, within one unit of the exact rounding for B <= 54.
+template <int B>
+__device__ __forceinline__ long long exp_fix_x2(unsigned long long X,
+                                                const unsigned long long* T64,
+                                                const unsigned long long* T4096) {
+  static_assert(B >= 40 && B <= 54, "fixed-point bits");
+  const unsigned long long Y = __umul64hi(X, kInvLn2Q63);  // X / ln 2 in units of 2^-57
+  const int n = (int)(Y >> 57);
+  if (n >= B + 1) return 0;  // at most half a unit
+  const unsigned long long g = Y & ((1ull << 45) - 1);       // g 2^57, g < 2^-12
+  const unsigned long long r = __umul64hi(g << 7, kLn2Q64);  // r 2^64, r < 2^-12.5
+  const unsigned rh = (unsigned)(r >> 20);                   // r 2^44, below 2^32
+  const unsigned long long r2 = (unsigned long long)rh * rh;  // r^2 2^88
+  const unsigned r2h = (unsigned)(r2 >> 32);                  // r^2 2^56, below 2^31
+  const unsigned r3 = (unsigned)(((unsigned long long)r2h * rh) >> 37);   // r^3 2^63
+  const unsigned r4 = (unsigned)(((unsigned long long)r2h * r2h) >> 49);  // r^4 2^63
+  const unsigned long long p =
+      0x8000000000000000ull - (r >> 1) + (r2 >> 26) - r3 / 6u + r4 / 24u;  // e^-r 2^63
+  const unsigned long long t = __umul64hi(T64[(Y >> 51) & 63], T4096[(Y >> 45) & 63]);  // 2^62
+  const unsigned long long q = __umul64hi(t, p);  // 2^-(Y 2^-57 - n) 2^61
+  const int s = 61 - B + n;                       // to 2^-B units and the factor 2^-n
+  return (long long)((q + (1ull << (s - 1))) >> s);
+}
+
 template <int B>
 __device__ __forceinline__ long long exp_fix(double d, const MathTab* __restrict__ T) {
   if (!(d > -38.5)) return 0;
@@ -228,6 +260,20 @@ __device__ __forceinline__ long long exp_fix(double d, const MathTab* __restrict
   const unsigned long long m = (unsigned long long)((b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll);
   const int sh = e - 1017;  // X = -d 2^58 (below 2^64 since -d < 2^6)
   return exp_fix_x<B>(sh >= 0 ? (m << sh) : (-sh < 64 ? (m >> -sh) : 0ull), T);
+}
+
+// round(e^d 2^B) for d <= 0 on the two-table exponential
+template <int B>
+__device__ __forceinline__ long long exp_fix2(double d, const unsigned long long* T64,
+                                              const unsigned long long* T4096) {
+  if (!(d > -38.5)) return 0;
+  const long long b = __double_as_longlong(-d);
+  if (b <= 0) return 1ll << B;
+  const int e = (int)(b >> 52);
+  if (e == 0) return 1ll << B;
+  const unsigned long long m = (unsigned long long)((b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll);
+  const int sh = e - 1017;
+  return exp_fix_x2<B>(sh >= 0 ? (m << sh) : (-sh < 64 ? (m >> -sh) : 0ull), T64, T4096);
 }
 
 // ---- the argument k ln 2 - x in 2^-58 fixed point, on the integer pipes ----
@@ -270,6 +316,34 @@ __device__ __forceinline__ long long weight_fix(double x, __int128 K, const Math
   if (X < 0) X = 0;  // x above the reference by rounding: weight 1
   if (X >= (__int128)kExpCutQ58) return 0;
   return exp_fix_x<B>((unsigned long long)X, T);
+}
+
+// The argument in 2^-52 units, in 64-bit integers: for a reference k with
+// |k| < 2048, K52 = round(k ln 2 2^52) (below 2^63) and x 2^52 truncated toward
+// zero (exact for |x| >= 1, |x| < 2^11; a log-weight beyond 2^11 in magnitude
+// lies more than 38.5 below such a reference, weight 0).  The argument is then
+// within 1.5 2^-52 of k ln 2 - x: a relative weight error below 2^-51.
+constexpr long long kExpCutQ52 = 0x268000000000000ll;  // 38.5 2^52
+
+__device__ __forceinline__ long long ref_q52(int k) {
+  return (long long)((ref_q58(k) + 32) >> 6);
+}
+
+template <int B>
+__device__ __forceinline__ long long weight_fix52(double x, long long K52,
+                                                  const unsigned long long* T64,
+                                                  const unsigned long long* T4096) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e >= 1034) return 0;  // |x| >= 2^11 (or -inf, NaN): far below the reference
+  const long long m = (b & 0x000FFFFFFFFFFFFFll) | (e ? 0x0010000000000000ll : 0ll);
+  const int sh = e - 1023;  // x 2^52 = m 2^sh
+  long long v = sh >= 0 ? (m << sh) : (-sh < 63 ? (m >> -sh) : 0ll);
+  if (b < 0) v = -v;
+  if (v <= K52 - kExpCutQ52) return 0;
+  long long X = K52 - v;
+  if (X < 0) X = 0;  // x above the reference by rounding: weight 1
+  return exp_fix_x2<B>((unsigned long long)X << 6, T64, T4096);
 }
 
 __device__ __forceinline__ long long exp_fix54(double d, const MathTab* __restrict__ T) {

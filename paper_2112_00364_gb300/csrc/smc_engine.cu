@@ -456,9 +456,16 @@ smc_status math_table(const MathTab** out) {
       h.inv_f53[j] = std::ldexp(h.inv_f[j], -53);
     }
     for (int j = 0; j < 32; ++j) h.exp2_j[j] = std::exp2((double)j / 32.0);
-    for (int j = 0; j < 128; ++j)
-      h.exp2_neg_q63[j] = (unsigned long long)std::llroundl(
-          std::ldexp(std::exp2l(-(long double)j / 128.0L), 63));
+    // 2^(-j/m) 2^63 rounded; j = 0 is 2^63 itself, outside the signed range
+    auto q63 = [](int j, int m) -> unsigned long long {
+      if (j == 0) return 1ull << 63;
+      return (unsigned long long)std::llroundl(std::ldexp(std::exp2l(-(long double)j / m), 63));
+    };
+    for (int j = 0; j < 128; ++j) h.exp2_neg_q63[j] = q63(j, 128);
+    for (int j = 0; j < 64; ++j) {
+      h.exp2_neg64_q63[j] = q63(j, 64);
+      h.exp2_neg4096_q63[j] = q63(j, 4096);
+    }
     {
       double acc = 0.0;
       h.lfact[0] = 0.0;

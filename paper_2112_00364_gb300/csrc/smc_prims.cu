@@ -6,19 +6,22 @@
 // segment kernel's integer arithmetic (smc_combine.cuh):
 //   1. rs_tile_reduce: per tile of TPB*IT weights, M_t = max, its power-of-two
 //      reference k_t = ceil(M_t / ln 2), the weights round(exp(x - k_t ln 2)
-//      2^50) on the integer pipes, their exact tile running sums E_j and total
-//      (smc_resample keeps the E_j in its workspace for pass 3)
+//      2^50) on the integer pipes (two-table exponential), their exact tile
+//      running sums E_j and total (smc_resample keeps the E_j in its
+//      workspace for pass 3)
 //   2. rs_combine (one CTA): k = max k_t, integer offsets O_t of the totals in
 //      the common unit U, S = O_T, out3 = {k ln 2, S U 2^-k, log-Z increment},
-//      and the 64.64 fixed-point offsets' scale S / N and start u S / N
-//   3. rs_ancestors: per tile, element j owns the offsets z_i = (i + u) S / N
-//      in [B_{j-1}, B_j), B_j = min(O_t + E_j 2^-(k - k_t + G), O_{t+1}) (the
-//      first element of a tile from the previous tile's last boundary, the last
-//      element of the population everything above): the counts c_j = #{ i :
-//      z_i < B_j } go to shared memory and the tile's offsets are spread over
-//      the threads, each writing a_i = j found by a binary search over the
-//      counts.  Every i is written exactly once and a_i = min{ j : P_j > z_i },
-//      the segment kernel's rule.
+//      and the scale N / S as a 64-bit mantissa and shift
+//   3. rs_ancestors: per tile, element j owns the offsets i + u in
+//      [Q_{j-1}, Q_j), Q_j = B_j N / S in 64.64 offset units, with
+//      B_j = min(O_t + E_j 2^-(k - k_t + G), O_{t+1}) (the first element of a
+//      tile from the previous tile's last boundary, the last element of the
+//      population everything above): c_j = #{ i : i + u < Q_j } = ceil(Q_j - u).
+//      Each element with a non-empty range marks its first offset in shared
+//      memory; an inclusive max-scan over the marks gives every offset its
+//      element, written out coalesced.  Every i is written exactly once and
+//      a_i = min{ j : Q_j > i + u }, the segment kernel's rule up to the
+//      rounding of N / S (below 2^-62 relative, far inside the 1e-12 band).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -66,26 +69,40 @@ __device__ __forceinline__ void load_tile(const double* __restrict__ x, int64_t 
 }
 
 // The search scalars of a population, written by rs_combine.
+// Offsets are counted in fixed point with F = 63 - bitlen(N) fraction bits
+// (N 2^F < 2^63): Q = B N / S 2^F for a boundary B in run units.
 struct RsScalars {
-  unsigned long long d_hi, d_lo, z0_hi, z0_lo;  // S / N and u S / N in 64.64 (units U)
-  unsigned long long inv_d;                      // floor(2^64 N / S)
-  long long tolZ;                                // 1e-12 N on the q scale, in units U
-  int32_t kmax, G, degenerate, pad_;
+  unsigned long long rn;  // floor(2^(64+L) N / S), in [2^63, 2^64)
+  long long uF;           // floor(u 2^F)
+  long long tolF;         // floor(1e-12 N 2^F)
+  int32_t L, F, kmax, G, degenerate, pad_;
 };
 
 // Weights as 2^-50 fixed-point integers: a tile of 4096 sums below 2^62.
 constexpr int kRsBits = 50;
 
+// The two exponential tables of exp_fix_x2 in shared memory.
+struct RsExpTab {
+  unsigned long long t64[64], t4096[64];
+};
+
+__device__ __forceinline__ void stage_exp_tables(RsExpTab& st, const MathTab* tab) {
+  if (threadIdx.x < 64) {
+    st.t64[threadIdx.x] = tab->exp2_neg64_q63[threadIdx.x];
+    st.t4096[threadIdx.x] = tab->exp2_neg4096_q63[threadIdx.x];
+  }
+}
+
 // The tile's weights round(exp(x - k_t ln 2) 2^50) (k_t from the tile max).
 __device__ __forceinline__ void tile_weights(const double (&v)[RS_IT], int kt, const MathTab* tab,
-                                             long long (&ef)[RS_IT]) {
+                                             const RsExpTab& st, long long (&ef)[RS_IT]) {
   if (kt == kDeadTile) {
 #pragma unroll
     for (int q = 0; q < RS_IT; ++q) ef[q] = 0;
   } else if (kt > -2048 && kt < 2048) {
-    const __int128 K = ref_q58(kt);
+    const long long K = ref_q52(kt);
 #pragma unroll
-    for (int q = 0; q < RS_IT; ++q) ef[q] = weight_fix<kRsBits>(v[q], K, tab);
+    for (int q = 0; q < RS_IT; ++q) ef[q] = weight_fix52<kRsBits>(v[q], K, st.t64, st.t4096);
   } else {
     const double kd = (double)kt;
 #pragma unroll
@@ -116,6 +133,8 @@ __global__ void __launch_bounds__(RS_TPB) rs_tile_reduce(const double* __restric
                                                          const MathTab* tab) {
   __shared__ long long sh[RS_TPB / 32 + 1];
   __shared__ int sh_k;
+  __shared__ RsExpTab st;
+  stage_exp_tables(st, tab);
   double v[RS_IT];
   load_tile(x, N, (int64_t)blockIdx.x * RS_TILE, v);
   long long key = order_key(v[0]);
@@ -126,7 +145,7 @@ __global__ void __launch_bounds__(RS_TPB) rs_tile_reduce(const double* __restric
   __syncthreads();
   const int kt = sh_k;
   long long E[RS_IT];
-  tile_weights(v, kt, tab, E);
+  tile_weights(v, kt, tab, st, E);
   tile_running_sums(E, sh);
   if (ecache) {
     longlong2* p = reinterpret_cast<longlong2*>(ecache + (int64_t)blockIdx.x * RS_TILE +
@@ -165,75 +184,103 @@ __global__ void __launch_bounds__(RS_TPB) rs_combine(const TileRec* __restrict__
   out3[0] = (double)c.kmax * kLn2;
   out3[1] = Sd * pow2i(c.G - kRsBits);
   out3[2] = (double)(c.kmax - kRsBits + c.G) * kLn2 + (tang_log(Sd, tab) - log_n);
-  const Q64 d = q_ratio((unsigned long long)c.S, (unsigned long long)N);
-  const Q64 z0 = q_scale(frac64(u), d);
-  s.d_hi = d.hi;
-  s.d_lo = d.lo;
-  s.z0_hi = z0.hi;
-  s.z0_lo = z0.lo;
-  s.inv_d = (unsigned long long)(((unsigned __int128)N << 64) / (unsigned long long)c.S);
-  s.tolZ = floor_i64(kBoundaryEps * Sd);
+  // N / S = rn 2^-(64+L) with rn in [2^63, 2^64): S in [2^61, 2^62] has sb = 62
+  // or 63 bits and N nb bits, so L = sb - nb puts N 2^(64+L) / S in (2^63, 2^65)
+  // (the numerator has 64 + sb <= 127 bits); one step down when it is >= 2^64.
+  const unsigned long long Su = (unsigned long long)c.S;
+  const int sb = 64 - __clzll((long long)Su), nb = 64 - __clzll((long long)N);
+  int L = sb - nb;
+  unsigned __int128 rn = ((unsigned __int128)N << (64 + L)) / Su;
+  if (rn >> 64) {
+    L -= 1;
+    rn = ((unsigned __int128)N << (64 + L)) / Su;
+  }
+  s.rn = (unsigned long long)rn;
+  s.L = L;
+  s.F = 63 - nb;
+  s.uF = (long long)(frac64(u) >> (64 - s.F));
+  s.tolF = (long long)(kBoundaryEps * (double)N * pow2i(s.F));
   s.kmax = c.kmax;
   s.G = c.G;
   *sc = s;
 }
 
-// O_t + E 2^-sh in 64.64 (E >= 0 a tile running sum), capped at cap
-__device__ __forceinline__ Q64 boundary(long long O_t, long long E, int sh, long long cap) {
-  Q64 b;
-  if (sh <= 0) {  // the run's unit is finer than the tile's: exact
-    b.hi = (unsigned long long)(O_t + (E << -sh));
-    b.lo = 0;
-  } else if (sh < 64) {
-    b.hi = (unsigned long long)(O_t + (E >> sh));
-    b.lo = (unsigned long long)E << (64 - sh);
-  } else {
-    b.hi = (unsigned long long)O_t;
-    b.lo = sh - 64 < 63 ? ((unsigned long long)E >> (sh - 64)) : 0ull;
-  }
-  const Q64 c{(unsigned long long)cap, 0ull};
-  return q_lt(c, b) ? c : b;
+// A tile's boundaries in offset units: Q_j = min(Q(O_t) + E_j 2^-sh N / S 2^F,
+// Q(O_{t+1})), Q(O) = floor(O N / S 2^F).  E_j <= s_t, so E_j 2^z with
+// z = clz(s_t) keeps 64 bits, and one multiply-high by rn gives
+// E_j 2^-sh N / S 2^F = umulhi(E_j 2^z, rn) 2^e, e = F - sh - L - z: within two
+// units of 2^-F, monotone in E_j.
+struct TileQ {
+  long long q0, qcap;
+  int z, e;
+};
+
+__device__ __forceinline__ long long q_of_offset(long long O, const RsScalars& sc) {
+  // 64 + L - F is sb or sb + 1 (62..64): see rs_combine
+  return (long long)(((unsigned __int128)(unsigned long long)O * sc.rn) >> (64 + sc.L - sc.F));
 }
 
-// c = min{ i in [0, N] : z_i >= B } with z_i = z0 + i d: an estimate from the
-// 0.64 reciprocal of d, then exact integer steps.  Adds to *near the offsets
-// c - 1 and c when they lie within tol of B.
-__device__ __forceinline__ int64_t count_below(Q64 B, Q64 z0, Q64 d, unsigned long long inv_d,
-                                               int64_t N, Q64 tol, unsigned* near) {
-  if (!q_lt(z0, B)) {  // z_0 >= B
-    if (q_lt(q_sub(z0, B), tol)) ++*near;
+__device__ __forceinline__ TileQ tile_q(long long O_t, long long O_t1, const TileRec& r,
+                                        const RsScalars& sc) {
+  TileQ q;
+  q.q0 = q_of_offset(O_t, sc);
+  q.qcap = q_of_offset(O_t1, sc);
+  if (r.k == kDeadTile || r.s <= 0) {
+    q.z = 0;
+    q.e = -64;  // no contribution
+  } else {
+    q.z = __clzll(r.s);
+    q.e = sc.F - (sc.kmax - r.k + sc.G) - sc.L - q.z;
+  }
+  return q;
+}
+
+__device__ __forceinline__ long long boundary_q(long long E, const TileQ& q, const RsScalars& sc) {
+  const unsigned long long m = __umul64hi((unsigned long long)E << q.z, sc.rn);
+  unsigned long long c;
+  if (q.e >= 0)
+    c = q.e < 64 ? (m << q.e) : ~0ull;
+  else
+    c = q.e > -64 ? (m >> -q.e) : 0ull;
+  const unsigned long long room = (unsigned long long)(q.qcap - q.q0);
+  return c < room ? q.q0 + (long long)c : q.qcap;
+}
+
+// c = #{ i in [0, N) : i + u < Q 2^-F } = ceil((Q - u 2^F) 2^-F), at most N.
+// Adds to *near the offsets c - 1 and c when they lie within 1e-12 N of Q.
+__device__ __forceinline__ int64_t count_below(long long Q, const RsScalars& sc, int64_t N,
+                                               unsigned* near) {
+  const long long V = Q - sc.uF;
+  if (V < 0) {  // Q below the first offset u
+    if (-V < sc.tolF) ++*near;
     return 0;
   }
-  const Q64 diff = q_sub(B, z0);
-  int64_t c = (int64_t)min((unsigned long long)N, __umul64hi(diff.hi, inv_d));
-  Q64 zc = q_add(z0, q_mul_u32((unsigned)c, d));  // z_c
-  while (c < N && q_lt(zc, B)) {
-    ++c;
-    zc = q_add(zc, d);
-  }
-  while (c > 0 && !q_lt(q_sub(zc, d), B)) {
-    --c;
-    zc = q_sub(zc, d);
-  }
-  // here z_{c-1} < B <= z_c (when those offsets exist)
-  if (c > 0 && !q_lt(tol, q_sub(B, q_sub(zc, d)))) ++*near;
-  if (c < N && q_lt(q_sub(zc, B), tol)) ++*near;
+  const long long one = 1ll << sc.F;
+  const long long f = V & (one - 1);
+  const int64_t c = min((int64_t)N, (int64_t)(V >> sc.F) + (f != 0 ? 1 : 0));
+  // offset c - 1 lies f below Q (a whole unit when f = 0); offset c lies
+  // one - f above it (on it when f = 0)
+  if (c > 0 && f != 0 && f < sc.tolF) ++*near;
+  if (c < N && (f == 0 || one - f < sc.tolF)) ++*near;
   return c;
 }
 
-// Pass 3: every element's upper boundary B_j and offset count c_j = #{ i :
-// z_i < B_j } into shared memory, then the tile's offsets [c_lo, c_end) spread
-// over the threads, each finding its element by a binary search over the
-// counts.  Element j owns [B_{j-1}, B_j); the first element of a tile starts
-// at the previous tile's last boundary, the last element of the population
-// owns everything above.
+// Pass 3: every element's offset count c_j (above), then the tile's offsets
+// [c_lo, c_end) in chunks of RS_TILE: the element j of a non-empty range
+// [c_{j-1}, c_j) marks position c_{j-1} with j, an inclusive max-scan over the
+// chunk (carrying the previous chunk's last element) gives each offset its
+// element, and the chunk is written out coalesced.  The first element of a
+// tile starts at the previous tile's last boundary; the last element of the
+// population owns everything above.
 __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
     const double* __restrict__ x, int64_t N, const TileRec* __restrict__ rec,
     const long long* __restrict__ O, const RsScalars* __restrict__ scp,
     const long long* __restrict__ ecache, int32_t* __restrict__ anc, unsigned long long* n_near,
     const MathTab* tab) {
   __shared__ long long sh[RS_TPB / 32 + 1];
-  __shared__ int64_t sh_c[RS_TILE + 1];
+  __shared__ int sh_last[RS_TPB + 1];
+  __shared__ __align__(16) int sh_m[RS_TILE];
+  __shared__ RsExpTab st;
   const int t = blockIdx.x;
   const int64_t base = (int64_t)t * RS_TILE;
   const int64_t j0 = base + (int64_t)threadIdx.x * RS_IT;
@@ -254,49 +301,81 @@ __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
       E[2 * q + 1] = w.y;
     }
   } else {
+    stage_exp_tables(st, tab);
+    __syncthreads();
     double v[RS_IT];
     load_tile(x, N, base, v);
-    tile_weights(v, r.k, tab, E);
+    tile_weights(v, r.k, tab, st, E);
     tile_running_sums(E, sh);
   }
-  const Q64 d{sc.d_hi, sc.d_lo}, z0{sc.z0_hi, sc.z0_lo};
-  const Q64 tol{(unsigned long long)sc.tolZ, 0ull};
-  const long long Ot = O[t], Ot1 = O[t + 1];
-  const int sh_t = r.k == kDeadTile ? 1 << 20 : sc.kmax - r.k + sc.G;
+  const long long Ot = O[t];
+  const TileQ tq = tile_q(Ot, O[t + 1], r, sc);
   unsigned near = 0;
+  int c[RS_IT];
 #pragma unroll
   for (int q = 0; q < RS_IT; ++q) {
     const int64_t j = j0 + q;
-    int64_t c = N;
-    if (j < N - 1) c = count_below(boundary(Ot, E[q], sh_t, Ot1), z0, d, sc.inv_d, N, tol, &near);
-    sh_c[threadIdx.x * RS_IT + q + 1] = c;
+    c[q] = (j < N - 1) ? (int)count_below(boundary_q(E[q], tq, sc), sc, N, &near) : (int)N;
   }
+  sh_last[threadIdx.x + 1] = c[RS_IT - 1];
   if (threadIdx.x == 0) {
     int64_t c0 = 0;
     if (t > 0) {  // the previous tile's last boundary
       const TileRec rp = rec[t - 1];
-      const int shp = rp.k == kDeadTile ? 1 << 20 : sc.kmax - rp.k + sc.G;
       unsigned dummy = 0;
-      c0 = count_below(boundary(O[t - 1], rp.s, shp, Ot), z0, d, sc.inv_d, N, tol, &dummy);
+      c0 = count_below(boundary_q(rp.s, tile_q(O[t - 1], Ot, rp, sc), sc), sc, N, &dummy);
     }
-    sh_c[0] = c0;
-  }
-  __syncthreads();
-  const int n_el = (int)min((int64_t)RS_TILE, N - base);
-  const int64_t c_lo = sh_c[0], c_end = sh_c[n_el];
-  for (int64_t i = c_lo + threadIdx.x; i < c_end; i += RS_TPB) {
-    int lo = 1, hi = n_el;  // first idx in [1, n_el] with sh_c[idx] > i
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (sh_c[mid] > i)
-        hi = mid;
-      else
-        lo = mid + 1;
-    }
-    anc[i] = (int32_t)(base + lo - 1);
+    sh_last[0] = (int)c0;
   }
   near = __reduce_add_sync(0xffffffffu, near);
   if ((threadIdx.x & 31) == 0 && near) atomicAdd(n_near, (unsigned long long)near);
+  __syncthreads();
+  const int c_prev = sh_last[threadIdx.x];  // count below this thread's first element
+  const int c_lo = sh_last[0], c_end = sh_last[RS_TPB];
+  const int jl0 = threadIdx.x * RS_IT;       // tile-local index of the first element
+  int carry = -1;
+  for (int cb = c_lo; cb < c_end; cb += RS_TILE) {
+    int4* m4 = reinterpret_cast<int4*>(sh_m);
+#pragma unroll
+    for (int q = 0; q < RS_IT / 4; ++q) m4[threadIdx.x + q * RS_TPB] = make_int4(-1, -1, -1, -1);
+    __syncthreads();
+    int lo = c_prev;
+#pragma unroll
+    for (int q = 0; q < RS_IT; ++q) {
+      if (lo < c[q] && lo >= cb && lo - cb < RS_TILE) sh_m[lo - cb] = jl0 + q;
+      lo = c[q];
+    }
+    __syncthreads();
+    // inclusive max-scan of the chunk: 16 consecutive marks per thread, then
+    // the threads' maxima by a block scan, then the carry
+    int m[RS_IT];
+    const int4* mp = reinterpret_cast<const int4*>(sh_m + jl0);
+#pragma unroll
+    for (int q = 0; q < RS_IT / 4; ++q) {
+      const int4 w = mp[q];
+      m[4 * q] = w.x;
+      m[4 * q + 1] = w.y;
+      m[4 * q + 2] = w.z;
+      m[4 * q + 3] = w.w;
+    }
+#pragma unroll
+    for (int q = 1; q < RS_IT; ++q) m[q] = max(m[q], m[q - 1]);
+    const long long run = block_incl_max_i64<RS_TPB>((long long)m[RS_IT - 1], sh);
+    sh_last[threadIdx.x + 1] = (int)run;
+    __syncthreads();
+    // the maximum over the threads before this one and the previous chunks
+    const int ex = max(carry, threadIdx.x ? sh_last[threadIdx.x] : -1);
+    int4* wp = reinterpret_cast<int4*>(sh_m + jl0);
+#pragma unroll
+    for (int q = 0; q < RS_IT / 4; ++q)
+      wp[q] = make_int4(max(m[4 * q], ex), max(m[4 * q + 1], ex), max(m[4 * q + 2], ex),
+                        max(m[4 * q + 3], ex));
+    __syncthreads();
+    const int n_here = min(RS_TILE, c_end - cb);
+    for (int k = threadIdx.x; k < n_here; k += RS_TPB) anc[cb + k] = (int32_t)(base + sh_m[k]);
+    carry = max(carry, sh_last[RS_TPB]);
+    __syncthreads();
+  }
 }
 
 // Particle duplication: dst[f][i] = src[f][anc[i]], 16-byte stores of
@@ -388,7 +467,14 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
     case 4: y[i] = log_unif53(bits, tab); break;
     case 5: y[i] = tang_log(Unif<double>::from64(bits), tab); break;
     case 6: y[i] = __longlong_as_double(exp_fix54(v, tab)); break;
-    default: y[i] = __longlong_as_double(to_fix54(tang_exp(v, tab))); break;
+    case 7: y[i] = __longlong_as_double(to_fix54(tang_exp(v, tab))); break;
+    case 8:
+      y[i] = __longlong_as_double(exp_fix2<54>(v, tab->exp2_neg64_q63, tab->exp2_neg4096_q63));
+      break;
+    default:
+      y[i] = __longlong_as_double(
+          weight_fix52<50>(v, 0ll, tab->exp2_neg64_q63, tab->exp2_neg4096_q63));
+      break;
   }
 }
 
@@ -397,7 +483,7 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
 using namespace smc;
 
 extern "C" smc_status smc_math_eval(int32_t fn, const double* x, double* y, int64_t n, void* stream) {
-  if (!x || !y || n < 0 || fn < 0 || fn > 7) return set_error(SMC_EINVAL, "bad argument");
+  if (!x || !y || n < 0 || fn < 0 || fn > 9) return set_error(SMC_EINVAL, "bad argument");
   if (n == 0) return SMC_OK;
   const MathTab* tab = nullptr;
   smc_status ts = math_table(&tab);

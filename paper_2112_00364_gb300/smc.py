@@ -482,11 +482,13 @@ def math_eval(fn: str, x):
     unif_log_bits / unif_log_table with x uint64 random bits (log of the FP64 uniform
     they make, reduced on the integer pipes / through the table log of the double), or
     exp_fix54 / table_exp_fix54: round(e^x 2^54) as int64 for x <= 0 (integer pipes /
-    table exponential rounded to that grid)."""
+    table exponential rounded to that grid), or exp2t_fix54 / exp2t_fix50: round(e^x
+    2^54) / round(e^x 2^50) from the two-table integer exponential."""
     import torch
 
     code = {"table_log": 0, "table_exp": 1, "lib_log": 2, "lib_exp": 3, "unif_log_bits": 4,
-            "unif_log_table": 5, "exp_fix54": 6, "table_exp_fix54": 7}[fn]
+            "unif_log_table": 5, "exp_fix54": 6, "table_exp_fix54": 7, "exp2t_fix54": 8,
+            "exp2t_fix50": 9}[fn]
     if code in (4, 5):
         x = np.ascontiguousarray(x, dtype=np.uint64).view(np.float64)
     xd = torch.as_tensor(x, dtype=torch.float64).cuda()

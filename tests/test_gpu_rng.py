@@ -136,3 +136,32 @@ def test_fixed_point_weight_exponential():
     assert np.abs(got - ref).max() <= 1
     assert np.abs(got - tab).max() <= 2
     assert got[d <= -38.5].max() == 0
+
+
+@pytest.mark.parametrize("bits", [54, 50])
+def test_two_table_fixed_point_exponential(bits):
+    """The standalone resampler's weights come from a cheaper integer
+    exponential (two 64-entry tables of 2^(-j/64) and 2^(-j/4096) and a degree-4
+    polynomial): round(e^d 2^B) within one unit of the exact rounding (decimal
+    arithmetic at 60 digits) for B = 54 and 50, 1.0 exactly at d = 0, 0 below
+    e^-38.5, and non-increasing in d over a fine sorted grid."""
+    from decimal import Decimal, getcontext
+
+    from paper_2112_00364_gb300 import smc
+
+    getcontext().prec = 60
+    rng = np.random.default_rng(22 + bits)
+    d = np.concatenate([-rng.uniform(0, 38.6, 20_000), -rng.uniform(0, 1e-3, 2_000),
+                        -rng.uniform(0, 0.7, 8_000), -np.arange(64) * np.log(2.0) / 64,
+                        -np.arange(64) * np.log(2.0) / 4096,
+                        [0.0, -1e-300, -38.1, -38.13, -38.2, -38.49, -38.6, -1000.0,
+                         -0.6931471805599453]])
+    got = smc.math_eval(f"exp2t_fix{bits}", d)
+    scale = Decimal(2) ** bits
+    ref = np.array([int((Decimal(float(x)).exp() * scale).to_integral_value()) for x in d])
+    assert np.abs(got - ref).max() <= 1
+    assert got[np.flatnonzero(d == 0.0)[0]] == 1 << bits
+    assert got[d <= -38.5].max() == 0
+    grid = -np.sort(rng.uniform(0, 3.0, 50_000))[::-1]  # increasing toward 0
+    g = smc.math_eval(f"exp2t_fix{bits}", grid)
+    assert np.all(np.diff(g) >= 0)
