@@ -22,12 +22,13 @@ _SRC = [_DIR / "smc_oracle.c"]
 _DEPS = _SRC + [_DIR / "smc_oracle.h", _DIR / "smc_oracle_prec.inc"]
 _LIB_PATH = _DIR / "liboracle.so"
 
-LG, CRBD, RATESHIFT, GEOMETRIC, SEIR = 1, 2, 3, 4, 5
+LG, CRBD, RATESHIFT, GEOMETRIC, SEIR, CRBD_DS = 1, 2, 3, 4, 5, 6
 FP64, FP32 = 0, 1
 OK, EINVAL, ENOMEM, EDEGENERATE, ESTEPLIMIT = 0, -1, -2, -4, -5
 
 DIST = {"uniform": 0, "normal": 1, "exponential": 2, "gamma1": 3, "uniform_ab": 4,
-        "bernoulli": 5, "poisson": 6, "lognormal": 7, "binomial": 8, "beta": 9, "gamma": 10}
+        "bernoulli": 5, "poisson": 6, "lognormal": 7, "binomial": 8, "beta": 9, "gamma": 10,
+        "neg_binomial": 11, "lomax": 12}
 
 _i32p = C.POINTER(C.c_int32)
 _f64p = C.POINTER(C.c_double)
@@ -181,7 +182,8 @@ def _model_struct(kind: int, precision: int, keep: list, *, obs=None, tree=None,
     return m
 
 
-KINDS = {"lg": LG, "crbd": CRBD, "rateshift": RATESHIFT, "geometric": GEOMETRIC, "seir": SEIR}
+KINDS = {"lg": LG, "crbd": CRBD, "rateshift": RATESHIFT, "geometric": GEOMETRIC, "seir": SEIR,
+         "crbd_ds": CRBD_DS}
 
 
 def smc_run(model: str, N: int, seed: int, run_id: int = 0, precision: int = FP64,
@@ -248,6 +250,6 @@ def smc_run(model: str, N: int, seed: int, run_id: int = 0, precision: int = FP6
 def _segments_hint(model: str, params: dict) -> int:
     if model in ("lg", "seir"):
         return len(params["obs"])
-    if model in ("crbd", "rateshift"):
+    if model in ("crbd", "rateshift", "crbd_ds"):
         return params["tree"].n_nodes
     return 4096

@@ -25,8 +25,12 @@
  *     a_i = min{ j : N P_j / S > i + u }, P_j the running sum of weights.
  *   - Models: the state-space model of Eq. 2 / Fig. 3 (generalised to
  *     x_t = a x_{t-1} + b + q z), the CRBD model of Listing 1, a rate-shift
- *     variant of it, the weighted geometric program of Fig. 2a, and the SEIR
- *     vector-borne disease model of Section 6.2 (Listing 2).
+ *     variant of it, the weighted geometric program of Fig. 2a, the SEIR
+ *     vector-borne disease model of Section 6.2 (Listing 2), and the CRBD
+ *     model with static delayed sampling of Section 6.3 (lambda and mu kept
+ *     as conjugate Gamma posteriors; the paper gives no formulas, the
+ *     reading is the standard Gamma-Poisson / Gamma-Exponential conjugacy:
+ *     draws from the predictive laws, each followed by its posterior update).
  *
  * Random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11) with
  * key (seed_lo, seed_hi XOR run_id) and counter (particle slot n,
@@ -130,9 +134,12 @@ static int model_setup(const orc_model *m, model_consts *mc) {
   if (m->kind == ORC_LG) {
     if (!m->obs || m->T <= 0 || !(m->r_sd > 0)) return ORC_EINVAL;
     mc->lg_lc = log(m->r_sd) + HALF_LOG_2PI_D;
-  } else if (m->kind == ORC_CRBD || m->kind == ORC_RATESHIFT) {
+  } else if (m->kind == ORC_CRBD || m->kind == ORC_RATESHIFT || m->kind == ORC_CRBD_DS) {
     if (m->n_nodes < 3 || !m->parent || !m->left || !m->age || !m->preorder) return ORC_EINVAL;
     if (m->kind == ORC_RATESHIFT && m->lam_stack_cap < 1) return ORC_EINVAL;
+    /* delayed sampling integrates the Gamma priors out: no fixed rates */
+    if (m->kind == ORC_CRBD_DS && (m->fixed_rates || !(m->lambda_scale > 0) || !(m->mu_scale > 0)))
+      return ORC_EINVAL;
     int32_t tips = (m->n_nodes + 1) / 2;
     double lnfact = 0.0;
     for (int32_t i = 2; i <= tips; i++) lnfact = lnfact + log((double)i);
@@ -235,6 +242,7 @@ int orc_n_fields(const orc_model *m, int32_t *n_real, int32_t *n_int, int32_t *s
     case ORC_RATESHIFT: *n_real = 2; *n_int = 2; *stack_cap = m->lam_stack_cap; return ORC_OK;
     case ORC_GEOMETRIC: *n_real = 0; *n_int = 2; return ORC_OK;
     case ORC_SEIR: *n_real = 6; *n_int = 10; return ORC_OK;
+    case ORC_CRBD_DS: *n_real = 4; *n_int = 1; return ORC_OK;
   }
   return ORC_EINVAL;
 }
@@ -266,6 +274,8 @@ static double lfact_d(int64_t k) {
 #define SFX(x) x##_d
 #define LOGR log
 #define EXPR exp
+#define LOG1PR log1p
+#define EXPM1R expm1
 #define COSR cos
 #define SQRTR sqrt
 #define FMAR fma
@@ -279,6 +289,8 @@ static double lfact_d(int64_t k) {
 #undef SFX
 #undef LOGR
 #undef EXPR
+#undef LOG1PR
+#undef EXPM1R
 #undef COSR
 #undef SQRTR
 #undef FMAR
@@ -292,6 +304,8 @@ static double lfact_d(int64_t k) {
 #define SFX(x) x##_f
 #define LOGR logf
 #define EXPR expf
+#define LOG1PR log1pf
+#define EXPM1R expm1f
 #define COSR cosf
 #define SQRTR sqrtf
 #define FMAR fmaf

@@ -25,6 +25,7 @@
 #define ORC_RATESHIFT 3
 #define ORC_GEOMETRIC 4
 #define ORC_SEIR 5 /* the vector-borne disease SEIR model of Section 6.2 / Listing 2 */
+#define ORC_CRBD_DS 6 /* CRBD with lambda and mu integrated out (static delayed sampling, Section 6.3) */
 
 #define ORC_FP64 0
 #define ORC_FP32 1 /* FP32 particle arithmetic, FP64 normaliser / scan / log Z */
