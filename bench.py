@@ -57,6 +57,10 @@ WORKLOADS = {
     "lg": dict(kind="lg", T=50, obs_seed=1, N=1024, precision="fp64"),
     # the vector-borne disease SEIR model (Section 6.2), 26 weeks of synthetic reports
     "seir182": dict(kind="seir", days=182, obs_seed=7, N=1 << 16, precision="fp64"),
+    # CRBD with static delayed sampling and ESS-triggered resampling (Section 6.3),
+    # on a synthetic 128-tip tree standing in for the paper's larger phylogeny
+    "crbd_ds128": dict(kind="crbd_ds", tips=128, tree_seed=6, N=100_000, precision="fp64",
+                       ess=0.5),
     "rateshift256": dict(kind="rateshift", tips=256, tree_seed=3, N=1 << 20, precision="fp32",
                          sigma=0.3),
     "batch512": dict(kind="batch", n_runs=512, spec_seed=4, precision="fp32"),
@@ -210,7 +214,7 @@ class Work:
                     p.update(sigma=w["sigma"], lam_stack_cap=tree.max_pending_right() + 1)
                 seg = tree.n_nodes
             self.runs.append(dict(kind=w["kind"], params=p, N=w["N"], seed=seed_base, run_id=0,
-                                  segments=seg))
+                                  segments=seg, ess=w.get("ess", 0.0)))
         self.units = sum(r["N"] * r["segments"] for r in self.runs)
 
     def config(self) -> dict:
@@ -244,6 +248,12 @@ class Work:
             cfg.update(model="linear-Gaussian SSM x_t=0.9x+N(0,1), y~N(x,0.5^2)",
                        n_particles=w["N"], checkpoints=w["T"],
                        observations=f"T={w['T']} simulated, seed {w['obs_seed']}")
+        elif w["kind"] == "crbd_ds":
+            cfg.update(model="CRBD (Listing 1) with lambda, mu integrated out (static delayed "
+                             "sampling), priors Gamma(1,1), Gamma(1,0.5), rho=1",
+                       n_particles=w["N"], checkpoints=self.runs[0]["segments"],
+                       resampling=f"ESS-triggered, threshold {w['ess']} N",
+                       tree=f"Yule {w['tips']} tips seed {w['tree_seed']}, height 1.0")
         else:
             cfg.update(model="CRBD (Listing 1), priors Gamma(1,1), Gamma(1,0.5), rho=1"
                        if w["kind"] == "crbd" else "rate-shift CRBD, lognormal multipliers sigma=0.3",
@@ -271,13 +281,44 @@ def oracle_throughput(work: Work, budget_s: float, max_runs: int, n_particles=No
         N = n_particles or r["N"]
         t0 = time.perf_counter()
         o = oracle.smc_run(r["kind"], N, seed=r["seed"] + runs // len(work.runs), run_id=r["run_id"],
-                           precision=prec, **r["params"])
+                           precision=prec, ess_threshold=r.get("ess", 0.0), **r["params"])
         t_tot += time.perf_counter() - t0
         if o["status"] < 0:
             raise RuntimeError(f"oracle status {o['status']}")
         units += N * r["segments"]
         runs += 1
     return units / t_tot, runs, t_tot, units
+
+
+def equal_error_comparison(work: Work, smc, torch, stream, n_seeds: int = 16) -> dict:
+    """Delayed sampling against the plain model at equal log-Z error (untimed
+    by the bench's clock): the same tree, N and resampling rule run through the
+    plain CRBD and the delayed-sampling CRBD for n_seeds seeds each; the log-Z
+    standard deviations give the variance ratio, i.e. how many more particles
+    the plain model needs for the same log-Z error (variance ~ 1/N), and the
+    CUDA-event times give each model's particle-steps/s."""
+    r = work.runs[0]
+    out = {}
+    for kind in ("crbd_ds", "crbd"):
+        m = smc.Model(kind, **r["params"])
+        lz, ms = [], 0.0
+        for s in range(n_seeds):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = smc.run(m, r["N"], seed=70000 + s, run_id=0, precision=work.precision,
+                          where="device", stream=stream, ess_threshold=r.get("ess", 0.0))
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            lz.append(float(res["log_z"].cpu()[0]))
+        m.close()
+        out[kind] = {"value": n_seeds * r["N"] * r["segments"] / (ms * 1e-3), "unit": UNIT,
+                     "log_z_mean": float(np.mean(lz)), "log_z_sd": float(np.std(lz, ddof=1))}
+    ratio = (out["crbd"]["log_z_sd"] / out["crbd_ds"]["log_z_sd"]) ** 2
+    return {"seeds": n_seeds, "delayed_sampling": out["crbd_ds"], "plain_crbd": out["crbd"],
+            "variance_ratio_plain_over_delayed": ratio,
+            "delayed_value_at_plain_error": out["crbd_ds"]["value"] * ratio}
 
 
 def run_reference(args, work: Work):
@@ -622,7 +663,7 @@ def main() -> int:
         r = work.runs[0]
         return [smc.run(models[0], r["N"], seed=r["seed"] + seed_off, run_id=r["run_id"],
                         precision=work.precision, where="device", stream=stream, outputs=outs[0],
-                        time_kernels=timed)]
+                        time_kernels=timed, ess_threshold=r.get("ess", 0.0))]
 
     for s in range(args.warmup):
         device_step(50000 + s, False)
@@ -713,7 +754,8 @@ def main() -> int:
         else:
             r = work.runs[0]
             smc.run(ms2[0], r["N"], seed=r["seed"] + s, run_id=r["run_id"],
-                    precision=work.precision, where="host", stream=stream, outputs=pinned[0])
+                    precision=work.precision, where="host", stream=stream, outputs=pinned[0],
+                    ess_threshold=r.get("ess", 0.0))
         for m2 in ms2:
             m2.close()
         e2e_total += time.perf_counter() - t0
@@ -723,6 +765,10 @@ def main() -> int:
         if dist:
             dist.destroy_process_group()
         return 0
+
+    equal_error = None
+    if work.w["kind"] == "crbd_ds":
+        equal_error = equal_error_comparison(work, smc, torch, stream)
 
     roof = None
     info = NCU.get(args.workload)
@@ -769,6 +815,8 @@ def main() -> int:
     }
     if plain:
         line["plain_one_run_per_launch"] = plain
+    if equal_error:
+        line["equal_log_z_error"] = equal_error
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -70,6 +70,12 @@ typedef int32_t smc_status;
 #define SMC_MODEL_SEIR 5 /* vector-borne disease SEIR (Section 6.2, Listing 2): obs = daily
                             reports (-1: none), T = days; PSTATE ints: block index, hS hE hI
                             hR mS mE mI mR z; reals: hLambda hDelta hGamma mLambda mDelta rho */
+#define SMC_MODEL_CRBD_DS 6 /* CRBD with static delayed sampling (Section 6.3): lambda and mu
+                             stay Gamma(shape, rate) posteriors updated by conjugacy, every
+                             rate-dependent draw from its predictive law (negative binomial
+                             counts, Lomax lifetimes); needs the Gamma priors (fixed_rates = 0,
+                             lambda_scale, mu_scale > 0); PSTATE reals: a_lambda b_lambda
+                             a_mu b_mu; ints: block index */
 
 #define SMC_PREC_FP64 0 /* FP64 particle arithmetic and log-weights */
 #define SMC_PREC_FP32 1 /* FP32 particle arithmetic and log-weights; FP64 reductions */
@@ -319,7 +325,9 @@ smc_status smc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, i
 /* n variates of one recipe, variate i drawn from counter (i, 0, d, 0) with d from 0:
  * dist 0 uniform(0,1), 1 normal(p1, p2), 2 exponential(rate p1), 3 gamma(1, scale p1),
  * 4 uniform(p1, p2), 5 bernoulli(p1), 6 poisson(p1), 7 lognormal(0, p1), 8 binomial(n = p1,
- * p = p2), 9 beta(p1, p2), 10 gamma(shape p1 >= 1, scale 1).
+ * p = p2), 9 beta(p1, p2), 10 gamma(shape p1 >= 1, scale 1), 11 negative binomial
+ * (Poisson(lambda p2) with lambda ~ Gamma(shape p1 >= 1, rate 1) integrated out), 12 Lomax
+ * (Exponential(mu) with mu ~ Gamma(shape p1, rate p2) integrated out).
  * out [n] f64 and blocks [n] int32 (Philox blocks consumed, may be NULL) are device
  * pointers.  Errors: SMC_EINVAL, SMC_ECUDA. */
 smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uint64_t seed,

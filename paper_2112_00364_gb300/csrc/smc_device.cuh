@@ -662,6 +662,46 @@ __device__ __forceinline__ R binomial_logpmf(int y, int z, R rho, const Stream& 
   return lp;
 }
 
+// ---- predictive draws of the delayed-sampling CRBD (Section 6.3) ----
+__device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+
+// Exponential(mu) with mu ~ Gamma(alpha, rate beta) integrated out (Lomax):
+// P(x > t) = (beta / (beta + t))^alpha; by inversion of one uniform,
+// x = beta (u^(-1/alpha) - 1) = beta expm1(-ln(u) / alpha).
+template <typename R>
+__device__ __forceinline__ R lomax(Stream& s, R alpha, R beta) {
+  return beta * m_expm1(neg_log_uniform<R>(s) / alpha);
+}
+
+// Poisson(lambda tau) with lambda ~ Gamma(alpha, rate beta) integrated out
+// (negative binomial, p = beta / (beta + tau), q = tau / (beta + tau)): mean
+// alpha tau / beta below 10 by sequential-search inversion of one uniform,
+// P(0) = exp(-alpha log1p(tau / beta)), P(n + 1) = P(n) (q (alpha + n) / (n + 1)),
+// at most 1000 terms; from 10 up the Gamma-Poisson mixture
+// lambda' = Gamma(alpha, 1) / beta (alpha >= 1), then Poisson(lambda' tau).
+template <typename R>
+__device__ __noinline__ int neg_binomial(Stream& s, R alpha, R beta, R tau) {
+  const R mean = alpha * tau / beta;
+  if (mean < (R)10.0) {
+    const R u = uniform01<R>(s);
+    const R q = tau / (beta + tau);
+    R pk = ex(-alpha * m_log1p(tau / beta), s);
+    R acc = pk;
+    int k = 0;
+    while (u > acc && k < 1000) {
+      pk = pk * (q * (alpha + (R)k) / (R)(k + 1));
+      acc = acc + pk;
+      k += 1;
+    }
+    return k;
+  }
+  const R lam = gamma_mt<R>(s, alpha) / beta;
+  return poisson<R>(s, lam * tau);
+}
+
 // ---- FP64 warp / block primitives (deterministic association order) ----
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll

@@ -407,6 +407,7 @@ __global__ void __launch_bounds__(TPB, 768 / TPB) wave_kernel(const RunDev* __re
     case SMC_MODEL_SEIR: step_tile<SeirModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
     case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
     case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    case SMC_MODEL_CRBD_DS: step_tile<TreeDsModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
     default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
   }
 }
@@ -492,6 +493,7 @@ int model_fields(int kind, int* n_real, int* n_int) {
     case SMC_MODEL_RATESHIFT: *n_real = 2; *n_int = 2; return 0;
     case SMC_MODEL_GEOMETRIC: *n_real = 0; *n_int = 2; return 0;
     case SMC_MODEL_SEIR: *n_real = 6; *n_int = 10; return 0;
+    case SMC_MODEL_CRBD_DS: *n_real = 4; *n_int = 1; return 0;
   }
   return -1;
 }
@@ -880,6 +882,10 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
   } else {
     smc_status st = check_tree(d);
     if (st) return st;
+    if (d->kind == SMC_MODEL_CRBD_DS &&
+        (d->fixed_rates || !(d->lambda_scale > 0.0) || !(d->mu_scale > 0.0)))
+      return set_error(SMC_EINVAL, "delayed-sampling CRBD integrates the Gamma priors out: "
+                                   "no fixed rates, lambda_scale and mu_scale > 0");
     blob = align_up(4 * (size_t)d->n_nodes, 256) * 3 + align_up(8 * (size_t)d->n_nodes, 256) * 2;
   }
   smc_model_s* m = new (std::nothrow) smc_model_s();
@@ -928,7 +934,7 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
     m->n_segments_known = d->T;
   }
   if (d->kind == SMC_MODEL_SEIR) m->n_segments_known = d->T;
-  if (d->kind == SMC_MODEL_CRBD || d->kind == SMC_MODEL_RATESHIFT) {
+  if (d->kind == SMC_MODEL_CRBD || d->kind == SMC_MODEL_RATESHIFT || d->kind == SMC_MODEL_CRBD_DS) {
     const int tips = (d->n_nodes + 1) / 2;
     double lnfact = 0.0;
     for (int i = 2; i <= tips; ++i) lnfact = lnfact + std::log((double)i);

@@ -494,6 +494,173 @@ struct TreeModel {
   }
 };
 
+// ------------------------------------------------------------------------
+// CRBD with static delayed sampling (Section 6.3): Listing 1's blocks with
+// lambda ~ Gamma(1, lambda_scale) and mu ~ Gamma(1, mu_scale) (shape, scale)
+// never drawn; each particle keeps their Gamma(shape, rate) posteriors
+// (a_l, b_l) and (a_m, b_m) (real fields 0-3) and every draw that involves a
+// rate comes from its predictive law, followed by the conjugate update:
+//   0 PRIOR   a_l = 1, b_l = 1/lambda_scale, a_m = 1, b_m = 1/mu_scale;
+//             weight(corrFactor); checkpoint
+//   1 BRANCH  node v = preorder[k]: lnProb1 = log E[exp(-mu dt)] =
+//             -a_m log1p(dt / b_m), b_m += dt; lnProb2 = log E[lambda] =
+//             log(a_l / b_l), a_l += 1 (internal) or ln rho (tip);
+//             n ~ NegBin(a_l, b_l, dt), a_l += n, b_l += dt
+//   2 HIDDEN  one hidden speciation event per execution, as in TreeModel, with
+//             dur ~ Lomax(a_m, b_m), a_m += 1, b_m += dur, and
+//             j ~ NegBin(a_l, b_l, bl), a_l += j, b_l += bl
+//   3 END     weight(lnProb1 + (lnProb2 + lnProb3)); checkpoint
+// ------------------------------------------------------------------------
+template <typename Real>
+struct TreeDsModel {
+  using R = Real;
+  static constexpr int NB = 4, N_REAL = 4, N_INT = 1;
+  static constexpr bool HAS_STACK = false;
+  enum { PRIOR = 0, BRANCH = 1, HIDDEN = 2, END = 3 };
+  struct Lane {
+    int pc, v, n_top, fsp, calls;
+    bool ckpt;
+    int overflow, limited;
+    R al, bl, am, bm, logw;
+    R start, stop, lnp1, lnp2, lnp3, cur_t;
+    R fr_t[SMC_MAX_DEPTH], fr_bl[SMC_MAX_DEPTH];
+    int fr_rem[SMC_MAX_DEPTH];
+  };
+  __device__ static void init(Lane& L) {
+    L.pc = PRIOR;
+    L.al = L.bl = L.am = L.bm = (R)0;
+    L.logw = (R)0;
+  }
+  __device__ static void gather(Lane& L, const StateView& Sc, const StateView&, int a, int,
+                                int N, const ModelDev&) {
+    L.al = Sc.rf<R>(0, a, N);
+    L.bl = Sc.rf<R>(1, a, N);
+    L.am = Sc.rf<R>(2, a, N);
+    L.bm = Sc.rf<R>(3, a, N);
+    L.pc = Sc.inf_(0, a, N);
+    L.logw = (R)0;
+  }
+  __device__ static void store(const Lane& L, const StateView& Sn, int i, int N) {
+    Sn.rf<R>(0, i, N) = L.al;
+    Sn.rf<R>(1, i, N) = L.bl;
+    Sn.rf<R>(2, i, N) = L.am;
+    Sn.rf<R>(3, i, N) = L.bm;
+    Sn.inf_(0, i, N) = L.pc;
+  }
+  __device__ static void begin(Lane& L) {
+    L.ckpt = false;
+    L.overflow = L.limited = 0;
+  }
+  __device__ static void block(int b, Lane& L, Stream& s, const ModelDev& md, const StateView&,
+                               int, int k, int) {
+    switch (b) {
+      case PRIOR: {
+        L.al = (R)1.0;
+        L.bl = (R)1.0 / (R)md.lambda_scale;
+        L.am = (R)1.0;
+        L.bm = (R)1.0 / (R)md.mu_scale;
+        L.logw = L.logw + (R)md.corr;
+        L.pc = BRANCH;
+        L.ckpt = true;
+        return;
+      }
+      case BRANCH: {
+        const int v = md.preorder[k];
+        const int p = md.parent[v];
+        L.v = v;
+        L.start = (R)md.age[p];
+        L.stop = (R)md.age[v];
+        const R dt = L.start - L.stop;
+        L.lnp1 = -L.am * m_log1p(dt / L.bm);
+        L.bm = L.bm + dt;
+        if (md.left[v] >= 0) {
+          L.lnp2 = lg(L.al / L.bl, s);
+          L.al = L.al + (R)1.0;
+        } else {
+          L.lnp2 = (R)md.log_rho;
+        }
+        L.n_top = neg_binomial<R>(s, L.al, L.bl, dt);
+        L.al = L.al + (R)L.n_top;
+        L.bl = L.bl + dt;
+        L.lnp3 = (R)0;
+        L.fsp = 0;
+        L.calls = 0;
+        L.pc = HIDDEN;
+        return;
+      }
+      case HIDDEN: {
+        // the next event (as in TreeModel): a child of the top frame, or the
+        // branch's next one; a finished frame returns true (ln 2 at the
+        // branch level)
+        for (;;) {
+          if (L.fsp == 0) {
+            if (L.n_top == 0) {
+              L.pc = END;
+              return;
+            }
+            L.n_top -= 1;
+            L.cur_t = uniform_ab<R>(s, L.stop, L.start);
+            break;
+          }
+          const int f = L.fsp - 1;
+          if (L.fr_rem[f] == 0) {
+            L.fsp = f;
+            if (f == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
+            continue;
+          }
+          L.fr_rem[f] -= 1;
+          const R t = L.fr_t[f];
+          L.cur_t = uniform_ab<R>(s, t - L.fr_bl[f], t);
+          break;
+        }
+        if (L.fsp + 1 > md.depth_cap) {
+          L.overflow = 1;
+          L.lnp3 = neg_inf<R>();
+          L.pc = END;
+          return;
+        }
+        L.calls += 1;
+        if (L.calls > md.call_limit) {
+          L.limited = 1;
+          L.lnp3 = neg_inf<R>();
+          L.pc = END;
+          return;
+        }
+        const R t = L.cur_t;
+        const R dur = lomax<R>(s, L.am, L.bm);
+        L.am = L.am + (R)1.0;
+        L.bm = L.bm + dur;
+        if (dur > t) {
+          if (bernoulli<R>(s, (R)md.rho)) {
+            L.lnp3 = neg_inf<R>();
+            L.pc = END;
+            return;
+          }
+        }
+        const R bl = dur < t ? dur : t;
+        const int j = neg_binomial<R>(s, L.al, L.bl, bl);
+        L.al = L.al + (R)j;
+        L.bl = L.bl + bl;
+        if (j == 0) {
+          if (L.fsp == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
+          return;
+        }
+        L.fr_t[L.fsp] = t;
+        L.fr_bl[L.fsp] = bl;
+        L.fr_rem[L.fsp] = j;
+        L.fsp += 1;
+        return;
+      }
+      default: {  // END
+        L.logw = L.logw + (L.lnp1 + (L.lnp2 + L.lnp3));
+        L.pc = (k + 1 == md.n_nodes) ? PC_STOP : BRANCH;
+        L.ckpt = true;
+        return;
+      }
+    }
+  }
+};
+
 // Per-warp PC-sorted dispatch: while any lane of the warp is still inside
 // its segment, pick the block index shared by the most such lanes (ties to
 // the larger index) and run that block on exactly those lanes.  The choice

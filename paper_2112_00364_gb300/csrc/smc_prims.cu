@@ -447,7 +447,9 @@ __global__ void sample_kernel(int dist, R p1, R p2, uint32_t k0, uint32_t k1, in
     case 7: v = (double)lognormal<R>(s, p1); break;
     case 8: v = (double)binomial<R>(s, (int)p1, p2); break;
     case 9: v = (double)beta_ab<R>(s, p1, p2); break;
-    default: v = (double)gamma_mt<R>(s, p1); break;
+    case 10: v = (double)gamma_mt<R>(s, p1); break;
+    case 11: v = (double)neg_binomial<R>(s, p1, (R)1.0, p2); break;
+    default: v = (double)lomax<R>(s, p1, p2); break;
   }
   out[i] = v;
   if (blocks) blocks[i] = (int32_t)s.d;
@@ -664,7 +666,7 @@ extern "C" smc_status smc_philox(const uint32_t* ctr, const uint32_t* key, uint3
 extern "C" smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2,
                                  uint64_t seed, uint32_t run_id, int64_t n, double* out,
                                  int32_t* blocks, void* stream) {
-  if (!out || n < 0 || dist < 0 || dist > 10) return set_error(SMC_EINVAL, "bad argument");
+  if (!out || n < 0 || dist < 0 || dist > 12) return set_error(SMC_EINVAL, "bad argument");
   if (n == 0) return SMC_OK;
   const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32) ^ run_id;
   const unsigned g = (unsigned)((n + 255) / 256);

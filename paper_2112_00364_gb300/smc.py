@@ -19,15 +19,16 @@ LIB_PATH = _PKG / "libsmc.so"
 OK, EINVAL, ENOMEM, ECUDA, EDEGENERATE, ESTEPLIMIT, ETIMEOUT, EBUSY = 0, -1, -2, -3, -4, -5, -6, -7
 ECANCELLED = -8
 WKILLED = 1
-MODEL_LG, MODEL_CRBD, MODEL_RATESHIFT, MODEL_GEOMETRIC, MODEL_SEIR = 1, 2, 3, 4, 5
+MODEL_LG, MODEL_CRBD, MODEL_RATESHIFT, MODEL_GEOMETRIC, MODEL_SEIR, MODEL_CRBD_DS = 1, 2, 3, 4, 5, 6
 KINDS = {"lg": MODEL_LG, "crbd": MODEL_CRBD, "rateshift": MODEL_RATESHIFT,
-         "geometric": MODEL_GEOMETRIC, "seir": MODEL_SEIR}
+         "geometric": MODEL_GEOMETRIC, "seir": MODEL_SEIR, "crbd_ds": MODEL_CRBD_DS}
 PREC_FP64, PREC_FP32 = 0, 1
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
 MEM_HOST, MEM_DEVICE = 0, 1
 MAX_DEPTH = 64
 DIST = {"uniform": 0, "normal": 1, "exponential": 2, "gamma1": 3, "uniform_ab": 4,
-        "bernoulli": 5, "poisson": 6, "lognormal": 7, "binomial": 8, "beta": 9, "gamma": 10}
+        "bernoulli": 5, "poisson": 6, "lognormal": 7, "binomial": 8, "beta": 9, "gamma": 10,
+        "neg_binomial": 11, "lomax": 12}
 
 _i32p = C.POINTER(C.c_int32)
 _f64p = C.POINTER(C.c_double)
