@@ -342,8 +342,9 @@ smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uin
  * bits) the fixed-point weight round(e^x[i] 2^54) for x[i] <= 0, 6 = computed
  * on the integer pipes (what the segment kernel uses), 7 = the table exponential
  * rounded to the same grid; fn 8 and 9 give round(e^x[i] 2^54) and round(e^x[i]
- * 2^50) from the two-table integer exponential of smc_resample.  x, y [n] f64
- * device pointers.
+ * 2^50) from the two-table integer exponential of smc_resample; fn 10 gives e^-x[i]
+ * (a double, x[i] in [0, 64)) from the same integer exponential, as the Poisson
+ * sampler forms it.  x, y [n] f64 device pointers.
  * Errors: SMC_EINVAL, SMC_ECUDA. */
 smc_status smc_math_eval(int32_t fn, const double *x, double *y, int64_t n, void *stream);
 

@@ -220,21 +220,15 @@ __device__ __forceinline__ long long exp_fix_x(unsigned long long X, const MathT
   return (long long)((q + (1ull << (s - 1))) >> s);
 }
 
-// The same exponential from two 64-entry tables, T64[j] = 2^(-j/64) and
-// T4096[j] = 2^(-j/4096) in Q63 (the caller stages them, e.g. in shared
-// memory), and a degree-4 polynomial on a remainder below 2^-12.5: Y = X / ln 2
-// = n + j1/64 + j2/4096 + g, 2^-g = e^-r with r = g ln 2, and
-// e^-r = 1 - r + r^2/2 - r^3/6 + r^4/24 (truncation below 2^-69), the terms
-// past r in 32-bit products.  Four 64-bit multiply-highs instead of ten;
-// relative error below 2^-55, within one unit of the exact rounding for B <= 54.
-template <int B>
-__device__ __forceinline__ long long exp_fix_x2(unsigned long long X,
-                                                const unsigned long long* T64,
-                                                const unsigned long long* T4096) {
-  static_assert(B >= 40 && B <= 54, "fixed-point bits");
-  const unsigned long long Y = __umul64hi(X, kInvLn2Q63);  // X / ln 2 in units of 2^-57
-  const int n = (int)(Y >> 57);
-  if (n >= B + 1) return 0;  // at most half a unit
+// 2^-(Y 2^-57 - n) in 2^-61 fixed point (in (2^60, 2^61]) for Y = y 2^57 and
+// n = floor(y): two 64-entry Q63 tables, T64[j] = 2^(-j/64) and
+// T4096[j] = 2^(-j/4096), and a degree-4 polynomial on the remainder
+// g < 2^-12 of y: 2^-g = e^-r with r = g ln 2, e^-r = 1 - r + r^2/2 - r^3/6 +
+// r^4/24 (truncation below 2^-69), the terms past r in 32-bit products.
+// Relative error below 2^-58.
+__device__ __forceinline__ unsigned long long exp2_frac_q61(unsigned long long Y,
+                                                            const unsigned long long* T64,
+                                                            const unsigned long long* T4096) {
   const unsigned long long g = Y & ((1ull << 45) - 1);       // g 2^57, g < 2^-12
   const unsigned long long r = __umul64hi(g << 7, kLn2Q64);  // r 2^64, r < 2^-12.5
   const unsigned rh = (unsigned)(r >> 20);                   // r 2^44, below 2^32
@@ -245,9 +239,43 @@ __device__ __forceinline__ long long exp_fix_x2(unsigned long long X,
   const unsigned long long p =
       0x8000000000000000ull - (r >> 1) + (r2 >> 26) - r3 / 6u + r4 / 24u;  // e^-r 2^63
   const unsigned long long t = __umul64hi(T64[(Y >> 51) & 63], T4096[(Y >> 45) & 63]);  // 2^62
-  const unsigned long long q = __umul64hi(t, p);  // 2^-(Y 2^-57 - n) 2^61
-  const int s = 61 - B + n;                       // to 2^-B units and the factor 2^-n
+  return __umul64hi(t, p);
+}
+
+// The same exponential from the two 64-entry tables (the caller stages them,
+// e.g. in shared memory): Y = X / ln 2 = n + j1/64 + j2/4096 + g and
+// exp2_frac_q61.  Four 64-bit multiply-highs instead of ten; within one unit
+// of the exact rounding for B <= 54.
+template <int B>
+__device__ __forceinline__ long long exp_fix_x2(unsigned long long X,
+                                                const unsigned long long* T64,
+                                                const unsigned long long* T4096) {
+  static_assert(B >= 40 && B <= 54, "fixed-point bits");
+  const unsigned long long Y = __umul64hi(X, kInvLn2Q63);  // X / ln 2 in units of 2^-57
+  const int n = (int)(Y >> 57);
+  if (n >= B + 1) return 0;  // at most half a unit
+  const unsigned long long q = exp2_frac_q61(Y, T64, T4096);  // 2^-(Y 2^-57 - n) 2^61
+  const int s = 61 - B + n;                                   // to 2^-B units and 2^-n
   return (long long)((q + (1ull << (s - 1))) >> s);
+}
+
+// e^-m as a double for 0 <= m < 64 on the integer pipes: X = m 2^58 from the
+// bits of m (truncated, error below 2^-58), Y = X / ln 2, q = exp2_frac_q61,
+// then q 2^-(61 + n) with one rounding of q to 53 bits and an exact exponent
+// shift: within about 0.6 ulp.  Outside [0, 64) the table exponential.
+__device__ __forceinline__ double exp_neg_int(double m, const MathTab* __restrict__ T) {
+  if (!(m >= 0.0 && m < 64.0)) return tang_exp(-m, T);
+  const long long b = __double_as_longlong(m);
+  const int e = (int)(b >> 52);
+  if (e == 0) return 1.0;  // m = 0 or subnormal: e^-m rounds to 1
+  const unsigned long long mt = (unsigned long long)((b & 0x000FFFFFFFFFFFFFll) | 0x0010000000000000ll);
+  const int sh = e - 1017;  // m 2^58 = mt 2^(e - 1075 + 58)
+  const unsigned long long X = sh >= 0 ? (mt << sh) : (-sh < 64 ? (mt >> -sh) : 0ull);
+  const unsigned long long Y = __umul64hi(X, kInvLn2Q63);
+  const int n = (int)(Y >> 57);
+  const unsigned long long q = exp2_frac_q61(Y, T->exp2_neg64_q63, T->exp2_neg4096_q63);
+  const double dq = __ull2double_rn(q);  // q in (2^60, 2^61]: exact power-of-two shift below
+  return __longlong_as_double(__double_as_longlong(dq) - ((long long)(61 + n) << 52));
 }
 
 template <int B>
@@ -374,13 +402,15 @@ template <typename R>
 struct Unif;
 template <>
 struct Unif<double> {
-  // ((w_hi:w_lo) >> 11) | 1, times 2^-53.  Built without an int->FP64
-  // conversion: 1 + (x >> 12) 2^-52 is assembled from bits, then
-  // (that - 1) + 2^-53 = (2 (x >> 12) + 1) 2^-53 = ((x >> 11) | 1) 2^-53,
-  // both subtractions exact.
+  // ((w_hi:w_lo) >> 11) | 1, times 2^-53, assembled from bits on the integer
+  // pipes: n = (x >> 11) | 1 is odd with its leading one at bit p (0..52), so
+  // n 2^-53 = 1.f 2^(p - 53) exactly, exponent field p + 970 and fraction
+  // (n << (52 - p)) without its leading one.  No FP64 operation.
   __device__ __forceinline__ static double from64(uint64_t x) {
-    const double one_plus = __longlong_as_double((long long)(0x3FF0000000000000ull | (x >> 12)));
-    return (one_plus - 1.0) + 0x1p-53;
+    const unsigned long long n = (x >> 11) | 1ull;
+    const int p = 63 - __clzll((long long)n);
+    const unsigned long long frac = (n << (52 - p)) & 0x000FFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(((unsigned long long)(p + 970) << 52) | frac));
   }
   __device__ __forceinline__ static double first(const Block4& b) {
     return from64(((uint64_t)b.w1 << 32) | b.w0);
@@ -399,6 +429,15 @@ struct Unif<float> {
     return (float)((b.w1 >> 8) | 1u) * 0x1p-24f;
   }
 };
+
+// a > b for non-negative (or +inf) a and b by their bit patterns, which order
+// like the values: an integer compare instead of an FP64 one
+__device__ __forceinline__ bool gt_nonneg(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
+__device__ __forceinline__ bool gt_nonneg(float a, float b) {
+  return __float_as_int(a) > __float_as_int(b);
+}
 
 // ---- precision-overloaded math (IEEE library calls, no fast-math) ----
 __device__ __forceinline__ double m_log(double x) { return log(x); }
@@ -506,7 +545,7 @@ __device__ __forceinline__ R uniform_ab(Stream& s, R lo, R hi) {
 
 template <typename R>
 __device__ __forceinline__ bool bernoulli(Stream& s, R p) {
-  return uniform01<R>(s) < p;
+  return gt_nonneg(p, uniform01<R>(s));  // u < p; a negative p is never above u
 }
 
 // Poisson(mean): sequential-search inversion below 10 (one uniform, at most
@@ -514,12 +553,16 @@ __device__ __forceinline__ bool bernoulli(Stream& s, R p) {
 // 10 up, one block per trial, at most 1000 trials.
 template <typename R>
 __device__ __noinline__ int poisson(Stream& s, R mean) {
-  if (mean < (R)10.0) {
+  if (gt_nonneg((R)10.0, mean)) {  // mean >= 0
     const R u = uniform01<R>(s);
     int k = 0;
-    R p = ex(-mean, s);
+    R p;
+    if constexpr (sizeof(R) == 8)
+      p = exp_neg_int(mean, s.tab);  // integer pipes: off the FP64 pipe
+    else
+      p = expf(-mean);
     R acc = p;
-    while (u > acc && k < 200) {
+    while (gt_nonneg(u, acc) && k < 200) {
       k += 1;
       if constexpr (sizeof(R) == 8)
         p = p * (mean * __ldg(&s.tab->inv_int[k]));  // mean / k off the chain through p

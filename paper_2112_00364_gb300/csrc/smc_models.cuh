@@ -456,7 +456,7 @@ struct TreeModel {
         }
         const R t = L.cur_t;
         const R dur = L.mu > (R)0 ? exponential_inv(s, L.mu, L.inv_mu) : exponential<R>(s, L.mu);
-        if (dur > t) {
+        if (gt_nonneg(dur, t)) {  // both >= 0
           if (bernoulli<R>(s, (R)md.rho)) {
             L.lnp3 = neg_inf<R>();
             L.pc = END;
@@ -630,7 +630,7 @@ struct TreeDsModel {
         const R dur = lomax<R>(s, L.am, L.bm);
         L.am = L.am + (R)1.0;
         L.bm = L.bm + dur;
-        if (dur > t) {
+        if (gt_nonneg(dur, t)) {  // both >= 0
           if (bernoulli<R>(s, (R)md.rho)) {
             L.lnp3 = neg_inf<R>();
             L.pc = END;

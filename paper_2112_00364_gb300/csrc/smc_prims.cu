@@ -473,10 +473,11 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
     case 8:
       y[i] = __longlong_as_double(exp_fix2<54>(v, tab->exp2_neg64_q63, tab->exp2_neg4096_q63));
       break;
-    default:
+    case 9:
       y[i] = __longlong_as_double(
           weight_fix52<50>(v, 0ll, tab->exp2_neg64_q63, tab->exp2_neg4096_q63));
       break;
+    default: y[i] = exp_neg_int(v, tab); break;
   }
 }
 
@@ -485,7 +486,7 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
 using namespace smc;
 
 extern "C" smc_status smc_math_eval(int32_t fn, const double* x, double* y, int64_t n, void* stream) {
-  if (!x || !y || n < 0 || fn < 0 || fn > 9) return set_error(SMC_EINVAL, "bad argument");
+  if (!x || !y || n < 0 || fn < 0 || fn > 10) return set_error(SMC_EINVAL, "bad argument");
   if (n == 0) return SMC_OK;
   const MathTab* tab = nullptr;
   smc_status ts = math_table(&tab);

@@ -484,19 +484,20 @@ def math_eval(fn: str, x):
     they make, reduced on the integer pipes / through the table log of the double), or
     exp_fix54 / table_exp_fix54: round(e^x 2^54) as int64 for x <= 0 (integer pipes /
     table exponential rounded to that grid), or exp2t_fix54 / exp2t_fix50: round(e^x
-    2^54) / round(e^x 2^50) from the two-table integer exponential."""
+    2^54) / round(e^x 2^50) from the two-table integer exponential, or exp_neg_int:
+    e^-x (double, 0 <= x < 64) from the same integer exponential."""
     import torch
 
     code = {"table_log": 0, "table_exp": 1, "lib_log": 2, "lib_exp": 3, "unif_log_bits": 4,
             "unif_log_table": 5, "exp_fix54": 6, "table_exp_fix54": 7, "exp2t_fix54": 8,
-            "exp2t_fix50": 9}[fn]
+            "exp2t_fix50": 9, "exp_neg_int": 10}[fn]
     if code in (4, 5):
         x = np.ascontiguousarray(x, dtype=np.uint64).view(np.float64)
     xd = torch.as_tensor(x, dtype=torch.float64).cuda()
     y = torch.empty_like(xd)
     _check(lib().smc_math_eval(code, _ptr(xd), _ptr(y), xd.numel(), None))
     out = y.cpu().numpy()
-    return out.view(np.int64) if code >= 6 else out
+    return out.view(np.int64) if 6 <= code <= 9 else out
 
 
 def version() -> str:

@@ -165,3 +165,24 @@ def test_two_table_fixed_point_exponential(bits):
     grid = -np.sort(rng.uniform(0, 3.0, 50_000))[::-1]  # increasing toward 0
     g = smc.math_eval(f"exp2t_fix{bits}", grid)
     assert np.all(np.diff(g) >= 0)
+
+
+def test_integer_pipe_exponential_double():
+    """The FP64 Poisson sampler forms e^-mean on the integer pipes (two-table
+    exponential, then one rounding of a 61-bit significand to 53 bits and an
+    exact exponent shift): within 1 ulp of the correctly rounded e^-m (decimal
+    arithmetic at 60 digits) over [0, 64), exactly 1 at 0, and the table
+    exponential outside the range."""
+    from decimal import Decimal, getcontext
+
+    from paper_2112_00364_gb300 import smc
+
+    getcontext().prec = 60
+    rng = np.random.default_rng(41)
+    m = np.concatenate([rng.uniform(0, 10, 40_000), rng.uniform(0, 64, 10_000),
+                        10.0 ** rng.uniform(-17, 0, 10_000), np.arange(64) * np.log(2.0) / 64,
+                        [0.0, 5e-324, 1e-300, 9.999999999999998, 63.99999999, 64.0, 100.0]])
+    got = smc.math_eval("exp_neg_int", m)
+    ref = np.array([float((-Decimal(float(x))).exp()) for x in m])
+    assert got[np.flatnonzero(m == 0.0)[0]] == 1.0
+    assert _ulp_diff(got, ref).max() <= 1
