@@ -86,6 +86,7 @@ struct MathTab {
   double inv_f52[192];  // (128 / j) 2^-52 (exact scaling of inv_f)
   double inv_f53[192];  // (128 / j) 2^-53
   unsigned long long exp2_neg_q63[128];  // round(2^(-j/128) 2^63)
+  unsigned long long inv_f_q62[192];        // round((128 / j) 2^62), j = 90..181 used
   unsigned long long exp2_neg64_q63[64];    // round(2^(-j/64) 2^63)
   unsigned long long exp2_neg4096_q63[64];  // round(2^(-j/4096) 2^63)
   double lfact[32];                      // log k!, k < 32 (sums of logs in order)
@@ -133,17 +134,21 @@ __device__ __forceinline__ double tang_log(double x, const MathTab* __restrict__
 }
 
 // log u for the FP64 uniform u = ((x >> 11) | 1) 2^-53 of 64 random bits x,
-// with the same reduction as tang_log done on the integer pipes: the
-// significand n = (x >> 11) | 1 gives the exponent (leading-zero count), the
-// halving test, the table point j and the exact difference m - F as an
-// integer; one conversion and one product form u = (m - F) / F.  Returns the
-// same bits as tang_log of that uniform.
+// with tang_log's reduction done on the integer pipes: the significand
+// n = (x >> 11) | 1 gives the exponent (leading-zero count), the halving test,
+// the table point j and the exact difference m - F as an integer, so that
+// v = (m - F) / F is one conversion and one product.  log1p(v) = v - v^2 q(v)
+// with q(v) = 1/2 - v/3 + v^2 (1/4 - v/5 + v^2 (1/6 - v/7 + v^2/8)) evaluated
+// in signed 2^-62 fixed point from v in 2^-64 fixed point (|v| < 2^-7.49; q
+// needs only 2^-46.5 relative accuracy, the remaining error being v^2 times
+// it), then converted exactly to a double: the FP64 pipe only forms v, v^2,
+// v - v^2 q and the e ln 2 + log F combination.  Within 2 ulp of log u.
 __device__ __forceinline__ double log_unif53(unsigned long long x, const MathTab* __restrict__ T) {
   const unsigned long long n = (x >> 11) | 1ull;  // u = n 2^-53, n odd, 1 <= n < 2^53
   const int p = 63 - __clzll((long long)n);
   const unsigned long long mb = n << (52 - p);    // significand with its leading 1 at bit 52
   int e = p - 53;
-  int j;
+  int j, sh;
   long long diff;
   double rf;
   if (mb >= 0x16A09E667F3BCDull) {  // m >= sqrt(2) (the double 1.4142135623730951): use m / 2
@@ -151,13 +156,30 @@ __device__ __forceinline__ double log_unif53(unsigned long long x, const MathTab
     j = (int)((mb + (1ull << 45)) >> 46);
     diff = (long long)mb - ((long long)j << 46);  // (m / 2 - j / 128) 2^53
     rf = __ldg(&T->inv_f53[j]);
+    sh = 13;  // v 2^64 = diff 2^11 (128 / j)
   } else {
     j = (int)((mb + (1ull << 44)) >> 45);
     diff = (long long)mb - ((long long)j << 45);  // (m - j / 128) 2^52
     rf = __ldg(&T->inv_f52[j]);
+    sh = 14;  // v 2^64 = diff 2^12 (128 / j)
   }
-  const double u = (double)diff * rf;
-  return tang_log_tail(u, j, e, T);
+  const double v = (double)diff * rf;
+  // v in 2^-64 fixed point: |diff| << sh below 2^59, times (128 / j) 2^62, over 2^64
+  const unsigned long long ad = (unsigned long long)(diff < 0 ? -diff : diff);
+  const long long vm = (long long)__umul64hi(ad << sh, __ldg(&T->inv_f_q62[j]));
+  const long long v64 = diff < 0 ? -vm : vm;
+  const long long v2 = __mul64hi(v64, v64);  // v^2 2^64
+  // coefficients in 2^-62 fixed point
+  constexpr long long k2 = 1ll << 61, k3 = 0x1555555555555555ll, k4 = 1ll << 60;
+  constexpr long long k5 = 0x0CCCCCCCCCCCCCCDll, k6 = 0x0AAAAAAAAAAAAAABll, k7 = 0x0924924924924925ll;
+  const long long c = k6 - __mul64hi(v64, k7) + (v2 >> 5);  // 1/6 - v/7 + v^2/8
+  const long long b = k4 - __mul64hi(v64, k5) + __mul64hi(v2, c);
+  const long long q = k2 - __mul64hi(v64, k3) + __mul64hi(v2, b);  // in (0.497, 0.503) 2^62
+  const double qd = __longlong_as_double(__double_as_longlong(__ll2double_rn(q)) - (62ll << 52));
+  const double pl = fma(-(v * v), qd, v);
+  const double de = (double)e;
+  const double hi = fma(de, kLn2Hi, __ldg(&T->log_f[j]));
+  return hi + fma(de, kLn2Lo, pl);
 }
 
 // exp x = 2^k 2^(j/32) e^r with n = 32 k + j = round(32 x / ln 2) and

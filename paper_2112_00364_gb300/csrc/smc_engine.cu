@@ -451,6 +451,7 @@ smc_status math_table(const MathTab** out) {
   if (!g_tab_ptr[dev]) {
     MathTab h;
     for (int j = 0; j < 192; ++j) {
+      h.inv_f_q62[j] = j >= 90 ? (unsigned long long)std::llroundl(std::ldexp(128.0L / j, 62)) : 0ull;
       h.log_f[j] = j ? std::log((double)j / 128.0) : 0.0;
       h.inv_f[j] = j ? 128.0 / (double)j : 0.0;
       h.inv_f52[j] = std::ldexp(h.inv_f[j], -52);
