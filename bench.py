@@ -75,15 +75,24 @@ WORKLOADS = {
 HBM_PEAK_GBS = 6778.0  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, per particle
 
-# FP64 operations the step kernel executes per particle-step (2 x DFMA + DADD +
-# DMUL) and its DRAM traffic per launch, from one ncu capture of the workload
-# (profiles folder); the traffic holds only for the kernel sources with the
-# recorded digest.
-NCU = {"crbd64": dict(fp64_flop_per_pstep=38.5, bytes_per_launch=3.27e6,
-                     fp64_pipe_elapsed=0.268, src_digest="33f36ef9cb607f1e")}
+# Per particle-step counts of the segment kernel from one ncu capture of the
+# workload (profiles folder): warp instructions issued, FP64 flop (2 x DFMA +
+# DADD + DMUL), DRAM traffic per launch and the FP64 pipe's busy fraction.  The
+# roofline basis is the unit that bounds the kernel: instruction issue for the
+# plain CRBD (latency-bound, most arithmetic on the integer pipes), the FP64
+# rate for the delayed-sampling CRBD (FP64 pipe busy 36-44% of a launch).  The
+# traffic holds only for the kernel sources with the recorded digest.
+NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=102.0, fp64_flop_per_pstep=12.55,
+                      bytes_per_launch=3.31e6, fp64_pipe_elapsed=0.166,
+                      src_digest="72fca7eeabfe53b5"),
+       "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=117.8, fp64_flop_per_pstep=196.6,
+                          bytes_per_launch=5.8e6, fp64_pipe_elapsed=0.398,
+                          src_digest="72fca7eeabfe53b5")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
+# 152 SMs x 4 schedulers x 2070 MHz, one warp instruction per scheduler per clock
+ISSUE_PEAK = 152 * 4 * 2070e6
 
 
 # the segment kernel's sources (the standalone resampling kernels are not among them)
@@ -95,7 +104,7 @@ RS_SOURCES = ("smc_prims.cu", "smc_device.cuh", "smc_combine.cuh")
 # DRAM traffic of one smc_resample call at 2^24 (the three kernels' dram__bytes
 # read + write in one ncu capture, profiles folder), valid for the sources with
 # the recorded digest.
-RS_NCU = dict(bytes_per_call=3.535e8, src_digest="2f19134deccb975f")
+RS_NCU = dict(bytes_per_call=3.530e8, src_digest="abe396c70f0b2385")
 
 
 def src_digest(sources=KERNEL_SOURCES) -> str:
@@ -772,16 +781,27 @@ def main() -> int:
 
     roof = None
     info = NCU.get(args.workload)
-    if info and info["fp64_flop_per_pstep"] and kern_launches and not batch:
+    if info and kern_launches and not batch:
         avg_launch_s = kern_ms / kern_launches * 1e-3
-        achieved = info["fp64_flop_per_pstep"] * work.runs[0]["N"] / avg_launch_s
+        n_part = work.runs[0]["N"]
         traffic = info["bytes_per_launch"] if info["src_digest"] == src_digest() else None
-        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, "traffic": traffic,
-                "kernel": "wave_kernel (fused segment kernel)",
-                "avg_launch_us": avg_launch_s * 1e6, "launches": kern_launches,
-                "fp64_pipe_active_of_elapsed_ncu": info["fp64_pipe_elapsed"],
-                "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM"}
+        common = {"traffic": traffic, "kernel": "wave_kernel (fused segment kernel)",
+                  "avg_launch_us": avg_launch_s * 1e6, "launches": kern_launches,
+                  "fp64_pipe_active_of_elapsed_ncu": info["fp64_pipe_elapsed"]}
+        if info["basis"] == "issue":
+            achieved = info["warp_inst_per_pstep"] * n_part / avg_launch_s
+            roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": ISSUE_PEAK / 1e12,
+                    "unit": "T warp-instructions/s", "frac": achieved / ISSUE_PEAK, **common,
+                    "per_unit": f"{info['warp_inst_per_pstep']} warp instructions per particle-step",
+                    "peak_source": "derived: 152 SMs x 4 schedulers x 2070 MHz, 1 issue/clk",
+                    "fp64": {"achieved_tflops": info["fp64_flop_per_pstep"] * n_part / avg_launch_s
+                             / 1e12, "peak_tflops": FP64_PEAK_FLOPS / 1e12}}
+        else:
+            achieved = info["fp64_flop_per_pstep"] * n_part / avg_launch_s
+            roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, **common,
+                    "per_unit": f"{info['fp64_flop_per_pstep']} FP64 flop per particle-step",
+                    "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM"}
     cpu = None
     if ws == 1:
         if batch:

@@ -736,9 +736,19 @@ __device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
 // Exponential(mu) with mu ~ Gamma(alpha, rate beta) integrated out (Lomax):
 // P(x > t) = (beta / (beta + t))^alpha; by inversion of one uniform,
 // x = beta (u^(-1/alpha) - 1) = beta expm1(-ln(u) / alpha).
+// x / a for a posterior shape or count a: a product with the table's 1/a when a
+// is an integer below 256 (within an ulp of the quotient), else the division
+__device__ __forceinline__ double div_shape(double x, double a, const MathTab* __restrict__ T) {
+  if (a >= 1.0 && a < 256.0 && a == floor(a)) return x * __ldg(&T->inv_int[(int)a]);
+  return x / a;
+}
+__device__ __forceinline__ float div_shape(float x, float a, const MathTab* __restrict__) {
+  return x / a;
+}
+
 template <typename R>
 __device__ __forceinline__ R lomax(Stream& s, R alpha, R beta) {
-  return beta * m_expm1(neg_log_uniform<R>(s) / alpha);
+  return beta * m_expm1(div_shape(neg_log_uniform<R>(s), alpha, s.tab));
 }
 
 // Poisson(lambda tau) with lambda ~ Gamma(alpha, rate beta) integrated out
@@ -753,11 +763,16 @@ __device__ __noinline__ int neg_binomial(Stream& s, R alpha, R beta, R tau) {
   if (mean < (R)10.0) {
     const R u = uniform01<R>(s);
     const R q = tau / (beta + tau);
-    R pk = ex(-alpha * m_log1p(tau / beta), s);
+    const R l0 = alpha * m_log1p(tau / beta);
+    R pk;
+    if constexpr (sizeof(R) == 8)
+      pk = exp_neg_int(l0, s.tab);  // integer pipes
+    else
+      pk = expf(-l0);
     R acc = pk;
     int k = 0;
-    while (u > acc && k < 1000) {
-      pk = pk * (q * (alpha + (R)k) / (R)(k + 1));
+    while (gt_nonneg(u, acc) && k < 1000) {
+      pk = pk * div_shape(q * (alpha + (R)k), (R)(k + 1), s.tab);
       acc = acc + pk;
       k += 1;
     }
