@@ -294,7 +294,7 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   // Weights, first per warp as soon as the warp's particles reached the
   // checkpoint (overlapping the tile's slower warps): the warp's max M_w, its
   // power-of-two reference k_w = ceil(M_w / ln 2), and e_j = exp(logw_j - k_w
-  // ln 2) 2^54 rounded to an integer (FP64 mode: on the integer pipes).  Then, after the tile barrier, the tile
+  // ln 2) 2^54 rounded to an integer on the integer pipes.  Then, after the tile barrier, the tile
   // reference k_t = max k_w, the exact shift of each weight to it, and the
   // tile's integer running sum E_j (the next segment's search keys).
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -302,10 +302,9 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   const double Mw = warp_max_key(lw);
   const int kw = Mw == -INFINITY ? kDeadTile : tile_exponent(Mw);
   if (valid && kw != kDeadTile) {
-    if constexpr (sizeof(R) == 4) {
-      // FP32 log-weights: FP32 exponential of an FP64 difference
-      ef = to_fix54((double)expf((float)(lw - (double)kw * kLn2)));
-    } else if (kw > -2048 && kw < 2048) {
+    // (an FP32 log-weight is exact as a double, so both precisions share the
+    // normaliser's integer-pipe exponential)
+    if (kw > -2048 && kw < 2048) {
       ef = weight_fix<54>(lw, ref_q58(kw), A.md.tab);  // integer pipes only
     } else {
       const double kd = (double)kw;
