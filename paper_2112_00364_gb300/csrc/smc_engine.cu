@@ -886,7 +886,8 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
         (d->fixed_rates || !(d->lambda_scale > 0.0) || !(d->mu_scale > 0.0)))
       return set_error(SMC_EINVAL, "delayed-sampling CRBD integrates the Gamma priors out: "
                                    "no fixed rates, lambda_scale and mu_scale > 0");
-    blob = align_up(4 * (size_t)d->n_nodes, 256) * 3 + align_up(8 * (size_t)d->n_nodes, 256) * 2;
+    blob = align_up(4 * (size_t)d->n_nodes, 256) * 3 + align_up(8 * (size_t)d->n_nodes, 256) * 2 +
+           align_up(sizeof(BranchRec) * (size_t)d->n_nodes, 256);
   }
   smc_model_s* m = new (std::nothrow) smc_model_s();
   if (!m) return set_error(SMC_ENOMEM, "host allocation failed");
@@ -962,6 +963,21 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
       const size_t M = d->n_nodes;
       ok = (md.parent = (const int*)put(d->parent, 4 * M)) && (md.left = (const int*)put(d->left, 4 * M)) &&
            (md.preorder = (const int*)put(d->preorder, 4 * M)) && (md.age = (const double*)put(d->age, 8 * M));
+      // the branch of each segment k >= 1 in traversal order (entry 0: the root, unused)
+      std::vector<BranchRec> br(M);
+      for (size_t k = 0; k < M; ++k) {
+        BranchRec r{};
+        const int v = d->preorder[k];
+        r.v = v;
+        r.stop = d->age[v];
+        if (k > 0) {
+          const int pa = d->parent[v];
+          r.start = d->age[pa];
+          r.flags = (d->left[v] >= 0 ? 1 : 0) | (d->left[pa] == v ? 2 : 0);
+        }
+        br[k] = r;
+      }
+      if (ok) ok = (md.branch = (const BranchRec*)put(br.data(), sizeof(BranchRec) * M)) != nullptr;
       if (ok && d->fixed_mult) ok = (md.fixed_mult = (const double*)put(d->fixed_mult, 8 * M)) != nullptr;
     }
     if (!ok) {

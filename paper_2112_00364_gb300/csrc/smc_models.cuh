@@ -17,11 +17,29 @@ namespace smc {
 
 // Model constants resident in device memory (Section 3.3: observations and
 // the tree are shared global constants, not per-particle state).
+// The observed branch of segment k of a tree model, precomputed on the host in
+// traversal order so that a branch block makes one 32-byte load instead of a
+// chain of dependent ones: node v = preorder[k], its parent's age (start) and
+// its own (stop), bit 0 of flags: v is internal, bit 1: v is its parent's left
+// child.
+struct BranchRec {
+  double start, stop;
+  int v, flags;
+  long long pad_;
+};
+
+__device__ __forceinline__ BranchRec load_branch(const BranchRec* __restrict__ b, int k) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(b + k));
+  const int4 c = __ldg(reinterpret_cast<const int4*>(b + k) + 1);
+  return BranchRec{a.x, a.y, c.x, c.y, 0};
+}
+
 struct ModelDev {
   int kind, T, n_nodes, fixed_rates, depth_cap, call_limit, lam_stack_cap, pad_;
   const MathTab* tab;  // this device's log / exp tables
   double log_rho;      // log(rho), computed on the host
   const double* obs;
+  const BranchRec* branch;  // tree models: [n_nodes], entry k for k >= 1
   const int* parent;
   const int* left;
   const int* preorder;
@@ -318,7 +336,7 @@ struct TreeModel {
   enum { PRIOR = 0, BRANCH = 1, HIDDEN = 2, END = 3 };
   struct Lane {
     int pc, sp, v, n_top, fsp, calls;
-    bool ckpt;
+    bool ckpt, internal;
     int overflow, limited;
     R lam, mu, logw, loglam, inv_mu;
     R lam_b, start, stop, lnp1, lnp2, lnp3, cur_t;
@@ -378,15 +396,16 @@ struct TreeModel {
         return;
       }
       case BRANCH: {
-        const int v = md.preorder[k];
-        const int p = md.parent[v];
+        const BranchRec br = load_branch(md.branch, k);
+        const int v = br.v;
         L.v = v;
+        L.internal = (br.flags & 1) != 0;
         R lam = L.lam;
         if (RS) {
           R lam_p;
           if (L.sp <= 0) {
             lam_p = L.lam;
-          } else if (md.left[p] == v) {
+          } else if (br.flags & 2) {
             lam_p = S.st<R>(L.sp - 1, i, N);  // left child: parent's rate stays pending
           } else {
             L.sp -= 1;  // right child: last use of the parent's rate
@@ -402,11 +421,11 @@ struct TreeModel {
           lam = lam_p * mult;
         }
         L.lam_b = lam;
-        L.start = (R)md.age[p];
-        L.stop = (R)md.age[v];
+        L.start = (R)br.start;
+        L.stop = (R)br.stop;
         const R dt = L.start - L.stop;
         L.lnp1 = -L.mu * dt;
-        L.lnp2 = (md.left[v] >= 0) ? (RS ? lg(lam, s) : L.loglam) : (R)md.log_rho;
+        L.lnp2 = L.internal ? (RS ? lg(lam, s) : L.loglam) : (R)md.log_rho;
         L.n_top = poisson<R>(s, lam * dt);
         if (L.n_top > 0 && L.mu > (R)0) L.inv_mu = (R)1 / L.mu;
         L.lnp3 = (R)0;
@@ -477,7 +496,7 @@ struct TreeModel {
       }
       default: {  // END
         L.logw = L.logw + (L.lnp1 + (L.lnp2 + L.lnp3));
-        if (RS && md.left[L.v] >= 0) {
+        if (RS && L.internal) {
           if (L.sp < md.lam_stack_cap) {
             S.st<R>(L.sp, i, N) = L.lam_b;
             L.sp += 1;
@@ -565,15 +584,14 @@ struct TreeDsModel {
         return;
       }
       case BRANCH: {
-        const int v = md.preorder[k];
-        const int p = md.parent[v];
-        L.v = v;
-        L.start = (R)md.age[p];
-        L.stop = (R)md.age[v];
+        const BranchRec br = load_branch(md.branch, k);
+        L.v = br.v;
+        L.start = (R)br.start;
+        L.stop = (R)br.stop;
         const R dt = L.start - L.stop;
         L.lnp1 = -L.am * m_log1p(dt / L.bm);
         L.bm = L.bm + dt;
-        if (md.left[v] >= 0) {
+        if (br.flags & 1) {
           L.lnp2 = lg(L.al / L.bl, s);
           L.al = L.al + (R)1.0;
         } else {
