@@ -82,12 +82,12 @@ RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, 
 # plain CRBD (latency-bound, most arithmetic on the integer pipes), the FP64
 # rate for the delayed-sampling CRBD (FP64 pipe busy 36-44% of a launch).  The
 # traffic holds only for the kernel sources with the recorded digest.
-NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=102.0, fp64_flop_per_pstep=12.55,
-                      bytes_per_launch=3.31e6, fp64_pipe_elapsed=0.166,
-                      src_digest="72fca7eeabfe53b5"),
-       "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=117.8, fp64_flop_per_pstep=196.6,
-                          bytes_per_launch=5.8e6, fp64_pipe_elapsed=0.398,
-                          src_digest="72fca7eeabfe53b5")}
+NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=102.2, fp64_flop_per_pstep=12.55,
+                      bytes_per_launch=3.35e6, fp64_pipe_elapsed=0.173,
+                      src_digest="1190210a230d9789"),
+       "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=117.2, fp64_flop_per_pstep=196.6,
+                          bytes_per_launch=5.77e6, fp64_pipe_elapsed=0.402,
+                          src_digest="1190210a230d9789")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
