@@ -230,7 +230,9 @@ typedef struct smc_server_s *smc_server_t;
 typedef struct {
   int32_t precision;          /* SMC_PREC_*: every request of a server uses it */
   int32_t max_resident_runs;  /* cap on runs resident at once (0 = 4096) */
-  int32_t poll_waves;         /* waves between looks at the finished runs (0 = 1) */
+  int32_t poll_waves;         /* waves launched between looks at the finished runs (0 = 2: the
+                                 host's per-look work then overlaps a queued wave; a finished
+                                 run is noticed at most poll_waves waves late) */
   int32_t pad_;
 } smc_server_cfg;
 

@@ -4,10 +4,11 @@
 //   1. admit queued requests while the resident-run cap and the device-memory
 //      budget allow (each admitted run gets its workspace from the stream-ordered
 //      pool and a zeroed run state, so it starts at segment 0 in the next wave);
-//   2. launch one wave: every resident run advances one segment (the same wave
-//      kernels as smc_run_batch, over the current run table);
-//   3. gather the resident runs' done flags into pinned memory and, one wave
-//      behind (so the GPU always has the next wave queued), retire the finished
+//   2. launch poll_waves waves (default 2): every resident run advances one
+//      segment per wave (the same wave kernels as smc_run_batch, over the
+//      current run table), so the host's work of step 3 overlaps a queued wave;
+//   3. gather the resident runs' done flags into pinned memory and, one poll
+//      behind (so the GPU always has the next waves queued), retire the finished
 //      runs: their outputs are copied into the callers' result buffers on the
 //      stream, an event marks them complete, and their workspace goes back to the
 //      pool after the copies.
@@ -392,6 +393,7 @@ extern "C" smc_status smc_server_create(size_t device_mem_budget, const smc_serv
     return cuda_fail(e, "server setup");
   }
   if (S->cfg.max_resident_runs <= 0) S->cfg.max_resident_runs = 4096;
+  if (S->cfg.poll_waves <= 0) S->cfg.poll_waves = 2;
   smc_status fs = alloc_flags(S, S->cfg.max_resident_runs);
   if (fs) {
     delete h;
