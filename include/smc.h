@@ -339,12 +339,14 @@ smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uin
  * FP64 logarithm the samplers use, 1 = the table-driven FP64 exponential, 2 = the
  * CUDA library log, 3 = the CUDA library exp; for fn 4 and 5 x[i] holds 64 random
  * bits b (read as uint64) and y[i] = log u of the FP64 uniform u = ((b >> 11) | 1)
- * 2^-53, 4 = reduced on the integer pipes (what the samplers use), 5 = the
- * table logarithm of u built as a double; for fn 6 and 7 y[i] holds (as int64
+ * 2^-53, 4 = reduced and its log1p polynomial evaluated on the integer pipes (what
+ * the samplers use), 5 = the table logarithm of u built as a double; for fn 6 and 7
+ * y[i] holds (as int64
  * bits) the fixed-point weight round(e^x[i] 2^54) for x[i] <= 0, 6 = computed
  * on the integer pipes (what the segment kernel uses), 7 = the table exponential
- * rounded to the same grid; fn 8 and 9 give round(e^x[i] 2^54) and round(e^x[i]
- * 2^50) from the two-table integer exponential of smc_resample; fn 10 gives e^-x[i]
+ * rounded to the same grid; fn 8 gives round(e^x[i] 2^54) from the two-table
+ * integer exponential, fn 9 round(e^x[i] 2^50) as smc_resample forms its weights
+ * with it (the argument in 2^-52 units); fn 10 gives e^-x[i]
  * (a double, x[i] in [0, 64)) from the same integer exponential, as the Poisson
  * sampler forms it.  x, y [n] f64 device pointers.
  * Errors: SMC_EINVAL, SMC_ECUDA. */

@@ -782,58 +782,7 @@ __device__ __noinline__ int neg_binomial(Stream& s, R alpha, R beta, R tau) {
   return poisson<R>(s, lam * tau);
 }
 
-// ---- FP64 warp / block primitives (deterministic association order) ----
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-__device__ __forceinline__ double warp_incl_scan(double v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const double t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v = v + t;
-  }
-  return v;
-}
-
-// Block max over TPB threads; every thread gets the result.  `sh` >= TPB/32 doubles.
-template <int TPB>
-__device__ __forceinline__ double block_max(double v, double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_max(v);
-  __syncthreads();
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  double r = sh[0];
-#pragma unroll
-  for (int w = 1; w < TPB / 32; ++w) r = fmax(r, sh[w]);
-  return r;
-}
-
-// Block inclusive scan over TPB threads (warp scans, then the warp totals
-// scanned in order by every thread).  `sh` >= TPB/32 doubles.
-template <int TPB>
-__device__ __forceinline__ double block_incl_scan(double v, double* sh) {
-  static_assert(TPB <= 1024 && TPB % 32 == 0, "block size");
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  v = warp_incl_scan(v);
-  __syncthreads();
-  if (lane == 31) sh[wid] = v;
-  __syncthreads();
-  if (wid == 0) {  // exclusive scan of the warp totals by the first warp
-    const double t = lane < TPB / 32 ? sh[lane] : 0.0;
-    const double it = warp_incl_scan(t);
-    const double ex = __shfl_up_sync(0xffffffffu, it, 1);
-    __syncwarp();
-    if (lane < TPB / 32) sh[lane] = lane ? ex : 0.0;
-  }
-  __syncthreads();
-  return wid > 0 ? sh[wid] + v : v;
-}
-
+// ---- warp / block primitives (integer, deterministic association order) ----
 // Block max of an int over TPB threads; every thread gets the result.
 template <int TPB>
 __device__ __forceinline__ int block_max_int(int v, int* sh) {
@@ -846,22 +795,6 @@ __device__ __forceinline__ int block_max_int(int v, int* sh) {
 #pragma unroll
   for (int w = 1; w < TPB / 32; ++w) r = max(r, sh[w]);
   return r;
-}
-
-// Block inclusive prefix max over TPB threads.  `sh` >= TPB/32 doubles.
-template <int TPB>
-__device__ __forceinline__ double block_incl_max(double v, double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const double t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v = fmax(v, t);
-  }
-  __syncthreads();
-  if (lane == 31) sh[wid] = v;
-  __syncthreads();
-  for (int w = 0; w < wid; ++w) v = fmax(v, sh[w]);
-  return v;
 }
 
 // Block inclusive prefix max of int64 keys over TPB threads.  `sh` >= TPB/32
