@@ -83,11 +83,11 @@ RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, 
 # rate for the delayed-sampling CRBD (FP64 pipe busy 36-44% of a launch).  The
 # traffic holds only for the kernel sources with the recorded digest.
 NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=102.2, fp64_flop_per_pstep=12.55,
-                      bytes_per_launch=3.36e6, fp64_pipe_elapsed=0.172,
-                      src_digest="89ecd4f9b16bbc28"),
+                      bytes_per_launch=3.35e6, fp64_pipe_elapsed=0.170,
+                      src_digest="37b190d5171775f5"),
        "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=117.2, fp64_flop_per_pstep=196.6,
-                          bytes_per_launch=5.78e6, fp64_pipe_elapsed=0.395,
-                          src_digest="89ecd4f9b16bbc28")}
+                          bytes_per_launch=5.79e6, fp64_pipe_elapsed=0.397,
+                          src_digest="37b190d5171775f5")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4

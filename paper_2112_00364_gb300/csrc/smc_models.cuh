@@ -304,6 +304,78 @@ struct SeirModel {
 };
 
 // ------------------------------------------------------------------------
+// The hidden-lineage frame machine shared by the tree models (Listing 1's
+// simBranch / crbdGoesUndetected / iter recursion made explicit): one hidden
+// speciation event per call.  The event is the next child of the top frame
+// (time ~ U(t - bl, t)) or the branch's next one (~ U(stop, start)); a frame
+// whose children all went undetected returns true (at the branch level that
+// multiplies the weight by 2: lnProb3 += ln 2).  Then the undetected-lineage
+// call at that time: a call deeper than depth_cap, or the (call_limit+1)-th
+// call of a segment, kills the particle; the lifetime dur comes from
+// M::lifetime; if dur > t the lineage is detected with probability rho (the
+// particle dies); the speciation count on min(dur, t) comes from M::count, and
+// a positive count pushes a frame.  M::lifetime and M::count take the model's
+// draws (and, for delayed sampling, update its posteriors).
+// ------------------------------------------------------------------------
+template <class M, typename R = typename M::R>
+__device__ __forceinline__ void hidden_event(typename M::Lane& L, Stream& s, const ModelDev& md,
+                                             int end_block) {
+  for (;;) {
+    if (L.fsp == 0) {
+      if (L.n_top == 0) {
+        L.pc = end_block;
+        return;
+      }
+      L.n_top -= 1;
+      L.cur_t = uniform_ab<R>(s, L.stop, L.start);
+      break;
+    }
+    const int f = L.fsp - 1;
+    if (L.fr_rem[f] == 0) {
+      L.fsp = f;
+      if (f == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
+      continue;
+    }
+    L.fr_rem[f] -= 1;
+    const R t = L.fr_t[f];
+    L.cur_t = uniform_ab<R>(s, t - L.fr_bl[f], t);
+    break;
+  }
+  if (L.fsp + 1 > md.depth_cap) {
+    L.overflow = 1;
+    L.lnp3 = neg_inf<R>();
+    L.pc = end_block;
+    return;
+  }
+  L.calls += 1;
+  if (L.calls > md.call_limit) {
+    L.limited = 1;
+    L.lnp3 = neg_inf<R>();
+    L.pc = end_block;
+    return;
+  }
+  const R t = L.cur_t;
+  const R dur = M::lifetime(L, s);
+  if (gt_nonneg(dur, t)) {  // both >= 0
+    if (bernoulli<R>(s, (R)md.rho)) {
+      L.lnp3 = neg_inf<R>();
+      L.pc = end_block;
+      return;
+    }
+  }
+  const R bl = dur < t ? dur : t;
+  const int j = M::count(L, s, bl);
+  if (j == 0) {  // returned true at once
+    if (L.fsp == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
+    return;
+  }
+  L.fr_t[L.fsp] = t;
+  L.fr_bl[L.fsp] = bl;
+  L.fr_rem[L.fsp] = j;
+  L.fsp += 1;
+}
+
+// ------------------------------------------------------------------------
 // Birth-death tree models (Listing 1).  PSTATE crossing checkpoints:
 // real 0 = lambda (RATESHIFT: the root rate lambda0), real 1 = mu, int 0 =
 // block index; RATESHIFT adds int 1 = stack pointer and the pending-rate
@@ -373,6 +445,11 @@ struct TreeModel {
     L.ckpt = false;
     L.overflow = L.limited = 0;
   }
+  // hidden_event's draws: a lifetime ~ Exp(mu), a speciation count ~ Poisson(lambda bl)
+  __device__ static R lifetime(Lane& L, Stream& s) {
+    return L.mu > (R)0 ? exponential_inv(s, L.mu, L.inv_mu) : exponential<R>(s, L.mu);
+  }
+  __device__ static int count(Lane& L, Stream& s, R bl) { return poisson<R>(s, L.lam_b * bl); }
   __device__ static void block(int b, Lane& L, Stream& s, const ModelDev& md, const StateView& S,
                                int i, int k, int N) {
     switch (b) {
@@ -435,63 +512,7 @@ struct TreeModel {
         return;
       }
       case HIDDEN: {
-        // the next event: a child of the top frame, or the branch's next one;
-        // a frame whose children all went undetected returns true (at the
-        // branch level that multiplies the weight by 2: lnProb3 += ln 2)
-        for (;;) {
-          if (L.fsp == 0) {
-            if (L.n_top == 0) {
-              L.pc = END;
-              return;
-            }
-            L.n_top -= 1;
-            L.cur_t = uniform_ab<R>(s, L.stop, L.start);
-            break;
-          }
-          const int f = L.fsp - 1;
-          if (L.fr_rem[f] == 0) {
-            L.fsp = f;
-            if (f == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
-            continue;
-          }
-          L.fr_rem[f] -= 1;
-          const R t = L.fr_t[f];
-          L.cur_t = uniform_ab<R>(s, t - L.fr_bl[f], t);
-          break;
-        }
-        // crbdGoesUndetected(cur_t)
-        if (L.fsp + 1 > md.depth_cap) {
-          L.overflow = 1;
-          L.lnp3 = neg_inf<R>();
-          L.pc = END;
-          return;
-        }
-        L.calls += 1;
-        if (L.calls > md.call_limit) {
-          L.limited = 1;
-          L.lnp3 = neg_inf<R>();
-          L.pc = END;
-          return;
-        }
-        const R t = L.cur_t;
-        const R dur = L.mu > (R)0 ? exponential_inv(s, L.mu, L.inv_mu) : exponential<R>(s, L.mu);
-        if (gt_nonneg(dur, t)) {  // both >= 0
-          if (bernoulli<R>(s, (R)md.rho)) {
-            L.lnp3 = neg_inf<R>();
-            L.pc = END;
-            return;
-          }
-        }
-        const R bl = dur < t ? dur : t;
-        const int j = poisson<R>(s, L.lam_b * bl);
-        if (j == 0) {  // returned true at once
-          if (L.fsp == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
-          return;
-        }
-        L.fr_t[L.fsp] = t;
-        L.fr_bl[L.fsp] = bl;
-        L.fr_rem[L.fsp] = j;
-        L.fsp += 1;
+        hidden_event<TreeModel>(L, s, md, END);
         return;
       }
       default: {  // END
@@ -570,6 +591,21 @@ struct TreeDsModel {
     L.ckpt = false;
     L.overflow = L.limited = 0;
   }
+  // hidden_event's draws from the predictive laws, each followed by its
+  // conjugate update: a lifetime ~ Lomax(a_m, b_m), then a_m += 1, b_m += dur;
+  // a speciation count ~ NegBin(a_l, b_l, bl), then a_l += j, b_l += bl
+  __device__ static R lifetime(Lane& L, Stream& s) {
+    const R dur = lomax<R>(s, L.am, L.bm);
+    L.am = L.am + (R)1.0;
+    L.bm = L.bm + dur;
+    return dur;
+  }
+  __device__ static int count(Lane& L, Stream& s, R bl) {
+    const int j = neg_binomial<R>(s, L.al, L.bl, bl);
+    L.al = L.al + (R)j;
+    L.bl = L.bl + bl;
+    return j;
+  }
   __device__ static void block(int b, Lane& L, Stream& s, const ModelDev& md, const StateView&,
                                int, int k, int) {
     switch (b) {
@@ -607,66 +643,7 @@ struct TreeDsModel {
         return;
       }
       case HIDDEN: {
-        // the next event (as in TreeModel): a child of the top frame, or the
-        // branch's next one; a finished frame returns true (ln 2 at the
-        // branch level)
-        for (;;) {
-          if (L.fsp == 0) {
-            if (L.n_top == 0) {
-              L.pc = END;
-              return;
-            }
-            L.n_top -= 1;
-            L.cur_t = uniform_ab<R>(s, L.stop, L.start);
-            break;
-          }
-          const int f = L.fsp - 1;
-          if (L.fr_rem[f] == 0) {
-            L.fsp = f;
-            if (f == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
-            continue;
-          }
-          L.fr_rem[f] -= 1;
-          const R t = L.fr_t[f];
-          L.cur_t = uniform_ab<R>(s, t - L.fr_bl[f], t);
-          break;
-        }
-        if (L.fsp + 1 > md.depth_cap) {
-          L.overflow = 1;
-          L.lnp3 = neg_inf<R>();
-          L.pc = END;
-          return;
-        }
-        L.calls += 1;
-        if (L.calls > md.call_limit) {
-          L.limited = 1;
-          L.lnp3 = neg_inf<R>();
-          L.pc = END;
-          return;
-        }
-        const R t = L.cur_t;
-        const R dur = lomax<R>(s, L.am, L.bm);
-        L.am = L.am + (R)1.0;
-        L.bm = L.bm + dur;
-        if (gt_nonneg(dur, t)) {  // both >= 0
-          if (bernoulli<R>(s, (R)md.rho)) {
-            L.lnp3 = neg_inf<R>();
-            L.pc = END;
-            return;
-          }
-        }
-        const R bl = dur < t ? dur : t;
-        const int j = neg_binomial<R>(s, L.al, L.bl, bl);
-        L.al = L.al + (R)j;
-        L.bl = L.bl + bl;
-        if (j == 0) {
-          if (L.fsp == 0) L.lnp3 = L.lnp3 + C<R>::ln2;
-          return;
-        }
-        L.fr_t[L.fsp] = t;
-        L.fr_bl[L.fsp] = bl;
-        L.fr_rem[L.fsp] = j;
-        L.fsp += 1;
+        hidden_event<TreeDsModel>(L, s, md, END);
         return;
       }
       default: {  // END
