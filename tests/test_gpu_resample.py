@@ -77,3 +77,34 @@ def test_gather_with_stack_bound(dtype, N):
     d2 = torch.from_numpy(dst0.copy()).cuda()
     smc.gather(torch.from_numpy(src).cuda(), d2, torch.from_numpy(anc).cuda())
     np.testing.assert_array_equal(d2.cpu().numpy(), src[:, anc])
+
+
+def test_resample_and_gather_bench_size():
+    """The benchmark's standalone step at its full size (2^24 log-weights
+    normal(0, 2), seed 24; a 2-field f64 state): every ancestor against the
+    oracle (differences only where the oracle flags the offset), the
+    normaliser and log-Z increment, and the gather element by element; with the
+    workspace and static entry points giving the same ancestors."""
+    import torch
+    from paper_2112_00364_gb300 import smc
+
+    N = 1 << 24
+    lw = inputs.random_logw(N, seed=24, scale=2.0)
+    for u in (0.5, 0.0123456789):
+        x = torch.from_numpy(lw).cuda()
+        anc, o3, nn = smc.resample(x, u)
+        a_g = anc.cpu().numpy()
+        a_o, flag, incr, m, S, rc = oracle.resample(lw, u)
+        assert rc == 0
+        diff = a_g != a_o
+        assert np.all(flag[diff] == 1), np.where(diff & (flag == 0))[0][:10]
+        assert np.all(np.diff(a_g) >= 0) and a_g[0] >= 0 and a_g[-1] < N
+        assert abs(o3[2].item() - incr) <= 1e-12 * max(1.0, abs(incr))
+        anc_s, _, _ = smc.resample_static(x, u)
+        assert torch.equal(anc_s, anc)
+    rng = np.random.default_rng(5)
+    src_h = rng.standard_normal((2, N))
+    src = torch.from_numpy(src_h).cuda()
+    dst = torch.empty_like(src)
+    smc.gather(src, dst, anc)
+    np.testing.assert_array_equal(dst.cpu().numpy(), src_h[:, a_g])
