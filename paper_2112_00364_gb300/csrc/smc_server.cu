@@ -107,7 +107,10 @@ struct Server {
   RunFlags* flags_dev = nullptr;
   RunFlags* flags_host[2] = {nullptr, nullptr};
   cudaEvent_t flags_ev[2] = {nullptr, nullptr};
-  std::vector<Request*> flags_owner[2];
+  // tickets of the runs whose flags a snapshot holds, in table order (tickets,
+  // not pointers: a retired request is deleted and its address may be reused
+  // by a request admitted before the snapshot is read)
+  std::vector<uint64_t> flags_owner[2];
   int flags_pending[2] = {0, 0};
   int cap_flags = 0;
   WavePlan plan;
@@ -235,13 +238,17 @@ int admit(Server* S, smc_status* err) {
 smc_status retire(Server* S, int b) {
   const int n = S->flags_pending[b];
   const RunFlags* f = S->flags_host[b];
-  std::vector<Request*>& owners = S->flags_owner[b];
+  const std::vector<uint64_t>& owners = S->flags_owner[b];
+  std::unordered_map<uint64_t, Request*> live;
+  live.reserve(S->resident.size() * 2 + 1);
+  for (Request* r : S->resident) live.emplace(r->ticket, r);
   for (int i = 0; i < n; ++i) {
-    Request* q = owners[i];
+    const auto lv = live.find(owners[i]);
+    if (lv == live.end()) continue;  // already retired
+    Request* q = lv->second;
     if (!(f[i].done || q->cancel)) continue;
-    auto it = std::find(S->resident.begin(), S->resident.end(), q);
-    if (it == S->resident.end()) continue;  // already retired
-    S->resident.erase(it);
+    live.erase(lv);
+    S->resident.erase(std::find(S->resident.begin(), S->resident.end(), q));
     S->table_dirty = true;
     // a finished run's state no longer changes, so this snapshot is final
     RunState hrs;
@@ -321,7 +328,8 @@ void worker_main(Server* S) {
     cudaMemcpyAsync(S->flags_host[parity], S->flags_dev, sizeof(RunFlags) * n, cudaMemcpyDeviceToHost,
                     S->stream);
     cudaEventRecord(S->flags_ev[parity], S->stream);
-    S->flags_owner[parity] = S->resident;
+    S->flags_owner[parity].clear();
+    for (Request* q : S->resident) S->flags_owner[parity].push_back(q->ticket);
     S->flags_pending[parity] = n;
     // one wave behind: the flags of the previous wave
     if (last_flags) {

@@ -77,3 +77,55 @@ def test_batch_of_one_and_device_outputs():
     a = smc.run(m, 5000, 3)
     torch.cuda.synchronize()
     assert float(b[0]["log_z"].cpu()[0]) == a["log_z_value"]
+
+
+def test_batch512_bench_workload():
+    """The batched benchmark workload in full: the 512 runs of the seeded mix
+    (half linear-Gaussian, half CRBD, N log-uniform 256..65,536), FP32 particles,
+    seeds as the benchmark's first rank draws them.  Every run finishes with a
+    finite log Z; a sample of 32 runs (the 8 smallest, 8 largest and 16 drawn at
+    random) give exactly what they give alone through smc_run; the 2 smallest
+    CRBD runs also follow the FP32 oracle to FP32 rounding."""
+    from paper_2112_00364_gb300 import smc
+
+    specs = inputs.batch_specs(512, seed=4)
+    models, runspecs, params = [], [], []
+    for q, sp in enumerate(specs):
+        if sp.kind == "lg":
+            p = dict(obs=inputs.lg_observations(sp.T, seed=sp.obs_seed))
+        else:
+            p = dict(tree=inputs.yule_tree(sp.tips, seed=sp.tree_seed))
+        models.append(smc.Model(sp.kind, **p))
+        runspecs.append(dict(N=sp.n_particles, seed=1 + sp.seed, run_id=q))
+        params.append((sp.kind, p))
+    batch = smc.run_batch(models, runspecs, precision="fp32")
+    assert all(b["run_status"] == 0 and np.isfinite(b["log_z_value"]) for b in batch)
+    sizes = np.array([sp.n_particles * sp.n_segments() for sp in specs])
+    order = np.argsort(sizes)
+    rng = np.random.default_rng(3)
+    pick = set(order[:8]) | set(order[-8:]) | set(rng.choice(512, 16, replace=False).tolist())
+    for q in sorted(pick):
+        sp = runspecs[q]
+        a = smc.run(models[q], sp["N"], sp["seed"], run_id=sp["run_id"], precision="fp32")
+        b = batch[q]
+        assert b["log_z_value"] == a["log_z_value"], q
+        assert b["n_segments"] == a["n_segments"]
+        np.testing.assert_array_equal(b["ancestors"], a["ancestors"])
+        np.testing.assert_array_equal(b["final_logw"], a["final_logw"])
+        np.testing.assert_array_equal(b["int_fields"], a["int_fields"])
+    crbd_small = [q for q in order if params[q][0] == "crbd"][:2]
+    for q in crbd_small:
+        kind, p = params[q]
+        sp = runspecs[q]
+        g = smc.run(models[q], sp["N"], sp["seed"], run_id=sp["run_id"], precision="fp32",
+                    record_all_ancestors=True)
+        o = oracle.smc_run(kind, sp["N"], sp["seed"], run_id=sp["run_id"],
+                           precision=oracle.FP32, follow=g["ancestors"], record_ancestors=True,
+                           **p)
+        assert g["n_segments"] == o["n_segments"]
+        n_off = max(1, o["n_resamples"] * sp["N"])
+        assert (o["n_hard_mismatch"] + o["n_flag_mismatch"]) / n_off < 2e-3
+        tol = 2e-5 * g["n_segments"] * max(1.0, abs(o["log_z"]) / g["n_segments"])
+        assert abs(g["log_z_value"] - o["log_z"]) <= tol
+    for m in models:
+        m.close()

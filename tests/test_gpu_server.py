@@ -96,3 +96,40 @@ def test_server_cancel_timeout_and_oversize():
         srv.submit(m, 1 << 24, 3)  # workspace larger than the whole budget
     assert e.value.status == smc.ENOMEM
     srv.close()
+
+
+def test_server_bench_mix_stream():
+    """The serving benchmark's request mix at its arrival rate: 400 requests
+    drawn as the benchmark draws them (sizes from the batch512 mix, Poisson
+    arrivals at 2000 requests/s), FP32, submitted on their arrival times so that
+    new runs join waves already in flight.  Every request completes, and each of
+    a sample of 40 equals its standalone smc_run bit for bit."""
+    from paper_2112_00364_gb300 import smc
+
+    specs = inputs.batch_specs(512, seed=4)
+    models = {}
+    arr = inputs.poisson_arrivals(2000.0, 0.2, seed=5)[:400]
+    rng = np.random.default_rng(5)
+    picks = rng.integers(0, len(specs), len(arr))
+    srv = smc.Server(96 << 30, precision="fp32")
+    tickets, reqs = [], []
+    t0 = time.perf_counter()
+    for a, q in zip(arr, picks):
+        sp = specs[q]
+        if q not in models:
+            p = (dict(obs=inputs.lg_observations(sp.T, seed=sp.obs_seed)) if sp.kind == "lg"
+                 else dict(tree=inputs.yule_tree(sp.tips, seed=sp.tree_seed)))
+            models[q] = smc.Model(sp.kind, **p)
+        while time.perf_counter() - t0 < a:
+            time.sleep(1e-4)
+        reqs.append((models[q], sp.n_particles, 1 + sp.seed, int(q)))
+        tickets.append(srv.submit(models[q], sp.n_particles, 1 + sp.seed, run_id=int(q)))
+    got = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["worker_status"] == 0
+    for i in np.random.default_rng(6).choice(len(reqs), 40, replace=False):
+        m, N, seed, rid = reqs[i]
+        _same(got[i], smc.run(m, N, seed, run_id=rid, precision="fp32"))
+    for m in models.values():
+        m.close()
