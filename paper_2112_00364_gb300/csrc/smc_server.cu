@@ -27,6 +27,7 @@
 #include <new>
 #include <thread>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "smc_engine.h"
@@ -72,7 +73,7 @@ struct Request {
   RunDev dev;
   cudaEvent_t done_ev = nullptr;
   double t_submit = 0.0;
-  bool cancel = false;
+  bool cancel = false;  // queued: written and read under the server mutex; resident: worker only
 };
 
 double now_s() {
@@ -92,6 +93,9 @@ struct Server {
   bool stop = false;
   std::deque<Request*> queue;
   std::unordered_map<uint64_t, int> state;  // ticket -> TicketState
+  // cancellations of resident runs, handed to the worker under `mu` (the
+  // resident list itself belongs to the worker thread alone)
+  std::unordered_set<uint64_t> cancel_req;
   std::unordered_map<uint64_t, int> final_status;
   std::unordered_map<uint64_t, double> latency;
   uint64_t next_ticket = 1;
@@ -177,6 +181,7 @@ smc_status upload_table(Server* S) {
 
 void finish_ticket(Server* S, Request* q, int status) {
   std::lock_guard<std::mutex> lk(S->mu);
+  S->cancel_req.erase(q->ticket);  // a cancel that came after the run finished
   S->state[q->ticket] = (status < 0 && status != SMC_EDEGENERATE && status != SMC_ESTEPLIMIT) ? T_FAILED : T_DONE;
   S->final_status[q->ticket] = status;
   S->latency[q->ticket] = now_s() - q->t_submit;
@@ -239,6 +244,12 @@ smc_status retire(Server* S, int b) {
   const int n = S->flags_pending[b];
   const RunFlags* f = S->flags_host[b];
   const std::vector<uint64_t>& owners = S->flags_owner[b];
+  {  // cancellations requested since the last look
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->cancel_req.empty())
+      for (Request* r : S->resident)
+        if (S->cancel_req.erase(r->ticket)) r->cancel = true;
+  }
   std::unordered_map<uint64_t, Request*> live;
   live.reserve(S->resident.size() * 2 + 1);
   for (Request* r : S->resident) live.emplace(r->ticket, r);
@@ -485,10 +496,12 @@ extern "C" smc_status smc_server_cancel(smc_server_t h, uint64_t ticket) {
   auto it = S->state.find(ticket);
   if (it == S->state.end()) return set_error(SMC_EINVAL, "unknown ticket");
   if (it->second >= T_COMPLETING) return SMC_OK;
-  for (Request* q : S->queue)
-    if (q->ticket == ticket) q->cancel = true;
-  for (Request* q : S->resident)
-    if (q->ticket == ticket) q->cancel = true;
+  if (it->second == T_QUEUED) {
+    for (Request* q : S->queue)
+      if (q->ticket == ticket) q->cancel = true;
+  } else {
+    S->cancel_req.insert(ticket);  // the worker marks the resident run
+  }
   return SMC_OK;
 }
 
