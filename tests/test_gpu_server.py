@@ -133,3 +133,45 @@ def test_server_bench_mix_stream():
         _same(got[i], smc.run(m, N, seed, run_id=rid, precision="fp32"))
     for m in models.values():
         m.close()
+
+
+def test_server_every_model_kind_and_ess():
+    """Requests of every model kind (rate-shift with its PSTATE stack, the
+    geometric program with its host-polled length, SEIR, the delayed-sampling
+    CRBD), some with ESS-triggered resampling, served together: each equals its
+    standalone smc_run bit for bit, ancestors and resampling decisions included."""
+    from paper_2112_00364_gb300 import smc
+
+    tree = inputs.yule_tree(24, seed=7)
+    cases = [
+        (smc.Model("rateshift", tree=tree, sigma=0.3, lam_stack_cap=tree.max_pending_right() + 1),
+         3000, 0.0),
+        (smc.Model("geometric"), 2000, 0.0),
+        (smc.Model("seir", obs=inputs.seir_observations(35, seed=7)), 1500, 0.0),
+        (smc.Model("crbd_ds", tree=tree), 4000, 0.5),
+        (smc.Model("crbd", tree=tree), 5000, 0.3),
+        (smc.Model("lg", obs=inputs.lg_observations(40, seed=2)), 2500, 0.5),
+    ]
+    srv = smc.Server(4096 << 20, precision="fp64")
+    tickets = []
+    for q, (m, N, tau) in enumerate(cases * 2):
+        tickets.append(srv.submit(m, N, 40 + q, run_id=q, record_all_ancestors=True,
+                                  ess_threshold=tau))
+        time.sleep(0.001)
+    got = [srv.wait(t) for t in tickets]
+    srv.close()
+    for q, ((m, N, tau), g) in enumerate(zip(cases * 2, got)):
+        a = smc.run(m, N, 40 + q, run_id=q, record_all_ancestors=True, ess_threshold=tau)
+        assert g["run_status"] == a["run_status"] and g["n_segments"] == a["n_segments"]
+        assert g["log_z_value"] == a["log_z_value"]
+        np.testing.assert_array_equal(g["final_logw"], a["final_logw"])
+        np.testing.assert_array_equal(g["int_fields"], a["int_fields"])
+        np.testing.assert_array_equal(g["ancestors"], a["ancestors"])
+        if "real_fields" in a:
+            np.testing.assert_array_equal(g["real_fields"], a["real_fields"])
+        if "resampled" in a:
+            np.testing.assert_array_equal(g["resampled"], a["resampled"])
+        if "stack" in a:
+            np.testing.assert_array_equal(g["stack"], a["stack"])
+    for m, _, _ in cases:
+        m.close()
