@@ -129,3 +129,39 @@ def test_batch512_bench_workload():
         assert abs(g["log_z_value"] - o["log_z"]) <= tol
     for m in models:
         m.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_every_model_kind_and_ess(precision):
+    """A batch holding every model kind (SEIR and the delayed-sampling CRBD
+    among them), some runs with ESS-triggered resampling at their own
+    thresholds: each run equals its standalone smc_run bit for bit, resampling
+    decisions included."""
+    from paper_2112_00364_gb300 import smc
+
+    tree = inputs.yule_tree(20, seed=9)
+    models = [smc.Model("seir", obs=inputs.seir_observations(28, seed=7)),
+              smc.Model("crbd_ds", tree=tree),
+              smc.Model("crbd", tree=tree),
+              smc.Model("lg", obs=inputs.lg_observations(30, seed=4)),
+              smc.Model("geometric"),
+              smc.Model("rateshift", tree=tree, sigma=0.3,
+                        lam_stack_cap=tree.max_pending_right() + 1)]
+    specs = [dict(N=1200, seed=11, run_id=0), dict(N=3000, seed=12, run_id=1, ess_threshold=0.5),
+             dict(N=2500, seed=13, run_id=2, ess_threshold=0.3), dict(N=700, seed=14, run_id=3),
+             dict(N=900, seed=15, run_id=4, ess_threshold=0.6), dict(N=1800, seed=16, run_id=5)]
+    batch = smc.run_batch(models, specs, precision=precision, record_all_ancestors=True)
+    for m, sp, b in zip(models, specs, batch):
+        a = smc.run(m, sp["N"], sp["seed"], run_id=sp["run_id"], precision=precision,
+                    record_all_ancestors=True, ess_threshold=sp.get("ess_threshold", 0.0))
+        assert b["run_status"] == a["run_status"] and b["n_segments"] == a["n_segments"]
+        assert b["log_z_value"] == a["log_z_value"]
+        np.testing.assert_array_equal(b["ancestors"], a["ancestors"])
+        np.testing.assert_array_equal(b["final_logw"], a["final_logw"])
+        np.testing.assert_array_equal(b["int_fields"], a["int_fields"])
+        if "real_fields" in a:
+            np.testing.assert_array_equal(b["real_fields"], a["real_fields"])
+        if "resampled" in a:
+            np.testing.assert_array_equal(b["resampled"], a["resampled"])
+    for m in models:
+        m.close()
