@@ -1,6 +1,9 @@
 // smc_device.cuh -- device building blocks of the particle-SMC engine:
-// counter-based random numbers, the variate recipes used by SAMPLE, and
-// warp/block FP64 reductions used by the normaliser and the scan.
+// counter-based random numbers, the variate recipes used by SAMPLE, the
+// table-driven and integer-pipe logarithms and exponentials they and the
+// normaliser use (GB300 runs FP64 at 2 DFMA per clock per SM, so the hot path
+// does what it can on the integer pipes), and the integer warp / block
+// reductions and scans of the normaliser and the search.
 //
 // Random numbers (Section 3.3 gives each particle its own seed; here the
 // generator is counter-based so no per-particle RNG state exists at all):

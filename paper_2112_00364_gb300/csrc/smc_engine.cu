@@ -5,28 +5,31 @@
 // one segment; it is one launch of wave_kernel per block-size bucket.  Each
 // CTA of a wave owns one tile (a run and a contiguous slice of its particles,
 // one particle per thread):
-//   prologue  (segment k > 0) systematic-resampling search for each particle's
-//             ancestor a_i = min{ j : q_j > i + u } over the previous segment's
-//             weights, then the particle duplication of Section 3.3: the
-//             ancestor's SoA fields are read straight into registers (the gather
-//             is fused into the load); a PSTATE stack is copied only up to its
-//             stack pointer;
+//   prologue  (segment k > 0) the previous segment's tiles combined into exact
+//             integer offsets (in every CTA, or read from the run's last CTA of
+//             the previous wave, smc_combine.cuh), log Z increment and the ESS
+//             decision; when resampling, the systematic search for each
+//             particle's ancestor a_i = min{ j : P_j > z_i } with z_i = (i + u)
+//             S / N in 64.64 fixed point, then the particle duplication of
+//             Section 3.3: the ancestor's SoA fields are read straight into
+//             registers (the gather is fused into the load); a PSTATE stack is
+//             copied only up to its stack pointer;
 //   segment   blocks run until the next checkpoint with per-warp PC-sorted
 //             dispatch (smc_models.cuh); draws from Philox counters;
 //   epilogue  per warp, as soon as its particles are done: the warp's max M_w,
-//             its power-of-two reference k_w = ceil(M_w / ln 2), the weights
-//             e_j = exp(logw_j - k_w ln 2) (FP64; in FP32 mode the difference is
-//             formed in FP64 and its exponential in FP32) rounded to integers
-//             e_j 2^54; after the tile barrier the tile reference k_t = max k_w,
-//             each weight shifted exactly to it, and the tile's integer running
-//             sum E_j (kept for the next segment's search) and total s_t; the
-//             run's last CTA to finish combines the run's tiles: k = max k_t,
-//             c_t = 2^(k_t - k) (exact, no exponential), non-decreasing offsets
-//             O_t of c_t s_t, S = total, log Z += k ln 2 + (log S - log N), the
-//             resampling uniform u_k and r = N / S.
-// The running sum the next search uses is P_j = O_t + c_t E_j 2^-54 and its
-// scaled boundary q_j = P_j r.  A run stops after the segment in which every
-// particle reached b_stop (no resampling after it); its later CTAs return at once.
+//             its power-of-two reference k_w = ceil(M_w / ln 2), and each weight
+//             round(exp(logw_j - k_w ln 2) 2^54) on the integer pipes (an FP32
+//             log-weight is exact as a double, so both precisions share it);
+//             after the tile barrier the tile reference k_t = max k_w, each
+//             weight shifted exactly to it, the tile's integer running sums E_j
+//             (the next segment's search keys) and its record {total, k_t,
+//             alive}; for runs combined in one CTA the run's last CTA to finish
+//             forms the offsets for the next wave.
+// The combine brings every tile total to the run's reference 2^k_max and a
+// common unit with a coarsening G that keeps S in [2^61, 2^62]: the offsets O_t
+// and S are exact integers, so the result does not depend on the order of the
+// sums.  A run stops after the segment in which every particle reached b_stop
+// (no resampling after it); its later CTAs return at once.
 //
 // A run's tile size depends only on its N (tile = ceil(N / 456) clamped to
 // 32..256, 456 = 152 SMs x 3 CTAs), so a run gives the same bits alone and in a
