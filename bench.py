@@ -33,6 +33,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -84,10 +85,10 @@ RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, 
 # traffic holds only for the kernel sources with the recorded digest.
 NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=102.2, fp64_flop_per_pstep=12.55,
                       bytes_per_launch=3.35e6, fp64_pipe_elapsed=0.170,
-                      src_digest="37b190d5171775f5"),
+                      src_digest="5a02dbfa4e28ad32"),
        "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=117.2, fp64_flop_per_pstep=196.6,
                           bytes_per_launch=5.79e6, fp64_pipe_elapsed=0.397,
-                          src_digest="37b190d5171775f5")}
+                          src_digest="5a02dbfa4e28ad32")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
@@ -104,13 +105,24 @@ RS_SOURCES = ("smc_prims.cu", "smc_device.cuh", "smc_combine.cuh")
 # DRAM traffic of one smc_resample call at 2^24 (the three kernels' dram__bytes
 # read + write in one ncu capture, profiles folder), valid for the sources with
 # the recorded digest.
-RS_NCU = dict(bytes_per_call=3.533e8, src_digest="6e9fe68cbff24990")
+RS_NCU = dict(bytes_per_call=3.533e8, src_digest="f95f11cc25487726")
 
 
-def src_digest(sources=KERNEL_SOURCES) -> str:
+def code_text(src: str) -> str:
+    """A CUDA/C++ source without its comments and blank space, so that the digest
+    changes with the code and not with its documentation (string literals in
+    these files hold no comment markers)."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
+def src_digest(sources=KERNEL_SOURCES, read=None) -> str:
+    """Digest of the code (comments and blank space stripped) of the sources."""
+    read = read or (lambda name: (ROOT / "paper_2112_00364_gb300" / "csrc" / name).read_text())
     h = hashlib.sha256()
     for name in sources:
-        h.update((ROOT / "paper_2112_00364_gb300" / "csrc" / name).read_bytes())
+        h.update(code_text(read(name)).encode())
     return h.hexdigest()[:16]
 
 
