@@ -127,3 +127,14 @@ def test_rateshift_full_config_properties():
     a = r["ancestors"][0]
     assert a.min() >= 0 and a.max() < (1 << 20) and np.all(np.diff(a) >= 0)
     assert r["n_overflow"] == 0 and r["n_limit"] == 0
+
+
+def test_rateshift_benchmark_tree_fp32_follows_oracle():
+    """The benchmark's rate-shift tree (256 tips, 511 checkpoints, sigma = 0.3)
+    in FP32 at N = 2^14 against the FP32 oracle in follow mode, to FP32 rounding
+    (the full N = 2^20 is checked by its invariants above)."""
+    tree = inputs.yule_tree(256, seed=3)
+    g, o = run_pair("rateshift", 1 << 14, 1, precision="fp32", tree=tree, sigma=0.3,
+                    lam_stack_cap=tree.max_pending_right() + 1)
+    assert g["n_segments"] == 511
+    _check_fp32(g, o)

@@ -83,3 +83,12 @@ def test_seir_full_size_invariants():
     assert f[1:].min() >= 0
     th = r["real_fields"]
     assert np.all((th > 0) & (th < 1))
+
+
+def test_seir_benchmark_workload_parity():
+    """The benchmark's SEIR workload in full (N = 2^16, 182 days of synthetic
+    weekly reports, FP64) against the oracle in follow mode, element by element."""
+    y = inputs.seir_observations(182, seed=7)
+    g, o = run_pair("seir", 1 << 16, 1, obs=y)
+    assert_parity_fp64(g, o)
+    assert g["n_segments"] == 182
