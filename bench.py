@@ -84,11 +84,11 @@ RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, 
 # rate for the delayed-sampling CRBD (FP64 pipe busy 36-44% of a launch).  The
 # traffic holds only for the kernel sources with the recorded digest.
 NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=102.2, fp64_flop_per_pstep=12.55,
-                      bytes_per_launch=3.35e6, fp64_pipe_elapsed=0.170,
-                      src_digest="5a02dbfa4e28ad32"),
-       "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=117.2, fp64_flop_per_pstep=196.6,
-                          bytes_per_launch=5.79e6, fp64_pipe_elapsed=0.397,
-                          src_digest="5a02dbfa4e28ad32")}
+                      bytes_per_launch=3.35e6, fp64_pipe_elapsed=0.171,
+                      src_digest="11fe17bcc318e458"),
+       "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=114.9, fp64_flop_per_pstep=170.6,
+                          bytes_per_launch=5.76e6, fp64_pipe_elapsed=0.382,
+                          src_digest="11fe17bcc318e458")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
@@ -105,7 +105,7 @@ RS_SOURCES = ("smc_prims.cu", "smc_device.cuh", "smc_combine.cuh")
 # DRAM traffic of one smc_resample call at 2^24 (the three kernels' dram__bytes
 # read + write in one ncu capture, profiles folder), valid for the sources with
 # the recorded digest.
-RS_NCU = dict(bytes_per_call=3.533e8, src_digest="f95f11cc25487726")
+RS_NCU = dict(bytes_per_call=3.537e8, src_digest="4b4fa07df8b86421")
 
 
 def code_text(src: str) -> str:

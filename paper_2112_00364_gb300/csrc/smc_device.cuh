@@ -762,17 +762,19 @@ __device__ __forceinline__ R lomax(Stream& s, R alpha, R beta) {
 // lambda' = Gamma(alpha, 1) / beta (alpha >= 1), then Poisson(lambda' tau).
 template <typename R>
 __device__ __noinline__ int neg_binomial(Stream& s, R alpha, R beta, R tau) {
-  const R mean = alpha * tau / beta;
+  const R r = tau / beta;  // one division for the mean and P(0)
+  const R mean = alpha * r;
   if (mean < (R)10.0) {
     const R u = uniform01<R>(s);
-    const R q = tau / (beta + tau);
-    const R l0 = alpha * m_log1p(tau / beta);
+    const R l0 = alpha * m_log1p(r);
     R pk;
     if constexpr (sizeof(R) == 8)
       pk = exp_neg_int(l0, s.tab);  // integer pipes
     else
       pk = expf(-l0);
     R acc = pk;
+    if (!gt_nonneg(u, acc)) return 0;  // n = 0: q is not needed
+    const R q = tau / (beta + tau);
     int k = 0;
     while (gt_nonneg(u, acc) && k < 1000) {
       pk = pk * div_shape(q * (alpha + (R)k), (R)(k + 1), s.tab);
