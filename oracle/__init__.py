@@ -28,7 +28,8 @@ OK, EINVAL, ENOMEM, EDEGENERATE, ESTEPLIMIT = 0, -1, -2, -4, -5
 
 DIST = {"uniform": 0, "normal": 1, "exponential": 2, "gamma1": 3, "uniform_ab": 4,
         "bernoulli": 5, "poisson": 6, "lognormal": 7, "binomial": 8, "beta": 9, "gamma": 10,
-        "neg_binomial": 11, "lomax": 12}
+        "neg_binomial": 11, "lomax": 12,
+        "neg_binomial_rate": 13}
 
 _i32p = C.POINTER(C.c_int32)
 _f64p = C.POINTER(C.c_double)

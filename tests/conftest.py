@@ -10,6 +10,12 @@ if str(ROOT) not in sys.path:
 HERE = Path(__file__).resolve().parent
 if str(HERE) not in sys.path:
     sys.path.insert(0, str(HERE))
+# A directory holding a modified copy of the oracle package, imported instead
+# of the repository's own: the planted-mistake test (test_oracle_mutants.py)
+# runs the oracle's pins against such copies in child processes.
+_ORACLE_UNDER_TEST = os.environ.get("SMC_ORACLE_UNDER_TEST")
+if _ORACLE_UNDER_TEST:
+    sys.path.insert(0, _ORACLE_UNDER_TEST)
 
 
 def pytest_configure(config):
@@ -18,6 +24,8 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
+    if not any("gpu" in item.keywords for item in items):
+        return
     try:
         import torch
 

@@ -12,10 +12,16 @@ rates' Gamma priors integrated out) and its two predictive samplers.
     8-tip and on a 2-tip tree;
   * integrating the rates out lowers the variance of log Zhat against the
     plain model at the same N;
+  * the same with a general rate (exposure 1): chi-square against nbinom with
+    p = beta / (beta + 1), in both ranges;
+  * the quadrature check also with rho = 1/2 and with other prior scales;
   * posterior bookkeeping: every finished particle's shapes are integers,
     a_lambda >= 1 + the internal non-root nodes, and b_lambda - 1/s_lambda and
     b_mu - 1/s_mu both count every observed branch length once (>= the tree
-    length, equal for a particle that drew no hidden lineage).
+    length, equal for a particle that drew no hidden lineage); with rho = 1
+    a_mu - 1 = a_lambda - 1 - (internal non-root nodes) (one hidden lineage per
+    hidden speciation) and b_mu - 1/s_mu = b_lambda - 1/s_lambda (every hidden
+    lifetime ended before the present and counts once in each).
 """
 import math
 
@@ -54,6 +60,17 @@ def test_negative_binomial_exact_pmf(alpha, ratio, prec):
     assert _chi2_pvalue(x, stats.nbinom.pmf(support, alpha, p), support) > 1e-3
 
 
+@pytest.mark.parametrize("alpha,beta", [(3.0, 2.0), (1.0, 0.25), (30.0, 0.5), (2.0, 0.1)])
+def test_negative_binomial_rate_exact_pmf(alpha, beta):
+    # exposure 1, rate beta: p = beta / (beta + 1), mean alpha / beta (inversion
+    # below 10, the Gamma-Poisson mixture from 10 up)
+    x = oracle.sample("neg_binomial_rate", 200_000, alpha, beta, seed=int(alpha * 3 + beta * 11))
+    assert np.all(x == np.round(x)) and x.min() >= 0
+    support = np.arange(int(x.max()) + 1)
+    pmf = stats.nbinom.pmf(support, alpha, beta / (beta + 1.0))
+    assert _chi2_pvalue(x, pmf, support) > 1e-3
+
+
 @pytest.mark.parametrize("alpha,beta", [(1.0, 2.0), (1.0, 0.3), (4.0, 1.5), (30.0, 12.0)])
 def test_lomax_ks(alpha, beta):
     x = oracle.sample("lomax", 100_000, alpha, beta, seed=int(alpha + 13 * beta))
@@ -65,11 +82,17 @@ def _many(kind, N, seeds, **params):
     return np.array([oracle.smc_run(kind, N, seed=s, **params)["log_z"] for s in seeds])
 
 
-@pytest.mark.parametrize("tips,tree_seed,N", [(8, 4, 4096), (2, 0, 512)])
-def test_crbd_ds_unbiased_vs_quadrature(tips, tree_seed, N):
+# Zhat / Z is right-skewed, so 100 seeds can understate its standard error;
+# the rho = 1/2 case with internal nodes takes 400
+@pytest.mark.parametrize("tips,tree_seed,N,rho,ls,ms,n_seeds", [(8, 4, 4096, 1.0, 1.0, 0.5, 100),
+                                                             (2, 0, 512, 1.0, 1.0, 0.5, 100),
+                                                             (2, 0, 512, 0.5, 2.0, 0.25, 100),
+                                                             (4, 1, 1024, 0.5, 1.0, 0.5, 400)])
+def test_crbd_ds_unbiased_vs_quadrature(tips, tree_seed, N, rho, ls, ms, n_seeds):
     tree = inputs.two_tip_tree(1.0) if tips == 2 else inputs.yule_tree(tips, seed=tree_seed)
-    lz = _many("crbd_ds", N, range(1, 101), tree=tree)
-    ok, mean, se = cf.unbiased_check(lz, cf.crbd_marginal_log_z(tree))
+    lz = _many("crbd_ds", N, range(1, n_seeds + 1), tree=tree, rho=rho, lambda_scale=ls,
+               mu_scale=ms)
+    ok, mean, se = cf.unbiased_check(lz, cf.crbd_marginal_log_z(tree, rho, ls, ms))
     assert ok, (mean, se)
 
 
@@ -80,9 +103,9 @@ def test_crbd_ds_lowers_log_z_variance():
     assert ds.var(ddof=1) < plain.var(ddof=1), (ds.var(ddof=1), plain.var(ddof=1))
 
 
-def test_crbd_ds_posterior_bookkeeping():
+@pytest.mark.parametrize("ls,ms", [(1.0, 0.5), (2.0, 0.25)])
+def test_crbd_ds_posterior_bookkeeping(ls, ms):
     tree = inputs.yule_tree(16, seed=5)
-    ls, ms = 1.0, 0.5
     r = oracle.smc_run("crbd_ds", 4096, seed=3, tree=tree, lambda_scale=ls, mu_scale=ms)
     assert r["status"] == 0 and np.all(r["int_fields"][0] == -1)
     a_l, b_l, a_m, b_m = r["real_fields"]
@@ -106,6 +129,14 @@ def test_crbd_ds_posterior_bookkeeping():
     np.testing.assert_allclose(b_l[none], 1 / ls + length, rtol=1e-12)
     np.testing.assert_allclose(b_m[none], 1 / ms + length, rtol=1e-12)
     assert np.all(a_l[none] == 1 + n_internal_nonroot)
+    # every hidden speciation event starts one hidden lineage, whose lifetime
+    # is drawn once (a_mu += 1); with rho = 1 a surviving particle's hidden
+    # lineages all ended before the present, so each added the same lifetime
+    # to b_mu and, as its exposure, to b_lambda
+    some = alive & (a_m > 1.0)
+    assert some.any()
+    np.testing.assert_array_equal(a_m[alive] - 1, a_l[alive] - 1 - n_internal_nonroot)
+    np.testing.assert_allclose(b_m[alive] - 1 / ms, b_l[alive] - 1 / ls, rtol=1e-12)
 
 
 def test_crbd_ds_rejects_fixed_rates():

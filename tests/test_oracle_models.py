@@ -60,11 +60,12 @@ def test_lg_single_particle_is_importance_sampling():
     assert ok, (mean, se)
 
 
-def test_crbd_fixed_rates_unbiased():
+@pytest.mark.parametrize("rho", [1.0, 0.5])
+def test_crbd_fixed_rates_unbiased(rho):
     tree = inputs.yule_tree(16, seed=2)
     lam, mu = 2.5, 0.8
-    lz = _many("crbd", 2048, range(1, 101), tree=tree, rates=(lam, mu))
-    ok, mean, se = cf.unbiased_check(lz, cf.crbd_log_z(tree, lam, mu))
+    lz = _many("crbd", 2048, range(1, 101), tree=tree, rates=(lam, mu), rho=rho)
+    ok, mean, se = cf.unbiased_check(lz, cf.crbd_log_z(tree, lam, mu, rho))
     assert ok, (mean, se)
 
 

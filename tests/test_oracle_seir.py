@@ -12,7 +12,20 @@
     BetaBinomial(d | e, a, b) 1{y <= k + d} / (k + d + 1) with hDelta's Beta(a, b)
     prior; mean Zhat / Z within 3 standard errors of 1 in both;
   * invariants of a full run: the human compartments sum to 7,370, every count
-    is non-negative, every particle finishes.
+    is non-negative, every particle finishes;
+  * the one-day transition law, particle by particle: two runs that never
+    resample (ESS threshold below 1/N) end one day apart on the same draws, so
+    every particle's state before and after day t is known.  Given the state
+    before, each flow is a sum of independent binomials by binomial thinning
+    (new exposed humans ~ Bin(hS, (1 - e^{-mI/hN}) hLambda), new infectious ~
+    Bin(hE, hDelta), recoveries ~ Bin(hI, hGamma); mosquitoes: susceptible ~
+    Bin(mS, (1 - pm) 6/7) + Bin(mN, 1/7) with pm = (1 - e^{-hI/hN}) mLambda,
+    exposed ~ Bin(mE, (1 - mDelta) 6/7) + Bin(mS, pm 6/7), infectious ~
+    Bin(mI, 6/7) + Bin(mE, mDelta 6/7)); the sums over particles of the
+    standardised residuals and of their squares must match the exact first,
+    second and fourth moments.  The unreported cases and the log-weight change
+    exactly as the condition step says: z += new infectious, and on a report
+    day the weight gains log Binomial(y | z, rho) (scipy) and z restarts at 0.
 """
 import numpy as np
 import pytest
@@ -112,3 +125,77 @@ def test_full_run_invariants():
     assert f[1:].min() >= 0
     th = r["real_fields"]
     assert np.all((th > 0) & (th < 1))
+
+
+def _binom_moments(n, p):
+    """mean, variance and fourth central moment of Binomial(n, p), elementwise"""
+    n = np.asarray(n, dtype=float)
+    p = np.asarray(p, dtype=float)
+    v = n * p * (1.0 - p)
+    return n * p, v, v * (1.0 + 3.0 * (n - 2.0) * p * (1.0 - p))
+
+
+def _sum_moments(*parts):
+    """moments of a sum of independent variables from their (mean, var, mu4)"""
+    m = sum(q[0] for q in parts)
+    v = sum(q[1] for q in parts)
+    m4 = sum(q[2] for q in parts)
+    for i in range(len(parts)):
+        for j in range(i + 1, len(parts)):
+            m4 = m4 + 6.0 * parts[i][1] * parts[j][1]
+    return m, v, m4
+
+
+def _check_flow(name, x, moments, n_sd=6.0):
+    mean, var, mu4 = moments
+    r = np.asarray(x, dtype=float) - mean
+    fixed = var <= 0
+    assert np.all(r[fixed] == 0), name  # a flow with no randomness is exact
+    z1 = r.sum() / np.sqrt(var.sum())
+    z2 = ((r * r).sum() - var.sum()) / np.sqrt(np.sum(mu4 - var * var))
+    assert abs(z1) < n_sd and abs(z2) < n_sd, (name, z1, z2)
+
+
+@pytest.mark.parametrize("day", [19, 20])  # day 20 carries a weekly report
+def test_one_day_transition_law(day):
+    y = inputs.seir_observations(day + 1, seed=7)
+    assert (y[day] == -1) == (day == 19)
+    N = 20_000
+    before = oracle.smc_run("seir", N, 11, obs=y[:day], ess_threshold=1e-9)
+    after = oracle.smc_run("seir", N, 11, obs=y[:day + 1], ess_threshold=1e-9)
+    assert before["n_resamples"] == 0 and after["n_resamples"] == 0
+    th = before["real_fields"]
+    np.testing.assert_array_equal(th, after["real_fields"])  # drawn once, on day 0
+    hS, hE, hI, hR, mS, mE, mI, mR, z = before["int_fields"][1:].astype(np.int64)
+    hS1, hE1, hI1, hR1, mS1, mE1, mI1, mR1, z1 = after["int_fields"][1:].astype(np.int64)
+    hN = hS + hE + hI + hR
+    assert np.all(hS1 + hE1 + hI1 + hR1 == hN)
+    assert np.all(mR == 0) and np.all(mR1 == 0)  # mosquitoes never recover
+    dE = hS - hS1
+    dR = hR1 - hR
+    dI = hI1 - hI + dR
+    s = 6.0 / 7.0
+    _check_flow("new exposed humans", dE,
+                _binom_moments(hS, (1.0 - np.exp(-mI / hN)) * th[0]))
+    _check_flow("new infectious humans", dI, _binom_moments(hE, th[1]))
+    _check_flow("recovered humans", dR, _binom_moments(hI, th[2]))
+    pm = (1.0 - np.exp(-hI / hN)) * th[3]
+    mN = mS + mE + mI + mR
+    _check_flow("susceptible mosquitoes", mS1,
+                _sum_moments(_binom_moments(mS, (1.0 - pm) * s), _binom_moments(mN, 1.0 / 7.0)))
+    _check_flow("exposed mosquitoes", mE1,
+                _sum_moments(_binom_moments(mE, (1.0 - th[4]) * s), _binom_moments(mS, pm * s)))
+    _check_flow("infectious mosquitoes", mI1,
+                _sum_moments(_binom_moments(mI, s), _binom_moments(mE, th[4] * s)))
+    if y[day] == -1:
+        np.testing.assert_array_equal(z1, z + dI)
+        np.testing.assert_array_equal(after["final_logw"], before["final_logw"])
+    else:
+        assert np.all(z1 == 0)
+        inc = stats.binom.logpmf(int(y[day]), z + dI, th[5])
+        lw0, lw1 = before["final_logw"], after["final_logw"]
+        live = np.isfinite(lw0)
+        assert live.sum() > N // 10
+        np.testing.assert_array_equal(np.isfinite(lw1[live]), np.isfinite(inc[live]))
+        ok = live & np.isfinite(inc)
+        np.testing.assert_allclose(lw1[ok] - lw0[ok], inc[ok], rtol=1e-9, atol=1e-9)
