@@ -86,6 +86,29 @@ def crbd_log_z_mu0(tree, lam) -> float:
     return crbd_corr(tree.n_tips) + (tree.n_tips - 2) * math.log(lam) - lam * L
 
 
+def crbd_log_z_depth1(tree, lam, mu) -> float:
+    """rho = 1 and a hidden-lineage depth cap of 1: a lineage started on an
+    observed branch may not itself speciate (its first event would be a call at
+    depth 2, which kills the particle), so it must die before the present with
+    no event: q(t) = int_0^t mu e^{-(lam + mu) s} ds for a lineage born t before
+    the present.  With Poisson(lam dt) events uniform on a branch [stop, start]
+    each weighted 2 q(t), the branch factor is
+    e^{-mu dt} exp(-lam dt + 2 lam int_stop^start q(t) dt)."""
+    r = lam + mu
+    tot = crbd_corr(tree.n_tips)
+    for v in range(tree.n_nodes):
+        p = tree.parent[v]
+        if p < 0:
+            continue
+        start, stop = float(tree.age[p]), float(tree.age[v])
+        dt = start - stop
+        int_q = mu / r * (dt - (math.exp(-r * stop) - math.exp(-r * start)) / r)
+        tot += -mu * dt - lam * dt + 2.0 * lam * int_q
+        if tree.left[v] >= 0:
+            tot += math.log(lam)
+    return tot
+
+
 def extinction_rk4(lam, mu, rho, t_lo, t_hi, steps=4000):
     """E(t) = P(a lineage alive at age t leaves no sampled descendant):
     dE/dt = mu - (lam + mu) E + lam E^2, E(0) = 1 - rho, integrated by RK4

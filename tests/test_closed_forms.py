@@ -1,7 +1,8 @@
 """The closed forms that pin the oracle, checked against independent routes
 (CPU only): brute-force numerical integration for the Kalman likelihood, an
-RK4 + Poisson-sum computation for the birth-death branch factor, and the
-mu = 0 special case."""
+RK4 + Poisson-sum computation for the birth-death branch factor, the
+mu = 0 special case, and a direct simulation for the depth-capped branch
+factor."""
 import math
 
 import numpy as np
@@ -49,6 +50,33 @@ def test_mu_zero_special_case():
     # the two-tip instance: Z = exp(-2 lam t_root)
     t2 = inputs.two_tip_tree(0.8)
     assert abs(cf.crbd_log_z_mu0(t2, 1.7) - (-2 * 1.7 * 0.8)) < 1e-12
+
+
+def test_depth_one_branch_factor_vs_simulation():
+    """crbd_log_z_depth1's branch factor against a direct simulation of the
+    hidden events on one branch with numpy's generator: Poisson(lam dt) events
+    uniform on the branch, each starting a lineage with an Exp(mu) lifetime that
+    must end before the present and hold no Poisson(lam x) event of its own."""
+    lam, mu, start, stop = 2.0, 1.3, 0.9, 0.35
+    rng = np.random.Generator(np.random.PCG64(17))
+    M = 400_000
+    n = rng.poisson(lam * (start - stop), size=M)
+    fac = np.exp(-mu * (start - stop)) * np.ones(M)
+    for k in range(1, int(n.max()) + 1):
+        sel = n >= k
+        t = rng.uniform(stop, start, size=sel.sum())
+        x = rng.exponential(1.0 / mu, size=sel.sum())
+        ok = (x < t) & (rng.poisson(lam * np.minimum(x, t)) == 0)
+        fac[sel] *= np.where(ok, 2.0, 0.0)
+    r = lam + mu
+    int_q = mu / r * ((start - stop) - (math.exp(-r * stop) - math.exp(-r * start)) / r)
+    exact = math.exp(-(lam + mu) * (start - stop) + 2 * lam * int_q)
+    assert abs(fac.mean() - exact) < 4 * fac.std() / math.sqrt(M)
+    # the two-tip tree (root age `start`): corr + two branches from the root to 0
+    tree = inputs.two_tip_tree(start)
+    int_q0 = mu / r * (start - (1.0 - math.exp(-r * start)) / r)
+    lz = cf.crbd_corr(2) + 2 * (-(lam + mu) * start + 2 * lam * int_q0)
+    assert abs(cf.crbd_log_z_depth1(tree, lam, mu) - lz) < 1e-12
 
 
 def test_lambda_equals_mu_is_continuous():

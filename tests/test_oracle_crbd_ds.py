@@ -108,6 +108,9 @@ def test_crbd_ds_posterior_bookkeeping(ls, ms):
     tree = inputs.yule_tree(16, seed=5)
     r = oracle.smc_run("crbd_ds", 4096, seed=3, tree=tree, lambda_scale=ls, mu_scale=ms)
     assert r["status"] == 0 and np.all(r["int_fields"][0] == -1)
+    # at these rates no hidden recursion comes near the depth cap (64) or the
+    # call limit (65,536 calls per branch)
+    assert r["n_overflow"] == 0 and r["n_limit"] == 0
     a_l, b_l, a_m, b_m = r["real_fields"]
     par = np.asarray(tree.parent)
     age = np.asarray(tree.age)

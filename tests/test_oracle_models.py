@@ -175,6 +175,17 @@ def test_ancestor_follow_mode_adopts():
     np.testing.assert_array_equal(c["ancestors"], fake)
 
 
+def test_depth_cap_one_closed_form():
+    # with depth_cap = 1 a hidden lineage may start on an observed branch but
+    # not speciate itself: Z has the closed form of closed_forms.crbd_log_z_depth1
+    tree = inputs.yule_tree(8, seed=8)
+    lam, mu = 2.0, 1.0
+    lz = _many("crbd", 2048, range(1, 101), tree=tree, rates=(lam, mu), depth_cap=1)
+    ok, mean, se = cf.unbiased_check(lz, cf.crbd_log_z_depth1(tree, lam, mu))
+    assert ok, (mean, se)
+
+
 def test_step_limit():
     r = oracle.smc_run("geometric", 256, seed=1, max_segments=2)
     assert r["status"] == oracle.ESTEPLIMIT
+    assert r["n_segments"] == 2  # the limit counts segments run

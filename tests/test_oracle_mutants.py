@@ -33,6 +33,12 @@ MUTANTS = [
     # the key schedule bumps by the wrong Weyl constant
     ("philox_round_key_word", C_SRC, "c0 = hi1 ^ c1 ^ k0;", "c0 = hi1 ^ c1 ^ k1;", 0),
     ("philox_key_bump", C_SRC, "k1 += PHILOX_W1;", "k1 += PHILOX_W0;", 0),
+    ("philox_multiplied_word", C_SRC, "uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;",
+     "uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c3;", 0),
+    ("key_ignores_run_id", C_SRC, "key[1] = (uint32_t)(seed >> 32) ^ run_id;",
+     "key[1] = (uint32_t)(seed >> 32);", 0),
+    ("fp32_uniform_bits", C_SRC, "return (float)((w[0] >> 8) | 1u) * 0x1p-24f; }",
+     "return (float)((w[0] >> 9) | 1u) * 0x1p-24f; }", 0),
     # variate recipes
     ("box_muller_angle_from_u1", P_SRC, "return rad * COSR(TWO_PIR * u2);",
      "return rad * COSR(TWO_PIR * u1);", 0),
@@ -42,6 +48,8 @@ MUTANTS = [
     ("gamma1_scale_as_rate", P_SRC, "return theta * -LOGR(u);", "return -LOGR(u) / theta;", 0),
     ("uniform_ab_offset", P_SRC, "return FMAR(hi - lo, u, lo);", "return FMAR(hi - lo, u, hi);", 0),
     ("bernoulli_flipped", P_SRC, "return u < p;", "return u > p;", 0),
+    ("lognormal_shift_not_scale", P_SRC, "return EXPR(sigma * SFX(normal01)(s));",
+     "return EXPR(sigma + SFX(normal01)(s));", 0),
     ("poisson_inversion_term", P_SRC, "p = p * mean / (R)k;", "p = p * mean / (R)(k + 1);", 0),
     ("poisson_ptrs_log_factorial", P_SRC, "- LGAMMAR(kr + (R)1.0))", "- LGAMMAR(kr))", 0),
     ("poisson_ptrs_shift", P_SRC, "U + mean + (R)0.43);", "U + mean + (R)1.43);", 0),
@@ -72,6 +80,9 @@ MUTANTS = [
      "*incr = mx + log(s);", 0),
     ("systematic_drops_offset_u", C_SRC, "double y = (double)i + u;", "double y = (double)i;", 0),
     ("systematic_scale", C_SRC, "double r = (double)N / S;", "double r = 1.0 / S;", 0),
+    ("normaliser_max_flipped", C_SRC, "if (lw[i] > mx) mx = lw[i];", "if (lw[i] < mx) mx = lw[i];", 0),
+    ("step_limit_off_by_one", P_SRC, "const int at_limit = !all_stop && k + 1 >= c->max_segments;",
+     "const int at_limit = !all_stop && k >= c->max_segments;", 0),
     ("ess_not_squared", C_SRC, "return (S * S) / q;", "return S / q;", 0),
     ("ess_comparison_flipped", P_SRC, "resample_now = ess < target;", "resample_now = ess > target;", 0),
     ("log_z_closes_every_checkpoint", P_SRC, "const int close = all_stop || at_limit || resample_now;",
@@ -87,6 +98,8 @@ MUTANTS = [
     ("lg_transition_sd", P_SRC, "FMAR((R)m->q_sd, z, (R)m->b)", "FMAR((R)m->r_sd, z, (R)m->b)", 0),
     ("lg_initial_sd", P_SRC, "P->x = FMAR((R)m->x0_sd, z0, (R)m->x0_mean);",
      "P->x = FMAR((R)m->q_sd, z0, (R)m->x0_mean);", 0),
+    ("lg_stops_a_step_early", P_SRC, "P->pc = ((int32_t)k + 1 == m->T) ? PC_STOP : 1;",
+     "P->pc = ((int32_t)k + 2 >= m->T) ? PC_STOP : 1;", 0),
     # CRBD (Listing 1)
     ("crbd_correction_tips", C_SRC, "mc->corr = (double)(tips - 1) * LN2_D - lnfact;",
      "mc->corr = (double)(tips) * LN2_D - lnfact;", 0),
@@ -101,9 +114,22 @@ MUTANTS = [
     ("crbd_hidden_count_length", P_SRC, "int32_t n = SFX(poisson)(&c->s, c->lam * bl);",
      "int32_t n = SFX(poisson)(&c->s, c->lam * t);", 0),
     ("crbd_hidden_event_window", P_SRC, "R lo = t - bl;", "R lo = (R)0.0;", 0),
+    ("crbd_skips_last_node", P_SRC, "P->pc = ((int32_t)k + 1 == m->n_nodes) ? PC_STOP : 1;",
+     "P->pc = ((int32_t)k + 2 >= m->n_nodes) ? PC_STOP : 1;", 0),
+    ("crbd_lambda_prior_scale", P_SRC, "P->lam = SFX(gamma1)(&s, (R)m->lambda_scale);",
+     "P->lam = SFX(gamma1)(&s, (R)m->mu_scale);", 0),
+    ("crbd_hidden_detection_probability", P_SRC,
+     "if (SFX(bernoulli)(&c->s, (R)c->m->rho)) return 0;",
+     "if (SFX(bernoulli)(&c->s, (R)1.0 - (R)c->m->rho)) return 0;", 0),
+    ("crbd_depth_cap_off_by_one", P_SRC, "if (depth > c->m->depth_cap) {",
+     "if (depth >= c->m->depth_cap) {", 0),
     # clade-specific rate shifts
     ("rateshift_root_rate", P_SRC, "lam = lam_p * mult;", "lam = P->lam * mult;", 0),
     ("rateshift_left_child_rate", P_SRC, "lam_p = P->stack[P->sp - 1];", "lam_p = P->stack[0];", 0),
+    ("rateshift_pushes_root_rate", P_SRC, "P->stack[P->sp] = lam;", "P->stack[P->sp] = P->lam;", 0),
+    ("resampled_stack_short", P_SRC,
+     "for (int32_t i = 0; i < src->sp; i++) dst->stack[i] = src->stack[i];",
+     "for (int32_t i = 0; i + 1 < src->sp; i++) dst->stack[i] = src->stack[i];", 0),
     # delayed sampling (Section 6.3): missing conjugate updates, wrong predictives
     ("ds_branch_survival_update", P_SRC, "g[3] = g[3] + dt;", "", 0),
     ("ds_node_speciation_update", P_SRC, "g[0] = g[0] + (R)1.0;", "", 0),
@@ -122,6 +148,13 @@ MUTANTS = [
     ("ds_hidden_detection_test", P_SRC, "if (dur > t) {", "if (dur < t) {", 1),
     ("ds_branch_drops_ln2", P_SRC, "acc = acc + LN2R;", "acc = acc;", 1),
     ("ds_hidden_event_window", P_SRC, "R lo = t - bl;", "R lo = (R)0.0;", 1),
+    ("ds_tip_drops_rho", P_SRC, "lnp2 = LOGR((R)m->rho);", "lnp2 = (R)0.0;", 0),
+    ("ds_drops_correction", P_SRC, "P->logw = P->logw + (R)mc->corr;", "P->logw = P->logw;", 1),
+    ("ds_skips_last_node", P_SRC, "P->pc = ((int32_t)k + 1 == m->n_nodes) ? PC_STOP : 1;",
+     "P->pc = ((int32_t)k + 2 >= m->n_nodes) ? PC_STOP : 1;", 1),
+    ("ds_hidden_detection_probability", P_SRC,
+     "if (SFX(bernoulli)(&c->s, (R)c->m->rho)) return 0;",
+     "if (SFX(bernoulli)(&c->s, (R)1.0 - (R)c->m->rho)) return 0;", 1),
     # SEIR (Listing 2)
     ("seir_incubation_rate", P_SRC, "hDeltaI = SFX(binomial)(&s, hEP, th[1]);",
      "hDeltaI = SFX(binomial)(&s, hEP, th[2]);", 0),
@@ -140,31 +173,63 @@ MUTANTS = [
      "SFX(binomial_logpmf)(y, C[8], th[5]);", 0),
     ("seir_initial_infectious", P_SRC, "const int32_t hI = 1 + SFX(poisson)(&s, (R)5.0);",
      "const int32_t hI = SFX(poisson)(&s, (R)5.0);", 0),
+    ("seir_initial_exposed_mean", P_SRC, "const int32_t hE = SFX(poisson)(&s, (R)5.0);",
+     "const int32_t hE = SFX(poisson)(&s, (R)4.0);", 0),
+    ("seir_initial_susceptible", P_SRC, "C[0] = n - hE - hI - hR;", "C[0] = n - hE - hI;", 0),
+    ("seir_mosquitoes_e_not_10", P_SRC,
+     "C[4] = (int32_t)FLOORR((R)n * EXPR(u * (R)2.302585092994045684));",
+     "C[4] = (int32_t)FLOORR((R)n * EXPR(u));", 0),
+    ("seir_incubation_prior", P_SRC,
+     "th[1] = SFX(beta)(&s, (R)1.0 + (R)2.0 / (R)4.4, (R)3.0 - (R)2.0 / (R)4.4);",
+     "th[1] = SFX(beta)(&s, (R)1.0 + (R)2.0 / (R)4.4, (R)3.0 + (R)2.0 / (R)4.4);", 0),
+    ("seir_reporting_prior", P_SRC, "th[5] = SFX(beta)(&s, (R)1.0, (R)1.0);",
+     "th[5] = SFX(beta)(&s, (R)2.0, (R)1.0);", 0),
+    ("seir_day0_cases", P_SRC, "hDeltaI = hI;", "hDeltaI = 0;", 0),
+    ("seir_stops_a_day_early", P_SRC, "P->pc = ((int32_t)k + 1 == m->T) ? PC_STOP : 1;",
+     "P->pc = ((int32_t)k + 2 >= m->T) ? PC_STOP : 1;", 1),
     # weighted geometric program (Fig. 2a)
     ("geometric_weight_sign", P_SRC, "P->logw = P->logw + (R)m->geo_logw;",
      "P->logw = P->logw - (R)m->geo_logw;", 0),
+    ("geometric_count", P_SRC, "P->count += 1;", "P->count += 2;", 0),
 ]
 
 PIN_FILES = sorted(str(p) for p in HERE.glob("test_oracle_*.py") if p.name != Path(__file__).name)
 PIN_FILES.append(str(HERE / "test_closed_forms.py"))
 
-# The pins of a mutant's own area run first (only to reach the failure sooner:
-# every mutant still runs the whole pin suite until its first failure).
+# The pins of a mutant's own area run first, as "file" or "file::test" (only
+# to reach the failure sooner: every mutant still runs the whole pin suite
+# until its first failure).
+def _in(f: str, *tests: str) -> list[str]:
+    return [str(HERE / f) + ("::" + s if s else "") for s in (tests or ("",))]
+
+
 AREA_FIRST = [
-    (("philox_", "box_muller_", "exponential_", "gamma1_", "uniform_ab_", "bernoulli_", "poisson_"),
-     "test_oracle_rng.py"),
-    (("gamma_mt_", "beta_", "binomial_", "log_factorial_", "seir_"), "test_oracle_seir.py"),
-    (("lomax_", "neg_binomial_", "ds_"), "test_oracle_crbd_ds.py"),
-    (("log_z_increment_", "systematic_"), "test_oracle_resample.py"),
-    (("ess_", "log_z_closes_", "kept_weights_"), "test_oracle_ess.py"),
+    (("philox_", "box_muller_", "exponential_", "gamma1_", "uniform_ab_", "bernoulli_",
+      "poisson_", "key_", "fp32_uniform_", "lognormal_"), _in("test_oracle_rng.py")),
+    (("gamma_mt_", "beta_", "binomial_"), _in("test_oracle_seir.py")),
+    (("log_factorial_", "seir_"),
+     _in("test_oracle_seir.py", "test_day_zero_draws", "test_one_day_transition_law",
+         "test_full_run_invariants") + _in("test_oracle_seir.py")),
+    (("lomax_", "neg_binomial_"), _in("test_oracle_crbd_ds.py")),
+    (("ds_",), _in("test_oracle_crbd_ds.py", "test_crbd_ds_posterior_bookkeeping",
+                   "test_crbd_ds_unbiased_vs_quadrature") + _in("test_oracle_crbd_ds.py")),
+    (("log_z_increment_", "systematic_", "normaliser_"), _in("test_oracle_resample.py")),
+    (("ess_", "log_z_closes_", "kept_weights_"), _in("test_oracle_ess.py")),
+    (("lg_", "state_not_resampled"),
+     _in("test_oracle_models.py", "test_lg_unbiased_vs_kalman", "test_eq2_ssm_unbiased_vs_kalman")),
+    (("crbd_",), _in("test_oracle_models.py", "test_crbd_fixed_rates_unbiased",
+                     "test_depth_cap_one_closed_form", "test_crbd_priors_unbiased_vs_quadrature")),
+    (("rateshift_", "resampled_stack_"),
+     _in("test_oracle_models.py", "test_rateshift_sigma_zero_is_crbd",
+         "test_rateshift_fixed_multipliers_unbiased")),
+    (("geometric_", "step_limit_"),
+     _in("test_oracle_models.py", "test_geometric_z_equals_two_and_posterior", "test_step_limit")),
 ]
 
 
 def _pin_order(name: str) -> list[str]:
-    first = next((f for prefixes, f in AREA_FIRST if name.startswith(prefixes)),
-                 "test_oracle_models.py")
-    head = str(HERE / first)
-    return [head] + [f for f in PIN_FILES if f != head]
+    head = next((h for prefixes, h in AREA_FIRST if name.startswith(prefixes)), [])
+    return head + PIN_FILES
 
 
 def _apply(text: str, old: str, new: str, which: int) -> str:
@@ -189,8 +254,9 @@ def _copy_oracle(dst: Path, mutant=None) -> Path:
 
 def _run_pins(root: Path, files: list[str]) -> tuple[int, str]:
     env = dict(os.environ, SMC_ORACLE_UNDER_TEST=str(root), PYTHONDONTWRITEBYTECODE="1")
+    # --keep-duplicates keeps the area's tests in front of the files that hold them
     cmd = [sys.executable, "-m", "pytest", "-x", "-q", "-rf", "-m", "not gpu",
-           "-p", "no:cacheprovider", *files]
+           "-p", "no:cacheprovider", "--keep-duplicates", *files]
     try:
         r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     except subprocess.TimeoutExpired:
@@ -221,6 +287,10 @@ def outcomes(tmp_path_factory):
 def test_mutant_names_unique_and_sites_found():
     names = [m[0] for m in MUTANTS]
     assert len(names) == len(set(names))
+    for _, heads in AREA_FIRST:  # the ordering hints name existing tests
+        for h in heads:
+            f, _, test = h.partition("::")
+            assert Path(f).exists() and (not test or f"def {test}(" in Path(f).read_text()), h
     for _, fname, old, _, which in MUTANTS:
         text = (ORACLE / fname).read_text()
         assert text.count(old) > which, (fname, old)

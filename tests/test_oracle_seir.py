@@ -5,6 +5,9 @@
     the draw for 1 - p), and the degenerate cases;
   * Gamma(shape) (Marsaglia-Tsang) and Beta(a, b): Kolmogorov-Smirnov against
     scipy's distributions, for the shapes the model's priors use;
+  * day 0's draws: the parameters against their Beta priors (KS), the initial
+    human compartments (Poisson chi-square, uniform recovered count) and the
+    log-uniform mosquito population;
   * a one-day run (one report at day 0): Z = sum_k P(hI = k) 1{y <= k} / (k + 1),
     the reporting probability integrated out under its uniform prior;
   * a two-day run (no report at day 0, one at day 1): z = hI + d with
@@ -87,6 +90,36 @@ def _many(N, obs, seeds):
         assert r["status"] == 0
         out.append(r["log_z"])
     return np.array(out)
+
+
+def test_day_zero_draws():
+    """Day 0 of Listing 2: the six parameters from their Beta priors, hI - 1 and
+    hE ~ Poisson(5), hR uniform on {0, ..., n - hI - hE}, hS the rest,
+    floor(n 10^u) susceptible mosquitoes with u ~ U(-1, 2) and no others, the
+    day's new infectious cases z = hI; a day without a report leaves the weight
+    at 0."""
+    N = 20_000
+    r = oracle.smc_run("seir", N, 5, obs=np.array([-1.0]))
+    assert r["status"] == 0 and r["log_z"] == 0.0
+    assert np.all(r["final_logw"] == 0.0)
+    th = r["real_fields"]
+    priors = [(1.0, 1.0), (1 + 2 / 4.4, 3 - 2 / 4.4), (1 + 2 / 4.5, 3 - 2 / 4.5), (1.0, 1.0),
+              (1 + 2 / 6.5, 3 - 2 / 6.5), (1.0, 1.0)]
+    for k, (a, b) in enumerate(priors):
+        assert stats.kstest(th[k], stats.beta(a, b).cdf).pvalue > 1e-4, k
+    pc, hS, hE, hI, hR, mS, mE, mI, mR, z = r["int_fields"].astype(np.int64)
+    assert np.all(pc == -1)
+    for x in (hI - 1, hE):
+        support = np.arange(int(x.max()) + 1)
+        assert _chi2_pvalue(x, stats.poisson.pmf(support, 5.0), support) > 1e-4
+    np.testing.assert_array_equal(hS, N_HUMANS - hE - hI - hR)
+    assert np.all((hR >= 0) & (hR <= N_HUMANS - hI - hE))
+    assert stats.kstest((hR + 0.5) / (N_HUMANS - hI - hE + 1), "uniform").pvalue > 1e-4
+    # mS = floor(n 10^u): u lies within 1/(n/10) of log10(mS / n)
+    u_hat = np.log10((mS + 0.5) / N_HUMANS)
+    assert stats.kstest(u_hat, stats.uniform(-1.0, 3.0).cdf).pvalue > 1e-4
+    assert np.all(mE == 0) and np.all(mI == 0) and np.all(mR == 0)
+    np.testing.assert_array_equal(z, hI)
 
 
 def test_one_day_closed_form():
