@@ -84,6 +84,10 @@ typedef int32_t smc_status;
 #define SMC_MEM_DEVICE 1
 
 #define SMC_MAX_DEPTH 64 /* largest hidden-lineage recursion cap the CRBD blocks accept */
+/* Largest particle count of one run: ancestor indices are int32, and a run's
+   last tile, rounded up to whole CTAs of at most 256 particles, stays below
+   2^31.  smc_run and smc_run_batch return SMC_EINVAL above it. */
+#define SMC_MAX_PARTICLES ((((int64_t)1) << 31) - 257)
 
 typedef struct smc_model_s *smc_model_t;
 
@@ -115,7 +119,7 @@ typedef struct {
 
 /* Per-run configuration. */
 typedef struct {
-  int64_t n_particles;   /* N >= 1 */
+  int64_t n_particles;   /* 1 <= N <= SMC_MAX_PARTICLES */
   uint64_t seed;         /* Philox key = (seed_lo32, seed_hi32 XOR run_id) */
   uint32_t run_id;
   int32_t precision;     /* SMC_PREC_* */

@@ -26,6 +26,7 @@ PREC_FP64, PREC_FP32 = 0, 1
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32}
 MEM_HOST, MEM_DEVICE = 0, 1
 MAX_DEPTH = 64
+MAX_PARTICLES = (1 << 31) - 257  # SMC_MAX_PARTICLES
 DIST = {"uniform": 0, "normal": 1, "exponential": 2, "gamma1": 3, "uniform_ab": 4,
         "bernoulli": 5, "poisson": 6, "lognormal": 7, "binomial": 8, "beta": 9, "gamma": 10,
         "neg_binomial": 11, "lomax": 12}

@@ -25,7 +25,8 @@ from scipy import integrate, special, stats
 
 
 # ----------------------------- Kalman ---------------------------------
-def kalman_loglik(y, a=0.9, b=0.0, q_sd=1.0, r_sd=0.5, x0_mean=0.0, x0_sd=1.0) -> float:
+def kalman_filter(y, a=0.9, b=0.0, q_sd=1.0, r_sd=0.5, x0_mean=0.0, x0_sd=1.0):
+    """log p(y_1..T) and the mean and variance of p(x_T | y_1..T)."""
     m, P = x0_mean, x0_sd ** 2
     ll = 0.0
     for yt in y:
@@ -36,7 +37,11 @@ def kalman_loglik(y, a=0.9, b=0.0, q_sd=1.0, r_sd=0.5, x0_mean=0.0, x0_sd=1.0) -
         K = P / S
         m = m + K * (yt - m)
         P = (1.0 - K) * P
-    return float(ll)
+    return float(ll), float(m), float(P)
+
+
+def kalman_loglik(y, a=0.9, b=0.0, q_sd=1.0, r_sd=0.5, x0_mean=0.0, x0_sd=1.0) -> float:
+    return kalman_filter(y, a, b, q_sd, r_sd, x0_mean, x0_sd)[0]
 
 
 # ------------------------ birth-death closed form ----------------------

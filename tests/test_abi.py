@@ -72,3 +72,18 @@ def test_resample_argument_checks():
     assert L.smc_resample_workspace_bytes(1 << 20) > 0
     assert L.smc_gather(None, None, None, None, 10, 1, 8, None) == smc.EINVAL
     assert L.smc_sample(9, 0, 0.0, 0.0, 1, 0, 10, None, None, None) == smc.EINVAL
+
+
+def test_particle_limit_agrees_across_header_engine_and_binding():
+    header = (ROOT / "include" / "smc.h").read_text()
+    m = re.search(r"#define SMC_MAX_PARTICLES \(\(\(\(int64_t\)1\) << (\d+)\) - (\d+)\)", header)
+    assert m, "SMC_MAX_PARTICLES not found"
+    from_header = (1 << int(m.group(1))) - int(m.group(2))
+    engine = (ROOT / "paper_2112_00364_gb300" / "csrc" / "smc_engine.h").read_text()
+    e = re.search(r"kMaxParticles = \(int64_t\)(0x[0-9a-f]+) - (\d+);", engine)
+    assert e, "kMaxParticles not found"
+    from_engine = int(e.group(1), 16) - int(e.group(2))
+    assert from_header == from_engine == smc.MAX_PARTICLES
+    # the last tile of a maximal run, rounded up to a whole 256-particle CTA,
+    # still indexes below 2^31
+    assert -(-smc.MAX_PARTICLES // 256) * 256 + 255 < 2 ** 31

@@ -26,6 +26,27 @@ def test_kalman_matches_numerical_integration_T2():
     assert abs(cf.kalman_loglik(y, a=a, q_sd=q, r_sd=r, x0_sd=s0) - math.log(val)) < 1e-9
 
 
+def test_kalman_filter_moments_match_numerical_integration_T2():
+    """Mean and variance of p(x2 | y1, y2) by 2-D integration over (x1, x2) of
+    N(x1; 0, a^2 s0^2 + q^2) N(y1; x1, r) N(x2; a x1, q) N(y2; x2, r): the
+    trapezoid rule on a fine grid, spectrally accurate for this smooth,
+    Gaussian-decaying integrand."""
+    y = np.array([0.7, -0.4])
+    a, q, r, s0 = 0.9, 1.0, 0.5, 1.0
+    g = np.linspace(-12.0, 12.0, 2401)
+    h = g[1] - g[0]
+    x1, x2 = np.meshgrid(g, g, indexing="ij")
+    joint = (stats.norm.pdf(x1, 0, math.sqrt(a * a * s0 * s0 + q * q))
+             * stats.norm.pdf(y[0], x1, r) * stats.norm.pdf(x2, a * x1, q)
+             * stats.norm.pdf(y[1], x2, r))
+    mom = [float((x2 ** k * joint).sum() * h * h) for k in range(3)]
+    mean = mom[1] / mom[0]
+    var = mom[2] / mom[0] - mean * mean
+    ll, m, P = cf.kalman_filter(y, a=a, q_sd=q, r_sd=r, x0_sd=s0)
+    assert abs(ll - math.log(mom[0])) < 1e-8
+    assert abs(m - mean) < 1e-8 and abs(P - var) < 1e-8
+
+
 @pytest.mark.parametrize("lam,mu,rho", [(2.0, 0.5, 1.0), (1.0, 1.0, 1.0), (0.7, 1.9, 1.0),
                                         (3.0, 1.0, 0.5)])
 def test_branch_factor_closed_form_vs_bruteforce(lam, mu, rho):
