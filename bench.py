@@ -73,7 +73,7 @@ WORKLOADS = {
                        precision="fp64"),
 }
 
-HBM_PEAK_GBS = 6778.0  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+HBM_PEAK_GBS = 6778.0  # measured GB300 copy bandwidth (MEASURED_PEAKS.json)
 RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, per particle
 
 # Per particle-step counts of the segment kernel from one ncu capture of the

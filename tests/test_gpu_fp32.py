@@ -96,8 +96,8 @@ def test_crbd_fp32_unbiased_fixed_rates_64_tips():
 
 
 def test_rateshift_fp32_matches_fp64_oracle_in_distribution():
-    """The log-Z error of FP32 particles against the FP64 oracle (north-star
-    precision statement): over 24 seeds the two means of log Zhat agree within
+    """The log-Z error of FP32 particles against the FP64 oracle (the FP32
+    mode's precision statement): over 24 seeds the two means of log Zhat agree within
     3 combined standard errors, and the mean difference is reported."""
     from paper_2112_00364_gb300 import smc
 

@@ -87,7 +87,7 @@ def test_rateshift_fp64_parity():
 
 
 def test_crbd_gpu_unbiased_vs_closed_form():
-    # spec statistical check: 100 seeds, 64-tip tree, N = 2^16, fixed rates
+    # unbiasedness at the benchmark size: 100 seeds, 64-tip tree, N = 2^16, fixed rates
     from paper_2112_00364_gb300 import smc
 
     tree = inputs.yule_tree(64, seed=2)
