@@ -442,8 +442,9 @@ extern "C" smc_status smc_server_submit(smc_server_t h, smc_model_t m, const smc
   q->ly = make_layout(m, &q->cfg);
   q->bytes = align_up(q->ly.total, 256);
   if (q->bytes > S->budget) {
+    const size_t need = q->bytes;
     delete q;
-    return set_error(SMC_ENOMEM, "request needs %zu bytes, more than the server budget", q->bytes);
+    return set_error(SMC_ENOMEM, "request needs %zu bytes, more than the server budget", need);
   }
   q->t_submit = now_s();
   {
