@@ -4,7 +4,6 @@ Sizes span several 256-particle tiles with a ragged last tile, plus the full
 linear-Gaussian (N=1024, T=50) and CRBD (64-tip tree, N=2^16) workloads in the
 launch configuration the benchmark times.
 """
-import math
 
 import numpy as np
 import pytest
