@@ -57,7 +57,10 @@ class OrcCfg(C.Structure):
     _fields_ = [("N", C.c_int64), ("seed", C.c_uint64), ("run_id", C.c_uint32),
                 ("max_segments", C.c_int32), ("follow_anc", _i32p), ("n_follow", C.c_int32),
                 ("pad_", C.c_int32), ("ess_threshold", C.c_double), ("follow_resampled", _i32p),
-                ("n_follow_resampled", C.c_int32), ("pad2_", C.c_int32)]
+                ("n_follow_resampled", C.c_int32), ("pad2_", C.c_int32),
+                ("resume_k", C.c_int32), ("pad3_", C.c_int32), ("resume_logw", _f64p),
+                ("resume_real", _f64p), ("resume_int", _i32p), ("resume_stack", _f64p),
+                ("resume_log_z", C.c_double)]
 
 
 class OrcOut(C.Structure):
@@ -69,7 +72,7 @@ class OrcOut(C.Structure):
         ("n_segments", C.c_int32), ("n_resamples", C.c_int32),
         ("final_logw", _f64p), ("real_fields", _f64p), ("int_fields", _i32p), ("stack", _f64p),
         ("ancestors", _i32p), ("resampled", _i32p), ("incr", _f64p), ("anc_capacity", C.c_int32),
-        ("incr_capacity", C.c_int32),
+        ("incr_capacity", C.c_int32), ("log_z_closed", C.c_double),
     ]
 
 
@@ -190,13 +193,15 @@ KINDS = {"lg": LG, "crbd": CRBD, "rateshift": RATESHIFT, "geometric": GEOMETRIC,
 def smc_run(model: str, N: int, seed: int, run_id: int = 0, precision: int = FP64,
             max_segments: int = 1 << 20, follow=None, record_ancestors: bool = False,
             record_incr: bool = False, ess_threshold: float = 0.0, follow_resampled=None,
-            **params) -> dict:
+            resume_from: dict | None = None, **params) -> dict:
     """Run the oracle SMC once.  `model` is one of lg / crbd / rateshift / geometric;
     params: obs, tree, rates=(lambda, mu), rho, sigma, fixed_mult, depth_cap,
     call_limit, lam_stack_cap, x0_mean, x0_sd, a, b, q_sd, r_sd, geo_p, geo_logw.
     follow: int32 [transitions, N] ancestors from another implementation (row k:
     after checkpoint k); ess_threshold tau > 0: resample only when ESS < tau N;
-    follow_resampled: int32 [transitions] another implementation's decisions."""
+    follow_resampled: int32 [transitions] another implementation's decisions.
+    resume_from: the result of a run of the same model, N, seed and run_id that
+    max_segments stopped (a snapshot); this run continues it from there."""
     keep: list = []
     m = _model_struct(KINDS[model], precision, keep, **params)
     nr, ni, sc = C.c_int32(), C.c_int32(), C.c_int32()
@@ -214,6 +219,21 @@ def smc_run(model: str, N: int, seed: int, run_id: int = 0, precision: int = FP6
         keep.append(follow_resampled)
         cfg.follow_resampled = _p(follow_resampled, C.c_int32)
         cfg.n_follow_resampled = follow_resampled.shape[0]
+    if resume_from is not None:
+        snap = {k: np.ascontiguousarray(resume_from[k2], dtype=dt) for k, k2, dt in
+                (("logw", "final_logw", np.float64), ("ints", "int_fields", np.int32))}
+        keep.extend(snap.values())
+        cfg.resume_k = int(resume_from["n_segments"])
+        cfg.resume_log_z = float(resume_from["log_z_closed"])
+        cfg.resume_logw, cfg.resume_int = _p(snap["logw"], C.c_double), _p(snap["ints"], C.c_int32)
+        if nr > 0:
+            rf = np.ascontiguousarray(resume_from["real_fields"], dtype=np.float64)
+            keep.append(rf)
+            cfg.resume_real = _p(rf, C.c_double)
+        if sc > 0:
+            st = np.ascontiguousarray(resume_from["stack"], dtype=np.float64)
+            keep.append(st)
+            cfg.resume_stack = _p(st, C.c_double)
     o = OrcOut()
     logw = np.empty(N)
     real = np.empty((max(nr, 1), N))
@@ -233,7 +253,8 @@ def smc_run(model: str, N: int, seed: int, run_id: int = 0, precision: int = FP6
         incr = np.empty(cap_seg)
         o.incr, o.incr_capacity = _p(incr, C.c_double), cap_seg
     rc = lib().orc_smc_run(C.byref(m), C.byref(cfg), C.byref(o))
-    res = dict(status=rc, log_z=o.log_z, n_segments=o.n_segments, n_resamples=o.n_resamples,
+    res = dict(status=rc, log_z=o.log_z, log_z_closed=o.log_z_closed, n_segments=o.n_segments,
+               n_resamples=o.n_resamples,
                n_flagged=o.n_flagged, n_flag_mismatch=o.n_flag_mismatch,
                n_hard_mismatch=o.n_hard_mismatch, n_overflow=o.n_overflow, n_limit=o.n_limit,
                n_ess_flagged=o.n_ess_flagged, n_dec_flag_mismatch=o.n_dec_flag_mismatch,

@@ -330,6 +330,14 @@ int orc_sample(int32_t dist, int32_t precision, double p1, double p2, uint64_t s
 int orc_smc_run(const orc_model *m, const orc_cfg *c, orc_out *o) {
   if (!m || !c || !o || c->N <= 0 || c->N > 0x7fffffff) return ORC_EINVAL;
   if (m->depth_cap < 0 || m->call_limit < 0) return ORC_EINVAL;
+  if (c->resume_k < 0) return ORC_EINVAL;
+  if (c->resume_k > 0) {
+    int32_t n_real, n_int, cap;
+    if (orc_n_fields(m, &n_real, &n_int, &cap)) return ORC_EINVAL;
+    if (!c->resume_logw || !c->resume_int || (n_real > 0 && !c->resume_real) ||
+        (cap > 0 && !c->resume_stack) || c->resume_k > c->max_segments)
+      return ORC_EINVAL;
+  }
   if (m->precision == ORC_FP64) return smc_run_d(m, c, o);
   if (m->precision == ORC_FP32) return smc_run_f(m, c, o);
   return ORC_EINVAL;

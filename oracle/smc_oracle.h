@@ -68,6 +68,21 @@ typedef struct {
   const int32_t *follow_resampled; /* [n_follow_resampled] another implementation's decisions */
   int32_t n_follow_resampled;
   int32_t pad2_;
+  /* Resume from a snapshot (0: a fresh run).  A snapshot is a run stopped by
+   * max_segments after resume_k >= 1 segments: its outputs hold the population at
+   * checkpoint resume_k - 1 before that checkpoint's resampling decision, in the
+   * orc_out layouts below, and resume_log_z is its log_z_closed.  The resumed run
+   * takes the decision at checkpoint resume_k - 1 and goes on with segment
+   * resume_k, with the same seed and run_id: every draw is the one the
+   * uninterrupted run makes, so it ends with the same results bit for bit.
+   * max_segments still counts from segment 0. */
+  int32_t resume_k;
+  int32_t pad3_;
+  const double *resume_logw;   /* [N] */
+  const double *resume_real;   /* [n_real][N] (NULL when n_real = 0) */
+  const int32_t *resume_int;   /* [n_int][N] */
+  const double *resume_stack;  /* [lam_stack_cap][N] (rate-shift; else NULL) */
+  double resume_log_z;
 } orc_cfg;
 
 typedef struct {
@@ -92,6 +107,9 @@ typedef struct {
   double *incr;         /* [incr_capacity] per-segment log-Z increments */
   int32_t anc_capacity;
   int32_t incr_capacity;
+  /* log Z without the closure made only because the step limit ended the run
+   * (equal to log_z otherwise): what a resumed run continues from */
+  double log_z_closed;
 } orc_out;
 
 #ifdef __cplusplus

@@ -191,6 +191,12 @@ MUTANTS = [
     ("geometric_weight_sign", P_SRC, "P->logw = P->logw + (R)m->geo_logw;",
      "P->logw = P->logw - (R)m->geo_logw;", 0),
     ("geometric_count", P_SRC, "P->count += 1;", "P->count += 2;", 0),
+    # snapshot / resume: a field not restored, the step limit's closure kept in
+    # the closed log Z, the snapshot's last segment run a second time
+    ("resume_forgets_stack_pointer", P_SRC, "P->sp = in[N + i];", "P->sp = 0;", 0),
+    ("resume_closed_log_z_includes_limit", P_SRC, "if (!at_limit) logz_closed = logz;",
+     "logz_closed = logz;", 0),
+    ("resume_reruns_last_segment", P_SRC, "    propagated = 1;\n", "    propagated = 0;\n", 0),
 ]
 
 PIN_FILES = sorted(str(p) for p in HERE.glob("test_oracle_*.py") if p.name != Path(__file__).name)
@@ -222,6 +228,7 @@ AREA_FIRST = [
     (("rateshift_", "resampled_stack_"),
      _in("test_oracle_models.py", "test_rateshift_sigma_zero_is_crbd",
          "test_rateshift_fixed_multipliers_unbiased")),
+    (("resume_",), _in("test_oracle_resume.py")),
     (("geometric_", "step_limit_"),
      _in("test_oracle_models.py", "test_geometric_z_equals_two_and_posterior", "test_step_limit")),
 ]

@@ -5,7 +5,7 @@ A copy of the oracle package is built with -fsanitize=address,undefined (any
 undefined behaviour aborts) and a quick subset of its tests runs against it in
 a child process with the sanitizer runtimes preloaded: the regression runs of
 every model, the resampling pins, the rate-shift stack, the kill rules, a SEIR
-transition day and the ESS rule.  An out-of-bounds access, a use after free,
+transition day, the ESS rule and snapshot / resume.  An out-of-bounds access, a use after free,
 a signed overflow or an invalid shift in the oracle fails the child.
 """
 from __future__ import annotations
@@ -32,6 +32,7 @@ SUBSET = [
     "test_oracle_seir.py::test_one_day_transition_law",
     "test_oracle_ess.py::test_threshold_above_one_equals_every_checkpoint",
     "test_oracle_crbd_ds.py::test_crbd_ds_posterior_bookkeeping",
+    "test_oracle_resume.py",
 ]
 
 
