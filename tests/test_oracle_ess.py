@@ -94,3 +94,33 @@ def test_importance_sampling_unbiased_lg():
     lz = np.array([_run("lg", 2048, s, obs=y, ess_threshold=1e-9)["log_z"] for s in range(1, 101)])
     ok, mean, se = cf.unbiased_check(lz, cf.kalman_loglik(y))
     assert ok, (mean, se)
+
+
+def test_follow_mode_adopts_decisions():
+    y = inputs.lg_observations(50, seed=1)
+    a = _run("lg", 1024, 7, obs=y, ess_threshold=0.5)
+    fake = a["resampled"].copy()
+    k = int(np.flatnonzero(fake)[0])
+    fake[k] = 0  # keep the population where the run resampled
+    b = _run("lg", 1024, 7, obs=y, ess_threshold=0.5, follow_resampled=fake)
+    np.testing.assert_array_equal(b["resampled"][: k + 1], fake[: k + 1])
+    assert b["n_dec_hard_mismatch"] + b["n_dec_flag_mismatch"] >= 1
+    assert b["log_z"] != a["log_z"]
+
+
+def test_ess_near_band_is_relative():
+    # geometric program: after segment 0 the weights are 1.5 (heads) or 1
+    # (tails); a snapshot there gives them exactly, so the threshold can be put
+    # 1e-7 above the ESS: inside the band 1e-9 tau N (about 5e-7), outside an
+    # absolute 1e-9
+    N = 1000
+    snap = oracle.smc_run("geometric", N, 4, max_segments=1)
+    lw = snap["final_logw"]
+    w = np.exp(lw - lw.max())
+    ess = w.sum() ** 2 / (w * w).sum()
+    assert 0.3 * N < ess < N
+    above = oracle.smc_run("geometric", N, 4, ess_threshold=(ess + 1e-7) / N)
+    below = oracle.smc_run("geometric", N, 4, ess_threshold=(ess - 1e-7) / N)
+    assert above["n_ess_flagged"] >= 1 and below["n_ess_flagged"] >= 1
+    # and the decision at checkpoint 0 falls on the side the threshold says
+    assert above["resampled"][0] == 1 and below["resampled"][0] == 0

@@ -191,6 +191,16 @@ MUTANTS = [
     ("geometric_weight_sign", P_SRC, "P->logw = P->logw + (R)m->geo_logw;",
      "P->logw = P->logw - (R)m->geo_logw;", 0),
     ("geometric_count", P_SRC, "P->count += 1;", "P->count += 2;", 0),
+    # follow mode and boundary flags (what every GPU parity test relies on)
+    ("follow_adopts_nothing", P_SRC, "if (fa[i] >= 0 && fa[i] < N) anc[i] = fa[i];", ";", 0),
+    ("follow_counts_swapped", P_SRC, "if (flag[i]) o->n_flag_mismatch += 1;",
+     "if (!flag[i]) o->n_flag_mismatch += 1;", 0),
+    ("follow_decision_ignored", P_SRC, "resample_now = c->follow_resampled[k] != 0;", ";", 0),
+    ("flag_tolerance_not_scaled", C_SRC, "const double tol = BOUNDARY_EPS * (double)N;",
+     "const double tol = BOUNDARY_EPS;", 0),
+    ("flag_lower_boundary_ignored", C_SRC, "if (a > 0 && fabs(q[a - 1] - y) < tol) f = 1;", ";", 0),
+    ("ess_near_band_absolute", P_SRC, "const int near = fabs(ess - target) <= 1e-9 * target;",
+     "const int near = fabs(ess - target) <= 1e-9;", 0),
     # snapshot / resume: a field not restored, the step limit's closure kept in
     # the closed log Z, the snapshot's last segment run a second time
     ("resume_forgets_stack_pointer", P_SRC, "P->sp = in[N + i];", "P->sp = 0;", 0),
@@ -229,6 +239,10 @@ AREA_FIRST = [
      _in("test_oracle_models.py", "test_rateshift_sigma_zero_is_crbd",
          "test_rateshift_fixed_multipliers_unbiased")),
     (("resume_",), _in("test_oracle_resume.py")),
+    (("follow_",), _in("test_oracle_models.py", "test_ancestor_follow_mode_adopts")
+     + _in("test_oracle_ess.py", "test_follow_mode_adopts_decisions")),
+    (("ess_near_",), _in("test_oracle_ess.py", "test_ess_near_band_is_relative")),
+    (("flag_",), _in("test_oracle_resample.py")),
     (("geometric_", "step_limit_"),
      _in("test_oracle_models.py", "test_geometric_z_equals_two_and_posterior", "test_step_limit")),
 ]

@@ -71,6 +71,23 @@ def test_boundary_flag():
     assert flag[0] == 1
 
 
+def test_boundary_flag_band_scales_with_n_and_covers_both_sides():
+    # equal weights: q_j = j + 1 exactly (S = N, N / S = 1), offsets y_i = i + u.
+    # The band is 1e-12 N = 1e-9 at N = 1000.
+    N = 1000
+    # y_i sits 5e-10 below q_i (the boundary of its own ancestor a_i = i)
+    anc, flag, *_ = oracle.resample(np.zeros(N), 1.0 - 5e-10)
+    np.testing.assert_array_equal(anc, np.arange(N))
+    assert flag.all()
+    # y_i sits 5e-10 above q_{i-1} (the boundary below its ancestor)
+    anc, flag, *_ = oracle.resample(np.zeros(N), 5e-10)
+    np.testing.assert_array_equal(anc, np.arange(N))
+    assert flag[1:].all() and flag[0] == 0  # no boundary below particle 0
+    # 2e-9 away from every boundary: outside the band
+    _, flag, *_ = oracle.resample(np.zeros(N), 2e-9)
+    assert flag.sum() == 0
+
+
 def test_single_particle():
     anc, flag, incr, m, S, rc = oracle.resample(np.array([-3.25]), 0.7)
     assert anc.tolist() == [0] and incr == -3.25
