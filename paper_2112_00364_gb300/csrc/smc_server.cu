@@ -226,8 +226,11 @@ int admit(Server* S, smc_status* err) {
     q->dev.start_wave = (unsigned)S->waves.load();  // its segment 0 runs in the next wave
     q->dev.redundant = combine_in_every_cta(q->ly.tile, q->ly.n_tiles, false);
     e = cudaMemsetAsync(q->dev.rs, 0, sizeof(RunState), S->stream);
-    if (e != cudaSuccess) {
+    if (e != cudaSuccess) {  // the run never became resident: close its ticket
       *err = cuda_fail(e, "cudaMemsetAsync(run state)");
+      cudaFreeAsync(q->ws, S->stream);
+      finish_ticket(S, q, *err);
+      delete q;
       return n;
     }
     S->in_use += q->bytes;
@@ -273,7 +276,13 @@ smc_status retire(Server* S, int b) {
     hrs.n_overflow = f[i].n_overflow;
     hrs.n_limit = f[i].n_limit;
     smc_status st = collect_run(q->model, &q->cfg, q->ly, q->ws, q->dev, hrs, q->result, S->stream);
-    if (st) return st;
+    if (st) {  // out of the resident list already: free it and close its ticket here
+      cudaFreeAsync(q->ws, S->stream);  // stream-ordered after the waves that used it
+      S->in_use -= q->bytes;
+      finish_ticket(S, q, st);
+      delete q;
+      return st;
+    }
     if (q->cancel) q->result->counters.status = SMC_ECANCELLED;
     SMC_CUDA_TRY(cudaEventCreateWithFlags(&q->done_ev, cudaEventDisableTiming));
     SMC_CUDA_TRY(cudaEventRecord(q->done_ev, S->stream));
@@ -360,6 +369,7 @@ void worker_main(Server* S) {
   reap(S, true);
   std::lock_guard<std::mutex> lk(S->mu);
   for (Request* q : S->resident) {
+    if (q->ws) cudaFreeAsync(q->ws, S->stream);
     S->state[q->ticket] = T_FAILED;
     S->final_status[q->ticket] = err ? err : SMC_EINVAL;
     delete q;
