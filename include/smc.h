@@ -150,6 +150,10 @@ typedef struct {
   int32_t n_ess_near;       /* ess_threshold > 0: checkpoints whose ESS lay within 1e-9 of tau N */
   smc_status status;        /* this run's own status (0, SMC_WKILLED, SMC_EDEGENERATE,
                                SMC_ESTEPLIMIT) */
+  int32_t pad2_;
+  int64_t n_draws;          /* Philox blocks drawn by the model's SAMPLE statements, summed over
+                               particles and segments (the resampling uniforms not included) */
+  int64_t n_blocks;         /* basic-block executions, summed over particles and segments */
 } smc_counters;
 
 /* Outputs of one run.  `where` says whether every pointer below is host or
@@ -227,8 +231,13 @@ smc_status smc_run_batch(const smc_model_t *ms, const smc_run_cfg *cfgs, smc_res
  * keep the worker from blocking) and its ticket completes.  A request's results
  * are identical to what smc_run gives for the same model and configuration.
  * The model handle and the result buffers must stay valid until the ticket is
- * done.  The paper runs one SMC at a time; this layer is the build's serving form
- * of the Section 3.3 engine. */
+ * done.  A request whose result collection fails completes with that error
+ * (after every copy already queued into its buffers has ended) while the other
+ * requests go on.  Fault injection for tests, on the host: when the environment
+ * variable SMC_SERVER_FAIL_TICKET holds a ticket number at smc_server_create,
+ * that ticket's retirement fails with SMC_ECUDA after its result copies were
+ * queued.  The paper runs one SMC at a time; this layer is the build's serving
+ * form of the Section 3.3 engine. */
 typedef struct smc_server_s *smc_server_t;
 
 typedef struct {
@@ -305,7 +314,10 @@ smc_status smc_resample(const double *logw, int64_t N, double u, int32_t *ancest
  * and it calls no allocating routine.  Limit: N <= SMC_RESAMPLE_STATIC_MAX_N
  * (larger N returns SMC_EINVAL with a message).  The first call on each device
  * resolves the array's device address (cudaGetSymbolAddress, with that device
- * current), so make that first call before any stream capture.  All calls share
+ * current) and, unless an earlier call of the library on that device did so,
+ * uploads the library's math tables with a synchronous cudaMemcpyToSymbol,
+ * which waits for the device; so make that first call before any stream
+ * capture, on a path where such a wait is allowed.  All calls share
  * the array: calls that overlap on the GPU race and must be serialised by the
  * caller (e.g. one stream).  Arguments, layouts and other errors as for
  * smc_resample; n_near is zeroed on `stream` by the call. */
@@ -352,7 +364,11 @@ smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uin
  * integer exponential, fn 9 round(e^x[i] 2^50) as smc_resample forms its weights
  * with it (the argument in 2^-52 units); fn 10 gives e^-x[i]
  * (a double, x[i] in [0, 64)) from the same integer exponential, as the Poisson
- * sampler forms it.  x, y [n] f64 device pointers.
+ * sampler forms it.  fn 11..16 are the FP32 mode's own single-precision
+ * functions of x[i] rounded to float (the result widened to f64): 11 log,
+ * 12 exp, 13 cos(2 pi x), 14 log1p, 15 expm1, 16 log k! for k = (int)x[i];
+ * fn 17..21 are CUDA's logf, expf, cospif(2x), log1pf, expm1f of the same
+ * float arguments, for comparison.  x, y [n] f64 device pointers.
  * Errors: SMC_EINVAL, SMC_ECUDA. */
 smc_status smc_math_eval(int32_t fn, const double *x, double *y, int64_t n, void *stream);
 

@@ -110,6 +110,8 @@ def lib():
         L.orc_smc_run.restype = C.c_int
         L.orc_n_fields.argtypes = [C.POINTER(OrcModel), _i32p, _i32p, _i32p]
         L.orc_n_fields.restype = C.c_int
+        L.orc_mathf.argtypes = [C.c_int32, _f64p, _f64p, C.c_int64]
+        L.orc_mathf.restype = C.c_int
         _lib = L
     return _lib
 
@@ -138,6 +140,20 @@ def sample(dist: str, n: int, p1: float = 0.0, p2: float = 0.0, seed: int = 1, r
     if rc != OK:
         raise ValueError(f"orc_sample rc={rc}")
     return (out, blocks) if return_blocks else out
+
+
+MATHF = {"log": 0, "exp": 1, "cos2pi": 2, "log1p": 3, "expm1": 4, "lfact": 5}
+
+
+def mathf(fn: str, x) -> np.ndarray:
+    """The FP32 mode's single-precision function `fn` of float32(x) (log k! of
+    int(x) for "lfact"), widened to float64."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    rc = lib().orc_mathf(MATHF[fn], _p(x, C.c_double), _p(y, C.c_double), x.shape[0])
+    if rc != OK:
+        raise ValueError(f"orc_mathf rc={rc}")
+    return y
 
 
 def resample(logw: np.ndarray, u: float):

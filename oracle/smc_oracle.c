@@ -114,10 +114,12 @@ static double u_second_d(const uint32_t w[4]) {
   uint64_t x = ((uint64_t)w[3] << 32) | (uint64_t)w[2];
   return (double)((x >> 11) | 1u) * 0x1p-53;
 }
-/* FP32 uniforms: the odd 24-bit integer (w >> 8) | 1 times 2^-24.
- * First uses w0, second w1. */
-static float u_first_f(const uint32_t w[4]) { return (float)((w[0] >> 8) | 1u) * 0x1p-24f; }
-static float u_second_f(const uint32_t w[4]) { return (float)((w[1] >> 8) | 1u) * 0x1p-24f; }
+/* FP32 uniforms: the odd 24-bit integer (w >> 8) | 1 times 2^-24, from the high
+ * word of the FP64 uniform's 64 bits: first w1, second w3.  An FP32 draw is then
+ * the FP64 draw of the same counter to within 2^-24, so that FP32 and FP64 runs
+ * of one seed can be compared result by result. */
+static float u_first_f(const uint32_t w[4]) { return (float)((w[1] >> 8) | 1u) * 0x1p-24f; }
+static float u_second_f(const uint32_t w[4]) { return (float)((w[3] >> 8) | 1u) * 0x1p-24f; }
 
 /* run-level constants computed once in double */
 typedef struct {
@@ -269,6 +271,186 @@ static double lfact_d(int64_t k) {
   return (x - 0.5) * log(x) - x + HALF_LOG_2PI_D + series;
 }
 
+/* --------------- FP32 elementary functions (FP32 mode) ---------------
+ * The FP32-particle mode defines its log, exp, cos(2 pi u), log1p and expm1 as
+ * the fixed sequences of single-precision operations below (fused
+ * multiply-adds only where fmaf is written; the file is compiled with
+ * -ffp-contract=off), so that its roundings are specified rather than left to
+ * a math library: the GPU library performs the same operations and gets the
+ * same bits.  The methods are textbook ones, with Taylor coefficients rounded
+ * to float:
+ *   log:   x = 2^e m with m in [sqrt(2)/2, sqrt(2)]; f = m - 1 (exact);
+ *          log(1 + f) = 2 atanh(f / (2 + f)) = f - s (f - R), s = f / (2 + f),
+ *          R = z (2/3 + 2z/5 + 2z^2/7 + 2z^3/9), z = s^2; plus e ln 2, ln 2 in
+ *          two parts so that e times the first part is exact.
+ *   exp:   x = n ln 2 + r, n = rint(x / ln 2); e^r = 1 + r + r^2 (1/2! + r/3! +
+ *          ... + r^5/7!); times 2^n.
+ *   cos(2 pi u): 4u = q + t exactly, |t| <= 1/2; cos(2 pi u) is cos(t pi/2),
+ *          -sin, -cos or sin of it for q = 0, 1, 2, 3 (mod 4), each from its
+ *          Taylor series in t (coefficients (pi/2)^n / n!).
+ *   log1p: the log series on x itself when 1 + x lies in [sqrt(2)/2, sqrt(2)],
+ *          else the log of u = 1 + x plus the rounding error of that sum over u.
+ *   expm1: x + x^2 (1/2! + ... + x^6/8!) for |x| < ln 2 / 2, else
+ *          2^n expm1(r) + (2^n - 1).
+ *   log k!: lfact_d rounded to float below 32, Stirling's series in float above.
+ * The constants are the float roundings of the exact values, as hex literals. */
+#define F_LN2_HI 0x1.62e4p-1f
+#define F_LN2_LO 0x1.7f7d1cp-20f
+#define F_INV_LN2 0x1.715476p+0f
+
+static float f_bits_to_float(uint32_t b) {
+  float f;
+  memcpy(&f, &b, sizeof f);
+  return f;
+}
+static uint32_t f_float_to_bits(float f) {
+  uint32_t b;
+  memcpy(&b, &f, sizeof b);
+  return b;
+}
+
+/* log(1 + f), f in [sqrt(2)/2 - 1, sqrt(2) - 1]: the atanh series */
+static float f_log1p_series(float f) {
+  const float s = f / (2.0f + f);
+  const float z = s * s;
+  float R = fmaf(z, 0x1.c71c72p-3f /* 2/9 */, 0x1.24924ap-2f /* 2/7 */);
+  R = fmaf(R, z, 0x1.99999ap-2f /* 2/5 */);
+  R = fmaf(R, z, 0x1.555556p-1f /* 2/3 */);
+  R = z * R;
+  return f - s * (f - R);
+}
+
+/* e ln 2 + l */
+static float f_plus_e_ln2(int32_t e, float l) {
+  if (e == 0) return l;
+  const float fe = (float)e;
+  const float lo = fmaf(fe, F_LN2_LO, l);
+  return fe * F_LN2_HI + lo;
+}
+
+/* split a positive normal float into 2^e m with m in [sqrt(2)/2, sqrt(2)] */
+static float f_split(uint32_t bits, int32_t *e) {
+  const uint32_t frac = bits & 0x7fffffu;
+  *e = (int32_t)(bits >> 23) - 127;
+  if (frac > 0x3504f3u) { /* m above float(sqrt 2): halve it */
+    *e += 1;
+    return f_bits_to_float(frac | (126u << 23));
+  }
+  return f_bits_to_float(frac | (127u << 23));
+}
+
+static float orc_logf(float x) {
+  if (!(x > 0.0f)) return x == 0.0f ? -INFINITY : NAN;
+  if (isinf(x)) return x;
+  int32_t extra = 0;
+  if (x < 0x1p-126f) { /* subnormal */
+    x = x * 0x1p24f;
+    extra = -24;
+  }
+  int32_t e;
+  const float m = f_split(f_float_to_bits(x), &e);
+  return f_plus_e_ln2(e + extra, f_log1p_series(m - 1.0f));
+}
+
+/* e^r - 1 - r as r^2 (1/2! + r/3! + ...), up to r^5/7! or, with deg8, r^6/8! */
+static float f_exp_tail(float r, int deg8) {
+  float q = 0x1.a01a02p-13f; /* 1/7! */
+  if (deg8) q = fmaf(r, 0x1.a01a02p-16f /* 1/8! */, q);
+  q = fmaf(q, r, 0x1.6c16c2p-10f); /* 1/6! */
+  q = fmaf(q, r, 0x1.111112p-7f);  /* 1/5! */
+  q = fmaf(q, r, 0x1.555556p-5f);  /* 1/4! */
+  q = fmaf(q, r, 0x1.555556p-3f);  /* 1/3! */
+  q = fmaf(q, r, 0x1p-1f);         /* 1/2! */
+  return (r * r) * q;
+}
+
+static float f_pow2(int32_t n) { /* 2^n, n in [-126, 127] */
+  return f_bits_to_float((uint32_t)(n + 127) << 23);
+}
+
+static float orc_expf(float x) {
+  if (isnan(x)) return x;
+  if (x > 89.0f) return INFINITY;
+  if (x < -104.0f) return 0.0f;
+  const float nf = rintf(x * F_INV_LN2);
+  float r = fmaf(-nf, F_LN2_HI, x);
+  r = fmaf(-nf, F_LN2_LO, r);
+  const float y = 1.0f + (r + f_exp_tail(r, 0));
+  const int32_t n = (int32_t)nf;
+  if (n > 127) return (y * 2.0f) * f_pow2(n - 1);
+  if (n < -126) return (y * f_pow2(n + 100)) * 0x1p-100f;
+  return y * f_pow2(n);
+}
+
+/* cos(2 pi u) for u in [0, 1] */
+static float orc_cos2pif(float u) {
+  const float v = 4.0f * u;
+  const float qf = rintf(v);
+  const float t = v - qf;
+  const float z = t * t;
+  const int32_t quad = (int32_t)qf & 3;
+  if (quad == 0 || quad == 2) {
+    float c = fmaf(z, -0x1.a6d1f2p-16f, 0x1.e1f506p-11f); /* (pi/2)^10/10!, ^8/8! */
+    c = fmaf(c, z, -0x1.55d3c8p-6f);                      /* (pi/2)^6/6! */
+    c = fmaf(c, z, 0x1.03c1f0p-2f);                       /* (pi/2)^4/4! */
+    c = fmaf(c, z, -0x1.3bd3ccp+0f);                      /* (pi/2)^2/2! */
+    const float cv = fmaf(z, c, 1.0f);
+    return quad == 0 ? cv : -cv;
+  }
+  float p = fmaf(z, 0x1.507834p-13f, -0x1.32d2ccp-8f); /* (pi/2)^9/9!, ^7/7! */
+  p = fmaf(p, z, 0x1.466bc6p-4f);                      /* (pi/2)^5/5! */
+  p = fmaf(p, z, -0x1.4abbcep-1f);                     /* (pi/2)^3/3! */
+  /* t pi/2 with pi/2 = 0x1.921fb6p+0 - 0x1.777a5cp-25 */
+  const float inner = fmaf(t * z, p, t * -0x1.777a5cp-25f);
+  const float sv = fmaf(t, 0x1.921fb6p+0f, inner);
+  return quad == 1 ? -sv : sv;
+}
+
+static float orc_log1pf(float x) {
+  if (!(x > -1.0f)) return x == -1.0f ? -INFINITY : NAN;
+  if (isinf(x)) return x;
+  if (x >= -0x1.2bec34p-2f && x <= 0x1.a8279ap-2f) return f_log1p_series(x);
+  const float u = 1.0f + x;
+  float err; /* the rounding error of 1 + x, exact: the larger operand first */
+  if (x > 1.0f)
+    err = 1.0f - (u - x);
+  else
+    err = x - (u - 1.0f);
+  const float c = err / u;
+  int32_t e;
+  const float m = f_split(f_float_to_bits(u), &e);
+  return f_plus_e_ln2(e, f_log1p_series(m - 1.0f) + c);
+}
+
+static float orc_expm1f(float x) {
+  if (isnan(x)) return x;
+  if (x > 89.0f) return INFINITY;
+  if (x < -104.0f) return -1.0f;
+  if (fabsf(x) < 0x1.62e430p-2f) return x + f_exp_tail(x, 1);
+  const float nf = rintf(x * F_INV_LN2);
+  float r = fmaf(-nf, F_LN2_HI, x);
+  r = fmaf(-nf, F_LN2_LO, r);
+  const float em = r + f_exp_tail(r, 1);
+  const int32_t n = (int32_t)nf;
+  if (n > 127) return (em + 1.0f) * 2.0f * f_pow2(n - 1);
+  const float p2 = f_pow2(n < -126 ? -126 : n);
+  return fmaf(p2, em, p2 - 1.0f);
+}
+
+static double lfact_d(int64_t k);
+
+static float orc_lfactf(int32_t k) {
+  if (k < 32) return (float)lfact_d(k < 0 ? 0 : k);
+  const float x = (float)k + 1.0f;
+  const float ix = 1.0f / x;
+  const float ix2 = ix * ix;
+  const float series = ix * (0x1.555556p-4f - ix2 * (0x1.6c16c2p-9f - ix2 * 0x1.a01a02p-11f));
+  const float a = (x - 0.5f) * orc_logf(x);
+  const float b = a - x;
+  const float c = b + 0x1.d67f1cp-1f; /* log(2 pi) / 2 */
+  return c + series;
+}
+
 /* ------------------ precision instantiations ------------------ */
 #define R double
 #define SFX(x) x##_d
@@ -276,14 +458,13 @@ static double lfact_d(int64_t k) {
 #define EXPR exp
 #define LOG1PR log1p
 #define EXPM1R expm1
-#define COSR cos
 #define SQRTR sqrt
 #define FMAR fma
 #define FABSR fabs
 #define FLOORR floor
-#define LGAMMAR lgamma
+#define LFACTR(k) lgamma((k) + 1.0)
+#define COS2PIR(u) cos(6.28318530717958647692 * (u))
 #define LN2R LN2_D
-#define TWO_PIR 6.28318530717958647692
 #include "smc_oracle_prec.inc"
 #undef R
 #undef SFX
@@ -291,29 +472,27 @@ static double lfact_d(int64_t k) {
 #undef EXPR
 #undef LOG1PR
 #undef EXPM1R
-#undef COSR
 #undef SQRTR
 #undef FMAR
 #undef FABSR
 #undef FLOORR
-#undef LGAMMAR
+#undef LFACTR
+#undef COS2PIR
 #undef LN2R
-#undef TWO_PIR
 
 #define R float
 #define SFX(x) x##_f
-#define LOGR logf
-#define EXPR expf
-#define LOG1PR log1pf
-#define EXPM1R expm1f
-#define COSR cosf
+#define LOGR orc_logf
+#define EXPR orc_expf
+#define LOG1PR orc_log1pf
+#define EXPM1R orc_expm1f
 #define SQRTR sqrtf
 #define FMAR fmaf
 #define FABSR fabsf
 #define FLOORR floorf
-#define LGAMMAR lgammaf
+#define LFACTR(k) orc_lfactf((int32_t)(k))
+#define COS2PIR(u) orc_cos2pif(u)
 #define LN2R 0.693147182f
-#define TWO_PIR 6.28318548f
 #include "smc_oracle_prec.inc"
 
 /* ------------------------- exported ------------------------- */
@@ -325,6 +504,24 @@ int orc_sample(int32_t dist, int32_t precision, double p1, double p2, uint64_t s
   if (precision == ORC_FP64) return sample_d(dist, p1, p2, key, n, out, blocks_used);
   if (precision == ORC_FP32) return sample_f(dist, p1, p2, key, n, out, blocks_used);
   return ORC_EINVAL;
+}
+
+int orc_mathf(int32_t fn, const double *x, double *y, int64_t n) {
+  for (int64_t i = 0; i < n; i++) {
+    const float v = (float)x[i];
+    float r;
+    switch (fn) {
+      case 0: r = orc_logf(v); break;
+      case 1: r = orc_expf(v); break;
+      case 2: r = orc_cos2pif(v); break;
+      case 3: r = orc_log1pf(v); break;
+      case 4: r = orc_expm1f(v); break;
+      case 5: r = orc_lfactf((int32_t)x[i]); break;
+      default: return ORC_EINVAL;
+    }
+    y[i] = (double)r;
+  }
+  return ORC_OK;
 }
 
 int orc_smc_run(const orc_model *m, const orc_cfg *c, orc_out *o) {

@@ -122,6 +122,9 @@ int orc_sample(int32_t dist, int32_t precision, double p1, double p2, uint64_t s
 int orc_resample(const double *logw, int64_t N, double u, int32_t *anc, int32_t *flag,
                  double *incr, double *m_out, double *S_out);
 int orc_smc_run(const orc_model *m, const orc_cfg *c, orc_out *o);
+/* The FP32 mode's single-precision functions of (float)x[i], widened into y[i]:
+ * fn 0 log, 1 exp, 2 cos(2 pi x), 3 log1p, 4 expm1, 5 log k! for k = (int)x[i]. */
+int orc_mathf(int32_t fn, const double *x, double *y, int64_t n);
 int orc_n_fields(const orc_model *m, int32_t *n_real, int32_t *n_int, int32_t *stack_cap);
 #ifdef __cplusplus
 }

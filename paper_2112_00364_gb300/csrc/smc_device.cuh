@@ -446,12 +446,14 @@ struct Unif<double> {
 };
 template <>
 struct Unif<float> {
-  // (w >> 8) | 1, times 2^-24 (24-bit integer: exact in float)
+  // (w >> 8) | 1, times 2^-24 (24-bit integer: exact in float), w the high word
+  // of the FP64 uniform's 64 bits (w1 of the first, w3 of the second): an FP32
+  // draw is then the FP64 draw of the same counter to within 2^-24
   __device__ __forceinline__ static float first(const Block4& b) {
-    return (float)((b.w0 >> 8) | 1u) * 0x1p-24f;
+    return (float)((b.w1 >> 8) | 1u) * 0x1p-24f;
   }
   __device__ __forceinline__ static float second(const Block4& b) {
-    return (float)((b.w1 >> 8) | 1u) * 0x1p-24f;
+    return (float)((b.w3 >> 8) | 1u) * 0x1p-24f;
   }
 };
 
@@ -464,30 +466,192 @@ __device__ __forceinline__ bool gt_nonneg(float a, float b) {
   return __float_as_int(a) > __float_as_int(b);
 }
 
-// ---- precision-overloaded math (IEEE library calls, no fast-math) ----
+// ---- FP32 elementary functions of the FP32-particle mode ----
+// The FP32 mode computes its logarithms, exponentials and the Box-Muller cosine
+// with the functions below, written out in single-precision operations (every
+// fused multiply-add an explicit fmaf; the library is built with -fmad=false),
+// not with CUDA's logf / expf / cosf: every rounding of the mode is then fixed
+// by these definitions, so that an implementation elsewhere that performs the
+// same operations gets the same bits.  Each follows a textbook method with
+// Taylor coefficients rounded to float and is within ~2 ulp of the exact value.
+//   log    x = 2^e m, m in [sqrt(2)/2, sqrt(2)], f = m - 1 (exact), s = f / (2 + f):
+//          log(1 + f) = 2 atanh(s) = f - s (f - R(s^2)), R(z) = z (2/3 + z (2/5 +
+//          z (2/7 + z 2/9))) (the atanh series; |s| <= 0.172), plus e ln 2 with
+//          a two-part ln 2 (e ln2_hi exact).
+//   exp    n = rint(x / ln 2), r = x - n ln 2 (two-part ln 2), |r| <= ln 2 / 2,
+//          e^r = 1 + (r + r^2 (1/2! + r (1/3! + ... + r / 7!))), times 2^n.
+//   cos(2 pi u)  4u = q + t exactly (q = rint(4u), |t| <= 1/2), then cos or
+//          -/+ sin of t pi/2 by quadrant from their Taylor series in t.
+//   log1p  the log core on x itself inside [sqrt(2)/2 - 1, sqrt(2) - 1], else on
+//          1 + x with the rounding error of that sum added as c / (1 + x).
+//   expm1  the Taylor series of e^x - 1 to x^8/8! for |x| < ln 2 / 2, else
+//          2^n expm1(r) + (2^n - 1) with the reduction of exp.
+//   log k! the math table's FP64 log k! rounded to float below 32, Stirling's
+//          series in float above.
+constexpr float kF32Ln2Hi = 0x1.62e4p-1f;     // ln 2 to 15 significant bits: e ln2_hi exact
+constexpr float kF32Ln2Lo = 0x1.7f7d1cp-20f;  // ln 2 - kF32Ln2Hi, rounded
+constexpr float kF32InvLn2 = 0x1.715476p+0f;
+constexpr float kF32Atanh3 = 0x1.555556p-1f, kF32Atanh5 = 0x1.99999ap-2f;  // 2/3, 2/5
+constexpr float kF32Atanh7 = 0x1.24924ap-2f, kF32Atanh9 = 0x1.c71c72p-3f;  // 2/7, 2/9
+constexpr float kF32Inv2 = 0x1p-1f, kF32Inv6 = 0x1.555556p-3f, kF32Inv24 = 0x1.555556p-5f;
+constexpr float kF32Inv120 = 0x1.111112p-7f, kF32Inv720 = 0x1.6c16c2p-10f;
+constexpr float kF32Inv5040 = 0x1.a01a02p-13f, kF32Inv40320 = 0x1.a01a02p-16f;
+// (pi/2)^n / n! with alternating signs; pi/2 itself as a two-part constant
+constexpr float kF32PiO2Hi = 0x1.921fb6p+0f, kF32PiO2Lo = -0x1.777a5cp-25f;
+constexpr float kF32S3 = -0x1.4abbcep-1f, kF32S5 = 0x1.466bc6p-4f, kF32S7 = -0x1.32d2ccp-8f,
+                kF32S9 = 0x1.507834p-13f;
+constexpr float kF32C2 = -0x1.3bd3ccp+0f, kF32C4 = 0x1.03c1f0p-2f, kF32C6 = -0x1.55d3c8p-6f,
+                kF32C8 = 0x1.e1f506p-11f, kF32C10 = -0x1.a6d1f2p-16f;
+constexpr float kF32HalfLog2Pi = 0x1.d67f1cp-1f;
+constexpr float kF32Inv12 = 0x1.555556p-4f, kF32Inv360 = 0x1.6c16c2p-9f,
+                kF32Inv1260 = 0x1.a01a02p-11f;
+
+// 2^n as a float for n in [-126, 127]
+__device__ __forceinline__ float f32_pow2i(int n) { return __int_as_float((n + 127) << 23); }
+
+// log(1 + f) for f in [sqrt(2)/2 - 1, sqrt(2) - 1]
+__device__ __forceinline__ float f32_log1p_core(float f) {
+  const float s = f / (2.0f + f);
+  const float z = s * s;
+  float R = fmaf(z, kF32Atanh9, kF32Atanh7);
+  R = fmaf(R, z, kF32Atanh5);
+  R = fmaf(R, z, kF32Atanh3);
+  R = z * R;
+  return f - s * (f - R);
+}
+
+// e ln 2 + l
+__device__ __forceinline__ float f32_add_eln2(int e, float l) {
+  if (e == 0) return l;
+  const float fe = (float)e;
+  return fe * kF32Ln2Hi + fmaf(fe, kF32Ln2Lo, l);
+}
+
+__device__ __forceinline__ float f32_log(float x) {
+  if (!(x > 0.0f)) return x == 0.0f ? -INFINITY : __int_as_float(0x7fc00000);
+  if (x == INFINITY) return x;
+  int ix = __float_as_int(x);
+  int e = -127;
+  if (ix < 0x00800000) {  // subnormal: scale by 2^24
+    ix = __float_as_int(x * 0x1p24f);
+    e -= 24;
+  }
+  const int mb = ix & 0x007fffff;
+  e += ix >> 23;
+  float m;
+  if (mb > 0x3504f3) {  // m above float(sqrt 2): use m / 2
+    m = __int_as_float(mb | (126 << 23));
+    e += 1;
+  } else {
+    m = __int_as_float(mb | (127 << 23));
+  }
+  return f32_add_eln2(e, f32_log1p_core(m - 1.0f));  // m - 1 exact
+}
+
+// e^r - 1 - r for |r| <= ln 2 / 2, as r^2 (1/2! + r (1/3! + ... ))
+__device__ __forceinline__ float f32_expm1_poly(float r, bool deg8) {
+  float q = deg8 ? fmaf(r, kF32Inv40320, kF32Inv5040) : kF32Inv5040;
+  q = fmaf(q, r, kF32Inv720);
+  q = fmaf(q, r, kF32Inv120);
+  q = fmaf(q, r, kF32Inv24);
+  q = fmaf(q, r, kF32Inv6);
+  q = fmaf(q, r, kF32Inv2);
+  return (r * r) * q;
+}
+
+__device__ __forceinline__ float f32_exp(float x) {
+  if (x != x) return x;
+  if (x > 89.0f) return INFINITY;
+  if (x < -104.0f) return 0.0f;
+  const float nf = rintf(x * kF32InvLn2);
+  float r = fmaf(-nf, kF32Ln2Hi, x);
+  r = fmaf(-nf, kF32Ln2Lo, r);
+  const float y = 1.0f + (r + f32_expm1_poly(r, false));
+  const int n = (int)nf;
+  if (n >= -126 && n <= 127) return y * f32_pow2i(n);
+  if (n > 127) return (y * 2.0f) * f32_pow2i(n - 1);
+  return (y * f32_pow2i(n + 100)) * 0x1p-100f;
+}
+
+// cos(2 pi u) for u in [0, 1]
+__device__ __forceinline__ float f32_cos2pi(float u) {
+  const float v = 4.0f * u;
+  const float qf = rintf(v);
+  const float t = v - qf;  // exact, |t| <= 1/2
+  const float z = t * t;
+  const int q = (int)qf & 3;
+  if (q & 1) {  // -/+ sin(t pi / 2)
+    float p = fmaf(z, kF32S9, kF32S7);
+    p = fmaf(p, z, kF32S5);
+    p = fmaf(p, z, kF32S3);
+    const float sn = fmaf(t, kF32PiO2Hi, fmaf(t * z, p, t * kF32PiO2Lo));
+    return q == 1 ? -sn : sn;
+  }
+  float p = fmaf(z, kF32C10, kF32C8);
+  p = fmaf(p, z, kF32C6);
+  p = fmaf(p, z, kF32C4);
+  p = fmaf(p, z, kF32C2);
+  const float cs = fmaf(z, p, 1.0f);
+  return q == 0 ? cs : -cs;
+}
+
+__device__ __forceinline__ float f32_log1p(float x) {
+  if (!(x > -1.0f)) return x == -1.0f ? -INFINITY : __int_as_float(0x7fc00000);
+  if (x == INFINITY) return x;
+  if (x >= -0x1.2bec34p-2f && x <= 0x1.a8279ap-2f) return f32_log1p_core(x);
+  const float u = 1.0f + x;
+  // the rounding error of 1 + x (exact: the larger operand first), over u
+  const float c = (x > 1.0f ? 1.0f - (u - x) : x - (u - 1.0f)) / u;
+  const int iu = __float_as_int(u);
+  const int mb = iu & 0x007fffff;
+  int e = (iu >> 23) - 127;
+  float m;
+  if (mb > 0x3504f3) {
+    m = __int_as_float(mb | (126 << 23));
+    e += 1;
+  } else {
+    m = __int_as_float(mb | (127 << 23));
+  }
+  return f32_add_eln2(e, f32_log1p_core(m - 1.0f) + c);
+}
+
+__device__ __forceinline__ float f32_expm1(float x) {
+  if (x != x) return x;
+  if (x > 89.0f) return INFINITY;
+  if (x < -104.0f) return -1.0f;
+  if (fabsf(x) < 0x1.62e430p-2f) return x + f32_expm1_poly(x, true);  // |x| < ln 2 / 2
+  const float nf = rintf(x * kF32InvLn2);
+  float r = fmaf(-nf, kF32Ln2Hi, x);
+  r = fmaf(-nf, kF32Ln2Lo, r);
+  const float em = r + f32_expm1_poly(r, true);
+  const int n = (int)nf;
+  if (n > 127) return (em + 1.0f) * 2.0f * f32_pow2i(n - 1);
+  const float two = f32_pow2i(n < -126 ? -126 : n);
+  return fmaf(two, em, two - 1.0f);
+}
+
+// ---- precision-overloaded math (IEEE library calls in FP64, the functions
+// above in FP32; no fast-math) ----
 __device__ __forceinline__ double m_log(double x) { return log(x); }
-__device__ __forceinline__ float m_log(float x) { return logf(x); }
-__device__ __forceinline__ double m_exp(double x) { return exp(x); }
-__device__ __forceinline__ float m_exp(float x) { return expf(x); }
-__device__ __forceinline__ double m_cos(double x) { return cos(x); }
-__device__ __forceinline__ float m_cos(float x) { return cosf(x); }
+__device__ __forceinline__ float m_log(float x) { return f32_log(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_fma(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float m_fma(float a, float b, float c) { return fmaf(a, b, c); }
-__device__ __forceinline__ double m_lgamma(double x) { return lgamma(x); }
-__device__ __forceinline__ float m_lgamma(float x) { return lgammaf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_fabs(double x) { return fabs(x); }
 __device__ __forceinline__ float m_fabs(float x) { return fabsf(x); }
+// cos(2 pi u), the Box-Muller angle
+__device__ __forceinline__ double cos_2pi(double u) { return cos(kTwoPi * u); }
+__device__ __forceinline__ float cos_2pi(float u) { return f32_cos2pi(u); }
 
 // Logarithm / exponential used by the samplers: FP64 through the tables,
-// FP32 through the IEEE single-precision library.
+// FP32 through the single-precision functions above.
 __device__ __forceinline__ double lg(double x, const Stream& s) { return tang_log(x, s.tab); }
-__device__ __forceinline__ float lg(float x, const Stream&) { return logf(x); }
+__device__ __forceinline__ float lg(float x, const Stream&) { return f32_log(x); }
 __device__ __forceinline__ double ex(double x, const Stream& s) { return tang_exp(x, s.tab); }
-__device__ __forceinline__ float ex(float x, const Stream&) { return expf(x); }
+__device__ __forceinline__ float ex(float x, const Stream&) { return f32_exp(x); }
 
 template <typename R>
 struct C;
@@ -516,7 +680,7 @@ __device__ __forceinline__ double log_first_uniform(const Block4& b, const Strea
   return log_unif53(((unsigned long long)b.w1 << 32) | b.w0, s.tab);
 }
 __device__ __forceinline__ float log_first_uniform(const Block4& b, const Stream&, float) {
-  return logf(Unif<float>::first(b));
+  return f32_log(Unif<float>::first(b));
 }
 
 template <typename R>
@@ -524,7 +688,7 @@ __device__ __forceinline__ R normal01(Stream& s) {
   const Block4 b = s.next();
   const R u2 = Unif<R>::second(b);
   const R rad = m_sqrt((R)-2.0 * log_first_uniform(b, s, (R)0));
-  return rad * m_cos(C<R>::two_pi * u2);
+  return rad * cos_2pi(u2);
 }
 
 // -ln u of the next uniform (FP64: straight from its random bits)
@@ -537,7 +701,7 @@ __device__ __forceinline__ double neg_log_uniform<double>(Stream& s) {
 }
 template <>
 __device__ __forceinline__ float neg_log_uniform<float>(Stream& s) {
-  return -logf(uniform01<float>(s));
+  return -f32_log(uniform01<float>(s));
 }
 
 // Exponential(rate): -ln(u) / rate
@@ -573,6 +737,20 @@ __device__ __forceinline__ bool bernoulli(Stream& s, R p) {
   return gt_nonneg(p, uniform01<R>(s));  // u < p; a negative p is never above u
 }
 
+// log k! for the Poisson rejection test: FP64 through the library's lgamma,
+// FP32 from the math table's FP64 log k! rounded to float below 32 and
+// Stirling's series in float operations above (x = k + 1:
+// (x - 1/2) log x - x + log(2 pi)/2 + 1/(12x) - 1/(360x^3) + 1/(1260x^5)).
+__device__ __forceinline__ float f32_lfact(int k, const MathTab* __restrict__ T) {
+  if (k < 32) return (float)__ldg(&T->lfact[k < 0 ? 0 : k]);
+  const float x = (float)k + 1.0f;
+  const float ix = 1.0f / x, ix2 = ix * ix;
+  const float series = ix * (kF32Inv12 - ix2 * (kF32Inv360 - ix2 * kF32Inv1260));
+  return (((x - 0.5f) * f32_log(x) - x) + kF32HalfLog2Pi) + series;
+}
+__device__ __forceinline__ double log_fact(double k, const MathTab*) { return lgamma(k + 1.0); }
+__device__ __forceinline__ float log_fact(float k, const MathTab* T) { return f32_lfact((int)k, T); }
+
 // Poisson(mean): sequential-search inversion below 10 (one uniform, at most
 // 200 terms); Hormann's transformed rejection with squeeze (PTRS, 1993) from
 // 10 up, one block per trial, at most 1000 trials.
@@ -585,7 +763,7 @@ __device__ __noinline__ int poisson(Stream& s, R mean) {
     if constexpr (sizeof(R) == 8)
       p = exp_neg_int(mean, s.tab);  // integer pipes: off the FP64 pipe
     else
-      p = expf(-mean);
+      p = f32_exp(-mean);
     R acc = p;
     while (gt_nonneg(u, acc) && k < 200) {
       k += 1;
@@ -612,7 +790,7 @@ __device__ __noinline__ int poisson(Stream& s, R mean) {
     if (us >= (R)0.07 && V <= vr) return (int)kr;
     if (kr < (R)0.0 || (us < (R)0.013 && V > us)) continue;
     if (m_log(V) + m_log(invalpha) - m_log(a / (us * us) + b) <=
-        -mean + kr * loglam - m_lgamma(kr + (R)1.0))
+        -mean + kr * loglam - log_fact(kr, s.tab))
       return (int)kr;
   }
   return (int)m_floor(mean);
@@ -732,9 +910,9 @@ __device__ __forceinline__ R binomial_logpmf(int y, int z, R rho, const Stream& 
 
 // ---- predictive draws of the delayed-sampling CRBD (Section 6.3) ----
 __device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
-__device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ float m_log1p(float x) { return f32_log1p(x); }
 __device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
-__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ float m_expm1(float x) { return f32_expm1(x); }
 
 // Exponential(mu) with mu ~ Gamma(alpha, rate beta) integrated out (Lomax):
 // P(x > t) = (beta / (beta + t))^alpha; by inversion of one uniform,
@@ -762,8 +940,9 @@ __device__ __forceinline__ R lomax(Stream& s, R alpha, R beta) {
 // lambda' = Gamma(alpha, 1) / beta (alpha >= 1), then Poisson(lambda' tau).
 template <typename R>
 __device__ __noinline__ int neg_binomial(Stream& s, R alpha, R beta, R tau) {
-  const R r = tau / beta;  // one division for the mean and P(0)
-  const R mean = alpha * r;
+  const R r = tau / beta;
+  // FP64: one division for the mean and P(0); FP32: the mean as (alpha tau) / beta
+  const R mean = sizeof(R) == 8 ? alpha * r : alpha * tau / beta;
   if (mean < (R)10.0) {
     const R u = uniform01<R>(s);
     const R l0 = alpha * m_log1p(r);
@@ -771,7 +950,7 @@ __device__ __noinline__ int neg_binomial(Stream& s, R alpha, R beta, R tau) {
     if constexpr (sizeof(R) == 8)
       pk = exp_neg_int(l0, s.tab);  // integer pipes
     else
-      pk = expf(-l0);
+      pk = f32_exp(-l0);
     R acc = pk;
     if (!gt_nonneg(u, acc)) return 0;  // n = 0: q is not needed
     const R q = tau / (beta + tau);

@@ -283,7 +283,7 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   }
   Stream s{A.k0, A.k1, (uint32_t)i, (uint32_t)k, 0u, 0u, A.md.tab};
   const bool active = valid && L.pc != PC_STOP;
-  run_segment<M>(L, s, A.md, Sn, i, k, N, active);
+  const int n_exec = run_segment<M>(L, s, A.md, Sn, i, k, N, active);
   double lw = -INFINITY;
   int alive = 0;
   if (valid) {
@@ -294,6 +294,9 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   }
   warp_add_u64(&rs->n_overflow, active ? (unsigned long long)L.overflow : 0ull);
   warp_add_u64(&rs->n_limit, active ? (unsigned long long)L.limited : 0ull);
+  // work counters: Philox blocks of the model's draw stream and blocks executed
+  warp_add_u64(&rs->n_draws, valid ? (unsigned long long)s.d : 0ull);
+  warp_add_u64(&rs->n_blocks, (unsigned long long)n_exec);
   // Weights, first per warp as soon as the warp's particles reached the
   // checkpoint (overlapping the tile's slower warps): the warp's max M_w, its
   // power-of-two reference k_w = ceil(M_w / ln 2), and e_j = exp(logw_j - k_w
@@ -831,6 +834,8 @@ smc_status collect_run(const smc_model_s* m, const smc_run_cfg* c, const Layout&
   ct.n_near_boundary = (int64_t)hrs.n_near;
   ct.n_overflow = (int64_t)hrs.n_overflow;
   ct.n_limit = (int64_t)hrs.n_limit;
+  ct.n_draws = (int64_t)hrs.n_draws;
+  ct.n_blocks = (int64_t)hrs.n_blocks;
   int st = hrs.status;
   if (st == 0 && !hrs.done) st = SMC_ESTEPLIMIT;
   if (st == 0 && (hrs.n_overflow || hrs.n_limit)) st = SMC_WKILLED;

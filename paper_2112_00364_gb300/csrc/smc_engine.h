@@ -25,6 +25,7 @@ struct RunState {
   unsigned long long d_hi, d_lo, z0_hi, z0_lo;
   long long tolZ;
   unsigned long long n_near, n_overflow, n_limit;
+  unsigned long long n_draws, n_blocks;  // Philox blocks drawn by the model, blocks executed
   int32_t done, status, n_segments, n_resamples;
   uint32_t arrive;
   int32_t kmax, G;        // the run's reference exponent and coarsening (one-CTA combine)

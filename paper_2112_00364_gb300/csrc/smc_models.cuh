@@ -660,10 +660,11 @@ struct TreeDsModel {
 // its segment, pick the block index shared by the most such lanes (ties to
 // the larger index) and run that block on exactly those lanes.  The choice
 // is warp-uniform, so every block body runs without intra-warp divergence
-// on its block index.
+// on its block index.  Returns the number of blocks this lane executed.
 template <class M>
-__device__ __forceinline__ void run_segment(typename M::Lane& L, Stream& s, const ModelDev& md,
-                                            const StateView& S, int i, int k, int N, bool active) {
+__device__ __forceinline__ int run_segment(typename M::Lane& L, Stream& s, const ModelDev& md,
+                                           const StateView& S, int i, int k, int N, bool active) {
+  int n_exec = 0;
   if (active) M::begin(L);
   for (;;) {
     const unsigned act = __ballot_sync(0xffffffffu, active);
@@ -678,9 +679,11 @@ __device__ __forceinline__ void run_segment(typename M::Lane& L, Stream& s, cons
     }
     if (active && L.pc == sel) {
       M::block(sel, L, s, md, S, i, k, N);
+      n_exec += 1;
       if (L.ckpt) active = false;
     }
   }
+  return n_exec;
 }
 
 }  // namespace smc

@@ -477,7 +477,18 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
       y[i] = __longlong_as_double(
           weight_fix52<50>(v, 0ll, tab->exp2_neg64_q63, tab->exp2_neg4096_q63));
       break;
-    default: y[i] = exp_neg_int(v, tab); break;
+    case 10: y[i] = exp_neg_int(v, tab); break;
+    case 11: y[i] = (double)f32_log((float)v); break;
+    case 12: y[i] = (double)f32_exp((float)v); break;
+    case 13: y[i] = (double)f32_cos2pi((float)v); break;
+    case 14: y[i] = (double)f32_log1p((float)v); break;
+    case 15: y[i] = (double)f32_expm1((float)v); break;
+    case 16: y[i] = (double)f32_lfact((int)v, tab); break;
+    case 17: y[i] = (double)logf((float)v); break;
+    case 18: y[i] = (double)expf((float)v); break;
+    case 19: y[i] = (double)cospif(2.0f * (float)v); break;
+    case 20: y[i] = (double)log1pf((float)v); break;
+    default: y[i] = (double)expm1f((float)v); break;
   }
 }
 
@@ -486,7 +497,7 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
 using namespace smc;
 
 extern "C" smc_status smc_math_eval(int32_t fn, const double* x, double* y, int64_t n, void* stream) {
-  if (!x || !y || n < 0 || fn < 0 || fn > 10) return set_error(SMC_EINVAL, "bad argument");
+  if (!x || !y || n < 0 || fn < 0 || fn > 21) return set_error(SMC_EINVAL, "bad argument");
   if (n == 0) return SMC_OK;
   const MathTab* tab = nullptr;
   smc_status ts = math_table(&tab);
@@ -601,6 +612,8 @@ std::mutex g_static_mu;
 double* g_static_ptr[128] = {nullptr};  // device address of the array, per device
 
 // Once per device, with that device current: resolve the array's device address.
+// (The math tables are uploaded by math_table() on the first call of the library
+// on a device that needs them, which may be this entry point's first call.)
 smc_status static_scratch(double** out) {
   int dev = -1;
   SMC_CUDA_TRY(cudaGetDevice(&dev));

@@ -21,6 +21,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -37,7 +38,7 @@ namespace smc {
 
 // Snapshot of a run's state after a wave: everything retiring it needs.
 struct RunFlags {
-  unsigned long long n_near, n_overflow, n_limit;
+  unsigned long long n_near, n_overflow, n_limit, n_draws, n_blocks;
   int32_t done, status, n_segments, n_resamples, n_ess_near, pad;
 };
 
@@ -55,6 +56,8 @@ __global__ void gather_flags_kernel(const RunDev* __restrict__ runs, int n, RunF
   f.n_near = rs->n_near;
   f.n_overflow = rs->n_overflow;
   f.n_limit = rs->n_limit;
+  f.n_draws = rs->n_draws;
+  f.n_blocks = rs->n_blocks;
   out[i] = f;
 }
 
@@ -123,6 +126,9 @@ struct Server {
   std::atomic<int64_t> waves{0}, completed{0}, particle_steps{0};
   std::atomic<int32_t> n_resident{0}, n_queued{0};
   std::atomic<int32_t> worker_error{0};
+  // host-side fault injection for tests: the retirement of this ticket fails
+  // after its result copies were queued (0 = off; SMC_SERVER_FAIL_TICKET)
+  uint64_t fail_ticket = 0;
 };
 
 namespace {
@@ -186,6 +192,22 @@ void finish_ticket(Server* S, Request* q, int status) {
   S->final_status[q->ticket] = status;
   S->latency[q->ticket] = now_s() - q->t_submit;
   S->cv_done.notify_all();
+}
+
+// A request taken out of the resident list whose retirement failed (its result
+// copies, its completion event or its workspace release): wait until the copies
+// already queued into its result buffers have ended, release its workspace and
+// close its ticket as failed, so that a waiter never sees the ticket done while
+// copies into its buffers are still in flight, and none is left to time out.
+void fail_retiring(Server* S, Request* q, smc_status st) {
+  cudaStreamSynchronize(S->stream);
+  if (q->done_ev) cudaEventDestroy(q->done_ev);
+  q->done_ev = nullptr;
+  if (q->ws) cudaFreeAsync(q->ws, S->stream);
+  S->in_use -= q->bytes;
+  finish_ticket(S, q, st);
+  S->completed += 1;
+  delete q;
 }
 
 // Admit queued requests that fit.  Returns the number admitted.
@@ -275,18 +297,26 @@ smc_status retire(Server* S, int b) {
     hrs.n_near = f[i].n_near;
     hrs.n_overflow = f[i].n_overflow;
     hrs.n_limit = f[i].n_limit;
+    hrs.n_draws = f[i].n_draws;
+    hrs.n_blocks = f[i].n_blocks;
     smc_status st = collect_run(q->model, &q->cfg, q->ly, q->ws, q->dev, hrs, q->result, S->stream);
-    if (st) {  // out of the resident list already: free it and close its ticket here
-      cudaFreeAsync(q->ws, S->stream);  // stream-ordered after the waves that used it
-      S->in_use -= q->bytes;
-      finish_ticket(S, q, st);
-      delete q;
-      return st;
+    if (!st && q->ticket == S->fail_ticket)
+      st = set_error(SMC_ECUDA, "injected failure retiring ticket %llu (SMC_SERVER_FAIL_TICKET)",
+                     (unsigned long long)q->ticket);
+    if (!st) {
+      if (q->cancel) q->result->counters.status = SMC_ECANCELLED;
+      cudaError_t e = cudaEventCreateWithFlags(&q->done_ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(q->done_ev, S->stream);
+      if (e == cudaSuccess) {
+        e = cudaFreeAsync(q->ws, S->stream);  // stream-ordered after the copies
+        if (e == cudaSuccess) q->ws = nullptr;
+      }
+      if (e != cudaSuccess) st = cuda_fail(e, "retiring a finished run");
     }
-    if (q->cancel) q->result->counters.status = SMC_ECANCELLED;
-    SMC_CUDA_TRY(cudaEventCreateWithFlags(&q->done_ev, cudaEventDisableTiming));
-    SMC_CUDA_TRY(cudaEventRecord(q->done_ev, S->stream));
-    SMC_CUDA_TRY(cudaFreeAsync(q->ws, S->stream));
+    if (st) {  // this request alone fails; the other runs go on
+      fail_retiring(S, q, st);
+      continue;
+    }
     S->in_use -= q->bytes;
     S->completing.push_back(q);
     S->particle_steps += (int64_t)q->dev.N * hrs.n_segments;
@@ -421,6 +451,8 @@ extern "C" smc_status smc_server_create(size_t device_mem_budget, const smc_serv
     delete h;
     return cuda_fail(e, "server setup");
   }
+  if (const char* inj = std::getenv("SMC_SERVER_FAIL_TICKET"))
+    S->fail_ticket = std::strtoull(inj, nullptr, 10);
   if (S->cfg.max_resident_runs <= 0) S->cfg.max_resident_runs = 4096;
   if (S->cfg.poll_waves <= 0) S->cfg.poll_waves = 2;
   smc_status fs = alloc_flags(S, S->cfg.max_resident_runs);

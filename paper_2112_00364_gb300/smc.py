@@ -71,7 +71,8 @@ class Counters(C.Structure):
     _fields_ = [("n_segments", C.c_int32), ("n_resamples", C.c_int32),
                 ("n_near_boundary", C.c_int64), ("n_overflow", C.c_int64),
                 ("n_limit", C.c_int64), ("device_ms", C.c_double), ("kernel_ms", C.c_double),
-                ("kernel_launches", C.c_int32), ("n_ess_near", C.c_int32), ("status", C.c_int32)]
+                ("kernel_launches", C.c_int32), ("n_ess_near", C.c_int32), ("status", C.c_int32),
+                ("pad2_", C.c_int32), ("n_draws", C.c_int64), ("n_blocks", C.c_int64)]
 
 
 class Result(C.Structure):
@@ -296,7 +297,7 @@ def _result_dict(st: int, r: Result, out: dict, where: str, record_all: bool) ->
                n_resamples=c.n_resamples, n_near_boundary=c.n_near_boundary,
                n_overflow=c.n_overflow, n_limit=c.n_limit, device_ms=c.device_ms,
                kernel_ms=c.kernel_ms, kernel_launches=c.kernel_launches, n_ess_near=c.n_ess_near,
-               **out)
+               n_draws=c.n_draws, n_blocks=c.n_blocks, **out)
     res["log_z_value"] = float(out["log_z"][0]) if where == "host" else None
     if record_all:
         n_tr = max(0, c.n_segments - 1)  # checkpoints after which the run went on
@@ -491,7 +492,11 @@ def math_eval(fn: str, x):
 
     code = {"table_log": 0, "table_exp": 1, "lib_log": 2, "lib_exp": 3, "unif_log_bits": 4,
             "unif_log_table": 5, "exp_fix54": 6, "table_exp_fix54": 7, "exp2t_fix54": 8,
-            "exp2t_fix50": 9, "exp_neg_int": 10}[fn]
+            "exp2t_fix50": 9, "exp_neg_int": 10,
+            # the FP32 mode's own single-precision functions, and CUDA's for comparison
+            "f32_log": 11, "f32_exp": 12, "f32_cos2pi": 13, "f32_log1p": 14, "f32_expm1": 15,
+            "f32_lfact": 16, "cuda_logf": 17, "cuda_expf": 18, "cuda_cos2pif": 19,
+            "cuda_log1pf": 20, "cuda_expm1f": 21}[fn]
     if code in (4, 5):
         x = np.ascontiguousarray(x, dtype=np.uint64).view(np.float64)
     xd = torch.as_tensor(x, dtype=torch.float64).cuda()

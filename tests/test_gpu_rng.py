@@ -49,23 +49,67 @@ def test_variates_fp64(dist, p1, p2):
 
 @pytest.mark.parametrize("dist,p1,p2", [("uniform", 0, 0), ("uniform_ab", -1.0, 3.0),
                                         ("bernoulli", 0.3, 0), ("exponential", 2.5, 0),
-                                        ("normal", 1.5, 2.0), ("poisson", 3.0, 0),
-                                        ("poisson", 50.0, 0)])
-def test_variates_fp32(dist, p1, p2):
+                                        ("gamma1", 0.5, 0), ("normal", 1.5, 2.0),
+                                        ("lognormal", 0.3, 0), ("poisson", 3.0, 0),
+                                        ("poisson", 9.99, 0), ("poisson", 10.0, 0),
+                                        ("poisson", 50.0, 0), ("poisson", 3000.0, 0),
+                                        ("binomial", 40, 0.1), ("binomial", 7370, 0.3),
+                                        ("binomial", 200, 0.9), ("beta", 1.45, 2.55),
+                                        ("gamma", 3.5, 0), ("neg_binomial", 2.0, 1.5),
+                                        ("neg_binomial", 30.0, 2.0), ("lomax", 3.0, 1.5)])
+def test_variates_fp32_bit_exact(dist, p1, p2):
+    """In FP32 mode the GPU's samplers and the oracle's perform the same
+    single-precision operations (the mode's own log / exp / cos(2 pi u) / log1p
+    / expm1 / log k! included), so every variate and every count of Philox
+    blocks consumed is identical, bit for bit."""
     from paper_2112_00364_gb300 import smc
 
     n = 200_000
-    g, _ = smc.sample(dist, n, p1, p2, seed=22, precision="fp32")
-    g = g.cpu().numpy()
-    o = oracle.sample(dist, n, p1, p2, seed=22, precision=oracle.FP32)
-    if dist in ("uniform", "uniform_ab", "bernoulli"):
-        np.testing.assert_array_equal(g, o)
-    elif dist == "poisson":
-        assert np.mean(g != o) < 2e-3
+    g, gb = smc.sample(dist, n, p1, p2, seed=22, precision="fp32")
+    o, ob = oracle.sample(dist, n, p1, p2, seed=22, precision=oracle.FP32, return_blocks=True)
+    np.testing.assert_array_equal(g.cpu().numpy(), o)
+    np.testing.assert_array_equal(gb.cpu().numpy(), ob)
+
+
+def _f32_grid():
+    return (np.arange(1 << 23, dtype=np.float64) * 2.0 + 1.0) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("fn", ["log", "exp", "cos2pi", "log1p", "expm1", "lfact"])
+def test_fp32_functions_bit_exact_and_near_cuda(fn):
+    """The FP32 mode's own functions on the GPU equal the oracle's bit for bit
+    (exhaustively over the FP32 uniform grid for log and cos(2 pi u), on wide
+    random samples otherwise) and stay within 2 ulp of CUDA's logf / expf /
+    cospif / log1pf / expm1f."""
+    from paper_2112_00364_gb300 import smc
+
+    rng = np.random.default_rng(31)
+    if fn in ("log", "cos2pi"):
+        x = np.concatenate([_f32_grid(), np.exp(rng.uniform(-100, 88, 1_000_000)), [1.0, 2.0]])
+        if fn == "cos2pi":
+            x = np.concatenate([_f32_grid(), rng.random(100_000), [0.0, 0.25, 0.5, 0.75, 1.0]])
+    elif fn == "exp":
+        x = np.concatenate([rng.uniform(-104, 89, 2_000_000), rng.uniform(-1e-3, 1e-3, 10_000),
+                            [0.0, 88.7, -87.3, -103.9]])
+    elif fn == "log1p":
+        x = np.concatenate([rng.uniform(-0.999, 2.0, 1_000_000), np.exp(rng.uniform(-40, 30, 500_000))])
+    elif fn == "expm1":
+        x = np.concatenate([rng.uniform(-5, 5, 1_000_000), rng.uniform(0, 88, 500_000),
+                            rng.uniform(-1e-3, 1e-3, 10_000)])
     else:
-        # CUDA's single-precision logf/cosf/expf are within 1-2 ulp of glibc's
-        scale = max(abs(p1), abs(p2), 1.0)
-        np.testing.assert_allclose(g, o, rtol=2e-6, atol=1e-6 * scale)
+        x = np.arange(0, 300_000, dtype=np.float64)
+    x = x.astype(np.float32).astype(np.float64)
+    g = smc.math_eval("f32_" + fn, x)
+    np.testing.assert_array_equal(g, oracle.mathf(fn, x))
+    if fn != "lfact":
+        c = smc.math_eval("cuda_" + {"cos2pi": "cos2pif"}.get(fn, fn + "f"), x)
+        ok = np.isfinite(c) & (np.abs(c) > 1e-30)
+        ia = g[ok].astype(np.float32).view(np.int32).astype(np.int64)
+        ib = c[ok].astype(np.float32).view(np.int32).astype(np.int64)
+        if fn == "cos2pi":  # near the zeros of cos compare in absolute terms
+            assert np.abs(g - c).max() <= 2 * 2.0 ** -24
+        else:
+            assert np.abs(ia - ib).max() <= 2
 
 
 def _ulp_diff(a, b):

@@ -175,3 +175,70 @@ def test_server_every_model_kind_and_ess():
             np.testing.assert_array_equal(g["stack"], a["stack"])
     for m, _, _ in cases:
         m.close()
+
+
+def test_server_failed_retirement_fails_only_that_request(monkeypatch):
+    """A request whose retirement fails after its result copies were queued
+    (injected on the host through SMC_SERVER_FAIL_TICKET) completes at once with
+    the error; every other request completes with its standalone result, the
+    worker keeps running and no run stays resident."""
+    from paper_2112_00364_gb300 import smc
+
+    reqs = _requests(6, seed=13)
+    monkeypatch.setenv("SMC_SERVER_FAIL_TICKET", "3")
+    srv = smc.Server(4096 << 20)
+    monkeypatch.delenv("SMC_SERVER_FAIL_TICKET")
+    tickets = [srv.submit(m, N, seed, run_id=rid) for m, N, seed, rid in reqs]
+    assert tickets[2] == 3
+    t0 = time.perf_counter()
+    got = [srv.wait(t, timeout=120.0) for t in tickets]
+    assert time.perf_counter() - t0 < 60.0
+    st = srv.stats()
+    srv.close()
+    assert got[2]["status"] == smc.ECUDA
+    assert st["worker_status"] == 0 and st["resident"] == 0 and st["completed"] == len(reqs)
+    for q, ((m, N, seed, rid), g) in enumerate(zip(reqs, got)):
+        if q != 2:
+            _same(g, smc.run(m, N, seed, run_id=rid))
+        m.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_served_results_equal_the_oracle(precision):
+    """Served results checked against the oracle itself (not only against
+    smc_run): twelve requests of the serving benchmark's mix (the smallest of
+    its linear-Gaussian and CRBD sizes, so that the oracle finishes quickly),
+    submitted together so that they share waves, each with every resampling's
+    ancestors recorded; each result equals the oracle in follow mode element by
+    element (bit for bit in FP32, to FP64 rounding in FP64)."""
+    import oracle
+    from parity import assert_parity_exact, assert_parity_fp64
+
+    from paper_2112_00364_gb300 import smc
+
+    specs = inputs.batch_specs(512, seed=4)
+    sizes = np.array([sp.n_particles * sp.n_segments() for sp in specs])
+    order = [int(q) for q in np.argsort(sizes)]
+    pick = [q for q in order if specs[q].kind == "lg"][:6] + \
+        [q for q in order if specs[q].kind == "crbd"][:6]
+    srv = smc.Server(4096 << 20, precision=precision)
+    reqs = []
+    for q in pick:
+        sp = specs[q]
+        p = (dict(obs=inputs.lg_observations(sp.T, seed=sp.obs_seed)) if sp.kind == "lg"
+             else dict(tree=inputs.yule_tree(sp.tips, seed=sp.tree_seed)))
+        m = smc.Model(sp.kind, **p)
+        t = srv.submit(m, sp.n_particles, 1 + sp.seed, run_id=q, record_all_ancestors=True)
+        reqs.append((sp, p, m, t, q))
+    got = [srv.wait(t) for _, _, _, t, _ in reqs]
+    srv.close()
+    for (sp, p, m, _, q), g in zip(reqs, got):
+        g["status"] = g["run_status"]
+        o = oracle.smc_run(sp.kind, sp.n_particles, 1 + sp.seed, run_id=q,
+                           precision=oracle.FP32 if precision == "fp32" else oracle.FP64,
+                           follow=g["ancestors"], record_ancestors=True, **p)
+        if precision == "fp32":
+            assert_parity_exact(g, o)
+        else:
+            assert_parity_fp64(g, o)
+        m.close()

@@ -37,11 +37,11 @@ MUTANTS = [
      "uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c3;", 0),
     ("key_ignores_run_id", C_SRC, "key[1] = (uint32_t)(seed >> 32) ^ run_id;",
      "key[1] = (uint32_t)(seed >> 32);", 0),
-    ("fp32_uniform_bits", C_SRC, "return (float)((w[0] >> 8) | 1u) * 0x1p-24f; }",
-     "return (float)((w[0] >> 9) | 1u) * 0x1p-24f; }", 0),
+    ("fp32_uniform_bits", C_SRC, "return (float)((w[1] >> 8) | 1u) * 0x1p-24f; }",
+     "return (float)((w[1] >> 9) | 1u) * 0x1p-24f; }", 0),
     # variate recipes
-    ("box_muller_angle_from_u1", P_SRC, "return rad * COSR(TWO_PIR * u2);",
-     "return rad * COSR(TWO_PIR * u1);", 0),
+    ("box_muller_angle_from_u1", P_SRC, "return rad * COS2PIR(u2);",
+     "return rad * COS2PIR(u1);", 0),
     ("box_muller_radius", P_SRC, "R rad = SQRTR((R)-2.0 * LOGR(u1));",
      "R rad = SQRTR((R)-1.0 * LOGR(u1));", 0),
     ("exponential_times_rate", P_SRC, "return -LOGR(u) / rate;", "return -LOGR(u) * rate;", 0),
@@ -51,7 +51,25 @@ MUTANTS = [
     ("lognormal_shift_not_scale", P_SRC, "return EXPR(sigma * SFX(normal01)(s));",
      "return EXPR(sigma + SFX(normal01)(s));", 0),
     ("poisson_inversion_term", P_SRC, "p = p * mean / (R)k;", "p = p * mean / (R)(k + 1);", 0),
-    ("poisson_ptrs_log_factorial", P_SRC, "- LGAMMAR(kr + (R)1.0))", "- LGAMMAR(kr))", 0),
+    ("poisson_ptrs_log_factorial", P_SRC, "- LFACTR(kr))", "- LFACTR(kr - (R)1.0))", 0),
+    # the FP32 mode's own elementary functions
+    ("fp32_fn_log_series_coef", C_SRC, "R = fmaf(R, z, 0x1.99999ap-2f /* 2/5 */);",
+     "R = fmaf(R, z, 0x1.24924ap-2f /* 2/5 */);", 0),
+    ("fp32_fn_log_drops_ln2_lo", C_SRC, "const float lo = fmaf(fe, F_LN2_LO, l);",
+     "const float lo = l;", 0),
+    ("fp32_fn_log_no_halving", C_SRC, "    *e += 1;\n    return f_bits_to_float(frac | (126u << 23));",
+     "    return f_bits_to_float(frac | (126u << 23));", 0),
+    ("fp32_fn_exp_tail_coef", C_SRC, "q = fmaf(q, r, 0x1.555556p-3f);  /* 1/3! */",
+     "q = fmaf(q, r, 0x1.555556p-5f);  /* 1/3! */", 0),
+    ("fp32_fn_exp_scale", C_SRC, "  return y * f_pow2(n);", "  return y * f_pow2(n + 1);", 0),
+    ("fp32_fn_cos2pi_quadrant_sign", C_SRC, "return quad == 1 ? -sv : sv;",
+     "return quad == 1 ? sv : -sv;", 0),
+    ("fp32_fn_cos2pi_series_coef", C_SRC, "c = fmaf(c, z, 0x1.03c1f0p-2f);",
+     "c = fmaf(c, z, 0x1.03c1f0p-3f);", 0),
+    ("fp32_fn_expm1_small_branch", C_SRC, "return x + f_exp_tail(x, 1);",
+     "return f_exp_tail(x, 1);", 0),
+    ("fp32_fn_lfact_half", C_SRC, "const float a = (x - 0.5f) * orc_logf(x);",
+     "const float a = (x + 0.5f) * orc_logf(x);", 0),
     ("poisson_ptrs_shift", P_SRC, "U + mean + (R)0.43);", "U + mean + (R)1.43);", 0),
     ("gamma_mt_d", P_SRC, "const R d = shape - (R)1.0 / (R)3.0;",
      "const R d = shape - (R)1.0 / (R)2.0;", 0),
@@ -104,7 +122,8 @@ MUTANTS = [
     ("crbd_correction_tips", C_SRC, "mc->corr = (double)(tips - 1) * LN2_D - lnfact;",
      "mc->corr = (double)(tips) * LN2_D - lnfact;", 0),
     ("crbd_survival_uses_lambda", P_SRC, "R lnp1 = -P->mu * dt;", "R lnp1 = -P->lam * dt;", 0),
-    ("crbd_tip_drops_rho", P_SRC, ": LOGR((R)m->rho);", ": (R)0.0;", 0),
+    ("crbd_tip_drops_rho", P_SRC, ": (R)log(m->rho); /* log rho: a run constant */",
+     ": (R)0.0;", 0),
     ("crbd_hidden_lifetime_rate", P_SRC, "R dur = SFX(exponential)(&c->s, c->mu);",
      "R dur = SFX(exponential)(&c->s, c->lam);", 0),
     ("crbd_hidden_detection_test", P_SRC, "if (dur > t) {", "if (dur < t) {", 0),
@@ -148,7 +167,7 @@ MUTANTS = [
     ("ds_hidden_detection_test", P_SRC, "if (dur > t) {", "if (dur < t) {", 1),
     ("ds_branch_drops_ln2", P_SRC, "acc = acc + LN2R;", "acc = acc;", 1),
     ("ds_hidden_event_window", P_SRC, "R lo = t - bl;", "R lo = (R)0.0;", 1),
-    ("ds_tip_drops_rho", P_SRC, "lnp2 = LOGR((R)m->rho);", "lnp2 = (R)0.0;", 0),
+    ("ds_tip_drops_rho", P_SRC, "lnp2 = (R)log(m->rho);", "lnp2 = (R)0.0;", 0),
     ("ds_drops_correction", P_SRC, "P->logw = P->logw + (R)mc->corr;", "P->logw = P->logw;", 1),
     ("ds_skips_last_node", P_SRC, "P->pc = ((int32_t)k + 1 == m->n_nodes) ? PC_STOP : 1;",
      "P->pc = ((int32_t)k + 2 >= m->n_nodes) ? PC_STOP : 1;", 1),
@@ -222,6 +241,7 @@ def _in(f: str, *tests: str) -> list[str]:
 AREA_FIRST = [
     (("philox_", "box_muller_", "exponential_", "gamma1_", "uniform_ab_", "bernoulli_",
       "poisson_", "key_", "fp32_uniform_", "lognormal_"), _in("test_oracle_rng.py")),
+    (("fp32_fn_",), _in("test_oracle_mathf.py")),
     (("gamma_mt_", "beta_", "binomial_"), _in("test_oracle_seir.py")),
     (("log_factorial_", "seir_"),
      _in("test_oracle_seir.py", "test_day_zero_draws", "test_one_day_transition_law",

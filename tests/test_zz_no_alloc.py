@@ -56,3 +56,25 @@ def test_static_rejects_populations_above_its_limit():
                                o3.data_ptr(), nn.data_ptr(), None)
     assert st == smc.EINVAL
     assert b"static scratch limit" in L.smc_last_error()
+
+
+def test_static_calls_leave_device_free_memory_unchanged():
+    """With caller-owned outputs, repeated calls allocate no device memory: the
+    device's free memory (cudaMemGetInfo) is the same before and after twenty
+    calls, once a first call has set up the device."""
+    import torch
+    from paper_2112_00364_gb300 import smc
+
+    N = 1_000_003
+    x = torch.from_numpy(inputs.random_logw(N, seed=11, scale=2.0)).cuda()
+    anc = torch.empty(N, dtype=torch.int32, device="cuda")
+    o3 = torch.empty(3, dtype=torch.float64, device="cuda")
+    nn = torch.empty(1, dtype=torch.int64, device="cuda")
+    smc.resample_static(x, 0.5, anc, o3, nn)  # first call on the device: set-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for k in range(20):
+        smc.resample_static(x, (k + 0.5) / 21, anc, o3, nn)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
