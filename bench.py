@@ -56,6 +56,10 @@ UNIT = "particle-steps/s"
 WORKLOADS = {
     "crbd64": dict(kind="crbd", tips=64, tree_seed=2, N=1 << 16, precision="fp64"),
     "lg": dict(kind="lg", T=50, obs_seed=1, N=1024, precision="fp64"),
+    # the same run with FP32 particles (the batched and served configurations' precision)
+    "lg_fp32": dict(kind="lg", T=50, obs_seed=1, N=1024, precision="fp32"),
+    # a small CRBD run (16 tiles of 32 particles), FP32 particles
+    "crbd_small": dict(kind="crbd", tips=32, tree_seed=2, N=512, precision="fp32"),
     # the vector-borne disease SEIR model (Section 6.2), 26 weeks of synthetic reports
     "seir182": dict(kind="seir", days=182, obs_seed=7, N=1 << 16, precision="fp64"),
     # CRBD with static delayed sampling and ESS-triggered resampling (Section 6.3),
@@ -73,7 +77,7 @@ WORKLOADS = {
                        precision="fp64"),
 }
 
-HBM_PEAK_GBS = 6778.0  # measured GB300 copy bandwidth (MEASURED_PEAKS.json)
+HBM_PEAK_GBS = 6800.0  # fallback HBM bandwidth when MEASURED_PEAKS.json is absent
 RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, per particle
 
 # Per particle-step counts of the segment kernel from one ncu capture of the
@@ -83,9 +87,9 @@ RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, 
 # plain CRBD (latency-bound, most arithmetic on the integer pipes), the FP64
 # rate for the delayed-sampling CRBD (FP64 pipe busy 36-44% of a launch).  The
 # traffic holds only for the kernel sources with the recorded digest.
-NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=102.2, fp64_flop_per_pstep=12.55,
-                      bytes_per_launch=3.35e6, fp64_pipe_elapsed=0.171,
-                      src_digest="11fe17bcc318e458"),
+NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=114.9, fp64_flop_per_pstep=18.8,
+                      bytes_per_launch=3.294e6, fp64_pipe_elapsed=0.188,
+                      src_digest="6b8867e3a8ee23a7"),
        "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=114.9, fp64_flop_per_pstep=170.6,
                           bytes_per_launch=5.76e6, fp64_pipe_elapsed=0.382,
                           src_digest="11fe17bcc318e458")}
@@ -97,8 +101,8 @@ ISSUE_PEAK = 152 * 4 * 2070e6
 
 
 # the segment kernel's sources (the standalone resampling kernels are not among them)
-KERNEL_SOURCES = ("smc_engine.cu", "smc_engine.h", "smc_models.cuh", "smc_device.cuh",
-                  "smc_combine.cuh")
+KERNEL_SOURCES = ("smc_engine.cu", "smc_step.cuh", "smc_engine.h", "smc_models.cuh",
+                  "smc_device.cuh", "smc_combine.cuh")
 # the standalone resampling kernels' sources
 RS_SOURCES = ("smc_prims.cu", "smc_device.cuh", "smc_combine.cuh")
 
@@ -117,12 +121,24 @@ def code_text(src: str) -> str:
     return " ".join(src.split())
 
 
+# Files that hold device and host code: only the part before the marker holds
+# what the segment kernel executes (the kernels and the structures they read).
+DEVICE_PART = {"smc_engine.cu": "// host side", "smc_engine.h": "struct Layout {"}
+
+
+def device_part(name: str, text: str) -> str:
+    mark = DEVICE_PART.get(name)
+    if mark and mark in text:
+        return text[: text.index(mark)]
+    return text
+
+
 def src_digest(sources=KERNEL_SOURCES, read=None) -> str:
-    """Digest of the code (comments and blank space stripped) of the sources."""
+    """Digest of the device code (comments and blank space stripped) of the sources."""
     read = read or (lambda name: (ROOT / "paper_2112_00364_gb300" / "csrc" / name).read_text())
     h = hashlib.sha256()
     for name in sources:
-        h.update(code_text(read(name)).encode())
+        h.update(code_text(device_part(name, read(name))).encode())
     return h.hexdigest()[:16]
 
 
@@ -410,8 +426,11 @@ def run_reference_resample(args, work: Work, ws: int) -> int:
     return 0
 
 
-def run_serve(args, work: Work, smc, torch, dist, ws: int, rank: int, local: int) -> int:
-    """Serve Poisson request streams through the continuous-batching server."""
+def serve_measure(steps: int, work: Work, smc, torch, dist, ws: int, local: int,
+                  with_cpu: bool = True, n_plain: int = 300) -> dict:
+    """Serve Poisson request streams through the continuous-batching server;
+    returns the measurements (throughput, p50/p99 latency, the plain
+    one-run-per-launch path on the first requests of the stream)."""
     w = work.w
     models = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
     srv = smc.Server(96 << 30, precision=work.precision)
@@ -447,11 +466,13 @@ def run_serve(args, work: Work, smc, torch, dist, ws: int, rank: int, local: int
             used.append((int(q), o))
             units += r["N"] * r["segments"]
             d2h += sum(t.numel() * t.element_size() for t in o.values())
-        lat = [srv.wait(t, timeout=600.0)["latency_s"] for t in tickets]
+        res = [srv.wait(t, timeout=600.0) for t in tickets]
         span = time.perf_counter() - t0
         for q, o in used:
             pool.setdefault(q, []).append(o)
-        return units, span, lat, len(arr), d2h
+        lat = [r_["latency_s"] for r_ in res]
+        lz = {(int(q), step): float(o["log_z"][0]) for (q, o) in used}
+        return units, span, lat, len(arr), d2h, lz
 
     stream_step(10_000, 0.2)  # warm-up
     torch.cuda.synchronize()
@@ -461,9 +482,12 @@ def run_serve(args, work: Work, smc, torch, dist, ws: int, rank: int, local: int
     if dist:
         dist.barrier()
     units, span, lats, nreq, d2h = 0, 0.0, [], 0, 0
-    for s in range(args.steps):
-        u, sp, la, n, b = stream_step(s, w["seconds_per_step"])
+    served_lz = {}
+    for s in range(steps):
+        u, sp, la, n, b, lz = stream_step(s, w["seconds_per_step"])
         units, span, lats, nreq, d2h = units + u, span + sp, lats + la, nreq + n, d2h + b
+        if s == 0:
+            served_lz = lz
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -471,46 +495,70 @@ def run_serve(args, work: Work, smc, torch, dist, ws: int, rank: int, local: int
     st = srv.stats()
     srv.close()
     value, span = job_rate(units, span, dist, torch.device("cuda", local))
-    # the first requests of the stream, served one run per launch in arrival order
+    # the first requests of the stream, served one run per launch in arrival order;
+    # each also checks that the served result equals the plain one (equal log-Z error)
     arr = inputs.poisson_arrivals(w["rate"], w["seconds_per_step"], seed=w["arrival_seed"])
     rng = np.random.Generator(np.random.PCG64(1000))
     picks = rng.integers(0, len(work.runs), len(arr))
-    n_plain = min(300, len(arr))
-    t_free, p_units, p_lat = 0.0, 0, []
+    n_plain = min(n_plain, len(arr))
+    t_free, p_units, p_lat, same, compared = 0.0, 0, [], 0, 0
     for a, q in list(zip(arr, picks))[:n_plain]:
         r = work.runs[q]
         t_start = max(t_free, a)
         c0 = time.perf_counter()
+        o = take(int(q))
         smc.run(models[q], r["N"], seed=r["seed"], run_id=r["run_id"], precision=work.precision,
-                outputs=take(int(q)))
+                outputs=o)
         t_free = t_start + (time.perf_counter() - c0)
         p_lat.append(t_free - a)
         p_units += r["N"] * r["segments"]
+        key = (int(q), 0)
+        if key in served_lz:
+            compared += 1
+            same += int(served_lz[key] == float(o["log_z"][0]))
+        pool.setdefault(int(q), []).append(o)
     plain = {"value": p_units / t_free, "unit": UNIT,
              "latency_ms": {"p50": 1e3 * float(np.percentile(p_lat, 50)),
                             "p99": 1e3 * float(np.percentile(p_lat, 99))},
              "what": f"the first {n_plain} requests of the stream, smc_run one after another in "
                      f"arrival order"}
+    for m in models:
+        m.close()
     cpu = None
-    if ws == 1:
+    if ws == 1 and with_cpu:
         v, runs, secs, _ = oracle_throughput(work, 1e9, 32)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the first {runs} of the 512 request sizes, run one after another "
                          f"({secs:.1f} s single-threaded)"}
+    return {"value": value, "unit": UNIT, "span_s": span, "requests": nreq,
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lats, 50)),
+                           "p99": 1e3 * float(np.percentile(lats, 99))},
+            "d2h_bytes": d2h, "server": st, "cpu_baseline": cpu, "clocks": clk,
+            "plain_one_run_per_launch": plain,
+            "equal_log_z_error": {"served_equal_plain_log_z": same, "compared": compared,
+                                  "rule": "a served request and the same request through smc_run "
+                                          "give the same log Z bit for bit"}}
+
+
+def run_serve(args, work: Work, smc, torch, dist, ws: int, rank: int, local: int) -> int:
+    """The serve2000 workload as the benchmark line."""
+    m = serve_measure(args.steps, work, smc, torch, dist, ws, local)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": 1, "ms_per_step": 1e3 * span / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": 1, "ms_per_step": 1e3 * m["span_s"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": work.config(), "requests": nreq,
-        "latency_ms": {"p50": 1e3 * float(np.percentile(lats, 50)),
-                       "p99": 1e3 * float(np.percentile(lats, 99))},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": d2h // args.steps},
-        "gpu_launches": int(st["waves"]), "server": st, "roofline": None, "cpu_baseline": cpu,
-        "clocks": clk, "plain_one_run_per_launch": plain,
+        "config": work.config(), "requests": m["requests"], "latency_ms": m["latency_ms"],
+        "e2e": {"value": m["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": m["d2h_bytes"] // args.steps},
+        "gpu_launches": int(m["server"]["waves"]), "server": m["server"], "roofline": None,
+        "cpu_baseline": m["cpu_baseline"], "clocks": m["clocks"],
+        "plain_one_run_per_launch": m["plain_one_run_per_launch"],
+        "equal_log_z_error": m["equal_log_z_error"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -584,19 +632,20 @@ def run_resample(args, work: Work, smc, torch, dist, ws: int, rank: int, local: 
         if dist:
             dist.destroy_process_group()
         return 0
+    peaks = load_peaks()
     rs_s = float(np.mean(rs_ms)) * 1e-3
     g_s = float(np.mean(g_ms)) * 1e-3
     rs_gbs = RS_BYTES * N / rs_s / 1e9
     g_bytes = 4 + 2 * 8 * w["fields"]
     g_gbs = g_bytes * N / g_s / 1e9
-    roof = {"bound": "hbm", "achieved": rs_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-            "frac": rs_gbs / HBM_PEAK_GBS,
+    roof = {"bound": "hbm", "achieved": rs_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": rs_gbs / peaks["hbm_gbs"],
             "traffic": RS_NCU["bytes_per_call"] if RS_NCU["src_digest"] == src_digest(RS_SOURCES)
             else None,
             "kernel": "smc_resample (rs_tile_reduce + rs_combine + rs_ancestors)",
             "bytes_per_particle": RS_BYTES, "avg_call_us": rs_s * 1e6,
-            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
-            "gather": {"achieved": g_gbs, "frac": g_gbs / HBM_PEAK_GBS, "avg_call_us": g_s * 1e6,
+            "peak_source": peaks["source"],
+            "gather": {"achieved": g_gbs, "frac": g_gbs / peaks["hbm_gbs"], "avg_call_us": g_s * 1e6,
                        "bytes_per_particle": g_bytes}}
     cpu = None
     if ws == 1:
@@ -625,6 +674,296 @@ def run_resample(args, work: Work, smc, torch, dist, ws: int, rank: int, local: 
     return 0
 
 
+def load_peaks() -> dict:
+    """The HBM copy bandwidth the roofline divides by: the driver's measurement
+    on the GB300s when its file is present, else the recipe's fallback."""
+    f = ROOT / "MEASURED_PEAKS.json"
+    try:
+        d = json.loads(f.read_text())
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json)"}
+    except (OSError, ValueError, KeyError):
+        return {"hbm_gbs": HBM_PEAK_GBS, "source": "fallback (no MEASURED_PEAKS.json)"}
+
+
+def rateshift_mean_sp(tree) -> float:
+    """Mean pending-rate stack depth over a rate-shift run's checkpoints: the
+    depth is a function of the traversal alone (a right child pops its parent's
+    rate, an internal node pushes its own), the same for every particle."""
+    sp, depths = 1, [1]  # the root's rate after the prior block
+    for k in range(1, tree.n_nodes):
+        v = int(tree.preorder[k])
+        p = int(tree.parent[v])
+        if int(tree.right[p]) == v:
+            sp -= 1
+        if int(tree.left[v]) >= 0:
+            sp += 1
+        depths.append(sp)
+    return float(np.mean(depths))
+
+
+def algorithmic_bytes(work: Work) -> tuple[float, str]:
+    """Bytes per particle-step the method must move (the state read through the
+    ancestor and written, the log-weight written and read, the ancestor written
+    and read), in this library's layout."""
+    kind = work.runs[0]["kind"]
+    if kind == "lg":
+        return 40.0, "x 8+8, logw 8+8, ancestor 4+4"
+    if kind == "crbd":
+        return 64.0, "lambda, mu 16+16, logw 8+8, ancestor 4+4, block index 4+4"
+    if kind == "rateshift":
+        sp = rateshift_mean_sp(work.runs[0]["params"]["tree"])
+        b = (8 + 4 * sp + 8) * 2 + 4 + 4 + 4 + 4
+        return b, (f"(lambda0, mu 8 + stack 4 sp + pc, sp 8) x 2 + logw 4+4 + ancestor 4+4, "
+                   f"mean sp {sp:.2f} over the checkpoints")
+    if kind == "seir":
+        return (6 * 4 + 10 * 4) * 2 + 16 + 8, "6 reals + 10 ints read and written, logw, ancestor"
+    return (4 * 8 + 4) * 2 + 16 + 8, "4 reals + block index read and written, logw, ancestor"
+
+
+class DeviceBench:
+    """A workload's runs with device-resident inputs and outputs, timed with CUDA
+    events on the launching stream, L2 flushed between timed steps."""
+
+    def __init__(self, work: Work, smc, torch, dev, launch: str = "waves"):
+        self.work, self.smc, self.torch, self.dev = work, smc, torch, dev
+        self.launch = launch
+        self.stream = torch.cuda.Stream(device=dev)
+        self.batch = work.w["kind"] == "batch"
+        self.models = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
+        self.outs = [self._outputs(m, r["N"]) for m, r in zip(self.models, work.runs)]
+        self.flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def _outputs(self, m, N):
+        t = self.torch
+        o = {"log_z": t.zeros(1, dtype=t.float64, device=self.dev),
+             "final_logw": t.zeros(N, dtype=t.float64, device=self.dev),
+             "ancestors": t.zeros((1, N), dtype=t.int32, device=self.dev),
+             "int_fields": t.zeros((m.n_int, N), dtype=t.int32, device=self.dev)}
+        if m.n_real:
+            o["real_fields"] = t.zeros((m.n_real, N), dtype=t.float64, device=self.dev)
+        if m.stack_cap:
+            o["stack"] = t.zeros((m.stack_cap, N), dtype=t.float64, device=self.dev)
+        return o
+
+    def step(self, seed_off: int, precision: str | None = None):
+        w, smc = self.work, self.smc
+        prec = precision or w.precision
+        if self.batch:
+            specs = [dict(N=r["N"], seed=r["seed"] + seed_off, run_id=r["run_id"], outputs=o)
+                     for r, o in zip(w.runs, self.outs)]
+            return smc.run_batch(self.models, specs, precision=prec, where="device",
+                                 stream=self.stream, launch_graph=self.launch == "graph")
+        r = w.runs[0]
+        return [smc.run(self.models[0], r["N"], seed=r["seed"] + seed_off, run_id=r["run_id"],
+                        precision=prec, where="device", stream=self.stream, outputs=self.outs[0],
+                        ess_threshold=r.get("ess", 0.0), launch=self.launch)]
+
+    def measure(self, steps: int, warmup: int, clocks=None, dist=None) -> dict:
+        torch = self.torch
+        for s in range(warmup):
+            self.step(50000 + s)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        step_ms, logz, statuses, launches = [], [], set(), 0
+        draws = blocks = 0
+        for s in range(steps):
+            with torch.cuda.stream(self.stream):
+                self.flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            res = self.step(s)
+            e1.record(self.stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            statuses.update(r["status"] for r in res)
+            logz.append(float(self.outs[0]["log_z"].cpu()[0]))
+            launches += res[0]["kernel_launches"]
+            draws += sum(r["n_draws"] for r in res)
+            blocks += sum(r["n_blocks"] for r in res)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = clocks.stop() if clocks else None
+        units = steps * self.work.units
+        return {"step_ms": step_ms, "logz": logz, "statuses": sorted(statuses),
+                "launches_per_step": launches // max(1, steps), "clocks": clk,
+                "draws_per_pstep": draws / units, "blocks_per_pstep": blocks / units,
+                "units": units}
+
+    def close(self):
+        for m in self.models:
+            m.close()
+
+
+def segment_roofline(work: Work, meas: dict, peaks: dict, name: str) -> dict:
+    """The segment kernel's roofline from the timed steps themselves: a step is
+    the run's waves (one wave_kernel launch per wave) plus a few small copies,
+    so the mean wave time is at most ms_per_step / waves; the achieved rates
+    below divide by that bound (never above the truth)."""
+    r = work.runs[0]
+    n_part = r["N"]
+    waves = meas["launches_per_step"]
+    t_wave = float(np.mean(meas["step_ms"])) * 1e-3 / max(1, waves)
+    b_per, b_what = algorithmic_bytes(work)
+    hbm = b_per * n_part / t_wave / 1e9
+    info = NCU.get(name)
+    traffic = None
+    if info and info.get("src_digest") == src_digest():
+        traffic = info["bytes_per_launch"]
+    hbm_obj = {"achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+               "frac": hbm / peaks["hbm_gbs"], "bytes_per_particle_step": b_per,
+               "bytes_what": b_what, "peak_source": peaks["source"]}
+    common = {"kernel": "wave_kernel (fused segment kernel)", "waves_per_step": waves,
+              "wave_us": t_wave * 1e6, "traffic": traffic,
+              "timing": "mean wave = ms_per_step / waves of the timed steps"}
+    if info and info["basis"] in ("issue", "fp64"):
+        issue = info["warp_inst_per_pstep"] * n_part / t_wave
+        fp64 = info["fp64_flop_per_pstep"] * n_part / t_wave
+        issue_obj = {"achieved": issue / 1e12, "peak": ISSUE_PEAK / 1e12,
+                     "unit": "T warp-instructions/s", "frac": issue / ISSUE_PEAK,
+                     "per_unit": f"{info['warp_inst_per_pstep']} warp instructions per "
+                                 f"particle-step (ncu)",
+                     "peak_source": "derived: 152 SMs x 4 schedulers x 2070 MHz"}
+        fp64_obj = {"achieved": fp64 / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
+                    "frac": fp64 / FP64_PEAK_FLOPS,
+                    "per_unit": f"{info['fp64_flop_per_pstep']} FP64 flop per particle-step (ncu)",
+                    "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM"}
+        main = issue_obj if info["basis"] == "issue" else fp64_obj
+        return {"bound": "alu", **{k: main[k] for k in ("achieved", "peak", "unit", "frac")},
+                "basis": "instruction issue" if info["basis"] == "issue" else "FP64 pipe",
+                **common, "per_unit": main["per_unit"], "peak_source": main["peak_source"],
+                "fp64": fp64_obj, "issue": issue_obj, "hbm": hbm_obj}
+    return {"bound": "hbm", **{k: hbm_obj[k] for k in ("achieved", "peak", "unit", "frac")},
+            **common, "per_unit": f"{b_per:.1f} algorithmic bytes per particle-step ({b_what})",
+            "peak_source": peaks["source"]}
+
+
+def e2e_measure(work: Work, smc, torch, stream, steps: int, dist, dev) -> tuple[float, int, int]:
+    """The same metric end to end through the public API: every step registers
+    the models from host data, runs, and copies the results to pinned host
+    memory; returns (rate, host->device bytes, device->host bytes) per step."""
+    batch = work.w["kind"] == "batch"
+    pinned = []
+    models0 = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
+    for m, r in zip(models0, work.runs):
+        N = r["N"]
+        o = {"log_z": torch.zeros(1, dtype=torch.float64).pin_memory(),
+             "final_logw": torch.zeros(N, dtype=torch.float64).pin_memory(),
+             "ancestors": torch.zeros((1, N), dtype=torch.int32).pin_memory(),
+             "int_fields": torch.zeros((m.n_int, N), dtype=torch.int32).pin_memory()}
+        if m.n_real:
+            o["real_fields"] = torch.zeros((m.n_real, N), dtype=torch.float64).pin_memory()
+        if m.stack_cap:
+            o["stack"] = torch.zeros((m.stack_cap, N), dtype=torch.float64).pin_memory()
+        pinned.append(o)
+    for m in models0:
+        m.close()
+    d2h = sum(t.numel() * t.element_size() for o in pinned for t in o.values())
+    total = 0.0
+    for s in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ms2 = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
+        if batch:
+            specs = [dict(N=r["N"], seed=r["seed"] + s, run_id=r["run_id"], outputs=o)
+                     for r, o in zip(work.runs, pinned)]
+            smc.run_batch(ms2, specs, precision=work.precision, where="host", stream=stream)
+        else:
+            r = work.runs[0]
+            smc.run(ms2[0], r["N"], seed=r["seed"] + s, run_id=r["run_id"],
+                    precision=work.precision, where="host", stream=stream, outputs=pinned[0],
+                    ess_threshold=r.get("ess", 0.0))
+        for m2 in ms2:
+            m2.close()
+        total += time.perf_counter() - t0
+    value, _ = job_rate(steps * work.units, total, dist, dev)
+    return value, work.input_bytes(), d2h
+
+
+def config_lines(smc, torch, dev, peaks: dict) -> dict:
+    """The metric's other configurations, measured in the same run on this GPU:
+    C1 (lg), C3 (rateshift256, with its roofline and its FP32 log-Z error
+    against the FP64 path on the same seeds), C4 (batch512 against the same
+    runs one run per launch) and C5 (serve2000, p50/p99 against the plain path)."""
+    out = {}
+    # C1: one 1024-particle run of 50 segments (latency-bound)
+    w = Work("lg", seed_base=1)
+    b = DeviceBench(w, smc, torch, dev)
+    m = b.measure(20, 3)
+    b.close()
+    ms = float(np.mean(m["step_ms"]))
+    out["lg"] = {"value": w.units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                 "roofline": segment_roofline(w, m, peaks, "lg"), "status": m["statuses"],
+                 "draws_per_particle_step": m["draws_per_pstep"],
+                 "blocks_per_particle_step": m["blocks_per_pstep"]}
+    # C3: rate-shift, 2^20 particles, FP32 particles / FP64 reductions
+    w = Work("rateshift256", seed_base=1)
+    b = DeviceBench(w, smc, torch, dev)
+    m = b.measure(3, 2)
+    ms = float(np.mean(m["step_ms"]))
+    errs, lz32, lz64 = [], [], []
+    for s in range(3):  # the same seeds at FP32 and FP64
+        b.step(900 + s, "fp32")
+        a = float(b.outs[0]["log_z"].cpu()[0])
+        b.step(900 + s, "fp64")
+        c = float(b.outs[0]["log_z"].cpu()[0])
+        lz32.append(a)
+        lz64.append(c)
+        errs.append(abs(a - c))
+    b.close()
+    out["rateshift256"] = {
+        "value": w.units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+        "roofline": segment_roofline(w, m, peaks, "rateshift256"), "status": m["statuses"],
+        "draws_per_particle_step": m["draws_per_pstep"],
+        "blocks_per_particle_step": m["blocks_per_pstep"],
+        "log_z_error_vs_fp64": {"per_result": errs, "fp32": lz32, "fp64": lz64,
+                                "what": "|log Z(FP32) - log Z(FP64)| for the same seed, run id "
+                                        "and N (the FP64 path equals the FP64 oracle to 1e-9 "
+                                        "relative; FP32 uniforms are the FP64 ones to 2^-24)",
+                                "monte_carlo_sd_fp64": float(np.std(lz64, ddof=1))}}
+    # C4: 512 uneven runs in one sequence of waves, against one run per launch
+    w = Work("batch512", seed_base=1)
+    b = DeviceBench(w, smc, torch, dev)
+    m = b.measure(2, 1)
+    ms = float(np.mean(m["step_ms"]))
+    batch_lz = [float(o["log_z"].cpu()[0]) for o in b.outs]  # the last timed step's seeds
+    seed_off = 1
+    t_plain, same = 0.0, 0
+    for q, (mo, r, o) in enumerate(zip(b.models, w.runs, b.outs)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        smc.run(mo, r["N"], seed=r["seed"] + seed_off, run_id=r["run_id"], precision=w.precision,
+                where="device", stream=b.stream, outputs=o)
+        e1.record(b.stream)
+        e1.synchronize()
+        t_plain += e0.elapsed_time(e1)
+        same += int(float(o["log_z"].cpu()[0]) == batch_lz[q])
+    b.close()
+    plain_v = w.units / (t_plain * 1e-3)
+    out["batch512"] = {"value": w.units / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                       "status": m["statuses"], "launches_per_step": m["launches_per_step"],
+                       "plain_one_run_per_launch": {"value": plain_v, "unit": UNIT,
+                                                    "ms": t_plain},
+                       "speedup_vs_plain": (w.units / (ms * 1e-3)) / plain_v,
+                       "equal_log_z_error": {"runs_with_identical_log_z": same, "runs": len(w.runs),
+                                             "rule": "each batched run and the same run through "
+                                                     "smc_run give the same log Z bit for bit"}}
+    # C5: one second of a Poisson stream at 2000 requests/s
+    w = Work("serve2000", seed_base=1)
+    sm = serve_measure(1, w, smc, torch, None, 1, 0, with_cpu=False, n_plain=200)
+    out["serve2000"] = {k: sm[k] for k in ("value", "unit", "requests", "latency_ms",
+                                            "plain_one_run_per_launch", "equal_log_z_error")}
+    out["serve2000"]["speedup_vs_plain"] = sm["value"] / sm["plain_one_run_per_launch"]["value"]
+    return out
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,6 +972,11 @@ def main() -> int:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="crbd64", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-configs", action="store_true",
+                    help="leave out the other configurations' sub-objects of the default line")
+    ap.add_argument("--launch", default="waves", choices=["waves", "graph", "one_cta"],
+                    help="launch form of the segments (results are the same bits)")
+    ap.add_argument("--launch-graph", action="store_true", help="the same as --launch graph")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     work = Work(args.workload, seed_base=1 + 100000 * rank)
@@ -656,39 +1000,7 @@ def main() -> int:
         return run_serve(args, work, smc, torch, dist, ws, rank, local)
     if work.w["kind"] == "resample":
         return run_resample(args, work, smc, torch, dist, ws, rank, local)
-    stream = torch.cuda.Stream()
-    batch = work.w["kind"] == "batch"
-    models = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
-
-    def dev_outputs(m, N):
-        o = {"log_z": torch.zeros(1, dtype=torch.float64, device=dev),
-             "final_logw": torch.zeros(N, dtype=torch.float64, device=dev),
-             "ancestors": torch.zeros((1, N), dtype=torch.int32, device=dev),
-             "int_fields": torch.zeros((m.n_int, N), dtype=torch.int32, device=dev)}
-        if m.n_real:
-            o["real_fields"] = torch.zeros((m.n_real, N), dtype=torch.float64, device=dev)
-        if m.stack_cap:
-            o["stack"] = torch.zeros((m.stack_cap, N), dtype=torch.float64, device=dev)
-        return o
-
-    outs = [dev_outputs(m, r["N"]) for m, r in zip(models, work.runs)]
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-
-    def device_step(seed_off: int, timed: bool):
-        """One step with inputs resident on the device; returns per-run results."""
-        if batch:
-            specs = [dict(N=r["N"], seed=r["seed"] + seed_off, run_id=r["run_id"], outputs=o)
-                     for r, o in zip(work.runs, outs)]
-            return smc.run_batch(models, specs, precision=work.precision, where="device",
-                                 stream=stream)
-        r = work.runs[0]
-        return [smc.run(models[0], r["N"], seed=r["seed"] + seed_off, run_id=r["run_id"],
-                        precision=work.precision, where="device", stream=stream, outputs=outs[0],
-                        time_kernels=timed, ess_threshold=r.get("ess", 0.0))]
-
-    for s in range(args.warmup):
-        device_step(50000 + s, False)
-    torch.cuda.synchronize()
+    peaks = load_peaks()
     gpu_index = local
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -696,127 +1008,45 @@ def main() -> int:
             gpu_index = int(vis.split(",")[local])
         except ValueError:
             pass
-    clocks = ClockSampler(gpu_index)
-    clocks.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    step_ms, kern_ms, kern_launches, logz, statuses = [], 0.0, 0, [], set()
-    for s in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = device_step(s, False)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        statuses.update(r["status"] for r in res)
-        logz.append(float(outs[0]["log_z"].cpu()[0]))
-    # Launch durations of the segment kernel: the same steps again with a CUDA
-    # event pair around every launch (an event between launches costs ~3 us of
-    # its own, so these steps are kept out of the value above).
-    for s in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        res = device_step(s, True)
-        kern_ms += sum(r["kernel_ms"] for r in res)
-        kern_launches += res[0]["kernel_launches"]
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    value, total_s = job_rate(args.steps * work.units, sum(step_ms) * 1e-3, dist, dev)
+    launch = "graph" if args.launch_graph else args.launch
+    bench = DeviceBench(work, smc, torch, dev, launch=launch)
+    meas = bench.measure(args.steps, args.warmup, ClockSampler(gpu_index), dist)
+    value, total_s = job_rate(meas["units"], sum(meas["step_ms"]) * 1e-3, dist, dev)
     total_ms = total_s * 1e3
 
     # the same runs one run per launch (plain path), timed once
     plain = None
-    if batch:
+    if bench.batch:
         torch.cuda.synchronize()
         t_plain = 0.0
-        for m, r, o in zip(models, work.runs, outs):
+        for m, r, o in zip(bench.models, work.runs, bench.outs):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            e0.record(bench.stream)
             smc.run(m, r["N"], seed=r["seed"], run_id=r["run_id"], precision=work.precision,
-                    where="device", stream=stream, outputs=o)
-            e1.record(stream)
+                    where="device", stream=bench.stream, outputs=o)
+            e1.record(bench.stream)
             e1.synchronize()
             t_plain += e0.elapsed_time(e1)
         plain = {"value": work.units / (t_plain * 1e-3), "unit": UNIT,
                  "what": "the same 512 runs through smc_run, one run after another"}
-
-    # end to end through the public API: host inputs in, host results out
-    pinned = []
-    for m, r in zip(models, work.runs):
-        N = r["N"]
-        o = {"log_z": torch.zeros(1, dtype=torch.float64).pin_memory(),
-             "final_logw": torch.zeros(N, dtype=torch.float64).pin_memory(),
-             "ancestors": torch.zeros((1, N), dtype=torch.int32).pin_memory(),
-             "int_fields": torch.zeros((m.n_int, N), dtype=torch.int32).pin_memory()}
-        if m.n_real:
-            o["real_fields"] = torch.zeros((m.n_real, N), dtype=torch.float64).pin_memory()
-        if m.stack_cap:
-            o["stack"] = torch.zeros((m.stack_cap, N), dtype=torch.float64).pin_memory()
-        pinned.append(o)
-    d2h = sum(t.numel() * t.element_size() for o in pinned for t in o.values())
-    e2e_steps = args.steps if not batch else max(1, min(args.steps, 3))
-    e2e_total = 0.0
-    for s in range(e2e_steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ms2 = [smc.Model(r["kind"], **r["params"]) for r in work.runs]
-        if batch:
-            specs = [dict(N=r["N"], seed=r["seed"] + s, run_id=r["run_id"], outputs=o)
-                     for r, o in zip(work.runs, pinned)]
-            smc.run_batch(ms2, specs, precision=work.precision, where="host", stream=stream)
-        else:
-            r = work.runs[0]
-            smc.run(ms2[0], r["N"], seed=r["seed"] + s, run_id=r["run_id"],
-                    precision=work.precision, where="host", stream=stream, outputs=pinned[0],
-                    ess_threshold=r.get("ess", 0.0))
-        for m2 in ms2:
-            m2.close()
-        e2e_total += time.perf_counter() - t0
-    e2e_value, e2e_total = job_rate(e2e_steps * work.units, e2e_total, dist, dev)
+    e2e_steps = args.steps if not bench.batch else max(1, min(args.steps, 3))
+    e2e_value, h2d, d2h = e2e_measure(work, smc, torch, bench.stream, e2e_steps, dist, dev)
 
     if rank != 0:
+        bench.close()
         if dist:
             dist.destroy_process_group()
         return 0
 
     equal_error = None
     if work.w["kind"] == "crbd_ds":
-        equal_error = equal_error_comparison(work, smc, torch, stream)
-
-    roof = None
-    info = NCU.get(args.workload)
-    if info and kern_launches and not batch:
-        avg_launch_s = kern_ms / kern_launches * 1e-3
-        n_part = work.runs[0]["N"]
-        traffic = info["bytes_per_launch"] if info["src_digest"] == src_digest() else None
-        common = {"traffic": traffic, "kernel": "wave_kernel (fused segment kernel)",
-                  "avg_launch_us": avg_launch_s * 1e6, "launches": kern_launches,
-                  "fp64_pipe_active_of_elapsed_ncu": info["fp64_pipe_elapsed"]}
-        if info["basis"] == "issue":
-            achieved = info["warp_inst_per_pstep"] * n_part / avg_launch_s
-            roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": ISSUE_PEAK / 1e12,
-                    "unit": "T warp-instructions/s", "frac": achieved / ISSUE_PEAK, **common,
-                    "per_unit": f"{info['warp_inst_per_pstep']} warp instructions per particle-step",
-                    "peak_source": "derived: 152 SMs x 4 schedulers x 2070 MHz, 1 issue/clk",
-                    "fp64": {"achieved_tflops": info["fp64_flop_per_pstep"] * n_part / avg_launch_s
-                             / 1e12, "peak_tflops": FP64_PEAK_FLOPS / 1e12}}
-        else:
-            achieved = info["fp64_flop_per_pstep"] * n_part / avg_launch_s
-            roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_FLOPS, **common,
-                    "per_unit": f"{info['fp64_flop_per_pstep']} FP64 flop per particle-step",
-                    "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM"}
+        equal_error = equal_error_comparison(work, smc, torch, bench.stream)
+    roof = None if bench.batch else segment_roofline(work, meas, peaks, args.workload)
+    bench.close()
     cpu = None
     if ws == 1:
-        if batch:
+        if bench.batch:
             v, runs, secs, _ = oracle_throughput(work, 1e9, 32)
             sample = (f"the first {runs} of the 512 runs of the batch, run one after another "
                       f"({secs:.1f} s single-threaded)")
@@ -827,28 +1057,41 @@ def main() -> int:
                       f"(of {work.runs[0]['N']}), seeds from {work.runs[0]['seed']}, "
                       f"{secs:.1f} s single-threaded")
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
-    lat = sorted(step_ms)
-    launches_per_step = (kern_launches // max(1, args.steps)) + len(work.runs)
+    configs = None
+    if ws == 1 and args.workload == "crbd64" and not args.no_configs:
+        configs = config_lines(smc, torch, dev, peaks)
+    lat = sorted(meas["step_ms"])
+    cfg_line = work.config()
+    cfg_line["launch"] = {"graph": "one captured CUDA graph per step",
+                          "one_cta": "every segment of a small run in one CTA (else waves)",
+                          "waves": "one launch per wave and CTA size, chained by dependent "
+                                   "launch"}[launch]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if work.precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": work.config(),
+        "config": cfg_line,
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-        "log_z_run0": {"mean": float(np.mean(logz)), "sd": float(np.std(logz))},
-        "status": sorted(statuses),
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": work.input_bytes(),
+        "log_z_run0": {"mean": float(np.mean(meas["logz"])), "sd": float(np.std(meas["logz"]))},
+        "status": meas["statuses"],
+        "work": {"draws_per_particle_step": meas["draws_per_pstep"],
+                 "blocks_per_particle_step": meas["blocks_per_pstep"],
+                 "what": "Philox blocks drawn by SAMPLE statements and basic blocks executed, "
+                         "per particle-step, from the run's device counters"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * launches_per_step,
+        "gpu_launches": args.steps * (meas["launches_per_step"] + len(work.runs)),
         "roofline": roof,
         "cpu_baseline": cpu,
-        "clocks": clk,
+        "clocks": meas["clocks"],
     }
     if plain:
         line["plain_one_run_per_launch"] = plain
     if equal_error:
         line["equal_log_z_error"] = equal_error
+    if configs:
+        line["configs"] = configs
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

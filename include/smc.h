@@ -83,6 +83,10 @@ typedef int32_t smc_status;
 #define SMC_MEM_HOST 0
 #define SMC_MEM_DEVICE 1
 
+#define SMC_LAUNCH_WAVES 0
+#define SMC_LAUNCH_GRAPH 1
+#define SMC_LAUNCH_ONE_CTA 2
+
 #define SMC_MAX_DEPTH 64 /* largest hidden-lineage recursion cap the CRBD blocks accept */
 /* Largest particle count of one run: ancestor indices are int32, and a run's
    last tile, rounded up to whole CTAs of at most 256 particles, stays below
@@ -126,7 +130,23 @@ typedef struct {
   int32_t max_segments;  /* 0 = the model's own segment count (unbounded models: 1 << 20) */
   int32_t record_all_ancestors; /* 1: keep every resampling's ancestors, 0: only the last */
   int32_t time_kernels;  /* 1: time every segment-kernel launch with CUDA events (counters) */
-  int32_t pad_;
+  int32_t launch_mode;   /* how the segments are launched; results are the same bits in
+                            every mode:
+                            SMC_LAUNCH_WAVES    one launch per segment (wave) and CTA size,
+                                                chained by programmatic dependent launch;
+                            SMC_LAUNCH_GRAPH    the waves of a known-length run captured in
+                                                one CUDA graph (on a stream other than the
+                                                legacy default stream; else waves): smc_run
+                                                keeps the graph in the model handle and
+                                                launches it again while the workspace, N and
+                                                precision stay the same, smc_run_batch
+                                                captures per call (cfgs[0] decides);
+                            SMC_LAUNCH_ONE_CTA  smc_run of a run of 32-particle tiles, at most
+                                                32 of them (linear-Gaussian, geometric) or 16
+                                                (the others), fresh (not resumed): every
+                                                segment in one CTA and one launch, the CTA
+                                                barrier as the checkpoint barrier (else
+                                                waves). */
   void *workspace;       /* optional caller-owned device workspace (>= smc_workspace_bytes);
                             NULL = the model handle allocates and caches one */
   size_t workspace_bytes;
@@ -135,6 +155,24 @@ typedef struct {
                             size (sum w)^2 / sum w^2 < tau N, otherwise the particles keep
                             their states and accumulated log-weights and the log-Z
                             increment waits for the next resampling or the end */
+  /* Resume from a snapshot (smc_run only; resume_k = 0: a fresh run).  Between
+   * checkpoints a run is its particles' states and log-weights, the log Z closed so
+   * far and its segment index, and every draw comes from a counter, so a run stopped
+   * by max_segments after k segments (SMC_ESTEPLIMIT) and resumed from its outputs
+   * with the same model, N, seed, run_id, precision and ess_threshold ends exactly
+   * as the uninterrupted run.  The snapshot arrays are that run's outputs, in the
+   * layouts of smc_result (host or device memory, resume_where); resume_log_z is its
+   * counters.log_z_closed.  The resumed run takes the resampling decision at
+   * checkpoint k - 1 and goes on with segment k; max_segments still counts from
+   * segment 0 (it must be 0 or >= k); its recorded ancestor rows and resampling
+   * decisions before checkpoint k - 1 are zero.  Errors: SMC_EINVAL. */
+  int32_t resume_k;
+  int32_t resume_where;        /* SMC_MEM_HOST or SMC_MEM_DEVICE */
+  const double *resume_logw;   /* [N] the snapshot's final_logw */
+  const double *resume_real;   /* [n_real][N] its real_fields (NULL when n_real = 0) */
+  const int32_t *resume_int;   /* [n_int][N] its int_fields */
+  const double *resume_stack;  /* [stack_cap][N] its stack (RATESHIFT; else NULL) */
+  double resume_log_z;         /* its counters.log_z_closed */
 } smc_run_cfg;
 
 /* Counters of one run (host struct, filled by smc_run before it returns). */
@@ -154,6 +192,19 @@ typedef struct {
   int64_t n_draws;          /* Philox blocks drawn by the model's SAMPLE statements, summed over
                                particles and segments (the resampling uniforms not included) */
   int64_t n_blocks;         /* basic-block executions, summed over particles and segments */
+  double log_z_closed;      /* log Z without the closure made only because the step limit
+                               ended the run (equal to log_z otherwise): what a resumed run
+                               continues from */
+  /* The checking build of the library (libsmc_debug.so, compiled with
+   * SMC_DEBUG_CHECKS) checks every ancestor index against [0, N), every gathered
+   * block index against the model's blocks and every gathered stack pointer
+   * against the stack capacity; an access found out of range is skipped (the
+   * particle is killed) and recorded here.  Always 0 in the release build. */
+  int32_t debug_code;       /* first violation: 1 ancestor, 2 block index, 3 stack pointer,
+                               4 dispatch; 0 = none */
+  int32_t pad3_;
+  int64_t debug_index;      /* the particle of the first violation */
+  int64_t debug_count;      /* violations found */
 } smc_counters;
 
 /* Outputs of one run.  `where` says whether every pointer below is host or
@@ -173,6 +224,34 @@ typedef struct {
                                 (record_all; else row 0 holds the last checkpoint's) */
   smc_counters counters;     /* filled on return */
 } smc_result;
+
+/* ---------------- tiling (the library's one tuned parameter) ----------------
+ * A run of N particles is cut into tiles of consecutive particles, one CTA per
+ * tile per wave.  The tile size is a function of N alone, from a table of N
+ * bands: the band with the smallest n_max >= N gives tiles of
+ * clamp(ceil(N / slots), tile_min, tile_max).  Since the tiling fixes how the
+ * weights are rounded to their tile's reference, a run gives the same bits
+ * alone, batched and served under one table.  The built-in table is data
+ * written by the library's autotuner (sweeps of candidate bands timed on a
+ * GB300). */
+typedef struct {
+  int64_t n_max;     /* the band holds runs of N <= n_max (the last band: >= SMC_MAX_PARTICLES) */
+  int32_t slots;     /* >= 1 */
+  int32_t tile_min;  /* 1 <= tile_min <= tile_max */
+  int32_t tile_max;  /* <= 256 */
+  int32_t pad_;
+} smc_tile_band;
+
+/* Replace the process's tile table (bands sorted by increasing n_max); NULL, 0
+ * restores the built-in table.  For tuning: runs in flight keep the tiling they
+ * started with; results of runs under different tables differ (within the
+ * method's rounding, not bit for bit).  Errors: SMC_EINVAL. */
+smc_status smc_set_tile_bands(const smc_tile_band *bands, int32_t n_bands);
+/* The current table: up to `cap` bands into `out` (may be NULL), their number
+ * into *n_bands.  Errors: SMC_EINVAL. */
+smc_status smc_get_tile_bands(smc_tile_band *out, int32_t cap, int32_t *n_bands);
+/* The tile size a run of n_particles gets now (0 if n_particles is out of range). */
+int32_t smc_tile_size(int64_t n_particles);
 
 /* Register a model: validates `d`, copies observations / tree arrays to device
  * memory owned by the returned handle.  Section 3.1 (the PCFG being run) and

@@ -3,7 +3,10 @@
 Each .cu file is compiled by nvcc in parallel (one -gencode, -lineinfo,
 -fmad=false so that every fused multiply-add in the kernels is an explicit
 fma() of the specification) and the objects are linked into one shared
-library next to this file.
+library next to this file.  The checking build ``libsmc_debug.so`` is the same
+sources compiled with SMC_DEBUG_CHECKS=1: every ancestor index, gathered block
+index and stack pointer is checked, and an out-of-range one is recorded in the
+run's counters and skipped instead of accessed.
 """
 from __future__ import annotations
 
@@ -18,7 +21,8 @@ CSRC = PKG / "csrc"
 INCLUDE = PKG.parent / "include"
 BUILD = PKG / "_build"
 LIB = PKG / "libsmc.so"
-SOURCES = ["smc_engine.cu", "smc_prims.cu", "smc_server.cu"]
+LIB_DEBUG = PKG / "libsmc_debug.so"
+SOURCES = ["smc_engine.cu", "smc_small.cu", "smc_prims.cu", "smc_server.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
@@ -39,22 +43,26 @@ def _deps() -> list[Path]:
         sorted(INCLUDE.glob("*.h")) + [Path(__file__)]
 
 
-def up_to_date() -> bool:
-    if not LIB.exists():
+def up_to_date(lib: Path = LIB) -> bool:
+    if not lib.exists():
         return False
-    t = LIB.stat().st_mtime
+    t = lib.stat().st_mtime
     return all(p.stat().st_mtime <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> Path:
-    if not force and up_to_date():
-        return LIB
-    BUILD.mkdir(exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False,
+          debug: bool = False) -> Path:
+    """Build libsmc.so (debug=True: the checking build libsmc_debug.so)."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and up_to_date(lib):
+        return lib
+    out = BUILD / ("debug" if debug else "release")
+    out.mkdir(parents=True, exist_ok=True)
     cc = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_v else []
+    extra = (["-Xptxas", "-v"] if ptxas_v else []) + (["-DSMC_DEBUG_CHECKS=1"] if debug else [])
 
     def compile_one(src: str):
-        obj = BUILD / (Path(src).stem + ".o")
+        obj = out / (Path(src).stem + ".o")
         cmd = [cc, "-c", str(CSRC / src), "-o", str(obj)] + _flags() + extra
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
@@ -67,18 +75,24 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         for _, err in results:
             if err:
                 print(err)
-    tmp = LIB.with_suffix(f".so.tmp{os.getpid()}")
+    tmp = lib.with_suffix(f".so.tmp{os.getpid()}")
     cmd = [cc, "-shared", "-o", str(tmp)] + [str(o) for o, _ in results] + \
         ["-gencode", GENCODE, "-Xcompiler", "-fPIC", "-lcudart"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> list[Path]:
+    """Both libraries, compiled at the same time."""
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        return list(ex.map(lambda d: build(force=force, debug=d), (False, True)))
 
 
 if __name__ == "__main__":
     import sys
 
-    build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_v="-v" in sys.argv,
+                debug="--debug" in sys.argv))

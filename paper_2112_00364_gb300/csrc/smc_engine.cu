@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <iterator>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -49,333 +50,9 @@
 #include "smc_engine.h"
 #include "smc_internal.h"
 #include "smc_models.cuh"
+#include "smc_step.cuh"
 
 namespace smc {
-
-__device__ __forceinline__ void warp_add_u64(unsigned long long* dst, unsigned long long v) {
-  v = __reduce_add_sync(0xffffffffu, (unsigned)v);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
-}
-
-// Finish segment k-1 of the run from its combined offsets (one thread):
-// log Z += k_max ln 2 + (log S - log N) with S = S_units U, the increment
-// record, and the end of the run.  Returns whether segment k runs.
-// Whether to resample after checkpoint k-1 (the same in every CTA: c is).
-__device__ __forceinline__ bool decide_resample(const RunDev& A, const Combined& c) {
-  return !A.ess || c.ess < A.ess_target;
-}
-
-__device__ __forceinline__ bool finish_segment(const RunDev& A, int k, const Combined& c,
-                                               bool resample) {
-  RunState* rs = A.rs;
-  if (c.kmax == kDeadTile) {
-    rs->log_z = -INFINITY;
-    rs->m = -INFINITY;
-    rs->S = 0.0;
-    A.incr[k - 1] = -INFINITY;
-    rs->status = SMC_EDEGENERATE;
-    rs->done = 1;
-    rs->n_segments = k;
-    return false;
-  }
-  const double Sd = (double)c.S;
-  const double inc = (double)(c.kmax - 54 + c.G) * kLn2 + (tang_log(Sd, A.md.tab) - A.log_n);
-  const bool go_on = c.alive && k < A.max_segments;
-  // the accumulated weights are closed into log Z when the population is
-  // resampled, at the end and at the step limit
-  const bool close = !go_on || resample;
-  if (close) rs->log_z = rs->log_z + inc;
-  A.incr[k - 1] = close ? inc : 0.0;
-  rs->m = (double)c.kmax * kLn2;
-  rs->S = Sd * pow2i(c.G - 54);
-  rs->n_segments = k;
-  if (go_on) {
-    A.dec[k - 1] = resample ? 1 : 0;
-    rs->n_resamples += resample ? 1 : 0;
-    if (A.ess && fabs(c.ess - A.ess_target) <= 1e-9 * A.ess_target) rs->n_ess_near += 1;
-  }
-  if (!c.alive) {
-    rs->done = 1;
-  } else if (!go_on) {
-    rs->status = SMC_ESTEPLIMIT;
-    rs->done = 1;
-  }
-  return go_on;
-}
-
-// What the search of segment k needs about segment k-1's weights.
-struct SearchCtx {
-  const long long* O;  // offsets in units U, O[T] = S
-  const int* ks;       // tile reference exponents (shared memory), or NULL: read the records
-  const TileRec* rec;
-  int kmax, G;
-  Q64 d, z0;           // S / N and u S / N in 64.64 (units U)
-  long long tolZ;      // 1e-12 N on the q scale, in units U
-};
-
-// The run's search scalars from its combined total (one thread).
-__device__ __forceinline__ void search_scalars(const Combined& c, int N, double u, Q64* d, Q64* z0,
-                                               long long* tolZ) {
-  *d = q_ratio((unsigned long long)c.S, (unsigned long long)N);
-  *z0 = q_scale(frac64(u), *d);
-  *tolZ = floor_i64(kBoundaryEps * (double)c.S);
-}
-
-// a_i = min{ j : q_j > y } for y = i + u, with q_j = P_j N / S and P_j the
-// running sum of the weights; on the P scale in units U the offset is
-// z_i = z_0 + i S / N (64.64 fixed point, exact and non-decreasing in i).  The
-// tile is t = max{ t : O_t <= z } (N - 1 if z lies above every offset); inside
-// it P_j = O_t + E_j 2^-(k_max - k_t + G), so P_j > z <=> E_j > floor((z - O_t)
-// 2^(k_max - k_t + G)) (E_j is an integer): one threshold per particle, then an
-// 8-ary search with integer compares (three rounds of independent loads for a
-// 256-particle tile).  If no element of tile t qualifies, the first element of
-// tile t+1 does.  The offset is flagged when it lies within 1e-12 N of q_a or
-// q_{a-1}, measured in the same units.  Integer arithmetic only.
-__device__ __forceinline__ int systematic_search(int i, const RunDev& A, const SearchCtx& X,
-                                                 const long long* __restrict__ E, bool* near) {
-  const int N = A.N, T = A.n_tiles;
-  const Q64 z = q_add(X.z0, q_mul_u32((unsigned)i, X.d));
-  const long long Z = (long long)z.hi;
-  int lo = 0, hi = T;  // O_0 = 0 <= z
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (X.O[mid] <= Z)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  if (lo >= T) {  // above the last offset (rounding at the top)
-    *near = Z - X.O[T] < X.tolZ;
-    return N - 1;
-  }
-  const int t = lo;
-  const int j0 = t * A.tile, j1 = min(N, j0 + A.tile);
-  const int kt = X.ks ? X.ks[t] : load_rec(X.rec + t).k;
-  const int sh = X.kmax - kt + X.G;
-  const long long F = q_threshold(z, X.O[t], sh);
-  const long long tolF = shl_sat(X.tolZ, sh);
-  // first j in [j0, j1) with E_j > F
-  long long Eb = 0;  // E_{b-1} for the current bracket start b (0 before the tile)
-  int b = j0, len = j1 - j0;
-  while (len > 8) {
-    const int w = (len + 7) >> 3;
-    long long v[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = E[b + min((m + 1) * w, len) - 1];
-    int m = 8;
-#pragma unroll
-    for (int q = 7; q >= 0; --q)
-      if (v[q] > F) m = q;
-    if (m == 8) {  // nothing in the tile qualifies
-      Eb = v[7];
-      b += len;
-      len = 0;
-      break;
-    }
-    if (m > 0) Eb = v[m - 1];
-    len = min((m + 1) * w, len) - m * w;
-    b += m * w;
-  }
-  int l = b + len;  // none found yet
-  long long El = 0;
-  if (len > 0) {
-    long long v[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = m < len ? E[b + m] : 0x7FFFFFFFFFFFFFFFll;
-    int m = 8;
-#pragma unroll
-    for (int q = 7; q >= 0; --q)
-      if (v[q] > F) m = q;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (q == m) El = v[q];
-      if (q < m && q < len) Eb = v[q];
-    }
-    if (m < len) l = b + m;
-  }
-  bool nr = F - Eb < tolF;
-  int a;
-  if (l < j1) {
-    a = l;
-    nr = nr || El - F <= tolF;
-  } else if (j1 < N) {  // the first element of the next tile
-    a = j1;
-    nr = nr || X.O[t + 1] - Z <= X.tolZ;
-  } else {
-    a = N - 1;
-  }
-  *near = nr;
-  return a;
-}
-
-// One tile of one run for segment k (the whole per-CTA body of a wave).
-template <class M, int TPB>
-__device__ __forceinline__ void step_tile(const RunDev& A, const int t, const int k, double* sh,
-                                          int* sh_last, int* sh_kw, long long* sh_O, int* sh_ks) {
-  using R = typename M::R;
-  RunState* rs = A.rs;
-  const int N = A.N;
-  const int i = t * A.tile + threadIdx.x;
-  const bool valid = (int)threadIdx.x < A.tile && i < N;
-  const int nb = k & 1, cb = nb ^ 1;
-  const StateView Sc = A.state[cb];
-  const StateView Sn = A.state[nb];
-  const bool redundant = A.redundant != 0;
-  typename M::Lane L;
-  bool near = false;
-  if (k > 0) {
-    SearchCtx X;
-    X.rec = A.rec[cb];
-    bool resample;
-    if (redundant) {
-      const Combined c = combine_offsets<TPB>(A.rec[cb], A.n_tiles, sh_O, sh_ks, sh,
-                                              A.ess ? A.tq[cb] : nullptr);
-      const bool go_on = c.kmax != kDeadTile && c.alive && k < A.max_segments;
-      resample = decide_resample(A, c);
-      if (t == 0 && threadIdx.x == 0) finish_segment(A, k, c, resample);
-      if (!go_on) return;
-      // the run's search scalars by one thread, shared through shared memory
-      unsigned long long* shq = reinterpret_cast<unsigned long long*>(sh + TPB / 32 + 1);
-      if (resample && threadIdx.x == 0) {
-        Q64 d, z0;
-        long long tolZ;
-        search_scalars(c, N, Unif<double>::first(philox(0u, (uint32_t)(k - 1), 0u, 1u, A.k0, A.k1)),
-                       &d, &z0, &tolZ);
-        shq[0] = d.hi;
-        shq[1] = d.lo;
-        shq[2] = z0.hi;
-        shq[3] = z0.lo;
-        shq[4] = (unsigned long long)tolZ;
-      }
-      __syncthreads();
-      X.O = sh_O;
-      X.ks = sh_ks;
-      X.kmax = c.kmax;
-      X.G = c.G;
-      X.d = Q64{shq[0], shq[1]};
-      X.z0 = Q64{shq[2], shq[3]};
-      X.tolZ = (long long)shq[4];
-    } else {
-      resample = rs->resample != 0;
-      X.O = A.tile_O;
-      X.ks = nullptr;
-      X.kmax = rs->kmax;
-      X.G = rs->G;
-      X.d = Q64{rs->d_hi, rs->d_lo};
-      X.z0 = Q64{rs->z0_hi, rs->z0_lo};
-      X.tolZ = rs->tolZ;
-    }
-    if (valid) {
-      const int row = A.record_all ? k - 1 : 0;
-      if (resample) {
-        const int a = systematic_search(i, A, X, A.E[cb], &near);
-        if (row < A.anc_rows) A.anc[(size_t)row * N + i] = a;
-        M::gather(L, Sc, Sn, a, i, N, A.md);
-      } else {  // not resampled: the particle keeps its state and its accumulated weight
-        if (row < A.anc_rows) A.anc[(size_t)row * N + i] = i;
-        M::gather(L, Sc, Sn, i, i, N, A.md);
-        L.logw = (R)A.logw[i];
-      }
-    }
-    warp_add_u64(&rs->n_near, near ? 1ull : 0ull);
-  } else if (valid) {
-    M::init(L);
-  }
-  Stream s{A.k0, A.k1, (uint32_t)i, (uint32_t)k, 0u, 0u, A.md.tab};
-  const bool active = valid && L.pc != PC_STOP;
-  const int n_exec = run_segment<M>(L, s, A.md, Sn, i, k, N, active);
-  double lw = -INFINITY;
-  int alive = 0;
-  if (valid) {
-    M::store(L, Sn, i, N);
-    lw = (double)L.logw;
-    A.logw[i] = lw;
-    alive = L.pc != PC_STOP;
-  }
-  warp_add_u64(&rs->n_overflow, active ? (unsigned long long)L.overflow : 0ull);
-  warp_add_u64(&rs->n_limit, active ? (unsigned long long)L.limited : 0ull);
-  // work counters: Philox blocks of the model's draw stream and blocks executed
-  warp_add_u64(&rs->n_draws, valid ? (unsigned long long)s.d : 0ull);
-  warp_add_u64(&rs->n_blocks, (unsigned long long)n_exec);
-  // Weights, first per warp as soon as the warp's particles reached the
-  // checkpoint (overlapping the tile's slower warps): the warp's max M_w, its
-  // power-of-two reference k_w = ceil(M_w / ln 2), and e_j = exp(logw_j - k_w
-  // ln 2) 2^54 rounded to an integer on the integer pipes.  Then, after the tile barrier, the tile
-  // reference k_t = max k_w, the exact shift of each weight to it, and the
-  // tile's integer running sum E_j (the next segment's search keys).
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  long long ef = 0;
-  const double Mw = warp_max_key(lw);
-  const int kw = Mw == -INFINITY ? kDeadTile : tile_exponent(Mw);
-  if (valid && kw != kDeadTile) {
-    // (an FP32 log-weight is exact as a double, so both precisions share the
-    // normaliser's integer-pipe exponential)
-    if (kw > -2048 && kw < 2048) {
-      ef = weight_fix<54>(lw, ref_q58(kw), A.md.tab);  // integer pipes only
-    } else {
-      const double kd = (double)kw;
-      const double d = fma(-kd, kLn2Lo, fma(-kd, kLn2Hi, lw));  // lw - kw ln 2, two-part ln 2
-      ef = exp_fix54(d, A.md.tab);
-    }
-  }
-  if (lane == 0) sh_kw[wid] = kw;
-  alive = __syncthreads_or(alive);
-  int kt = sh_kw[0];
-#pragma unroll
-  for (int w = 1; w < TPB / 32; ++w) kt = max(kt, sh_kw[w]);
-  const int shift = kw == kDeadTile ? 64 : kt - kw;
-  if (shift >= 63)
-    ef = 0;
-  else if (shift > 0)
-    ef = (ef + (1ll << (shift - 1))) >> shift;
-  const long long E = block_incl_scan_i64<TPB>(ef, reinterpret_cast<long long*>(sh));
-  if (valid) A.E[nb][i] = E;
-  if (A.ess) {  // the tile's sum of squared weights, units 2^-54 of 2^(2 k_t)
-    const unsigned long long u = (unsigned long long)ef;
-    const long long sq = (long long)((__umul64hi(u, u) << 10) | ((u * u) >> 54));
-    __syncthreads();
-    const long long Q = block_incl_scan_i64<TPB>(sq, reinterpret_cast<long long*>(sh));
-    if (threadIdx.x == TPB - 1) A.tq[nb][t] = Q;
-  }
-  if (threadIdx.x == TPB - 1) {
-    TileRec r;
-    r.s = E;
-    r.k = kt;
-    r.alive = alive;
-    A.rec[nb][t] = r;
-  }
-  if (redundant) return;  // the next wave combines
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&rs->arrive, 1u);
-    *sh_last = (prev == (unsigned)A.n_tiles - 1u);
-  }
-  __syncthreads();
-  if (*sh_last) {  // the run's last tile of segment k: combine for the next wave
-    __threadfence();
-    const Combined c = combine_offsets<TPB>(A.rec[nb], A.n_tiles, A.tile_O, nullptr, sh,
-                                            A.ess ? A.tq[nb] : nullptr);
-    if (threadIdx.x == 0) {
-      const bool resample = decide_resample(A, c);
-      rs->resample = resample ? 1 : 0;
-      if (finish_segment(A, k + 1, c, resample) && resample) {
-        Q64 d, z0;
-        long long tolZ;
-        search_scalars(c, N, Unif<double>::first(philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1)), &d,
-                       &z0, &tolZ);
-        rs->kmax = c.kmax;
-        rs->G = c.G;
-        rs->d_hi = d.hi;
-        rs->d_lo = d.lo;
-        rs->z0_hi = z0.hi;
-        rs->z0_lo = z0.lo;
-        rs->tolZ = tolZ;
-      }
-      rs->arrive = 0;
-    }
-  }
-}
 
 // One wave: CTA b runs tile cta_map[b].y of run cta_map[b].x, segment
 // k = wave - start_wave of that run.
@@ -492,6 +169,11 @@ smc_status math_table(const MathTab** out) {
   return SMC_OK;
 }
 
+void graph_cache_clear(GraphCache* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  *g = GraphCache();
+}
+
 int model_fields(int kind, int* n_real, int* n_int) {
   switch (kind) {
     case SMC_MODEL_LG: *n_real = 1; *n_int = 1; return 0;
@@ -504,10 +186,46 @@ int model_fields(int kind, int* n_real, int* n_int) {
   return -1;
 }
 
+// ---- tiling: a function of N alone, from a table of N bands ----
+// The built-in table is data written by the autotuner (autotune.py sweeps the
+// candidate rules per band on a GB300 and writes smc_tile_table.inc); a band
+// {n_max, slots, tile_min, tile_max} gives a run of N <= n_max particles tiles
+// of clamp(ceil(N / slots), tile_min, tile_max) particles.  Because the tile of
+// a run depends on its N alone, a run gives the same bits alone, batched and
+// served.  smc_set_tile_bands replaces the table for the process (tuning).
+namespace {
+constexpr smc_tile_band kBuiltinBands[] = {
+#include "smc_tile_table.inc"
+};
+std::mutex g_band_mu;
+std::vector<smc_tile_band> g_bands(std::begin(kBuiltinBands), std::end(kBuiltinBands));
+
+smc_status check_bands(const smc_tile_band* b, int n) {
+  if (n < 1 || n > 64) return set_error(SMC_EINVAL, "n_bands must be in 1..64");
+  for (int i = 0; i < n; ++i) {
+    if (b[i].slots < 1) return set_error(SMC_EINVAL, "band %d: slots must be >= 1", i);
+    if (b[i].tile_min < 1 || b[i].tile_min > b[i].tile_max || b[i].tile_max > 256)
+      return set_error(SMC_EINVAL, "band %d: need 1 <= tile_min <= tile_max <= 256", i);
+    if (i > 0 && b[i].n_max <= b[i - 1].n_max)
+      return set_error(SMC_EINVAL, "band n_max must increase");
+  }
+  if (b[n - 1].n_max < kMaxParticles)
+    return set_error(SMC_EINVAL, "the last band must reach SMC_MAX_PARTICLES");
+  return SMC_OK;
+}
+}  // namespace
+
 int tile_for(int64_t N) {
-  int64_t t = (N + kTileSlots - 1) / kTileSlots;
-  t = std::max<int64_t>(t, 32);
-  t = std::min<int64_t>(t, 256);
+  std::lock_guard<std::mutex> lock(g_band_mu);
+  const smc_tile_band* b = &g_bands.back();
+  for (const smc_tile_band& x : g_bands)
+    if (N <= x.n_max) {
+      b = &x;
+      break;
+    }
+  int64_t t = (N + b->slots - 1) / b->slots;
+  t = std::max<int64_t>(t, b->tile_min);
+  t = std::min<int64_t>(t, b->tile_max);
   t = std::min<int64_t>(t, N);
   return (int)std::max<int64_t>(t, 1);
 }
@@ -564,6 +282,10 @@ Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
   L.fin_real = take(8 * N * (size_t)m->n_real);
   L.fin_int = take(4 * N * (size_t)m->n_int);
   L.fin_stack = take(8 * N * (size_t)m->stack_cap);
+  // a host snapshot to resume from is copied here
+  L.snap = take(c->resume_k > 0 && c->resume_where == SMC_MEM_HOST
+                    ? (8 + 8 * (size_t)m->n_real + 8 * (size_t)m->stack_cap) * N + 4 * N * (size_t)m->n_int
+                    : 0);
   L.total = off;
   return L;
 }
@@ -571,6 +293,7 @@ Layout make_layout(const smc_model_s* m, const smc_run_cfg* c) {
 RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws) {
   RunDev A;
   std::memset(&A, 0, sizeof(A));
+  const size_t N_ = (size_t)c->n_particles;
   A.md = m->md;
   for (int b = 0; b < 2; ++b) {
     A.state[b].real = ws + Ly.real[b];
@@ -601,6 +324,24 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
   A.anc_rows = Ly.anc_rows;
   A.k0 = (uint32_t)(c->seed & 0xffffffffu);
   A.k1 = (uint32_t)(c->seed >> 32) ^ c->run_id;
+  A.resume_k = c->resume_k;
+  if (c->resume_k > 0) {
+    if (c->resume_where == SMC_MEM_HOST) {  // the copies made by stage_snapshot
+      char* p = ws + Ly.snap;
+      A.snap_logw = (const double*)p;
+      p += 8 * N_;
+      A.snap_real = (const double*)p;
+      p += 8 * N_ * (size_t)m->n_real;
+      A.snap_stack = (const double*)p;
+      p += 8 * N_ * (size_t)m->stack_cap;
+      A.snap_int = (const int32_t*)p;
+    } else {
+      A.snap_logw = c->resume_logw;
+      A.snap_real = c->resume_real;
+      A.snap_int = c->resume_int;
+      A.snap_stack = c->resume_stack;
+    }
+  }
   return A;
 }
 
@@ -677,18 +418,69 @@ smc_status upload_wave(const std::vector<RunDev>& runs, void* meta, cudaStream_t
 
 namespace {
 
+// Whether a graph instantiated earlier launches exactly these waves: the wave
+// kernels' arguments are the run-table and CTA-map addresses and the wave
+// index, so a graph captured for the same addresses, CTA counts, precision and
+// number of waves is reusable once the run table (device memory) is uploaded.
+bool graph_matches(const GraphCache* g, const WavePlan& W, int precision, int max_waves) {
+  if (!g->exec || g->runs != W.runs || g->precision != precision || g->waves != max_waves)
+    return false;
+  for (int b = 0; b < 4; ++b)
+    if (g->maps[b] != W.maps[b] || g->n_ctas[b] != W.n_ctas[b]) return false;
+  return true;
+}
+
+// Capture max_waves waves on `st` into a graph and instantiate it into g.
+smc_status capture_waves(GraphCache* g, const WavePlan& W, int precision, int max_waves,
+                         cudaStream_t st) {
+  graph_cache_clear(g);
+  SMC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < max_waves && e == cudaSuccess; ++k) e = launch_wave(W, precision, st, (unsigned)k);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e != cudaSuccess ? e : e2, "capturing the waves in a graph");
+  }
+  e = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g->exec = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate(waves)");
+  }
+  g->runs = W.runs;
+  g->precision = precision;
+  g->waves = max_waves;
+  for (int b = 0; b < 4; ++b) {
+    g->maps[b] = W.maps[b];
+    g->n_ctas[b] = W.n_ctas[b];
+  }
+  return SMC_OK;
+}
+
 // Runs waves until every run is done or `max_waves` waves ran.  Known-length
-// batches launch exactly max_waves waves without reading anything back;
-// otherwise the run states are polled every 16 waves.  A run of S segments
-// needs S + 1 waves: the wave after its last segment combines that segment.
+// batches launch exactly max_waves waves without reading anything back (as one
+// CUDA graph when `graph` is given and the stream can be captured); otherwise
+// the run states are polled every 16 waves.  A run of S segments needs S + 1
+// waves: the wave after its last segment combines that segment.
 smc_status drive_waves(const WavePlan& W, int precision, const std::vector<RunState*>& states,
                        int max_waves, bool known, cudaStream_t st, std::vector<cudaEvent_t>* evs,
-                       bool timed, int* launched, double* kernel_ms) {
+                       bool timed, int* launched, double* kernel_ms, GraphCache* graph = nullptr) {
   *launched = 0;
   *kernel_ms = 0.0;
   timed = timed && evs;
   int kernels_per_wave = 0;
   for (int b = 0; b < 4; ++b) kernels_per_wave += W.n_ctas[b] ? 1 : 0;
+  if (known && graph && !timed && st != nullptr && st != cudaStreamLegacy) {
+    if (!graph_matches(graph, W, precision, max_waves)) {
+      smc_status s = capture_waves(graph, W, precision, max_waves, st);
+      if (s) return s;
+    }
+    SMC_CUDA_TRY(cudaGraphLaunch(graph->exec, st));
+    *launched = kernels_per_wave * max_waves;
+    return SMC_OK;
+  }
   int waves = 0;
   auto one = [&]() -> smc_status {
     if (timed) {
@@ -836,6 +628,10 @@ smc_status collect_run(const smc_model_s* m, const smc_run_cfg* c, const Layout&
   ct.n_limit = (int64_t)hrs.n_limit;
   ct.n_draws = (int64_t)hrs.n_draws;
   ct.n_blocks = (int64_t)hrs.n_blocks;
+  ct.log_z_closed = hrs.log_z_closed;
+  ct.debug_code = hrs.dbg_code;
+  ct.debug_index = hrs.dbg_index;
+  ct.debug_count = (int64_t)hrs.dbg_count;
   int st = hrs.status;
   if (st == 0 && !hrs.done) st = SMC_ESTEPLIMIT;
   if (st == 0 && (hrs.n_overflow || hrs.n_limit)) st = SMC_WKILLED;
@@ -853,6 +649,38 @@ smc_status check_cfg(const smc_model_s* m, const smc_run_cfg* c) {
     return set_error(SMC_EINVAL, "max_segments must be in 0..2^24");
   if (!(c->ess_threshold >= 0.0 && c->ess_threshold < 1e300))
     return set_error(SMC_EINVAL, "ess_threshold must be finite and >= 0");
+  if (c->launch_mode < SMC_LAUNCH_WAVES || c->launch_mode > SMC_LAUNCH_ONE_CTA)
+    return set_error(SMC_EINVAL, "unknown launch_mode");
+  if (c->resume_k < 0) return set_error(SMC_EINVAL, "resume_k must be >= 0");
+  if (c->resume_k > 0) {
+    if (c->resume_where != SMC_MEM_HOST && c->resume_where != SMC_MEM_DEVICE)
+      return set_error(SMC_EINVAL, "resume_where must be SMC_MEM_HOST or SMC_MEM_DEVICE");
+    if (!c->resume_logw || !c->resume_int || (m->n_real > 0 && !c->resume_real) ||
+        (m->stack_cap > 0 && !c->resume_stack))
+      return set_error(SMC_EINVAL, "a resumed run needs the snapshot's log-weights and fields");
+    const int limit = c->max_segments > 0 ? c->max_segments
+                      : (m->n_segments_known > 0 ? m->n_segments_known : kUnboundedSegments);
+    if (c->resume_k > limit)
+      return set_error(SMC_EINVAL, "resume_k %d beyond the run's segment limit %d", c->resume_k, limit);
+  }
+  return SMC_OK;
+}
+
+// Copy a host snapshot into the workspace area the resumed run reads it from.
+smc_status stage_snapshot(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws,
+                          cudaStream_t cs) {
+  if (c->resume_k <= 0 || c->resume_where != SMC_MEM_HOST) return SMC_OK;
+  const size_t N = (size_t)c->n_particles;
+  char* p = ws + Ly.snap;
+  SMC_CUDA_TRY(cudaMemcpyAsync(p, c->resume_logw, 8 * N, cudaMemcpyHostToDevice, cs));
+  p += 8 * N;
+  if (m->n_real)
+    SMC_CUDA_TRY(cudaMemcpyAsync(p, c->resume_real, 8 * N * m->n_real, cudaMemcpyHostToDevice, cs));
+  p += 8 * N * (size_t)m->n_real;
+  if (m->stack_cap)
+    SMC_CUDA_TRY(cudaMemcpyAsync(p, c->resume_stack, 8 * N * m->stack_cap, cudaMemcpyHostToDevice, cs));
+  p += 8 * N * (size_t)m->stack_cap;
+  SMC_CUDA_TRY(cudaMemcpyAsync(p, c->resume_int, 4 * N * m->n_int, cudaMemcpyHostToDevice, cs));
   return SMC_OK;
 }
 
@@ -866,6 +694,35 @@ smc_status check_result(const smc_result* r) {
 }  // namespace smc
 
 using namespace smc;
+
+extern "C" smc_status smc_set_tile_bands(const smc_tile_band* bands, int32_t n_bands) {
+  std::vector<smc_tile_band> next;
+  if (!bands && n_bands == 0) {
+    next.assign(std::begin(kBuiltinBands), std::end(kBuiltinBands));
+  } else {
+    if (!bands) return set_error(SMC_EINVAL, "NULL bands");
+    smc_status st = check_bands(bands, n_bands);
+    if (st) return st;
+    next.assign(bands, bands + n_bands);
+  }
+  std::lock_guard<std::mutex> lock(g_band_mu);
+  g_bands.swap(next);
+  return SMC_OK;
+}
+
+extern "C" smc_status smc_get_tile_bands(smc_tile_band* out, int32_t cap, int32_t* n_bands) {
+  if (!n_bands) return set_error(SMC_EINVAL, "NULL n_bands");
+  std::lock_guard<std::mutex> lock(g_band_mu);
+  *n_bands = (int32_t)g_bands.size();
+  if (out)
+    for (int i = 0; i < (int)g_bands.size() && i < cap; ++i) out[i] = g_bands[i];
+  return SMC_OK;
+}
+
+extern "C" int32_t smc_tile_size(int64_t n_particles) {
+  if (n_particles < 1 || n_particles > kMaxParticles) return 0;
+  return tile_for(n_particles);
+}
 
 extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* out) {
   if (!d || !out) return set_error(SMC_EINVAL, "NULL argument");
@@ -1005,6 +862,7 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
 
 extern "C" void smc_model_destroy(smc_model_t m) {
   if (!m) return;
+  graph_cache_clear(&m->graph);
   if (m->ws) cudaFree(m->ws);
   if (m->dev_blob) cudaFree(m->dev_blob);
   if (m->ev0) cudaEventDestroy(m->ev0);
@@ -1035,6 +893,7 @@ extern "C" smc_status smc_workspace_bytes(smc_model_t m, const smc_run_cfg* c, s
 }
 
 extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r, void* stream) {
+  NvtxRange nv_all("smc_run");
   smc_status st = check_cfg(m, c);
   if (st) return st;
   if ((st = check_result(r))) return st;
@@ -1063,21 +922,51 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
   }
   runs[0] = make_rundev(m, c, Ly, ws);
   runs[0].redundant = combine_in_every_cta(Ly.tile, Ly.n_tiles, true);
+  // a resumed run's first wave is its segment resume_k - 1 (the snapshot's load)
+  const int skip = c->resume_k > 0 ? c->resume_k - 1 : 0;
+  runs[0].start_wave = (unsigned)(-skip);
   WavePlan W;
   SMC_CUDA_TRY(cudaMemsetAsync(runs[0].rs, 0, sizeof(RunState), cs));
+  if (c->resume_k > 0) {
+    const double lz[1] = {c->resume_log_z};
+    SMC_CUDA_TRY(cudaMemcpyAsync(&runs[0].rs->log_z, lz, 8, cudaMemcpyHostToDevice, cs));
+    SMC_CUDA_TRY(cudaMemcpyAsync(&runs[0].rs->log_z_closed, lz, 8, cudaMemcpyHostToDevice, cs));
+    SMC_CUDA_TRY(cudaStreamSynchronize(cs));  // the pageable sources above are locals
+    if ((st = stage_snapshot(m, c, Ly, ws, cs))) return st;
+    // the rows before checkpoint resume_k - 1 belong to the run that made the snapshot
+    if (c->record_all_ancestors && skip > 0) {
+      const size_t rows = std::min<size_t>((size_t)skip, (size_t)Ly.anc_rows);
+      SMC_CUDA_TRY(cudaMemsetAsync(runs[0].anc, 0, 4 * (size_t)c->n_particles * rows, cs));
+      SMC_CUDA_TRY(cudaMemsetAsync(runs[0].dec, 0, 4 * (size_t)skip, cs));
+    }
+  }
   if ((st = upload_wave(runs, ws + meta_off, cs, &W, &m->staging))) return st;
   SMC_CUDA_TRY(cudaEventRecord(m->ev0, cs));
   const bool known = m->n_segments_known > 0 && Ly.max_segments >= m->n_segments_known;
   int launched = 0;
   double kms = 0.0;
   std::vector<RunState*> states{runs[0].rs};
-  st = drive_waves(W, c->precision, states, (known ? m->n_segments_known : Ly.max_segments) + 1, known, cs,
-                   &m->ev_seg, c->time_kernels != 0, &launched, &kms);
-  if (st) return st;
+  NvtxRange nv_waves("smc_run/waves");
+  // a small run (32-particle tiles, few enough for one CTA) runs every segment
+  // in one launch; the same tiles and integers as the waves
+  const bool small = c->launch_mode == SMC_LAUNCH_ONE_CTA && c->resume_k == 0 &&
+                     !c->time_kernels && Ly.tile == 32 &&
+                     Ly.n_tiles <= small_run_max_tiles(m->desc.kind);
+  if (small) {
+    SMC_CUDA_TRY(launch_small_run(m->desc.kind, c->precision, W.runs, cs));
+    launched = 1;
+  } else {
+    st = drive_waves(W, c->precision, states,
+                     (known ? m->n_segments_known : Ly.max_segments) + 1 - skip, known, cs,
+                     &m->ev_seg, c->time_kernels != 0, &launched, &kms,
+                     c->launch_mode == SMC_LAUNCH_GRAPH ? &m->graph : nullptr);
+    if (st) return st;
+  }
   SMC_CUDA_TRY(cudaEventRecord(m->ev1, cs));
   RunState hrs;
   SMC_CUDA_TRY(cudaMemcpyAsync(&hrs, runs[0].rs, sizeof(RunState), cudaMemcpyDeviceToHost, cs));
   SMC_CUDA_TRY(cudaStreamSynchronize(cs));
+  NvtxRange nv_collect("smc_run/collect");
   float ms = 0.f;
   cudaEventElapsedTime(&ms, m->ev0, m->ev1);
   if ((st = collect_run(m, c, Ly, ws, runs[0], hrs, r, cs))) return st;
@@ -1093,6 +982,7 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
 
 extern "C" smc_status smc_run_batch(const smc_model_t* ms, const smc_run_cfg* cfgs, smc_result* res,
                                     int32_t n_runs, void* stream) {
+  NvtxRange nv_all("smc_run_batch");
   if (!ms || !cfgs || !res || n_runs < 1) return set_error(SMC_EINVAL, "bad batch arguments");
   smc_status st;
   const int prec = cfgs[0].precision;
@@ -1100,6 +990,7 @@ extern "C" smc_status smc_run_batch(const smc_model_t* ms, const smc_run_cfg* cf
     if ((st = check_cfg(ms[q], &cfgs[q]))) return st;
     if ((st = check_result(&res[q]))) return st;
     if (cfgs[q].precision != prec) return set_error(SMC_EINVAL, "a batch must use one precision");
+    if (cfgs[q].resume_k != 0) return set_error(SMC_EINVAL, "resume is for smc_run only");
   }
   cudaStream_t cs = (cudaStream_t)stream;
   std::vector<Layout> lys(n_runs);
@@ -1148,8 +1039,11 @@ extern "C" smc_status smc_run_batch(const smc_model_t* ms, const smc_run_cfg* cf
   SMC_CUDA_TRY(cudaEventRecord(e0, cs));
   int launched = 0;
   double kms = 0.0;
-  st = drive_waves(W, prec, states, max_waves + 1, known, cs, nullptr, false, &launched, &kms);
+  GraphCache graph;
+  st = drive_waves(W, prec, states, max_waves + 1, known, cs, nullptr, false, &launched, &kms,
+                   cfgs[0].launch_mode == SMC_LAUNCH_GRAPH ? &graph : nullptr);
   if (st) {
+    graph_cache_clear(&graph);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
@@ -1158,7 +1052,9 @@ extern "C" smc_status smc_run_batch(const smc_model_t* ms, const smc_run_cfg* cf
   std::vector<RunState> h(n_runs);
   for (int q = 0; q < n_runs; ++q)
     SMC_CUDA_TRY(cudaMemcpyAsync(&h[q], states[q], sizeof(RunState), cudaMemcpyDeviceToHost, cs));
-  SMC_CUDA_TRY(cudaStreamSynchronize(cs));
+  const cudaError_t se = cudaStreamSynchronize(cs);
+  graph_cache_clear(&graph);  // its launch has completed
+  if (se != cudaSuccess) return cuda_fail(se, "cudaStreamSynchronize(batch)");
   float msec = 0.f;
   cudaEventElapsedTime(&msec, e0, e1);
   cudaEventDestroy(e0);

@@ -15,11 +15,11 @@ constexpr int kMaxAncRows = 4096;
 constexpr int kMaxSegments = 1 << 24;
 constexpr int kUnboundedSegments = 1 << 20;
 constexpr int64_t kMaxParticles = (int64_t)0x7fffffff - 256;
-constexpr int64_t kTileSlots = 456;  // tile = ceil(N / 456): 152 SMs x 3 resident CTAs
 
 // Per-run device state (one struct per run, in the run's workspace).
 struct RunState {
   double log_z, m, S;
+  double log_z_closed;  // log Z without a closure made only because the step limit ended the run
   // the next search's scalars when the run combines in one CTA: S / N and
   // u S / N in 64.64 fixed point, and the boundary tolerance (units U)
   unsigned long long d_hi, d_lo, z0_hi, z0_lo;
@@ -31,6 +31,12 @@ struct RunState {
   int32_t kmax, G;        // the run's reference exponent and coarsening (one-CTA combine)
   int32_t resample;       // the one-CTA combine's decision for the next wave
   int32_t n_ess_near;     // ESS decisions within 1e-9 of the threshold
+  // checking build (SMC_DEBUG_CHECKS): the first out-of-range access found and
+  // skipped (code: 1 ancestor, 2 block index, 3 stack pointer, 4 dispatch), its
+  // particle, and how many were found
+  int32_t dbg_code, dbg_pad;
+  long long dbg_index;
+  unsigned long long dbg_count;
 };
 
 // Everything a CTA needs about its run (copied to shared memory per CTA).
@@ -54,11 +60,17 @@ struct RunDev {
   int redundant;        // combine a segment's tiles in every CTA of the next wave (else in the last CTA)
   int ess;              // ess_tau > 0 (an integer flag for the kernel's branches)
   uint32_t k0, k1;
+  // resume from a snapshot: segment resume_k - 1 loads the population (device copies)
+  int resume_k;
+  const double* snap_logw;
+  const double* snap_real;
+  const int32_t* snap_int;
+  const double* snap_stack;
 };
 
 struct Layout {
   size_t real[2], ints[2], stack[2], logw, E[2], rec[2], tq[2], dec, tO, rs, anc, incr,
-      fin_real, fin_int, fin_stack, total;
+      fin_real, fin_int, fin_stack, snap, total;
   int n_tiles, tile, anc_rows, max_segments;
 };
 
@@ -68,6 +80,22 @@ struct WavePlan {
   const int2* maps[4] = {nullptr, nullptr, nullptr, nullptr};
   int n_ctas[4] = {0, 0, 0, 0};
 };
+
+// An instantiated CUDA graph of a known-length sequence of waves and the wave
+// plan it was captured for.
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  const RunDev* runs = nullptr;
+  const int2* maps[4] = {nullptr, nullptr, nullptr, nullptr};
+  int n_ctas[4] = {0, 0, 0, 0};
+  int precision = -1, waves = 0;
+};
+void graph_cache_clear(GraphCache* g);
+
+// A whole run in one CTA (smc_small.cu): for runs of 32-particle tiles, at most
+// small_run_max_tiles(kind) of them; one launch, grid 1.
+int small_run_max_tiles(int kind);
+cudaError_t launch_small_run(int kind, int precision, const RunDev* runs, cudaStream_t st);
 
 }  // namespace smc
 
@@ -82,6 +110,7 @@ struct smc_model_s {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> ev_seg;  // per-launch timing pairs (time_kernels)
   std::vector<char> staging;        // host staging of the run table
+  smc::GraphCache graph;            // smc_run's captured waves (SMC_LAUNCH_GRAPH)
 };
 
 namespace smc {

@@ -1,6 +1,7 @@
 // smc_internal.h -- host-side helpers shared by the library's translation units.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdarg>
 #include <cstdint>
@@ -25,5 +26,14 @@ inline smc_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// An NVTX range around a host phase of a call (shown by Nsight Systems and
+// other NVTX tools; without one attached the calls do nothing).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace smc

@@ -70,6 +70,17 @@ struct StateView {
   }
 };
 
+// A snapshot of a population in smc_result's output layouts (device memory):
+// log-weights [N], real fields [n_real][N] (f64), int fields [n_int][N], stack
+// rows [cap][N] (f64).  A model's load() puts particle i of it into the lane and
+// into the state buffer being written (its stack rows).
+struct SnapView {
+  const double* logw;
+  const double* real;
+  const int32_t* ints;
+  const double* stack;
+};
+
 // ------------------------------------------------------------------------
 // Linear-Gaussian state-space model (Eq. 2 family, blocks of Fig. 3):
 //   block 0 `init`: x = x0_mean + x0_sd z, then a non-checkpoint jump to iter;
@@ -103,6 +114,12 @@ struct LgModel {
   __device__ static void store(const Lane& L, const StateView& Sn, int i, int N) {
     Sn.rf<R>(0, i, N) = L.x;
     Sn.inf_(0, i, N) = L.pc;
+  }
+  __device__ static void load(Lane& L, const StateView&, const SnapView& P, int i, int N,
+                              const Stream&) {
+    L.x = (R)P.real[i];
+    L.pc = P.ints[i];
+    L.logw = (R)P.logw[i];
   }
   __device__ static void begin(Lane& L) {
     L.ckpt = false;
@@ -158,6 +175,12 @@ struct GeoModel {
   __device__ static void store(const Lane& L, const StateView& Sn, int i, int N) {
     Sn.inf_(0, i, N) = L.pc;
     Sn.inf_(1, i, N) = L.count;
+  }
+  __device__ static void load(Lane& L, const StateView&, const SnapView& P, int i, int N,
+                              const Stream&) {
+    L.pc = P.ints[i];
+    L.count = P.ints[(size_t)N + i];
+    L.logw = (R)P.logw[i];
   }
   __device__ static void begin(Lane& L) {
     L.ckpt = false;
@@ -228,6 +251,15 @@ struct SeirModel {
     for (int f = 0; f < 9; ++f) Sn.inf_(f + 1, i, N) = L.c[f];
 #pragma unroll
     for (int f = 0; f < 6; ++f) Sn.rf<R>(f, i, N) = L.th[f];
+  }
+  __device__ static void load(Lane& L, const StateView&, const SnapView& P, int i, int N,
+                              const Stream&) {
+    L.pc = P.ints[i];
+#pragma unroll
+    for (int f = 0; f < 9; ++f) L.c[f] = P.ints[(size_t)(f + 1) * N + i];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) L.th[f] = (R)P.real[(size_t)f * N + i];
+    L.logw = (R)P.logw[i];
   }
   __device__ static void begin(Lane& L) {
     L.ckpt = false;
@@ -441,6 +473,22 @@ struct TreeModel {
     Sn.inf_(0, i, N) = L.pc;
     if (RS) Sn.inf_(1, i, N) = L.sp;
   }
+  // the snapshot holds lambda and mu; CRBD's internal log(lambda) is formed again
+  // exactly as the prior block formed it
+  __device__ static void load(Lane& L, const StateView& Sn, const SnapView& P, int i, int N,
+                              const Stream& s) {
+    L.lam = (R)P.real[i];
+    L.mu = (R)P.real[(size_t)N + i];
+    L.pc = P.ints[i];
+    L.logw = (R)P.logw[i];
+    L.sp = 0;
+    if (RS) {
+      L.sp = P.ints[(size_t)N + i];
+      for (int r = 0; r < L.sp; ++r) Sn.st<R>(r, i, N) = (R)P.stack[(size_t)r * N + i];
+    } else {
+      L.loglam = lg(L.lam, s);
+    }
+  }
   __device__ static void begin(Lane& L) {
     L.ckpt = false;
     L.overflow = L.limited = 0;
@@ -586,6 +634,15 @@ struct TreeDsModel {
     Sn.rf<R>(2, i, N) = L.am;
     Sn.rf<R>(3, i, N) = L.bm;
     Sn.inf_(0, i, N) = L.pc;
+  }
+  __device__ static void load(Lane& L, const StateView&, const SnapView& P, int i, int N,
+                              const Stream&) {
+    L.al = (R)P.real[i];
+    L.bl = (R)P.real[(size_t)N + i];
+    L.am = (R)P.real[(size_t)2 * N + i];
+    L.bm = (R)P.real[(size_t)3 * N + i];
+    L.pc = P.ints[i];
+    L.logw = (R)P.logw[i];
   }
   __device__ static void begin(Lane& L) {
     L.ckpt = false;

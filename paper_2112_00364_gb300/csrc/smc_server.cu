@@ -39,7 +39,11 @@ namespace smc {
 // Snapshot of a run's state after a wave: everything retiring it needs.
 struct RunFlags {
   unsigned long long n_near, n_overflow, n_limit, n_draws, n_blocks;
-  int32_t done, status, n_segments, n_resamples, n_ess_near, pad;
+  double log_z_closed;
+  long long dbg_index;
+  unsigned long long dbg_count;
+  int32_t dbg_code;
+  int32_t done, status, n_segments, n_resamples, n_ess_near;
 };
 
 __global__ void gather_flags_kernel(const RunDev* __restrict__ runs, int n, RunFlags* out) {
@@ -52,12 +56,15 @@ __global__ void gather_flags_kernel(const RunDev* __restrict__ runs, int n, RunF
   f.n_segments = rs->n_segments;
   f.n_resamples = rs->n_resamples;
   f.n_ess_near = rs->n_ess_near;
-  f.pad = 0;
   f.n_near = rs->n_near;
   f.n_overflow = rs->n_overflow;
   f.n_limit = rs->n_limit;
   f.n_draws = rs->n_draws;
   f.n_blocks = rs->n_blocks;
+  f.log_z_closed = rs->log_z_closed;
+  f.dbg_code = rs->dbg_code;
+  f.dbg_index = rs->dbg_index;
+  f.dbg_count = rs->dbg_count;
   out[i] = f;
 }
 
@@ -299,6 +306,10 @@ smc_status retire(Server* S, int b) {
     hrs.n_limit = f[i].n_limit;
     hrs.n_draws = f[i].n_draws;
     hrs.n_blocks = f[i].n_blocks;
+    hrs.log_z_closed = f[i].log_z_closed;
+    hrs.dbg_code = f[i].dbg_code;
+    hrs.dbg_index = f[i].dbg_index;
+    hrs.dbg_count = f[i].dbg_count;
     smc_status st = collect_run(q->model, &q->cfg, q->ly, q->ws, q->dev, hrs, q->result, S->stream);
     if (!st && q->ticket == S->fail_ticket)
       st = set_error(SMC_ECUDA, "injected failure retiring ticket %llu (SMC_SERVER_FAIL_TICKET)",
@@ -349,7 +360,10 @@ void worker_main(Server* S) {
   bool last_flags = false;
   smc_status err = SMC_OK;
   while (!err) {
-    admit(S, &err);
+    {
+      NvtxRange nv("smc_server/admit");
+      admit(S, &err);
+    }
     if (err) break;
     if (S->resident.empty()) {
       if (last_flags) {
@@ -366,6 +380,7 @@ void worker_main(Server* S) {
     }
     if (S->table_dirty && (err = upload_table(S))) break;
     const int per_poll = std::max(1, S->cfg.poll_waves);
+    NvtxRange nv_waves("smc_server/waves");
     for (int w = 0; w < per_poll && !err; ++w) {
       cudaError_t e = launch_wave(S->plan, S->cfg.precision, S->stream, (unsigned)S->waves.load());
       if (e != cudaSuccess) err = cuda_fail(e, "wave launch");
@@ -387,6 +402,7 @@ void worker_main(Server* S) {
         err = set_error(SMC_ECUDA, "wave failed");
         break;
       }
+      NvtxRange nv("smc_server/retire");
       if ((err = retire(S, parity ^ 1))) break;
     }
     last_flags = true;
@@ -474,6 +490,7 @@ extern "C" smc_status smc_server_submit(smc_server_t h, smc_model_t m, const smc
   Server* S = &h->s;
   if (c->precision != S->cfg.precision)
     return set_error(SMC_EINVAL, "request precision differs from the server's");
+  if (c->resume_k != 0) return set_error(SMC_EINVAL, "resume is for smc_run only");
   if (S->worker_error) return set_error(S->worker_error, "server worker stopped after an error");
   Request* q = new (std::nothrow) Request();
   if (!q) return set_error(SMC_ENOMEM, "host allocation failed");

@@ -8,6 +8,7 @@ library cannot be loaded the import of ``lib()`` fails loudly.
 from __future__ import annotations
 
 import ctypes as C
+import os
 from dataclasses import dataclass
 from pathlib import Path
 
@@ -63,8 +64,11 @@ class RunCfg(C.Structure):
     _fields_ = [("n_particles", C.c_int64), ("seed", C.c_uint64), ("run_id", C.c_uint32),
                 ("precision", C.c_int32), ("max_segments", C.c_int32),
                 ("record_all_ancestors", C.c_int32), ("time_kernels", C.c_int32),
-                ("pad_", C.c_int32), ("workspace", _vp),
-                ("workspace_bytes", C.c_size_t), ("ess_threshold", C.c_double)]
+                ("launch_mode", C.c_int32), ("workspace", _vp),
+                ("workspace_bytes", C.c_size_t), ("ess_threshold", C.c_double),
+                ("resume_k", C.c_int32), ("resume_where", C.c_int32), ("resume_logw", _vp),
+                ("resume_real", _vp), ("resume_int", _vp), ("resume_stack", _vp),
+                ("resume_log_z", C.c_double)]
 
 
 class Counters(C.Structure):
@@ -72,13 +76,20 @@ class Counters(C.Structure):
                 ("n_near_boundary", C.c_int64), ("n_overflow", C.c_int64),
                 ("n_limit", C.c_int64), ("device_ms", C.c_double), ("kernel_ms", C.c_double),
                 ("kernel_launches", C.c_int32), ("n_ess_near", C.c_int32), ("status", C.c_int32),
-                ("pad2_", C.c_int32), ("n_draws", C.c_int64), ("n_blocks", C.c_int64)]
+                ("pad2_", C.c_int32), ("n_draws", C.c_int64), ("n_blocks", C.c_int64),
+                ("log_z_closed", C.c_double), ("debug_code", C.c_int32), ("pad3_", C.c_int32),
+                ("debug_index", C.c_int64), ("debug_count", C.c_int64)]
 
 
 class Result(C.Structure):
     _fields_ = [("where", C.c_int32), ("ancestors_rows", C.c_int32), ("log_z", _vp),
                 ("final_logw", _vp), ("ancestors", _vp), ("real_fields", _vp),
                 ("int_fields", _vp), ("stack", _vp), ("resampled", _vp), ("counters", Counters)]
+
+
+class TileBand(C.Structure):
+    _fields_ = [("n_max", C.c_int64), ("slots", C.c_int32), ("tile_min", C.c_int32),
+                ("tile_max", C.c_int32), ("pad_", C.c_int32)]
 
 
 class ServerCfg(C.Structure):
@@ -96,16 +107,20 @@ _lib = None
 
 
 def lib():
-    """Load libsmc.so (building it first if the sources are newer)."""
+    """Load libsmc.so (building it first if the sources are newer); with the
+    environment variable SMC_LIB_VARIANT=debug, the checking build
+    libsmc_debug.so instead (one variant per process)."""
     global _lib
     if _lib is None:
         from . import build as _build
 
-        if not _build.up_to_date():
-            _build.build()
-        if not LIB_PATH.exists():
-            raise RuntimeError(f"CUDA library missing: {LIB_PATH}")
-        L = C.CDLL(str(LIB_PATH))
+        debug = os.environ.get("SMC_LIB_VARIANT", "") == "debug"
+        path = _build.LIB_DEBUG if debug else LIB_PATH
+        if not _build.up_to_date(path):
+            _build.build(debug=debug)
+        if not path.exists():
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = C.CDLL(str(path))
         L.smc_model_register.argtypes = [C.POINTER(ModelDesc), C.POINTER(_vp)]
         L.smc_model_register.restype = C.c_int32
         L.smc_model_destroy.argtypes = [_vp]
@@ -148,6 +163,12 @@ def lib():
         L.smc_sample.restype = C.c_int32
         L.smc_math_eval.argtypes = [C.c_int32, _vp, _vp, C.c_int64, _vp]
         L.smc_math_eval.restype = C.c_int32
+        L.smc_set_tile_bands.argtypes = [_vp, C.c_int32]
+        L.smc_set_tile_bands.restype = C.c_int32
+        L.smc_get_tile_bands.argtypes = [_vp, C.c_int32, C.POINTER(C.c_int32)]
+        L.smc_get_tile_bands.restype = C.c_int32
+        L.smc_tile_size.argtypes = [C.c_int64]
+        L.smc_tile_size.restype = C.c_int32
         L.smc_last_error.argtypes = []
         L.smc_last_error.restype = C.c_char_p
         L.smc_version.argtypes = []
@@ -237,10 +258,14 @@ class Model:
         return out.value
 
 
+LAUNCH = {"waves": 0, "graph": 1, "one_cta": 2}
+
+
 def _cfg(N, seed, run_id, precision, max_segments, record_all, workspace, time_kernels=False,
-         ess_threshold=0.0):
+         ess_threshold=0.0, launch="waves"):
     c = RunCfg()
     c.time_kernels = int(time_kernels)
+    c.launch_mode = LAUNCH[launch]
     c.ess_threshold = float(ess_threshold)
     c.n_particles, c.seed, c.run_id = N, seed, run_id
     c.precision = PRECISIONS[precision]
@@ -297,7 +322,9 @@ def _result_dict(st: int, r: Result, out: dict, where: str, record_all: bool) ->
                n_resamples=c.n_resamples, n_near_boundary=c.n_near_boundary,
                n_overflow=c.n_overflow, n_limit=c.n_limit, device_ms=c.device_ms,
                kernel_ms=c.kernel_ms, kernel_launches=c.kernel_launches, n_ess_near=c.n_ess_near,
-               n_draws=c.n_draws, n_blocks=c.n_blocks, **out)
+               n_draws=c.n_draws, n_blocks=c.n_blocks, log_z_closed=c.log_z_closed,
+               debug_code=c.debug_code, debug_index=c.debug_index, debug_count=c.debug_count,
+               **out)
     res["log_z_value"] = float(out["log_z"][0]) if where == "host" else None
     if record_all:
         n_tr = max(0, c.n_segments - 1)  # checkpoints after which the run went on
@@ -310,12 +337,35 @@ def _result_dict(st: int, r: Result, out: dict, where: str, record_all: bool) ->
 def run(model: Model, N: int, seed: int, run_id: int = 0, precision: str = "fp64",
         max_segments: int = 0, record_all_ancestors: bool = False, where: str = "host",
         stream=None, workspace=None, outputs: dict | None = None,
-        time_kernels: bool = False, ess_threshold: float = 0.0) -> dict:
+        time_kernels: bool = False, ess_threshold: float = 0.0,
+        launch: str = "waves", launch_graph: bool = False,
+        resume_from: dict | None = None) -> dict:
     """smc_run.  where="host": outputs are numpy arrays; where="device": outputs are
     torch CUDA tensors (allocated here unless passed in `outputs`).  ess_threshold
-    tau > 0: resample only when ESS < tau N."""
+    tau > 0: resample only when ESS < tau N.  launch: "waves", "graph" (the waves as
+    one captured CUDA graph; needs a stream other than the legacy default stream;
+    launch_graph=True says the same) or "one_cta" (a small run in one CTA).
+    resume_from: the result of a run of the same model, N, seed, run_id, precision
+    and ess_threshold that max_segments stopped (a snapshot); this run continues it."""
     cfg = _cfg(N, seed, run_id, precision, max_segments, record_all_ancestors, workspace,
-               time_kernels, ess_threshold)
+               time_kernels, ess_threshold, "graph" if launch_graph else launch)
+    keep = []
+    if resume_from is not None:
+        snap = resume_from
+        dev = hasattr(snap["final_logw"], "data_ptr")
+        if not dev:
+            snap = {k: np.ascontiguousarray(snap[k]) if snap.get(k) is not None else None
+                    for k in ("final_logw", "real_fields", "int_fields", "stack")}
+            keep.append(snap)
+        cfg.resume_k = int(resume_from["n_segments"])
+        cfg.resume_where = MEM_DEVICE if dev else MEM_HOST
+        cfg.resume_logw = _ptr(snap["final_logw"])
+        cfg.resume_int = _ptr(snap["int_fields"])
+        if model.n_real:
+            cfg.resume_real = _ptr(snap["real_fields"])
+        if model.stack_cap:
+            cfg.resume_stack = _ptr(snap["stack"])
+        cfg.resume_log_z = float(resume_from["log_z_closed"])
     rows = _rows(model, max_segments, record_all_ancestors)
     out = _alloc_outputs(model, N, rows, where, outputs)
     r = _result_struct(out, where, rows)
@@ -326,7 +376,7 @@ def run(model: Model, N: int, seed: int, run_id: int = 0, precision: str = "fp64
 
 
 def run_batch(models: list, specs: list, precision: str = "fp64", where: str = "host",
-              record_all_ancestors: bool = False, stream=None) -> list:
+              record_all_ancestors: bool = False, stream=None, launch_graph: bool = False) -> list:
     """smc_run_batch.  specs[q] = dict(N=..., seed=..., run_id=0, max_segments=0);
     returns one result dict per run (same keys as run())."""
     n = len(models)
@@ -335,7 +385,8 @@ def run_batch(models: list, specs: list, precision: str = "fp64", where: str = "
     outs, rows_l = [], []
     for q, (m, sp) in enumerate(zip(models, specs)):
         c = _cfg(sp["N"], sp["seed"], sp.get("run_id", 0), precision, sp.get("max_segments", 0),
-                 record_all_ancestors, None, False, sp.get("ess_threshold", 0.0))
+                 record_all_ancestors, None, False, sp.get("ess_threshold", 0.0),
+                 "graph" if launch_graph else "waves")
         cfgs[q] = c
         rows = _rows(m, sp.get("max_segments", 0), record_all_ancestors)
         out = _alloc_outputs(m, sp["N"], rows, where, sp.get("outputs"))
@@ -504,6 +555,31 @@ def math_eval(fn: str, x):
     _check(lib().smc_math_eval(code, _ptr(xd), _ptr(y), xd.numel(), None))
     out = y.cpu().numpy()
     return out.view(np.int64) if 6 <= code <= 9 else out
+
+
+def set_tile_bands(bands) -> None:
+    """Replace the process's tile table: a list of (n_max, slots, tile_min,
+    tile_max) with increasing n_max; None restores the built-in table."""
+    if bands is None:
+        _check(lib().smc_set_tile_bands(None, 0))
+        return
+    arr = (TileBand * len(bands))()
+    for i, (n_max, slots, tmin, tmax) in enumerate(bands):
+        arr[i].n_max, arr[i].slots, arr[i].tile_min, arr[i].tile_max = n_max, slots, tmin, tmax
+    _check(lib().smc_set_tile_bands(arr, len(bands)))
+
+
+def get_tile_bands() -> list:
+    n = C.c_int32()
+    _check(lib().smc_get_tile_bands(None, 0, C.byref(n)))
+    arr = (TileBand * max(1, n.value))()
+    _check(lib().smc_get_tile_bands(arr, n.value, C.byref(n)))
+    return [(b.n_max, b.slots, b.tile_min, b.tile_max) for b in arr[: n.value]]
+
+
+def tile_size(N: int) -> int:
+    """The tile size a run of N particles gets under the current table."""
+    return int(lib().smc_tile_size(N))
 
 
 def version() -> str:

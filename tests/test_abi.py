@@ -87,3 +87,31 @@ def test_particle_limit_agrees_across_header_engine_and_binding():
     # the last tile of a maximal run, rounded up to a whole 256-particle CTA,
     # still indexes below 2^31
     assert -(-smc.MAX_PARTICLES // 256) * 256 + 255 < 2 ** 31
+
+
+def test_tile_table_rules_and_validation():
+    """The tile size is a function of N from the table of N bands (host only):
+    the built-in table reaches the largest run and keeps tiles in 1..256; a
+    replacement table is applied and validated; None restores the built-in."""
+    builtin = smc.get_tile_bands()
+    assert builtin and builtin[-1][0] >= smc.MAX_PARTICLES
+    for N in (1, 31, 32, 1000, 4097, 65536, 300_001, 1 << 20, smc.MAX_PARTICLES):
+        t = smc.tile_size(N)
+        assert 1 <= t <= min(256, N)
+    assert smc.tile_size(0) == 0 and smc.tile_size(smc.MAX_PARTICLES + 1) == 0
+    try:
+        smc.set_tile_bands([(1000, 10, 32, 128), (smc.MAX_PARTICLES, 456, 32, 256)])
+        assert smc.tile_size(900) == 90
+        assert smc.tile_size(100) == 32 and smc.tile_size(5000) == 32
+        assert smc.tile_size(1 << 20) == 256
+        for bad in ([(1000, 0, 32, 64), (smc.MAX_PARTICLES, 1, 1, 1)],      # slots 0
+                    [(smc.MAX_PARTICLES, 1, 64, 32)],                      # min > max
+                    [(smc.MAX_PARTICLES, 1, 1, 512)],                      # above 256
+                    [(1000, 1, 1, 1)],                                     # does not reach
+                    [(1000, 1, 1, 1), (1000, 1, 1, 1)]):                   # not increasing
+            with pytest.raises(smc.SmcError):
+                smc.set_tile_bands(bad)
+        assert smc.tile_size(900) == 90  # a rejected table leaves the current one
+    finally:
+        smc.set_tile_bands(None)
+    assert smc.get_tile_bands() == builtin

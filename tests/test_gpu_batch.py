@@ -163,3 +163,79 @@ def test_batch_every_model_kind_and_ess(precision):
             np.testing.assert_array_equal(b["resampled"], a["resampled"])
     for m in models:
         m.close()
+
+
+def test_graph_launch_gives_the_same_bits():
+    """Waves launched as one captured CUDA graph give exactly the results of the
+    same waves launched one by one: smc_run (the graph kept in the model handle
+    and launched again for new seeds, captured again when N changes) and
+    smc_run_batch (captured per call), FP64 and FP32."""
+    import torch
+    from paper_2112_00364_gb300 import smc
+
+    s = torch.cuda.Stream()
+    tree = inputs.yule_tree(24, seed=5)
+    m = smc.Model("crbd", tree=tree)
+    for N, seed, prec in [(3000, 1, "fp64"), (3000, 2, "fp64"), (3000, 3, "fp32"),
+                          (777, 4, "fp64"), (3000, 5, "fp64")]:
+        a = smc.run(m, N, seed, precision=prec, stream=s, record_all_ancestors=True)
+        g = smc.run(m, N, seed, precision=prec, stream=s, record_all_ancestors=True,
+                    launch_graph=True)
+        assert g["log_z_value"] == a["log_z_value"] and g["n_segments"] == a["n_segments"]
+        np.testing.assert_array_equal(g["ancestors"], a["ancestors"])
+        np.testing.assert_array_equal(g["final_logw"], a["final_logw"])
+        np.testing.assert_array_equal(g["real_fields"], a["real_fields"])
+    specs = inputs.batch_specs(24, seed=8)
+    models = [smc.Model(sp.kind, **(dict(obs=inputs.lg_observations(sp.T, seed=sp.obs_seed))
+                                    if sp.kind == "lg" else
+                                    dict(tree=inputs.yule_tree(sp.tips, seed=sp.tree_seed))))
+              for sp in specs]
+    rs = [dict(N=sp.n_particles, seed=sp.seed, run_id=q) for q, sp in enumerate(specs)]
+    for prec in ("fp32", "fp64"):
+        a = smc.run_batch(models, rs, precision=prec, stream=s)
+        g = smc.run_batch(models, rs, precision=prec, stream=s, launch_graph=True)
+        for x, y in zip(a, g):
+            assert x["log_z_value"] == y["log_z_value"]
+            np.testing.assert_array_equal(x["final_logw"], y["final_logw"])
+            np.testing.assert_array_equal(x["ancestors"], y["ancestors"])
+    for mm in models + [m]:
+        mm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_one_cta_launch_gives_the_same_bits(precision):
+    """A small run (32-particle tiles, few enough for one CTA) launched as one
+    CTA that runs every segment gives exactly what its waves give, for every
+    model kind, ESS-triggered resampling and record_all included; one case
+    against the oracle too."""
+    import oracle
+    from parity import assert_parity_exact, assert_parity_fp64
+
+    from paper_2112_00364_gb300 import smc
+
+    tree = inputs.yule_tree(20, seed=9)
+    cases = [("lg", dict(obs=inputs.lg_observations(40, seed=3)), 1024, 0.0),
+             ("lg", dict(obs=inputs.lg_observations(25, seed=4)), 700, 0.5),
+             ("geometric", {}, 999, 0.0),
+             ("crbd", dict(tree=tree), 512, 0.0),
+             ("rateshift", dict(tree=tree, sigma=0.3, lam_stack_cap=tree.max_pending_right() + 1),
+              480, 0.5),
+             ("crbd_ds", dict(tree=tree), 300, 0.5),
+             ("seir", dict(obs=inputs.seir_observations(21, seed=7)), 512, 0.0)]
+    for q, (kind, p, N, tau) in enumerate(cases):
+        m = smc.Model(kind, **p)
+        kw = dict(precision=precision, record_all_ancestors=True, ess_threshold=tau)
+        a = smc.run(m, N, 60 + q, **kw)
+        b = smc.run(m, N, 60 + q, launch="one_cta", **kw)
+        assert b["kernel_launches"] == 1, kind
+        assert a["log_z_value"] == b["log_z_value"] and a["n_segments"] == b["n_segments"], kind
+        for key in ("final_logw", "int_fields", "ancestors", "resampled", "real_fields", "stack"):
+            if key in a:
+                np.testing.assert_array_equal(a[key], b[key])
+        assert (a["n_near_boundary"], a["n_draws"], a["n_blocks"]) == \
+            (b["n_near_boundary"], b["n_draws"], b["n_blocks"])
+        if q == 3:
+            o = oracle.smc_run(kind, N, 60 + q, follow=b["ancestors"], record_ancestors=True,
+                               precision=oracle.FP64 if precision == "fp64" else oracle.FP32, **p)
+            (assert_parity_fp64 if precision == "fp64" else assert_parity_exact)(b, o)
+        m.close()
