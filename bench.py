@@ -101,8 +101,8 @@ ISSUE_PEAK = 152 * 4 * 2070e6
 
 
 # the segment kernel's sources (the standalone resampling kernels are not among them)
-KERNEL_SOURCES = ("smc_engine.cu", "smc_step.cuh", "smc_engine.h", "smc_models.cuh",
-                  "smc_device.cuh", "smc_combine.cuh")
+KERNEL_SOURCES = ("smc_engine.cu", "smc_step.cuh", "smc_waves_kind.cu", "smc_engine.h",
+                  "smc_models.cuh", "smc_device.cuh", "smc_combine.cuh")
 # the standalone resampling kernels' sources
 RS_SOURCES = ("smc_prims.cu", "smc_device.cuh", "smc_combine.cuh")
 

@@ -79,6 +79,7 @@ struct WavePlan {
   const RunDev* runs = nullptr;
   const int2* maps[4] = {nullptr, nullptr, nullptr, nullptr};
   int n_ctas[4] = {0, 0, 0, 0};
+  int kind = 0;  // the model of every run of the plan (SMC_MODEL_*), 0 when they differ
 };
 
 // An instantiated CUDA graph of a known-length sequence of waves and the wave
@@ -130,6 +131,9 @@ size_t wave_meta_bytes(const std::vector<RunDev>& runs);
 smc_status upload_wave(const std::vector<RunDev>& runs, void* meta, cudaStream_t st, WavePlan* W,
                        std::vector<char>* staging);
 cudaError_t launch_wave(const WavePlan& W, int precision, cudaStream_t st, unsigned wave);
+// the waves of a plan whose runs all run the linear-Gaussian or the CRBD model
+cudaError_t launch_wave_kind(const WavePlan& W, int precision, cudaStream_t st, unsigned wave);
+int uniform_kind(const std::vector<RunDev>& runs);
 smc_status collect_run(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws,
                        const RunDev& A, const RunState& hrs, smc_result* r, cudaStream_t cs);
 smc_status check_cfg(const smc_model_s* m, const smc_run_cfg* c);

@@ -186,6 +186,7 @@ smc_status upload_table(Server* S) {
     if (!maps[b].empty()) std::memcpy(S->pinned_meta + off, maps[b].data(), sizeof(int2) * maps[b].size());
     off = align_up(off + sizeof(int2) * maps[b].size(), 256);
   }
+  S->plan.kind = uniform_kind(runs);
   SMC_CUDA_TRY(cudaMemcpyAsync(S->meta, S->pinned_meta, off, cudaMemcpyHostToDevice, S->stream));
   SMC_CUDA_TRY(cudaEventRecord(S->meta_ev, S->stream));
   S->table_dirty = false;

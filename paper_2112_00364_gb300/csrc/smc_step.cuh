@@ -379,4 +379,82 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   }
 }
 
+// One wave: CTA b runs tile cta_map[b].y of run cta_map[b].x, segment
+// k = wave - start_wave of that run.
+// 768 resident threads per SM (three 256-thread CTAs: the grid sizing of
+// tile_for) bounds the kernel to 85 registers per thread.
+// KIND 0 dispatches on each run's model; a KIND of SMC_MODEL_* is the kernel of
+// waves whose runs all run that model (only its block table is compiled in).
+template <typename R, int TPB, int KIND>
+__global__ void __launch_bounds__(TPB, 768 / TPB) wave_kernel(const RunDev* __restrict__ runs,
+                                                   const int2* __restrict__ cta_map, unsigned wave) {
+  __shared__ __align__(16) RunDev sr;
+  __shared__ double sh[TPB / 32 + 2 + TPB + 1];
+  __shared__ int sh_last;
+  __shared__ int sh_kw[TPB / 32];
+  __shared__ long long sh_O[redundant_cap(TPB)];
+  __shared__ int sh_ks[redundant_cap(TPB)];
+  const int2 rt = cta_map[blockIdx.x];
+  {
+    const int* src = reinterpret_cast<const int*>(runs + rt.x);
+    int* dst = reinterpret_cast<int*>(&sr);
+    for (int w = threadIdx.x; w < (int)(sizeof(RunDev) / 4); w += TPB) dst[w] = src[w];
+  }
+  __syncthreads();
+  // Waves are launched with programmatic stream serialisation: the next wave's
+  // CTAs may start (and copy their run table, which no kernel writes) while
+  // this wave's last CTAs still run; everything below reads what the previous
+  // wave wrote, so it waits for that wave's completion first.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  RunState* rs = sr.rs;
+  if (*(volatile int32_t*)&rs->done) return;
+  const int k = (int)(wave - sr.start_wave);  // wraps correctly past 2^32 waves
+  if (k < 0) return;
+  if (KIND == SMC_MODEL_LG) {
+    step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks);
+    return;
+  }
+  if (KIND == SMC_MODEL_CRBD) {
+    step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks);
+    return;
+  }
+  switch (sr.md.kind) {
+    case SMC_MODEL_LG: step_tile<LgModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    case SMC_MODEL_SEIR: step_tile<SeirModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    case SMC_MODEL_CRBD: step_tile<TreeModel<R, false>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    case SMC_MODEL_RATESHIFT: step_tile<TreeModel<R, true>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    case SMC_MODEL_CRBD_DS: step_tile<TreeDsModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+    default: step_tile<GeoModel<R>, TPB>(sr, rt.y, k, sh, &sh_last, sh_kw, sh_O, sh_ks); break;
+  }
+}
+
+// One bucket of a wave, launched so that it may begin before the kernel ahead
+// of it in the stream has finished (wave_kernel waits for it where it must).
+template <typename R, int TPB, int KIND>
+cudaError_t launch_pdl(const RunDev* runs, const int2* map, int n, cudaStream_t st, unsigned wave) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)n);
+  cfg.blockDim = dim3(TPB);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, wave_kernel<R, TPB, KIND>, runs, map, wave);
+}
+
+template <typename R, int KIND>
+cudaError_t launch_bucket(int b, const RunDev* runs, const int2* map, int n, cudaStream_t st,
+                          unsigned wave) {
+  switch (b) {
+    case 0: return launch_pdl<R, 32, KIND>(runs, map, n, st, wave);
+    case 1: return launch_pdl<R, 64, KIND>(runs, map, n, st, wave);
+    case 2: return launch_pdl<R, 128, KIND>(runs, map, n, st, wave);
+    default: return launch_pdl<R, 256, KIND>(runs, map, n, st, wave);
+  }
+}
+
 }  // namespace smc
