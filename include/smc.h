@@ -404,6 +404,45 @@ smc_status smc_resample(const double *logw, int64_t N, double u, int32_t *ancest
 smc_status smc_resample_static(const double *logw, int64_t N, double u, int32_t *ancestors,
                                double *out3, int64_t *n_near, void *stream);
 
+/* ---------------- one population sharded over ranks ----------------
+ * Section 3.3's parallel systematic resampling of a population held by several
+ * GPUs in consecutive slices: rank r holds particles [first_r, first_r +
+ * n_local_r) of n_total, every slice starting on a whole tile of
+ * SMC_RESAMPLE_TILE particles and every slice but the last holding whole tiles.
+ * The exchange step between the ranks is the tiles' records:
+ *   1. every rank: smc_shard_reduce on its slice writes its tiles' records;
+ *   2. the ranks exchange the records (an all-gather in rank order: the records
+ *      of the whole population in tile order, 16 bytes a tile);
+ *   3. every rank: smc_shard_ancestors combines all records (the same integers,
+ *      S, log-Z increment and search scalars on every rank) and searches the
+ *      offsets its own tiles own, [range[0], range[1]): ancestors[i] for those i
+ *      (global particle indices, all inside its slice);
+ *   4. the new particle i, owned by the rank whose slice holds index i, copies
+ *      the state of particle ancestors[i] from the rank that searched i
+ *      (paper_2112_00364_gb300/shard.py exchanges the states).
+ * The ancestors, S and the increment are those smc_resample gives for the
+ * whole population on one GPU, bit for bit.  All pointers are device pointers. */
+#define SMC_RESAMPLE_TILE 4096
+/* Bytes of the records of a slice of n_local particles (16 per tile). */
+size_t smc_shard_records_bytes(int64_t n_local);
+/* Step 1: the tiles' records of a slice (logw [n_local] f64, 16-byte aligned;
+ * records [smc_shard_records_bytes(n_local)], 16-byte aligned).
+ * Errors: SMC_EINVAL, SMC_ECUDA. */
+smc_status smc_shard_reduce(const double *logw, int64_t n_local, void *records, void *stream);
+/* Workspace bytes of smc_shard_ancestors for a population of n_total. */
+size_t smc_shard_workspace_bytes(int64_t n_total);
+/* Step 3: logw [n_local] of the slice starting at particle `first`; records_all
+ * [tiles of n_total] in tile order; u in (0,1) the checkpoint's uniform (the same
+ * on every rank); ancestors [n_total] int32 (only [range[0], range[1]) written);
+ * range [2] int64; out3 [3] f64 = {m, S, log-Z increment} as smc_resample; n_near
+ * [1] int64 (this rank's near-boundary offsets, zeroed by the call); workspace of
+ * smc_shard_workspace_bytes(n_total), 256-byte aligned.  Errors: SMC_EINVAL (a
+ * slice not on whole tiles, bad sizes, NULL), SMC_ECUDA. */
+smc_status smc_shard_ancestors(const double *logw, int64_t n_local, int64_t first,
+                               const void *records_all, int64_t n_total, double u,
+                               int32_t *ancestors, int64_t *range, double *out3, int64_t *n_near,
+                               void *workspace, size_t workspace_bytes, void *stream);
+
 /* Particle duplication with a stack-pointer-bounded copy (Section 3.3): for each
  * field f and particle i, dst[f][i] = src[f][anc[i]] (fields field-major, elem_bytes
  * 4 or 8 each); if sp != NULL, stack rows s >= sp[anc[i]] are not copied (they are

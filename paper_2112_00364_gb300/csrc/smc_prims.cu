@@ -277,28 +277,40 @@ __device__ __forceinline__ int64_t count_below(long long Q, const RsScalars& sc,
 // element, and the chunk is written out coalesced.  The first element of a
 // tile starts at the previous tile's last boundary; the last element of the
 // population owns everything above.
+//
+// A slice of a population sharded over ranks runs the same kernel on its own
+// tiles: x holds the slice's n_local log-weights, its first tile is tile t0 of
+// the population (N = n_total particles), rec and O cover every tile of the
+// population, and the ancestors of the offsets its tiles own are written at
+// their global offsets; `range` (if not NULL) receives those offsets' range.
 __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
-    const double* __restrict__ x, int64_t N, const TileRec* __restrict__ rec,
-    const long long* __restrict__ O, const RsScalars* __restrict__ scp,
-    const long long* __restrict__ ecache, int32_t* __restrict__ anc, unsigned long long* n_near,
-    const MathTab* tab) {
+    const double* __restrict__ x, int64_t n_local, int t0, int64_t N,
+    const TileRec* __restrict__ rec, const long long* __restrict__ O,
+    const RsScalars* __restrict__ scp, const long long* __restrict__ ecache,
+    int32_t* __restrict__ anc, unsigned long long* n_near, int64_t* range, const MathTab* tab) {
   __shared__ long long sh[RS_TPB / 32 + 1];
   __shared__ int sh_last[RS_TPB + 1];
   __shared__ __align__(16) int sh_m[RS_TILE];
   __shared__ RsExpTab st;
-  const int t = blockIdx.x;
-  const int64_t base = (int64_t)t * RS_TILE;
+  const int tl = blockIdx.x;         // the slice's tile
+  const int t = t0 + tl;             // the population's tile
+  const int64_t lbase = (int64_t)tl * RS_TILE, base = (int64_t)t * RS_TILE;
+  const int64_t lj0 = lbase + (int64_t)threadIdx.x * RS_IT;
   const int64_t j0 = base + (int64_t)threadIdx.x * RS_IT;
   const RsScalars sc = *scp;
   if (sc.degenerate) {  // every weight zero: identity
     for (int q = 0; q < RS_IT; ++q)
-      if (j0 + q < N) anc[j0 + q] = (int32_t)(j0 + q);
+      if (lj0 + q < n_local) anc[j0 + q] = (int32_t)(j0 + q);
+    if (range && tl == 0 && threadIdx.x == 0) {
+      range[0] = (int64_t)t0 * RS_TILE;
+      range[1] = (int64_t)t0 * RS_TILE + n_local;
+    }
     return;
   }
   const TileRec r = rec[t];
   long long E[RS_IT];
   if (ecache) {
-    const longlong2* p = reinterpret_cast<const longlong2*>(ecache + j0);
+    const longlong2* p = reinterpret_cast<const longlong2*>(ecache + lj0);
 #pragma unroll
     for (int q = 0; q < RS_IT / 2; ++q) {
       const longlong2 w = __ldcs(p + q);
@@ -309,7 +321,7 @@ __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
     stage_exp_tables(st, tab);
     __syncthreads();
     double v[RS_IT];
-    load_tile(x, N, base, v);
+    load_tile(x, n_local, lbase, v);
     tile_weights(v, r.k, tab, st, E);
     tile_running_sums(E, sh);
   }
@@ -337,6 +349,10 @@ __global__ void __launch_bounds__(RS_TPB) rs_ancestors(
   __syncthreads();
   const int c_prev = sh_last[threadIdx.x];  // count below this thread's first element
   const int c_lo = sh_last[0], c_end = sh_last[RS_TPB];
+  if (range && threadIdx.x == 0) {
+    if (tl == 0) range[0] = c_lo;
+    if (tl == (int)gridDim.x - 1) range[1] = c_end;
+  }
   const int jl0 = threadIdx.x * RS_IT;       // tile-local index of the first element
   int carry = -1;
   for (int cb = c_lo; cb < c_end; cb += RS_TILE) {
@@ -565,8 +581,8 @@ smc_status rs_launch(const double* logw, int64_t N, double u, int32_t* ancestors
   SMC_CUDA_TRY(cudaGetLastError());
   rs_combine<<<1, 256, 0, cs>>>(w.rec, nt, N, std::log((double)N), u, w.O, w.sc, out3, tab);
   SMC_CUDA_TRY(cudaGetLastError());
-  rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, N, w.rec, w.O, w.sc, w.ecache, ancestors,
-                                      reinterpret_cast<unsigned long long*>(n_near), tab);
+  rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, N, 0, N, w.rec, w.O, w.sc, w.ecache, ancestors,
+                                      reinterpret_cast<unsigned long long*>(n_near), nullptr, tab);
   SMC_CUDA_TRY(cudaGetLastError());
   return SMC_OK;
 }
@@ -652,6 +668,79 @@ extern "C" smc_status smc_resample_static(const double* logw, int64_t N, double 
   if (st) return st;
   return rs_launch(logw, N, u, ancestors, out3, n_near,
                    rs_carve((char*)base, (N + RS_TILE - 1) / RS_TILE, false), (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// One population sharded over ranks: the same three kernels, split at the
+// exchange of the tile records.  Each rank reduces its own slice (pass 1); once
+// every rank holds the records of the whole population in tile order, each runs
+// the combine over all of them (the same integers on every rank) and pass 3 on
+// its own tiles, with its first tile's index as the offset.
+extern "C" size_t smc_shard_records_bytes(int64_t n_local) {
+  if (n_local < 1) return 0;
+  return sizeof(TileRec) * (size_t)((n_local + RS_TILE - 1) / RS_TILE);
+}
+
+extern "C" smc_status smc_shard_reduce(const double* logw, int64_t n_local, void* records,
+                                       void* stream) {
+  if (!logw || !records) return set_error(SMC_EINVAL, "NULL pointer");
+  if (n_local < 1 || n_local > 0x7fffffffLL) return set_error(SMC_EINVAL, "n_local must be in 1..2^31-1");
+  if ((reinterpret_cast<uintptr_t>(logw) & 15) != 0)
+    return set_error(SMC_EINVAL, "logw must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(records) & 15) != 0)
+    return set_error(SMC_EINVAL, "records must be 16-byte aligned");
+  const MathTab* tab = nullptr;
+  smc_status ts = math_table(&tab);
+  if (ts) return ts;
+  NvtxRange nv("smc_shard_reduce");
+  const int nt = (int)((n_local + RS_TILE - 1) / RS_TILE);
+  rs_tile_reduce<<<nt, RS_TPB, 0, (cudaStream_t)stream>>>(logw, n_local, (TileRec*)records, nullptr,
+                                                          tab);
+  SMC_CUDA_TRY(cudaGetLastError());
+  return SMC_OK;
+}
+
+extern "C" size_t smc_shard_workspace_bytes(int64_t n_total) {
+  if (n_total < 1) return 0;
+  const int64_t nt = (n_total + RS_TILE - 1) / RS_TILE;
+  return align_up(8 * (size_t)(nt + 1), 256) + align_up(sizeof(RsScalars), 256);
+}
+
+extern "C" smc_status smc_shard_ancestors(const double* logw, int64_t n_local, int64_t first,
+                                          const void* records_all, int64_t n_total, double u,
+                                          int32_t* ancestors, int64_t* range, double* out3,
+                                          int64_t* n_near, void* workspace,
+                                          size_t workspace_bytes, void* stream) {
+  smc_status st = rs_check(logw, n_total, u, ancestors, out3, n_near);
+  if (st) return st;
+  if (!records_all || !range || !workspace) return set_error(SMC_EINVAL, "NULL pointer");
+  if (first < 0 || first % RS_TILE != 0 || n_local < 1 || first + n_local > n_total)
+    return set_error(SMC_EINVAL, "the slice must start on a whole tile (%d particles) inside "
+                                 "the population", RS_TILE);
+  if (first + n_local < n_total && n_local % RS_TILE != 0)
+    return set_error(SMC_EINVAL, "every slice but the last holds whole tiles of %d", RS_TILE);
+  if (workspace_bytes < smc_shard_workspace_bytes(n_total))
+    return set_error(SMC_EINVAL, "workspace too small");
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0)
+    return set_error(SMC_EINVAL, "workspace must be 256-byte aligned");
+  const MathTab* tab = nullptr;
+  if ((st = math_table(&tab))) return st;
+  NvtxRange nv("smc_shard_ancestors");
+  cudaStream_t cs = (cudaStream_t)stream;
+  const int nt_all = (int)((n_total + RS_TILE - 1) / RS_TILE);
+  const int nt = (int)((n_local + RS_TILE - 1) / RS_TILE);
+  char* w = (char*)workspace;
+  long long* O = (long long*)w;
+  RsScalars* sc = (RsScalars*)(w + align_up(8 * (size_t)(nt_all + 1), 256));
+  const TileRec* rec = (const TileRec*)records_all;
+  SMC_CUDA_TRY(cudaMemsetAsync(n_near, 0, sizeof(int64_t), cs));
+  rs_combine<<<1, 256, 0, cs>>>(rec, nt_all, n_total, std::log((double)n_total), u, O, sc, out3, tab);
+  SMC_CUDA_TRY(cudaGetLastError());
+  rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, n_local, (int)(first / RS_TILE), n_total, rec, O, sc,
+                                      nullptr, ancestors,
+                                      reinterpret_cast<unsigned long long*>(n_near), range, tab);
+  SMC_CUDA_TRY(cudaGetLastError());
+  return SMC_OK;
 }
 
 extern "C" smc_status smc_gather(const void* src, void* dst, const int32_t* anc, const int32_t* sp,

@@ -163,6 +163,15 @@ def lib():
         L.smc_sample.restype = C.c_int32
         L.smc_math_eval.argtypes = [C.c_int32, _vp, _vp, C.c_int64, _vp]
         L.smc_math_eval.restype = C.c_int32
+        L.smc_shard_records_bytes.argtypes = [C.c_int64]
+        L.smc_shard_records_bytes.restype = C.c_size_t
+        L.smc_shard_reduce.argtypes = [_vp, C.c_int64, _vp, _vp]
+        L.smc_shard_reduce.restype = C.c_int32
+        L.smc_shard_workspace_bytes.argtypes = [C.c_int64]
+        L.smc_shard_workspace_bytes.restype = C.c_size_t
+        L.smc_shard_ancestors.argtypes = [_vp, C.c_int64, C.c_int64, _vp, C.c_int64, C.c_double,
+                                          _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]
+        L.smc_shard_ancestors.restype = C.c_int32
         L.smc_set_tile_bands.argtypes = [_vp, C.c_int32]
         L.smc_set_tile_bands.restype = C.c_int32
         L.smc_get_tile_bands.argtypes = [_vp, C.c_int32, C.POINTER(C.c_int32)]
@@ -503,10 +512,52 @@ def resample_static(logw, u: float, ancestors=None, out3=None, n_near=None, stre
     return anc, o3, nn
 
 
+RESAMPLE_TILE = 4096
+
+
+def shard_reduce(logw, stream=None):
+    """smc_shard_reduce: the tiles' records of this rank's slice (a uint8 CUDA
+    tensor, 16 bytes a tile)."""
+    import torch
+
+    n = logw.numel()
+    rec = torch.empty(int(lib().smc_shard_records_bytes(n)), dtype=torch.uint8, device=logw.device)
+    _check(lib().smc_shard_reduce(_ptr(logw), n, _ptr(rec), _stream(stream)))
+    return rec
+
+
+def shard_ancestors(logw, first: int, records_all, n_total: int, u: float, ancestors=None,
+                    stream=None):
+    """smc_shard_ancestors: returns (ancestors [n_total] int32 with [lo, hi) written,
+    range int64 [2] = (lo, hi), out3 [3], n_near [1]), CUDA tensors."""
+    import torch
+
+    dev = logw.device
+    anc = ancestors if ancestors is not None else torch.empty(n_total, dtype=torch.int32, device=dev)
+    rng = torch.empty(2, dtype=torch.int64, device=dev)
+    o3 = torch.empty(3, dtype=torch.float64, device=dev)
+    nn = torch.empty(1, dtype=torch.int64, device=dev)
+    ws = torch.empty(int(lib().smc_shard_workspace_bytes(n_total)), dtype=torch.uint8, device=dev)
+    _check(lib().smc_shard_ancestors(_ptr(logw), logw.numel(), first, _ptr(records_all), n_total,
+                                     u, _ptr(anc), _ptr(rng), _ptr(o3), _ptr(nn), _ptr(ws),
+                                     ws.numel(), _stream(stream)))
+    return anc, rng, o3, nn
+
+
 def gather(src, dst, anc, sp=None, stream=None):
     """dst[f][i] = src[f][anc[i]] for 2-D [n_fields, N] device tensors of 4- or 8-byte elements."""
     n_fields, N = src.shape
     _check(lib().smc_gather(_ptr(src), _ptr(dst), _ptr(anc), _ptr(sp), N, n_fields,
+                            src.element_size(), _stream(stream)))
+    return dst
+
+
+def gather_row(src, dst, anc, first: int = 0, stream=None):
+    """dst[i] = src[anc[i] - first] for 1-D device tensors of 4- or 8-byte
+    elements (anc int32 [dst.numel()]; src holds the particles first.. of a
+    population indexed from 0)."""
+    src_at = _ptr(src) - first * src.element_size()  # the population's element 0
+    _check(lib().smc_gather(src_at, _ptr(dst), _ptr(anc), None, dst.numel(), 1,
                             src.element_size(), _stream(stream)))
     return dst
 
