@@ -724,7 +724,7 @@ class DeviceBench:
     """A workload's runs with device-resident inputs and outputs, timed with CUDA
     events on the launching stream, L2 flushed between timed steps."""
 
-    def __init__(self, work: Work, smc, torch, dev, launch: str = "waves"):
+    def __init__(self, work: Work, smc, torch, dev, launch: str = "auto"):
         self.work, self.smc, self.torch, self.dev = work, smc, torch, dev
         self.launch = launch
         self.stream = torch.cuda.Stream(device=dev)
@@ -769,7 +769,7 @@ class DeviceBench:
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        step_ms, logz, statuses, launches = [], [], set(), 0
+        step_ms, logz, statuses, launches, segs = [], [], set(), 0, 0
         draws = blocks = 0
         for s in range(steps):
             with torch.cuda.stream(self.stream):
@@ -784,6 +784,7 @@ class DeviceBench:
             statuses.update(r["status"] for r in res)
             logz.append(float(self.outs[0]["log_z"].cpu()[0]))
             launches += res[0]["kernel_launches"]
+            segs += res[0]["n_segments"]
             draws += sum(r["n_draws"] for r in res)
             blocks += sum(r["n_blocks"] for r in res)
         torch.cuda.synchronize()
@@ -793,6 +794,7 @@ class DeviceBench:
         units = steps * self.work.units
         return {"step_ms": step_ms, "logz": logz, "statuses": sorted(statuses),
                 "launches_per_step": launches // max(1, steps), "clocks": clk,
+                "segments_per_step": segs / max(1, steps),
                 "draws_per_pstep": draws / units, "blocks_per_pstep": blocks / units,
                 "units": units}
 
@@ -805,11 +807,15 @@ def segment_roofline(work: Work, meas: dict, peaks: dict, name: str) -> dict:
     """The segment kernel's roofline from the timed steps themselves: a step is
     the run's waves (one wave_kernel launch per wave) plus a few small copies,
     so the mean wave time is at most ms_per_step / waves; the achieved rates
-    below divide by that bound (never above the truth)."""
+    below divide by that bound (never above the truth).  A small run launched as
+    one kernel (one CTA or one cluster for all its segments) is divided by its
+    segments instead."""
     r = work.runs[0]
     n_part = r["N"]
     waves = meas["launches_per_step"]
-    t_wave = float(np.mean(meas["step_ms"])) * 1e-3 / max(1, waves)
+    one_launch = waves == 1 and meas.get("segments_per_step", 1) > 1
+    per_step = meas["segments_per_step"] if one_launch else waves
+    t_wave = float(np.mean(meas["step_ms"])) * 1e-3 / max(1, per_step)
     b_per, b_what = algorithmic_bytes(work)
     hbm = b_per * n_part / t_wave / 1e9
     info = NCU.get(name)
@@ -822,6 +828,10 @@ def segment_roofline(work: Work, meas: dict, peaks: dict, name: str) -> dict:
     common = {"kernel": "wave_kernel (fused segment kernel)", "waves_per_step": waves,
               "wave_us": t_wave * 1e6, "traffic": traffic,
               "timing": "mean wave = ms_per_step / waves of the timed steps"}
+    if one_launch:
+        common = {"kernel": "small_run_kernel (every segment of the run in one launch)",
+                  "segments_per_step": per_step, "segment_us": t_wave * 1e6, "traffic": None,
+                  "timing": "mean segment = ms_per_step / segments of the timed steps"}
     if info and info["basis"] in ("issue", "fp64"):
         issue = info["warp_inst_per_pstep"] * n_part / t_wave
         fp64 = info["fp64_flop_per_pstep"] * n_part / t_wave
@@ -974,7 +984,8 @@ def main() -> int:
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-configs", action="store_true",
                     help="leave out the other configurations' sub-objects of the default line")
-    ap.add_argument("--launch", default="waves", choices=["waves", "graph", "one_cta"],
+    ap.add_argument("--launch", default="auto",
+                    choices=["auto", "waves", "graph", "one_cta", "cluster"],
                     help="launch form of the segments (results are the same bits)")
     ap.add_argument("--launch-graph", action="store_true", help="the same as --launch graph")
     args = ap.parse_args()
@@ -1062,8 +1073,12 @@ def main() -> int:
         configs = config_lines(smc, torch, dev, peaks)
     lat = sorted(meas["step_ms"])
     cfg_line = work.config()
-    cfg_line["launch"] = {"graph": "one captured CUDA graph per step",
+    cfg_line["launch"] = {"auto": "the library's choice: every segment of a small run in "
+                                  "one thread-block cluster, else one launch per wave",
+                          "graph": "one captured CUDA graph per step",
                           "one_cta": "every segment of a small run in one CTA (else waves)",
+                          "cluster": "every segment of a small run in one thread-block "
+                                     "cluster (else waves)",
                           "waves": "one launch per wave and CTA size, chained by dependent "
                                    "launch"}[launch]
     line = {

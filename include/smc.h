@@ -83,9 +83,11 @@ typedef int32_t smc_status;
 #define SMC_MEM_HOST 0
 #define SMC_MEM_DEVICE 1
 
-#define SMC_LAUNCH_WAVES 0
+#define SMC_LAUNCH_AUTO 0
 #define SMC_LAUNCH_GRAPH 1
 #define SMC_LAUNCH_ONE_CTA 2
+#define SMC_LAUNCH_CLUSTER 3
+#define SMC_LAUNCH_WAVES 4
 
 #define SMC_MAX_DEPTH 64 /* largest hidden-lineage recursion cap the CRBD blocks accept */
 /* Largest particle count of one run: ancestor indices are int32, and a run's
@@ -132,6 +134,9 @@ typedef struct {
   int32_t time_kernels;  /* 1: time every segment-kernel launch with CUDA events (counters) */
   int32_t launch_mode;   /* how the segments are launched; results are the same bits in
                             every mode:
+                            SMC_LAUNCH_AUTO     (0, the default) SMC_LAUNCH_CLUSTER where it
+                                                applies (and the GPU launches it), else
+                                                SMC_LAUNCH_WAVES;
                             SMC_LAUNCH_WAVES    one launch per segment (wave) and CTA size,
                                                 chained by programmatic dependent launch;
                             SMC_LAUNCH_GRAPH    the waves of a known-length run captured in
@@ -146,7 +151,14 @@ typedef struct {
                                                 (the others), fresh (not resumed): every
                                                 segment in one CTA and one launch, the CTA
                                                 barrier as the checkpoint barrier (else
-                                                waves). */
+                                                waves);
+                            SMC_LAUNCH_CLUSTER  smc_run of a run of 32-particle tiles, at most
+                                                32 of them, fresh: every segment in one
+                                                launch of one thread-block cluster (2 warps,
+                                                i.e. 2 tiles, a CTA in clusters of up to 16
+                                                CTAs, or 4 in up to 8 where the GPU does not
+                                                schedule 16), the cluster barrier as the
+                                                checkpoint barrier (else waves). */
   void *workspace;       /* optional caller-owned device workspace (>= smc_workspace_bytes);
                             NULL = the model handle allocates and caches one */
   size_t workspace_bytes;
@@ -486,7 +498,11 @@ smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uin
  * functions of x[i] rounded to float (the result widened to f64): 11 log,
  * 12 exp, 13 cos(2 pi x), 14 log1p, 15 expm1, 16 log k! for k = (int)x[i];
  * fn 17..21 are CUDA's logf, expf, cospif(2x), log1pf, expm1f of the same
- * float arguments, for comparison.  x, y [n] f64 device pointers.
+ * float arguments, for comparison; fn 22 reads pairs (x[2j], x[2j+1]) = (S, N) as
+ * 64-bit integer patterns (S < 2^63, 1 <= N < 2^31) and writes (y[2j], y[2j+1]) =
+ * floor(S 2^64 / N) as 64.64 fixed point (integer part, fraction bits), the
+ * ratio the systematic search scales its offsets by (n even).  x, y [n] f64
+ * device pointers.
  * Errors: SMC_EINVAL, SMC_ECUDA. */
 smc_status smc_math_eval(int32_t fn, const double *x, double *y, int64_t n, void *stream);
 

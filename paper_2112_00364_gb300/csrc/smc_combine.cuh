@@ -227,11 +227,40 @@ __device__ __forceinline__ Q64 q_sub(Q64 a, Q64 b) {
 __device__ __forceinline__ bool q_lt(Q64 a, Q64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 
 // S / N in 64.64 (S < 2^63, N >= 1)
+// One digit of a long division in base 2^32: floor(num / N) and the remainder
+// for num < N 2^32 and 1 <= N < 2^31.  The FP64 product num (1/N) carries three
+// roundings of relative size 2^-53 on a quotient below 2^32, so it lies within
+// 2^-19 of num / N and its truncation within one of the digit; one correction
+// step each way makes it exact.
+__device__ __forceinline__ unsigned long long div_digit(unsigned long long num, long long N,
+                                                        double inv, unsigned long long* rem) {
+  long long q = (long long)((double)(long long)num * inv);
+  long long r = (long long)num - q * N;
+  if (r < 0) {
+    q -= 1;
+    r += N;
+  } else if (r >= N) {
+    q += 1;
+    r -= N;
+  }
+  *rem = (unsigned long long)r;
+  return (unsigned long long)q;
+}
+
+// S / N in 64.64 fixed point, floor(S 2^64 / N) exactly, for S < 2^63 and
+// 1 <= N < 2^31: four base-2^32 digits (two of the integer part, two of the
+// fraction), no 128-bit division.
 __device__ __forceinline__ Q64 q_ratio(unsigned long long S, unsigned long long N) {
+  const long long n = (long long)N;
+  const double inv = 1.0 / (double)n;
+  unsigned long long r;
+  const unsigned long long q1 = div_digit(S >> 32, n, inv, &r);
+  const unsigned long long q2 = div_digit((r << 32) | (S & 0xffffffffull), n, inv, &r);
+  const unsigned long long q3 = div_digit(r << 32, n, inv, &r);
+  const unsigned long long q4 = div_digit(r << 32, n, inv, &r);
   Q64 d;
-  d.hi = S / N;
-  const unsigned long long rem = S - d.hi * N;
-  d.lo = (unsigned long long)(((unsigned __int128)rem << 64) / N);
+  d.hi = (q1 << 32) + q2;
+  d.lo = (q3 << 32) + q4;
   return d;
 }
 

@@ -595,7 +595,7 @@ smc_status check_cfg(const smc_model_s* m, const smc_run_cfg* c) {
     return set_error(SMC_EINVAL, "max_segments must be in 0..2^24");
   if (!(c->ess_threshold >= 0.0 && c->ess_threshold < 1e300))
     return set_error(SMC_EINVAL, "ess_threshold must be finite and >= 0");
-  if (c->launch_mode < SMC_LAUNCH_WAVES || c->launch_mode > SMC_LAUNCH_ONE_CTA)
+  if (c->launch_mode < SMC_LAUNCH_AUTO || c->launch_mode > SMC_LAUNCH_WAVES)
     return set_error(SMC_EINVAL, "unknown launch_mode");
   if (c->resume_k < 0) return set_error(SMC_EINVAL, "resume_k must be >= 0");
   if (c->resume_k > 0) {
@@ -893,15 +893,24 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
   double kms = 0.0;
   std::vector<RunState*> states{runs[0].rs};
   NvtxRange nv_waves("smc_run/waves");
-  // a small run (32-particle tiles, few enough for one CTA) runs every segment
-  // in one launch; the same tiles and integers as the waves
-  const bool small = c->launch_mode == SMC_LAUNCH_ONE_CTA && c->resume_k == 0 &&
-                     !c->time_kernels && Ly.tile == 32 &&
-                     Ly.n_tiles <= small_run_max_tiles(m->desc.kind);
+  // a small run (32-particle tiles, few enough for one CTA or one cluster) runs
+  // every segment in one launch: the same tiles and integers as the waves
+  const int one = c->launch_mode == SMC_LAUNCH_AUTO ? SMC_LAUNCH_CLUSTER : c->launch_mode;
+  const bool small = (one == SMC_LAUNCH_ONE_CTA || one == SMC_LAUNCH_CLUSTER) &&
+                     c->resume_k == 0 && !c->time_kernels && Ly.tile == 32 &&
+                     Ly.n_tiles <= small_run_max_tiles(m->desc.kind, one);
+  bool waves = !small;
   if (small) {
-    SMC_CUDA_TRY(launch_small_run(m->desc.kind, c->precision, W.runs, cs));
-    launched = 1;
-  } else {
+    const cudaError_t e = launch_small_run(m->desc.kind, c->precision, one, W.runs, Ly.n_tiles, cs);
+    if (e != cudaSuccess && c->launch_mode == SMC_LAUNCH_AUTO) {
+      cudaGetLastError();  // a cluster the GPU cannot place: the waves instead
+      waves = true;
+    } else {
+      SMC_CUDA_TRY(e);
+      launched = 1;
+    }
+  }
+  if (waves) {
     st = drive_waves(W, c->precision, states,
                      (known ? m->n_segments_known : Ly.max_segments) + 1 - skip, known, cs,
                      &m->ev_seg, c->time_kernels != 0, &launched, &kms,

@@ -93,10 +93,12 @@ struct GraphCache {
 };
 void graph_cache_clear(GraphCache* g);
 
-// A whole run in one CTA (smc_small.cu): for runs of 32-particle tiles, at most
-// small_run_max_tiles(kind) of them; one launch, grid 1.
-int small_run_max_tiles(int kind);
-cudaError_t launch_small_run(int kind, int precision, const RunDev* runs, cudaStream_t st);
+// A whole run in one launch (smc_small.cu): for runs of 32-particle tiles, at
+// most small_run_max_tiles(kind, launch_mode) of them; launch_mode
+// SMC_LAUNCH_ONE_CTA (grid 1) or SMC_LAUNCH_CLUSTER (one thread-block cluster).
+int small_run_max_tiles(int kind, int launch_mode);
+cudaError_t launch_small_run(int kind, int precision, int launch_mode, const RunDev* runs,
+                             int n_tiles, cudaStream_t st);
 
 }  // namespace smc
 

@@ -167,13 +167,29 @@ __global__ void __launch_bounds__(RS_TPB) rs_tile_reduce(const double* __restric
   }
 }
 
-// Single CTA: combine nt tile records.  O has nt + 1 entries (O[nt] = S).
-__global__ void __launch_bounds__(256) rs_combine(const TileRec* __restrict__ rec, int nt,
-                                                  int64_t N, double log_n, double u,
-                                                  long long* __restrict__ O, RsScalars* sc,
-                                                  double* out3, const MathTab* tab) {
-  __shared__ double sh[256 / 32 + 2 + 256 + 1];
-  const Combined c = combine_offsets<256>(rec, nt, O, nullptr, sh);
+// Single CTA: combine nt tile records.  O has nt + 1 entries (O[nt] = S).  Up
+// to RS_STAGE_TILES tiles the records are read once, all at a time, into shared
+// memory (k_t and s_t, the offsets then formed in place and written out
+// coalesced); beyond, each pass reads them again from L2.
+constexpr int RS_COMBINE_TPB = 1024;
+constexpr int RS_STAGE_TILES = 4096;
+constexpr size_t RS_STAGE_BYTES = 8 * (RS_STAGE_TILES + 1) + 4 * RS_STAGE_TILES;
+
+__global__ void __launch_bounds__(RS_COMBINE_TPB) rs_combine(const TileRec* __restrict__ rec, int nt,
+                                                             int64_t N, double log_n, double u,
+                                                             long long* __restrict__ O,
+                                                             RsScalars* sc, double* out3,
+                                                             const MathTab* tab) {
+  __shared__ double sh[RS_COMBINE_TPB / 32 + 2 + RS_COMBINE_TPB + 1];
+  extern __shared__ __align__(16) unsigned char rs_stage[];
+  const bool stage = nt <= RS_STAGE_TILES;
+  long long* Ow = stage ? reinterpret_cast<long long*>(rs_stage) : O;
+  int* ks = stage ? reinterpret_cast<int*>(rs_stage + 8 * (RS_STAGE_TILES + 1)) : nullptr;
+  const Combined c = combine_offsets<RS_COMBINE_TPB>(rec, nt, Ow, ks, sh);
+  if (stage) {
+    __syncthreads();  // O[nt] from thread 0
+    for (int q = threadIdx.x; q <= nt; q += RS_COMBINE_TPB) O[q] = Ow[q];
+  }
   if (threadIdx.x != 0) return;
   RsScalars s;
   std::memset(&s, 0, sizeof(s));
@@ -480,6 +496,14 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
                                  int64_t n, const MathTab* tab) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (fn == 22) {  // pairs (S, N) as 64-bit patterns -> the 64.64 ratio (hi, lo)
+    if (i & 1) return;
+    const Q64 d = q_ratio((unsigned long long)__double_as_longlong(x[i]),
+                          (unsigned long long)__double_as_longlong(x[i + 1]));
+    y[i] = __longlong_as_double((long long)d.hi);
+    y[i + 1] = __longlong_as_double((long long)d.lo);
+    return;
+  }
   const double v = x[i];
   const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
   switch (fn) {
@@ -518,7 +542,8 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
 using namespace smc;
 
 extern "C" smc_status smc_math_eval(int32_t fn, const double* x, double* y, int64_t n, void* stream) {
-  if (!x || !y || n < 0 || fn < 0 || fn > 21) return set_error(SMC_EINVAL, "bad argument");
+  if (!x || !y || n < 0 || fn < 0 || fn > 22) return set_error(SMC_EINVAL, "bad argument");
+  if (fn == 22 && (n & 1)) return set_error(SMC_EINVAL, "fn 22 takes pairs: n must be even");
   if (n == 0) return SMC_OK;
   const MathTab* tab = nullptr;
   smc_status ts = math_table(&tab);
@@ -569,6 +594,30 @@ smc_status rs_check(const double* logw, int64_t N, double u, const int32_t* anc,
   return SMC_OK;
 }
 
+// rs_combine with its staging area (above the default 48 KB of dynamic shared
+// memory: the opt-in is set once per device).
+std::mutex g_combine_mu;
+bool g_combine_ready[128];
+
+smc_status launch_rs_combine(const TileRec* rec, int nt, int64_t N, double u, long long* O,
+                             RsScalars* sc, double* out3, const MathTab* tab, cudaStream_t cs) {
+  int dev = -1;
+  SMC_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return set_error(SMC_EINVAL, "device ordinal %d out of range", dev);
+  {
+    std::lock_guard<std::mutex> lock(g_combine_mu);
+    if (!g_combine_ready[dev]) {
+      SMC_CUDA_TRY(cudaFuncSetAttribute(rs_combine, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)RS_STAGE_BYTES));
+      g_combine_ready[dev] = true;
+    }
+  }
+  rs_combine<<<1, RS_COMBINE_TPB, RS_STAGE_BYTES, cs>>>(rec, nt, N, std::log((double)N), u, O, sc,
+                                                        out3, tab);
+  SMC_CUDA_TRY(cudaGetLastError());
+  return SMC_OK;
+}
+
 smc_status rs_launch(const double* logw, int64_t N, double u, int32_t* ancestors, double* out3,
                      int64_t* n_near, const RsScratch& w, cudaStream_t cs) {
   NvtxRange nv("smc_resample");
@@ -579,8 +628,7 @@ smc_status rs_launch(const double* logw, int64_t N, double u, int32_t* ancestors
   SMC_CUDA_TRY(cudaMemsetAsync(n_near, 0, sizeof(int64_t), cs));
   rs_tile_reduce<<<nt, RS_TPB, 0, cs>>>(logw, N, w.rec, w.ecache, tab);
   SMC_CUDA_TRY(cudaGetLastError());
-  rs_combine<<<1, 256, 0, cs>>>(w.rec, nt, N, std::log((double)N), u, w.O, w.sc, out3, tab);
-  SMC_CUDA_TRY(cudaGetLastError());
+  if ((ts = launch_rs_combine(w.rec, nt, N, u, w.O, w.sc, out3, tab, cs))) return ts;
   rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, N, 0, N, w.rec, w.O, w.sc, w.ecache, ancestors,
                                       reinterpret_cast<unsigned long long*>(n_near), nullptr, tab);
   SMC_CUDA_TRY(cudaGetLastError());
@@ -734,8 +782,7 @@ extern "C" smc_status smc_shard_ancestors(const double* logw, int64_t n_local, i
   RsScalars* sc = (RsScalars*)(w + align_up(8 * (size_t)(nt_all + 1), 256));
   const TileRec* rec = (const TileRec*)records_all;
   SMC_CUDA_TRY(cudaMemsetAsync(n_near, 0, sizeof(int64_t), cs));
-  rs_combine<<<1, 256, 0, cs>>>(rec, nt_all, n_total, std::log((double)n_total), u, O, sc, out3, tab);
-  SMC_CUDA_TRY(cudaGetLastError());
+  if ((st = launch_rs_combine(rec, nt_all, n_total, u, O, sc, out3, tab, cs))) return st;
   rs_ancestors<<<nt, RS_TPB, 0, cs>>>(logw, n_local, (int)(first / RS_TILE), n_total, rec, O, sc,
                                       nullptr, ancestors,
                                       reinterpret_cast<unsigned long long*>(n_near), range, tab);

@@ -105,7 +105,16 @@ __device__ __forceinline__ void search_scalars(const Combined& c, int N, double 
 // 8-ary search with integer compares (three rounds of independent loads for a
 // 256-particle tile).  If no element of tile t qualifies, the first element of
 // tile t+1 does.  The offset is flagged when it lies within 1e-12 N of q_a or
-// q_{a-1}, measured in the same units.  Integer arithmetic only.
+// q_{a-1}, measured in the same units.  Integer arithmetic only.  kL2: the
+// running sums were written by other CTAs of the same launch (a cluster's run),
+// so they are read at L2, past this SM's L1.
+template <bool kL2>
+__device__ __forceinline__ long long load_sum(const long long* p) {
+  if (kL2) return __ldcg(p);
+  return *p;
+}
+
+template <bool kL2 = false>
 __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const SearchCtx& X,
                                                  const long long* __restrict__ E, bool* near) {
   const int N = A.N, T = A.n_tiles;
@@ -136,7 +145,7 @@ __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const S
     const int w = (len + 7) >> 3;
     long long v[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = E[b + min((m + 1) * w, len) - 1];
+    for (int m = 0; m < 8; ++m) v[m] = load_sum<kL2>(E + b + min((m + 1) * w, len) - 1);
     int m = 8;
 #pragma unroll
     for (int q = 7; q >= 0; --q)
@@ -156,7 +165,7 @@ __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const S
   if (len > 0) {
     long long v[8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = m < len ? E[b + m] : 0x7FFFFFFFFFFFFFFFll;
+    for (int m = 0; m < 8; ++m) v[m] = m < len ? load_sum<kL2>(E + b + m) : 0x7FFFFFFFFFFFFFFFll;
     int m = 8;
 #pragma unroll
     for (int q = 7; q >= 0; --q)

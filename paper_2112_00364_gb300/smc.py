@@ -267,11 +267,11 @@ class Model:
         return out.value
 
 
-LAUNCH = {"waves": 0, "graph": 1, "one_cta": 2}
+LAUNCH = {"auto": 0, "graph": 1, "one_cta": 2, "cluster": 3, "waves": 4}
 
 
 def _cfg(N, seed, run_id, precision, max_segments, record_all, workspace, time_kernels=False,
-         ess_threshold=0.0, launch="waves"):
+         ess_threshold=0.0, launch="auto"):
     c = RunCfg()
     c.time_kernels = int(time_kernels)
     c.launch_mode = LAUNCH[launch]
@@ -347,13 +347,15 @@ def run(model: Model, N: int, seed: int, run_id: int = 0, precision: str = "fp64
         max_segments: int = 0, record_all_ancestors: bool = False, where: str = "host",
         stream=None, workspace=None, outputs: dict | None = None,
         time_kernels: bool = False, ess_threshold: float = 0.0,
-        launch: str = "waves", launch_graph: bool = False,
+        launch: str = "auto", launch_graph: bool = False,
         resume_from: dict | None = None) -> dict:
     """smc_run.  where="host": outputs are numpy arrays; where="device": outputs are
     torch CUDA tensors (allocated here unless passed in `outputs`).  ess_threshold
-    tau > 0: resample only when ESS < tau N.  launch: "waves", "graph" (the waves as
-    one captured CUDA graph; needs a stream other than the legacy default stream;
-    launch_graph=True says the same) or "one_cta" (a small run in one CTA).
+    tau > 0: resample only when ESS < tau N.  launch: "auto" (the library's choice:
+    "cluster" where it applies, else "waves"), "waves", "graph" (the waves as one
+    captured CUDA graph; needs a stream other than the legacy default stream;
+    launch_graph=True says the same), "one_cta" (a small run in one CTA) or
+    "cluster" (a small run in one thread-block cluster).
     resume_from: the result of a run of the same model, N, seed, run_id, precision
     and ess_threshold that max_segments stopped (a snapshot); this run continues it."""
     cfg = _cfg(N, seed, run_id, precision, max_segments, record_all_ancestors, workspace,
@@ -589,7 +591,9 @@ def math_eval(fn: str, x):
     exp_fix54 / table_exp_fix54: round(e^x 2^54) as int64 for x <= 0 (integer pipes /
     table exponential rounded to that grid), or exp2t_fix54 / exp2t_fix50: round(e^x
     2^54) / round(e^x 2^50) from the two-table integer exponential, or exp_neg_int:
-    e^-x (double, 0 <= x < 64) from the same integer exponential."""
+    e^-x (double, 0 <= x < 64) from the same integer exponential, or q_ratio: x an
+    [n, 2] array of (S, N) integers, returns [n, 2] uint64 (integer part, fraction
+    bits) of floor(S 2^64 / N)."""
     import torch
 
     code = {"table_log": 0, "table_exp": 1, "lib_log": 2, "lib_exp": 3, "unif_log_bits": 4,
@@ -598,13 +602,17 @@ def math_eval(fn: str, x):
             # the FP32 mode's own single-precision functions, and CUDA's for comparison
             "f32_log": 11, "f32_exp": 12, "f32_cos2pi": 13, "f32_log1p": 14, "f32_expm1": 15,
             "f32_lfact": 16, "cuda_logf": 17, "cuda_expf": 18, "cuda_cos2pif": 19,
-            "cuda_log1pf": 20, "cuda_expm1f": 21}[fn]
+            "cuda_log1pf": 20, "cuda_expm1f": 21, "q_ratio": 22}[fn]
+    if code == 22:
+        x = np.ascontiguousarray(x, dtype=np.uint64).reshape(-1).view(np.float64)
     if code in (4, 5):
         x = np.ascontiguousarray(x, dtype=np.uint64).view(np.float64)
     xd = torch.as_tensor(x, dtype=torch.float64).cuda()
     y = torch.empty_like(xd)
     _check(lib().smc_math_eval(code, _ptr(xd), _ptr(y), xd.numel(), None))
     out = y.cpu().numpy()
+    if code == 22:
+        return out.view(np.uint64).reshape(-1, 2)
     return out.view(np.int64) if 6 <= code <= 9 else out
 
 

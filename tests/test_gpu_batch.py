@@ -202,12 +202,13 @@ def test_graph_launch_gives_the_same_bits():
         mm.close()
 
 
+@pytest.mark.parametrize("launch", ["one_cta", "cluster"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_one_cta_launch_gives_the_same_bits(precision):
-    """A small run (32-particle tiles, few enough for one CTA) launched as one
-    CTA that runs every segment gives exactly what its waves give, for every
-    model kind, ESS-triggered resampling and record_all included; one case
-    against the oracle too."""
+def test_one_launch_forms_give_the_same_bits(precision, launch):
+    """A small run (32-particle tiles, few enough for one CTA or one cluster)
+    launched as one CTA, or one thread-block cluster, that runs every segment
+    gives exactly what its waves give, for every model kind, ESS-triggered
+    resampling and record_all included; one case against the oracle too."""
     import oracle
     from parity import assert_parity_exact, assert_parity_fp64
 
@@ -222,11 +223,15 @@ def test_one_cta_launch_gives_the_same_bits(precision):
               480, 0.5),
              ("crbd_ds", dict(tree=tree), 300, 0.5),
              ("seir", dict(obs=inputs.seir_observations(21, seed=7)), 512, 0.0)]
+    if launch == "cluster":  # up to 32 tiles for every model, the last CTA half full
+        cases += [("crbd", dict(tree=tree), 1024, 0.5),
+                  ("seir", dict(obs=inputs.seir_observations(21, seed=7)), 1000, 0.0),
+                  ("crbd_ds", dict(tree=tree), 33, 0.0)]
     for q, (kind, p, N, tau) in enumerate(cases):
         m = smc.Model(kind, **p)
         kw = dict(precision=precision, record_all_ancestors=True, ess_threshold=tau)
-        a = smc.run(m, N, 60 + q, **kw)
-        b = smc.run(m, N, 60 + q, launch="one_cta", **kw)
+        a = smc.run(m, N, 60 + q, launch="waves", **kw)
+        b = smc.run(m, N, 60 + q, launch=launch, **kw)
         assert b["kernel_launches"] == 1, kind
         assert a["log_z_value"] == b["log_z_value"] and a["n_segments"] == b["n_segments"], kind
         for key in ("final_logw", "int_fields", "ancestors", "resampled", "real_fields", "stack"):

@@ -242,3 +242,31 @@ def test_integer_pipe_exponential_double():
     ref = np.array([float((-Decimal(float(x))).exp()) for x in m])
     assert got[np.flatnonzero(m == 0.0)[0]] == 1.0
     assert _ulp_diff(got, ref).max() <= 1
+
+
+def test_q_ratio_exact():
+    """The search's offset scale S / N in 64.64 fixed point: floor(S 2^64 / N)
+    exactly (Python's integers), over the whole argument range (S < 2^63,
+    N < 2^31), at quotient digits that are exact integers, one below and one
+    above (the correction steps), and at the extremes."""
+    from paper_2112_00364_gb300 import smc
+
+    rng = np.random.default_rng(17)
+    pairs = []
+    for _ in range(20000):
+        N = int(rng.integers(1, 1 << 31))
+        S = int(rng.integers(0, 1 << 63))
+        pairs.append((S, N))
+    for N in (1, 2, 3, 7, 1024, 65536, (1 << 20) + 1, (1 << 31) - 257, (1 << 31) - 1):
+        for S in (0, 1, N - 1, N, N + 1, (1 << 61), (1 << 62) + 12345, (1 << 63) - 1):
+            pairs.append((S, N))
+        for m in (1, 2, 12345, (1 << 31) - 1):  # S a multiple of N, and one either side
+            for dS in (-1, 0, 1):
+                S = m * N + dS
+                if 0 <= S < (1 << 63):
+                    pairs.append((S, N))
+    x = np.array(pairs, dtype=np.uint64)
+    got = smc.math_eval("q_ratio", x)
+    for (S, N), (hi, lo) in zip(pairs, got):
+        q = (S << 64) // N
+        assert (int(hi), int(lo)) == (q >> 64, q & ((1 << 64) - 1)), (S, N)
