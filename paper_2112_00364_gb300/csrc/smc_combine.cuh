@@ -249,10 +249,9 @@ __device__ __forceinline__ unsigned long long div_digit(unsigned long long num, 
 
 // S / N in 64.64 fixed point, floor(S 2^64 / N) exactly, for S < 2^63 and
 // 1 <= N < 2^31: four base-2^32 digits (two of the integer part, two of the
-// fraction), no 128-bit division.
-__device__ __forceinline__ Q64 q_ratio(unsigned long long S, unsigned long long N) {
+// fraction), no 128-bit division.  inv = 1 / N rounded to nearest.
+__device__ __forceinline__ Q64 q_ratio(unsigned long long S, unsigned long long N, double inv) {
   const long long n = (long long)N;
-  const double inv = 1.0 / (double)n;
   unsigned long long r;
   const unsigned long long q1 = div_digit(S >> 32, n, inv, &r);
   const unsigned long long q2 = div_digit((r << 32) | (S & 0xffffffffull), n, inv, &r);

@@ -46,12 +46,148 @@ __device__ __forceinline__ unsigned cluster_rank() {
   return r;
 }
 
-// Every thread of every CTA of the cluster: the writes before it (global and
-// shared) are visible to every thread of the cluster after it.
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile(
-      "barrier.cluster.arrive.release;\n\t"
-      "barrier.cluster.wait.acquire;" ::: "memory");
+// The cluster barrier in its two halves: the writes of every thread of the
+// cluster before its arrive are visible to every thread after its wait; work
+// between the two overlaps the other CTAs' arrival.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// systematic_search for one warp of a small run (tiles of 32 particles): each
+// lane's tile from the offsets as there; then, per distinct tile among the
+// lanes (one or two, the offsets being non-decreasing), the tile's 32 running
+// sums in one load (lane l holds E_{j0+l}) and every lane of that tile finds
+// its first j with E_j > F by a binary search over the shuffled values.  The
+// same ancestors and near-boundary flags as systematic_search; one dependent
+// load of the sums instead of the 8-ary search's two.  Every lane calls it;
+// `want` marks the lanes whose offset is searched.
+__device__ __forceinline__ int small_search(int i, bool want, const RunDev& A, const SearchCtx& X,
+                                            const long long* E, bool* near) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int N = A.N, T = A.n_tiles, lane = threadIdx.x & 31;
+  int a = i, t = -1;
+  bool nr = false, need = false;
+  long long F = 0, tolF = 0, Z = 0;
+  if (want) {
+    const Q64 z = q_add(X.z0, q_mul_u32((unsigned)i, X.d));
+    Z = (long long)z.hi;
+    int lo = 0, hi = T;  // O_0 = 0 <= z
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (X.O[mid] <= Z)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    if (lo >= T) {  // above the last offset (rounding at the top)
+      nr = Z - X.O[T] < X.tolZ;
+      a = N - 1;
+    } else {
+      t = lo;
+      const int sh = X.kmax - X.ks[t] + X.G;
+      F = q_threshold(z, X.O[t], sh);
+      tolF = shl_sat(X.tolZ, sh);
+      need = true;
+    }
+  }
+  unsigned pending = __ballot_sync(kAll, need);
+  while (pending) {
+    const int tg = __shfl_sync(kAll, t, __ffs(pending) - 1);
+    const int j0 = tg * 32, len = min(32, N - j0);
+    const long long e = lane < len ? __ldcg(E + j0 + lane) : 0x7FFFFFFFFFFFFFFFll;
+    // pos = #{ l < len : E_{j0+l} <= F } (the sums are non-decreasing)
+    int pos = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+      const long long v = __shfl_sync(kAll, e, pos + step - 1);
+      if (v <= F) pos += step;
+    }
+    const long long e31 = __shfl_sync(kAll, e, 31);
+    if (pos == 31 && e31 <= F) pos = 32;
+    pos = min(pos, len);
+    const long long El = __shfl_sync(kAll, e, min(pos, 31));
+    const long long Eb = __shfl_sync(kAll, e, max(pos - 1, 0));
+    const bool mine = need && t == tg;
+    if (mine) {
+      nr = F - (pos > 0 ? Eb : 0ll) < tolF;
+      if (pos < len) {
+        a = j0 + pos;
+        nr = nr || El - F <= tolF;
+      } else if (j0 + len < N) {  // the first element of the next tile
+        a = j0 + len;
+        nr = nr || X.O[tg + 1] - Z <= X.tolZ;
+      } else {
+        a = N - 1;
+      }
+    }
+    pending &= ~__ballot_sync(kAll, mine);
+  }
+  *near = nr;
+  return a;
+}
+
+// The warp's sum of a 64-bit per-lane count, added by lane 0.
+__device__ __forceinline__ void warp_add_u64_wide(unsigned long long* dst, unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+// The combine of at most 32 tiles by one warp, lane t holding tile t: the
+// integers of combine_offsets (the same k_max, coarsening G, unit totals,
+// exact offsets and S, and the effective sample size summed in the same
+// order) from warp shuffles, with no CTA barrier.  Writes O[0..nt] (O[nt] = S)
+// and ks[0..nt) to the warp's own shared arrays.
+__device__ __forceinline__ Combined combine_warp(const TileRec* rec, int nt, const long long* q,
+                                                 long long* O, int* ks) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  TileRec r;
+  r.s = 0;
+  r.k = kDeadTile;
+  r.alive = 0;
+  if (lane < nt) r = load_rec(rec + lane);
+  Combined c;
+  c.kmax = __reduce_max_sync(kAll, r.k);
+  c.alive = __any_sync(kAll, r.alive) ? 1 : 0;
+  c.G = 0;
+  c.S = 0;
+  c.ess = 0.0;
+  if (lane < nt) ks[lane] = r.k;
+  if (c.kmax == kDeadTile) {
+    __syncwarp();
+    return c;
+  }
+  long long b = lane < nt ? magnitude(r.s, r.k, c.kmax) : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(kAll, b, o);
+  c.G = (64 - __clzll(b)) + 20 - 62;
+  const long long v = lane < nt ? to_run_units(r.s, r.k, c.kmax, c.G) : 0;
+  long long inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(kAll, inc, o);
+    if (lane >= o) inc += y;
+  }
+  c.S = __shfl_sync(kAll, inc, 31);
+  if (lane < nt) O[lane] = inc - v;
+  if (lane == 0) O[nt] = c.S;
+  if (q) {
+    double acc = 0.0;
+    if (lane < nt && r.k != kDeadTile) {
+      const int d2 = 2 * (c.kmax - r.k);
+      if (d2 < 900) acc = acc + (double)__ldcg(q + lane) * pow2i(-54 - d2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(kAll, acc, o);
+    const double sd = (double)c.S * pow2i(c.G - 54);
+    c.ess = acc > 0.0 ? (sd * sd) / acc : 0.0;
+  }
+  __syncwarp();
+  return c;
 }
 
 // CL: launched as one cluster of ceil(n_tiles / (TPB / 32)) CTAs (else one CTA).
@@ -61,10 +197,8 @@ __global__ void __launch_bounds__(TPB, 1) small_run_kernel(const RunDev* __restr
   constexpr int WPC = TPB / 32;
   static_assert(CL || WPC >= 16, "one CTA holds the whole run");
   __shared__ __align__(16) RunDev sr;
-  __shared__ double sh[TPB / 32 + 2 + TPB + 1];
-  __shared__ long long sh_O[kSmallMaxTiles + 1];
-  __shared__ int sh_ks[kSmallMaxTiles + 1];
-  __shared__ unsigned long long shq[5];
+  __shared__ long long sh_O[WPC][kSmallMaxTiles + 1];  // each warp's own offsets
+  __shared__ int sh_ks[WPC][kSmallMaxTiles + 1];
   {
     const int* src = reinterpret_cast<const int*>(runs);
     int* dst = reinterpret_cast<int*>(&sr);
@@ -75,11 +209,19 @@ __global__ void __launch_bounds__(TPB, 1) small_run_kernel(const RunDev* __restr
   RunState* rs = A.rs;
   const int N = A.N;
   const bool lead = !CL || cluster_rank() == 0;  // the CTA that closes each segment
-  const int t = (CL ? (int)cluster_rank() * WPC : 0) + (int)(threadIdx.x >> 5);
+  const int wid = (int)(threadIdx.x >> 5);
+  const int t = (CL ? (int)cluster_rank() * WPC : 0) + wid;
   const int lane = threadIdx.x & 31;
   const int i = t * 32 + lane;  // the tile of this path is 32 particles
   const bool tile_live = t < A.n_tiles;
   const bool valid = tile_live && i < N;
+  // segment k - 1's closing (log Z, its records) waits for the barrier that
+  // ends segment k, where it overlaps the other CTAs' arrival
+  Combined c_close;
+  bool resample_close = false;
+  double u = 0.0;  // the uniform of the next search, drawn in the barrier's shadow
+  // the run's counters, summed per lane over the segments and added once
+  unsigned long long n_near = 0, n_overflow = 0, n_limit = 0, n_draws = 0, n_blocks = 0;
   for (int k = 0;; ++k) {
     const int nb = k & 1, cb = nb ^ 1;
     const StateView Sc = A.state[cb];
@@ -87,36 +229,43 @@ __global__ void __launch_bounds__(TPB, 1) small_run_kernel(const RunDev* __restr
     typename M::Lane L;
     bool near = false;
     if (k > 0) {
-      const Combined c = combine_offsets<TPB>(A.rec[cb], A.n_tiles, sh_O, sh_ks, sh,
-                                              A.ess ? A.tq[cb] : nullptr);
+      const Combined c = combine_warp(A.rec[cb], A.n_tiles, A.ess ? A.tq[cb] : nullptr,
+                                      sh_O[wid], sh_ks[wid]);
       const bool go_on = c.kmax != kDeadTile && c.alive && k < A.max_segments;
       const bool resample = decide_resample(A, c);
-      if (lead && threadIdx.x == 0) finish_segment(A, k, c, resample);
-      if (!go_on) break;  // the same c in every thread: a uniform exit
-      if (resample && threadIdx.x == 0) {
+      if (!go_on) {  // the same c in every thread: a uniform exit
+        if (lead && threadIdx.x == 0) finish_segment(A, k, c, resample);
+        break;
+      }
+      c_close = c;
+      resample_close = resample;
+      // the run's search scalars by each warp's lane 0, broadcast to its lanes
+      unsigned long long q5[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+      if (resample && lane == 0) {
         Q64 d, z0;
         long long tolZ;
-        search_scalars(c, N, Unif<double>::first(philox(0u, (uint32_t)(k - 1), 0u, 1u, A.k0, A.k1)),
-                       &d, &z0, &tolZ);
-        shq[0] = d.hi;
-        shq[1] = d.lo;
-        shq[2] = z0.hi;
-        shq[3] = z0.lo;
-        shq[4] = (unsigned long long)tolZ;
+        search_scalars(c, N, A.inv_n, u, &d, &z0, &tolZ);
+        q5[0] = d.hi;
+        q5[1] = d.lo;
+        q5[2] = z0.hi;
+        q5[3] = z0.lo;
+        q5[4] = (unsigned long long)tolZ;
       }
-      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 5; ++q) q5[q] = __shfl_sync(0xffffffffu, q5[q], 0);
       SearchCtx X;
       X.rec = A.rec[cb];
-      X.O = sh_O;
-      X.ks = sh_ks;
+      X.O = sh_O[wid];
+      X.ks = sh_ks[wid];
       X.kmax = c.kmax;
       X.G = c.G;
-      X.d = Q64{shq[0], shq[1]};
-      X.z0 = Q64{shq[2], shq[3]};
-      X.tolZ = (long long)shq[4];
+      X.d = Q64{q5[0], q5[1]};
+      X.z0 = Q64{q5[2], q5[3]};
+      X.tolZ = (long long)q5[4];
+      const int a_s = resample ? small_search(i, valid, A, X, A.E[cb], &near) : i;
       if (valid) {
         const int row = A.record_all ? k - 1 : 0;
-        int a = resample ? systematic_search<true>(i, A, X, A.E[cb], &near) : i;
+        int a = a_s;
         bool bad = false;
         if (SMC_DEBUG_CHECKS) {
           if (!(a >= 0 && a < N)) {
@@ -144,7 +293,7 @@ __global__ void __launch_bounds__(TPB, 1) small_run_kernel(const RunDev* __restr
           L.logw = (R)A.logw[i];
         }
       }
-      warp_add_u64(&rs->n_near, near ? 1ull : 0ull);
+      n_near += near ? 1ull : 0ull;
     } else if (valid) {
       M::init(L);
     }
@@ -164,10 +313,10 @@ __global__ void __launch_bounds__(TPB, 1) small_run_kernel(const RunDev* __restr
       A.logw[i] = lw;
       alive = L.pc != PC_STOP;
     }
-    warp_add_u64(&rs->n_overflow, active ? (unsigned long long)L.overflow : 0ull);
-    warp_add_u64(&rs->n_limit, active ? (unsigned long long)L.limited : 0ull);
-    warp_add_u64(&rs->n_draws, valid ? (unsigned long long)s.d : 0ull);
-    warp_add_u64(&rs->n_blocks, (unsigned long long)n_exec);
+    n_overflow += active ? (unsigned long long)L.overflow : 0ull;
+    n_limit += active ? (unsigned long long)L.limited : 0ull;
+    n_draws += valid ? (unsigned long long)s.d : 0ull;
+    n_blocks += (unsigned long long)n_exec;
     // the tile's weights: a warp is a tile, so its reference is the warp's
     long long ef = 0;
     const double Mw = warp_max_key(lw);
@@ -198,11 +347,19 @@ __global__ void __launch_bounds__(TPB, 1) small_run_kernel(const RunDev* __restr
       A.rec[nb][t] = r;
     }
     // the segment's records, running sums and states, for the next combine
+    if (CL) cluster_arrive();
+    if (k > 0 && lead && threadIdx.x == 0) finish_segment(A, k, c_close, resample_close);
+    if (lane == 0) u = Unif<double>::first(philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1));
     if (CL)
-      cluster_barrier();
+      cluster_wait();
     else
       __syncthreads();
   }
+  warp_add_u64_wide(&rs->n_near, n_near);
+  warp_add_u64_wide(&rs->n_overflow, n_overflow);
+  warp_add_u64_wide(&rs->n_limit, n_limit);
+  warp_add_u64_wide(&rs->n_draws, n_draws);
+  warp_add_u64_wide(&rs->n_blocks, n_blocks);
 }
 
 // One CTA: register-light models run up to 32 tiles (1024 threads, 64
