@@ -99,53 +99,79 @@ template <int TPB>
 __device__ Combined combine_offsets(const TileRec* rec, int nt, long long* O, int* ks, double* sh,
                                     const long long* q = nullptr) {
   constexpr int P = 4;  // consecutive tiles per thread per chunk
-  int* shi = reinterpret_cast<int*>(sh);
-  long long* shl = reinterpret_cast<long long*>(sh);
+  constexpr int W = TPB / 32;
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // disjoint shared regions, one per reduction, so none needs a barrier before reuse
+  int* sk = reinterpret_cast<int*>(sh);                     // [2W] warps' (k max, alive)
+  long long* sm = reinterpret_cast<long long*>(sh) + W;     // [W] warps' magnitude sums
+  long long* ss = reinterpret_cast<long long*>(sh) + 2 * W;  // [W] warps' unit totals
+  double* qs = sh + 3 * W;                                   // [1] effective sample size
   int kl = kDeadTile, al = 0;
-  for (int q = threadIdx.x; q < nt; q += TPB) {
-    const TileRec r = load_rec(rec + q);
+  for (int t = threadIdx.x; t < nt; t += TPB) {
+    const TileRec r = load_rec(rec + t);
     if (ks) {
-      ks[q] = r.k;
-      O[q] = r.s;
+      ks[t] = r.k;
+      O[t] = r.s;
     }
     kl = max(kl, r.k);
     al |= r.alive;
   }
+  kl = __reduce_max_sync(kAll, kl);
+  al = (int)__reduce_or_sync(kAll, (unsigned)al);
+  if (lane == 0) {
+    sk[2 * wid] = kl;
+    sk[2 * wid + 1] = al;
+  }
+  __syncthreads();
   Combined c;
-  c.kmax = block_max_int<TPB>(kl, shi);
-  c.alive = __syncthreads_or(al);
+  c.kmax = sk[0];
+  c.alive = sk[1];
+#pragma unroll
+  for (int w = 1; w < W; ++w) {
+    c.kmax = max(c.kmax, sk[2 * w]);
+    c.alive |= sk[2 * w + 1];
+  }
+  c.alive = c.alive ? 1 : 0;
   c.G = 0;
   c.S = 0;
   c.ess = 0.0;
-  if (c.kmax == kDeadTile) return c;
+  if (c.kmax == kDeadTile) {
+    __syncthreads();
+    return c;
+  }
   // G from b = sum over live tiles of (floor(s_t 2^-(k_max - k_t + 20)) + 1),
   // which lies between the exact sum T of the totals in units of 2^20 U (at
   // G = 0) and T + n_tiles: G = bitlen(b) - 42 gives 2^(41+G) <= b < 2^(42+G),
-  // so S = sum v_t is within [2^61 - n_tiles 2^(20-G), 2^62 + n_tiles]
+  // so S = sum v_t is within [2^61 - n_tiles 2^(20-G), 2^62 + n_tiles].  (With
+  // ks each thread reads back the tiles it staged itself.)
   long long bl = 0;
-  for (int q = threadIdx.x; q < nt; q += TPB) {
+  for (int t = threadIdx.x; t < nt; t += TPB) {
     if (ks)
-      bl += magnitude(O[q], ks[q], c.kmax);
+      bl += magnitude(O[t], ks[t], c.kmax);
     else {
-      const TileRec r = load_rec(rec + q);
+      const TileRec r = load_rec(rec + t);
       bl += magnitude(r.s, r.k, c.kmax);
     }
   }
-  const long long bsum = block_incl_scan_i64<TPB>(bl, shl);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bl += __shfl_xor_sync(kAll, bl, o);
+  if (lane == 0) sm[wid] = bl;
   __syncthreads();
-  if (threadIdx.x == TPB - 1) shl[0] = bsum;
-  __syncthreads();
-  const long long bnd = shl[0];
-  __syncthreads();
+  long long bnd = sm[0];
+#pragma unroll
+  for (int w = 1; w < W; ++w) bnd += sm[w];
   c.G = (64 - __clzll(bnd)) + 20 - 62;
+  // the totals in units U and their exclusive prefix sums, P consecutive tiles
+  // a thread, chunk by chunk
   long long carry = 0;
   for (int base = 0; base < nt; base += TPB * P) {
     long long v[P];
     long long tot = 0;
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int t = base + threadIdx.x * P + q;
-      v[q] = 0;
+    for (int p = 0; p < P; ++p) {
+      const int t = base + threadIdx.x * P + p;
+      v[p] = 0;
       if (t < nt) {
         long long st;
         int kt;
@@ -157,46 +183,54 @@ __device__ Combined combine_offsets(const TileRec* rec, int nt, long long* O, in
           st = r.s;
           kt = r.k;
         }
-        v[q] = to_run_units(st, kt, c.kmax, c.G);
+        v[p] = to_run_units(st, kt, c.kmax, c.G);
       }
-      tot += v[q];
+      tot += v[p];
     }
-    const long long incl = block_incl_scan_i64<TPB>(tot, shl);
-    long long off = carry + (incl - tot);
+    long long inc = tot;
 #pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const int t = base + threadIdx.x * P + q;
-      if (t < nt) O[t] = off;
-      off += v[q];
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(kAll, inc, o);
+      if (lane >= o) inc += y;
     }
+    if (lane == 31) ss[wid] = inc;
     __syncthreads();
-    if (threadIdx.x == TPB - 1) shl[0] = incl;
-    __syncthreads();
-    carry += shl[0];
-    __syncthreads();
+    long long off = carry + (inc - tot), all = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const long long x = ss[w];
+      if (w < wid) off += x;
+      all += x;
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int t = base + threadIdx.x * P + p;
+      if (t < nt) O[t] = off;
+      off += v[p];
+    }
+    carry += all;
+    if (base + TPB * P < nt) __syncthreads();  // every thread has read ss
   }
   c.S = carry;
   if (threadIdx.x == 0) O[nt] = carry;
-  if (q) {
-    double* qs = sh + TPB / 32 + 1;
-    if (threadIdx.x < 32) {
-      double acc = 0.0;
-      for (int t = threadIdx.x; t < nt; t += 32) {
-        const int kt = ks ? ks[t] : load_rec(rec + t).k;
+  if (q && wid == 0) {  // sum w^2 relative to 2^(2 k_max), in FP64, by the first warp
+    double acc = 0.0;
+    for (int t = lane; t < nt; t += 32) {
+      const int kt = ks ? ks[t] : load_rec(rec + t).k;
+      if (kt != kDeadTile) {
         const int d2 = 2 * (c.kmax - kt);
-        if (kt != kDeadTile && d2 < 900) acc = acc + (double)__ldcg(q + t) * pow2i(-54 - d2);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o);
-      if (threadIdx.x == 0) {
-        const double s = (double)carry * pow2i(c.G - 54);
-        qs[0] = acc > 0.0 ? (s * s) / acc : 0.0;
+        if (d2 < 900) acc = acc + (double)__ldcg(q + t) * pow2i(-54 - d2);
       }
     }
-    __syncthreads();
-    c.ess = qs[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc = acc + __shfl_xor_sync(kAll, acc, o);
+    if (lane == 0) {
+      const double sd = (double)carry * pow2i(c.G - 54);
+      qs[0] = acc > 0.0 ? (sd * sd) / acc : 0.0;
+    }
   }
-  __syncthreads();
+  __syncthreads();  // the offsets (and the ESS) for every thread
+  if (q) c.ess = qs[0];
   return c;
 }
 
@@ -226,37 +260,34 @@ __device__ __forceinline__ Q64 q_sub(Q64 a, Q64 b) {
 
 __device__ __forceinline__ bool q_lt(Q64 a, Q64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 
-// S / N in 64.64 (S < 2^63, N >= 1)
 // One digit of a long division in base 2^32: floor(num / N) and the remainder
-// for num < N 2^32 and 1 <= N < 2^31.  The FP64 product num (1/N) carries three
-// roundings of relative size 2^-53 on a quotient below 2^32, so it lies within
-// 2^-19 of num / N and its truncation within one of the digit; one correction
-// step each way makes it exact.
-__device__ __forceinline__ unsigned long long div_digit(unsigned long long num, long long N,
-                                                        double inv, unsigned long long* rem) {
-  long long q = (long long)((double)(long long)num * inv);
-  long long r = (long long)num - q * N;
-  if (r < 0) {
-    q -= 1;
-    r += N;
-  } else if (r >= N) {
+// for num < N 2^32 and 1 <= N < 2^31, from the per-run reciprocal
+// R = floor((2^64 - 1) / N).  2^64 / N - R < 2, so num R 2^-64 lies within one
+// below num / N (num < 2^63) and its integer part is the digit or one less; one
+// correction step makes it exact.  Integer pipes only.
+__device__ __forceinline__ unsigned long long div_digit(unsigned long long num, unsigned long long N,
+                                                        unsigned long long R,
+                                                        unsigned long long* rem) {
+  unsigned long long q = __umul64hi(num, R);
+  unsigned long long r = num - q * N;
+  if (r >= N) {
     q += 1;
     r -= N;
   }
-  *rem = (unsigned long long)r;
-  return (unsigned long long)q;
+  *rem = r;
+  return q;
 }
 
 // S / N in 64.64 fixed point, floor(S 2^64 / N) exactly, for S < 2^63 and
 // 1 <= N < 2^31: four base-2^32 digits (two of the integer part, two of the
-// fraction), no 128-bit division.  inv = 1 / N rounded to nearest.
-__device__ __forceinline__ Q64 q_ratio(unsigned long long S, unsigned long long N, double inv) {
-  const long long n = (long long)N;
+// fraction), no division instruction.  R = floor((2^64 - 1) / N).
+__device__ __forceinline__ Q64 q_ratio(unsigned long long S, unsigned long long N,
+                                       unsigned long long R) {
   unsigned long long r;
-  const unsigned long long q1 = div_digit(S >> 32, n, inv, &r);
-  const unsigned long long q2 = div_digit((r << 32) | (S & 0xffffffffull), n, inv, &r);
-  const unsigned long long q3 = div_digit(r << 32, n, inv, &r);
-  const unsigned long long q4 = div_digit(r << 32, n, inv, &r);
+  const unsigned long long q1 = div_digit(S >> 32, N, R, &r);
+  const unsigned long long q2 = div_digit((r << 32) | (S & 0xffffffffull), N, R, &r);
+  const unsigned long long q3 = div_digit(r << 32, N, R, &r);
+  const unsigned long long q4 = div_digit(r << 32, N, R, &r);
   Q64 d;
   d.hi = (q1 << 32) + q2;
   d.lo = (q3 << 32) + q4;

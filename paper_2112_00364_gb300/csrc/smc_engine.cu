@@ -276,7 +276,7 @@ RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly,
   A.rs = (RunState*)(ws + Ly.rs);
   A.N = (int)c->n_particles;
   A.log_n = std::log((double)c->n_particles);
-  A.inv_n = 1.0 / (double)c->n_particles;
+  A.recip_n = ~0ull / (unsigned long long)c->n_particles;
   A.n_tiles = Ly.n_tiles;
   A.tile = Ly.tile;
   A.max_segments = Ly.max_segments;

@@ -52,7 +52,8 @@ struct RunDev {
   int32_t* anc;       // ancestor rows
   double* incr;       // [max_segments] per-segment log-Z increments
   RunState* rs;
-  double log_n, inv_n;  // log N and 1 / N, computed on the host
+  double log_n;                // log N, computed on the host
+  unsigned long long recip_n;  // floor((2^64 - 1) / N), the search scalars' divisor
   double ess_tau;       // 0: resample after every checkpoint; > 0: only when ESS < ess_tau N
   double ess_target;    // ess_tau N
   int N, n_tiles, tile, max_segments, record_all, anc_rows;

@@ -499,7 +499,7 @@ __global__ void math_eval_kernel(int fn, const double* __restrict__ x, double* _
   if (fn == 22) {  // pairs (S, N) as 64-bit patterns -> the 64.64 ratio (hi, lo)
     if (i & 1) return;
     const unsigned long long n = (unsigned long long)__double_as_longlong(x[i + 1]);
-    const Q64 d = q_ratio((unsigned long long)__double_as_longlong(x[i]), n, 1.0 / (double)(long long)n);
+    const Q64 d = n ? q_ratio((unsigned long long)__double_as_longlong(x[i]), n, ~0ull / n) : Q64{0, 0};
     y[i] = __longlong_as_double((long long)d.hi);
     y[i + 1] = __longlong_as_double((long long)d.lo);
     return;

@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(TPB, 1) small_run_kernel(const RunDev* __restr
       if (resample && lane == 0) {
         Q64 d, z0;
         long long tolZ;
-        search_scalars(c, N, A.inv_n, u, &d, &z0, &tolZ);
+        search_scalars(c, N, A.recip_n, u, &d, &z0, &tolZ);
         q5[0] = d.hi;
         q5[1] = d.lo;
         q5[2] = z0.hi;

@@ -89,9 +89,9 @@ struct SearchCtx {
 };
 
 // The run's search scalars from its combined total (one thread).
-__device__ __forceinline__ void search_scalars(const Combined& c, int N, double inv_n, double u,
-                                               Q64* d, Q64* z0, long long* tolZ) {
-  *d = q_ratio((unsigned long long)c.S, (unsigned long long)N, inv_n);
+__device__ __forceinline__ void search_scalars(const Combined& c, int N, unsigned long long recip_n,
+                                               double u, Q64* d, Q64* z0, long long* tolZ) {
+  *d = q_ratio((unsigned long long)c.S, (unsigned long long)N, recip_n);
   *z0 = q_scale(frac64(u), *d);
   *tolZ = floor_i64(kBoundaryEps * (double)c.S);
 }
@@ -228,7 +228,7 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
       if (resample && threadIdx.x == 0) {
         Q64 d, z0;
         long long tolZ;
-        search_scalars(c, N, A.inv_n, Unif<double>::first(philox(0u, (uint32_t)(k - 1), 0u, 1u, A.k0, A.k1)),
+        search_scalars(c, N, A.recip_n, Unif<double>::first(philox(0u, (uint32_t)(k - 1), 0u, 1u, A.k0, A.k1)),
                        &d, &z0, &tolZ);
         shq[0] = d.hi;
         shq[1] = d.lo;
@@ -373,7 +373,7 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
       if (finish_segment(A, k + 1, c, resample) && resample) {
         Q64 d, z0;
         long long tolZ;
-        search_scalars(c, N, A.inv_n, Unif<double>::first(philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1)), &d,
+        search_scalars(c, N, A.recip_n, Unif<double>::first(philox(0u, (uint32_t)k, 0u, 1u, A.k0, A.k1)), &d,
                        &z0, &tolZ);
         rs->kmax = c.kmax;
         rs->G = c.G;
