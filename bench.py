@@ -738,6 +738,7 @@ class DeviceBench:
         o = {"log_z": t.zeros(1, dtype=t.float64, device=self.dev),
              "final_logw": t.zeros(N, dtype=t.float64, device=self.dev),
              "ancestors": t.zeros((1, N), dtype=t.int32, device=self.dev),
+             "resampled": t.zeros(1, dtype=t.int32, device=self.dev),
              "int_fields": t.zeros((m.n_int, N), dtype=t.int32, device=self.dev)}
         if m.n_real:
             o["real_fields"] = t.zeros((m.n_real, N), dtype=t.float64, device=self.dev)
@@ -866,6 +867,7 @@ def e2e_measure(work: Work, smc, torch, stream, steps: int, dist, dev) -> tuple[
         o = {"log_z": torch.zeros(1, dtype=torch.float64).pin_memory(),
              "final_logw": torch.zeros(N, dtype=torch.float64).pin_memory(),
              "ancestors": torch.zeros((1, N), dtype=torch.int32).pin_memory(),
+             "resampled": torch.zeros(1, dtype=torch.int32).pin_memory(),
              "int_fields": torch.zeros((m.n_int, N), dtype=torch.int32).pin_memory()}
         if m.n_real:
             o["real_fields"] = torch.zeros((m.n_real, N), dtype=torch.float64).pin_memory()

@@ -337,8 +337,11 @@ size_t wave_meta_bytes(const std::vector<RunDev>& runs) {
 
 // Copies the run table and the per-bucket CTA maps to `meta` (device) and
 // fills W with their device addresses.
+// The run table and CTA maps to device memory at `meta`.  From pageable
+// staging the call waits for the copy; from `pinned` (at least
+// wave_meta_bytes(runs), not rewritten before the copy has run) it does not.
 smc_status upload_wave(const std::vector<RunDev>& runs, void* meta, cudaStream_t st, WavePlan* W,
-                       std::vector<char>* staging) {
+                       std::vector<char>* staging, char* pinned) {
   const size_t run_bytes = align_up(sizeof(RunDev) * runs.size(), 256);
   std::vector<int2> maps[4];
   for (size_t r = 0; r < runs.size(); ++r) {
@@ -356,6 +359,11 @@ smc_status upload_wave(const std::vector<RunDev>& runs, void* meta, cudaStream_t
     off = align_up(off + sizeof(int2) * maps[b].size(), 256);
   }
   W->kind = uniform_kind(runs);
+  if (pinned) {
+    std::memcpy(pinned, staging->data(), off);
+    SMC_CUDA_TRY(cudaMemcpyAsync(meta, pinned, off, cudaMemcpyHostToDevice, st));
+    return SMC_OK;
+  }
   SMC_CUDA_TRY(cudaMemcpyAsync(meta, staging->data(), off, cudaMemcpyHostToDevice, st));
   // the source is pageable host memory: wait for the copy before it can change
   SMC_CUDA_TRY(cudaStreamSynchronize(st));
@@ -814,6 +822,11 @@ extern "C" void smc_model_destroy(smc_model_t m) {
   if (m->ev0) cudaEventDestroy(m->ev0);
   if (m->ev1) cudaEventDestroy(m->ev1);
   for (cudaEvent_t e : m->ev_seg) cudaEventDestroy(e);
+  if (m->pin_ev) {
+    cudaEventSynchronize(m->pin_ev);
+    cudaEventDestroy(m->pin_ev);
+  }
+  if (m->pin) cudaFreeHost(m->pin);
   delete m;
 }
 
@@ -886,7 +899,22 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
       SMC_CUDA_TRY(cudaMemsetAsync(runs[0].dec, 0, 4 * (size_t)skip, cs));
     }
   }
-  if ((st = upload_wave(runs, ws + meta_off, cs, &W, &m->staging))) return st;
+  // the run table through the handle's pinned buffer (no wait for the copy),
+  // once the previous call's upload from it has run
+  if (m->pin_ev) SMC_CUDA_TRY(cudaEventSynchronize(m->pin_ev));
+  const size_t meta_bytes = wave_meta_bytes(runs);
+  if (m->pin_bytes < meta_bytes) {
+    if (m->pin) cudaFreeHost(m->pin);
+    m->pin = nullptr;
+    m->pin_bytes = 0;
+    if (cudaMallocHost(&m->pin, meta_bytes) == cudaSuccess)
+      m->pin_bytes = meta_bytes;
+    else
+      cudaGetLastError();  // pageable staging instead
+  }
+  if (m->pin && !m->pin_ev) SMC_CUDA_TRY(cudaEventCreateWithFlags(&m->pin_ev, cudaEventDisableTiming));
+  if ((st = upload_wave(runs, ws + meta_off, cs, &W, &m->staging, m->pin))) return st;
+  if (m->pin) SMC_CUDA_TRY(cudaEventRecord(m->pin_ev, cs));
   SMC_CUDA_TRY(cudaEventRecord(m->ev0, cs));
   const bool known = m->n_segments_known > 0 && Ly.max_segments >= m->n_segments_known;
   int launched = 0;

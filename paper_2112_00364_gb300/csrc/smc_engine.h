@@ -114,6 +114,9 @@ struct smc_model_s {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> ev_seg;  // per-launch timing pairs (time_kernels)
   std::vector<char> staging;        // host staging of the run table
+  char* pin = nullptr;              // smc_run's pinned copy of it (uploaded without a wait)
+  size_t pin_bytes = 0;
+  cudaEvent_t pin_ev = nullptr;     // recorded after that upload: the buffer is free again
   smc::GraphCache graph;            // smc_run's captured waves (SMC_LAUNCH_GRAPH)
 };
 
@@ -132,7 +135,7 @@ Layout make_layout(const smc_model_s* m, const smc_run_cfg* c);
 RunDev make_rundev(const smc_model_s* m, const smc_run_cfg* c, const Layout& Ly, char* ws);
 size_t wave_meta_bytes(const std::vector<RunDev>& runs);
 smc_status upload_wave(const std::vector<RunDev>& runs, void* meta, cudaStream_t st, WavePlan* W,
-                       std::vector<char>* staging);
+                       std::vector<char>* staging, char* pinned = nullptr);
 cudaError_t launch_wave(const WavePlan& W, int precision, cudaStream_t st, unsigned wave);
 // the waves of a plan whose runs all run the linear-Gaussian or the CRBD model
 cudaError_t launch_wave_kind(const WavePlan& W, int precision, cudaStream_t st, unsigned wave);
