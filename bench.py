@@ -87,12 +87,12 @@ RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, 
 # plain CRBD (latency-bound, most arithmetic on the integer pipes), the FP64
 # rate for the delayed-sampling CRBD (FP64 pipe busy 36-44% of a launch).  The
 # traffic holds only for the kernel sources with the recorded digest.
-NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=114.9, fp64_flop_per_pstep=18.8,
-                      bytes_per_launch=3.294e6, fp64_pipe_elapsed=0.188,
-                      src_digest="6b8867e3a8ee23a7"),
-       "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=114.9, fp64_flop_per_pstep=170.6,
-                          bytes_per_launch=5.76e6, fp64_pipe_elapsed=0.382,
-                          src_digest="11fe17bcc318e458")}
+NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=113.5, fp64_flop_per_pstep=18.8,
+                      bytes_per_launch=3.337e6, fp64_pipe_elapsed=0.191,
+                      src_digest="b548986ee6bc8b29"),
+       "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=110.1, fp64_flop_per_pstep=169.1,
+                          bytes_per_launch=5.56e6, fp64_pipe_elapsed=0.353,
+                          src_digest="b548986ee6bc8b29")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
@@ -109,7 +109,7 @@ RS_SOURCES = ("smc_prims.cu", "smc_device.cuh", "smc_combine.cuh")
 # DRAM traffic of one smc_resample call at 2^24 (the three kernels' dram__bytes
 # read + write in one ncu capture, profiles folder), valid for the sources with
 # the recorded digest.
-RS_NCU = dict(bytes_per_call=3.537e8, src_digest="4b4fa07df8b86421")
+RS_NCU = dict(bytes_per_call=3.529e8, src_digest="9d459fcec27c2c1f")
 
 
 def code_text(src: str) -> str:
