@@ -192,6 +192,39 @@ __device__ __forceinline__ int systematic_search(int i, const RunDev& A, const S
   return a;
 }
 
+// One L2 line into this SM's L1 ahead of its use (a hint: nothing waits on it).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %0;\n\tprefetch.global.L1 [g];\n\t}"
+               :: "l"(p));
+}
+
+// The lines of particles [lo, hi) of one array of elements of esz bytes.
+template <int TPB>
+__device__ __forceinline__ void prefetch_range(const void* base, int lo, int hi, int esz) {
+  const char* b = static_cast<const char*>(base) + (size_t)lo * esz;
+  const int lines = ((hi - lo) * esz + 127) >> 7;
+  for (int j = threadIdx.x; j < lines; j += TPB) prefetch_l1(b + (size_t)j * 128);
+}
+
+// Before the offsets are read, pull into L1 what this tile's search and gather
+// will most likely need: systematic ancestors of a tile's
+// particles lie mostly in the tiles t - 1 .. t + 1, so the previous segment's
+// running sums and PSTATE rows of those particles (written by the previous
+// wave).  Their loads then overlap the combine instead of following it.
+template <class M, int TPB>
+__device__ __forceinline__ void prefetch_neighbours(const RunDev& A, int t, int cb) {
+  using R = typename M::R;
+  const int lo = max(0, (t - 1) * A.tile);
+  const int hi = (int)min((long long)A.N, (long long)(t + 2) * A.tile);  // N may be near 2^31
+  if (lo >= hi) return;
+  const StateView& S = A.state[cb];
+  prefetch_range<TPB>(A.E[cb], lo, hi, 8);
+#pragma unroll
+  for (int f = 0; f < M::N_REAL; ++f) prefetch_range<TPB>(&S.rf<R>(f, 0, A.N), lo, hi, (int)sizeof(R));
+#pragma unroll
+  for (int f = 0; f < M::N_INT; ++f) prefetch_range<TPB>(&S.inf_(f, 0, A.N), lo, hi, 4);
+}
+
 // One tile of one run for segment k (the whole per-CTA body of a wave).
 template <class M, int TPB>
 __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const int k, double* sh,
@@ -213,6 +246,9 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
   if (load) {
     if (valid) M::load(L, Sn, SnapView{A.snap_logw, A.snap_real, A.snap_int, A.snap_stack}, i, N, s);
   } else if (k > 0) {
+    // (a run combined in every CTA keeps its offsets in shared memory and its
+    // combine short: there the prefetch measured no gain)
+    if (!redundant) prefetch_neighbours<M, TPB>(A, t, cb);
     SearchCtx X;
     X.rec = A.rec[cb];
     bool resample;
