@@ -87,12 +87,12 @@ RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, 
 # plain CRBD (latency-bound, most arithmetic on the integer pipes), the FP64
 # rate for the delayed-sampling CRBD (FP64 pipe busy 36-44% of a launch).  The
 # traffic holds only for the kernel sources with the recorded digest.
-NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=113.5, fp64_flop_per_pstep=18.8,
-                      bytes_per_launch=3.337e6, fp64_pipe_elapsed=0.191,
-                      src_digest="b548986ee6bc8b29"),
-       "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=110.1, fp64_flop_per_pstep=169.1,
-                          bytes_per_launch=5.56e6, fp64_pipe_elapsed=0.353,
-                          src_digest="b548986ee6bc8b29")}
+NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=113.9, fp64_flop_per_pstep=18.8,
+                      bytes_per_launch=3.295e6, fp64_pipe_elapsed=0.185,
+                      src_digest="470cbd0d0ecb1069"),
+       "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=110.2, fp64_flop_per_pstep=169.1,
+                          bytes_per_launch=5.41e6, fp64_pipe_elapsed=0.353,
+                          src_digest="470cbd0d0ecb1069")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
