@@ -81,7 +81,87 @@ __device__ MathTab g_math_tab;
 namespace {
 std::mutex g_tab_mu;
 const MathTab* g_tab_ptr[128] = {nullptr};
+
+// Device blocks kept after the model handle that owned them is destroyed, so
+// that registering a model and running it (a caller that builds a model per
+// request) reuses a block instead of a cudaMalloc / cudaFree pair, which
+// synchronise the device.  Blocks up to 256 MB, 1 GB and 32 blocks in all;
+// a failed cudaMalloc frees the device's kept blocks and tries once more.
+struct KeptBlock {
+  int dev;
+  void* p;
+  size_t bytes;
+};
+std::mutex g_kept_mu;
+std::vector<KeptBlock> g_kept;
+constexpr size_t kKeepMaxBlock = 256ull << 20, kKeepMaxTotal = 1ull << 30, kKeepMaxCount = 32;
+
+void kept_flush(int dev) {
+  std::lock_guard<std::mutex> lock(g_kept_mu);
+  for (size_t q = 0; q < g_kept.size();) {
+    if (g_kept[q].dev == dev) {
+      cudaFree(g_kept[q].p);
+      g_kept.erase(g_kept.begin() + (long)q);
+    } else {
+      ++q;
+    }
+  }
+}
 }  // namespace
+
+cudaError_t block_alloc(void** p, size_t* got, size_t bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(g_kept_mu);
+    long best = -1;
+    for (size_t q = 0; q < g_kept.size(); ++q) {
+      const KeptBlock& b = g_kept[q];
+      if (b.dev == dev && b.bytes >= bytes && b.bytes <= 2 * bytes &&
+          (best < 0 || b.bytes < g_kept[(size_t)best].bytes))
+        best = (long)q;
+    }
+    if (best >= 0) {
+      *p = g_kept[(size_t)best].p;
+      *got = g_kept[(size_t)best].bytes;
+      g_kept.erase(g_kept.begin() + best);
+      return cudaSuccess;
+    }
+  }
+  e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    kept_flush(dev);
+    e = cudaMalloc(p, bytes);
+  }
+  if (e == cudaSuccess) *got = bytes;
+  return e;
+}
+
+void block_free(void* p, size_t bytes, int dev) {
+  if (!p) return;
+  if (bytes <= kKeepMaxBlock) {
+    std::lock_guard<std::mutex> lock(g_kept_mu);
+    size_t total = bytes;
+    for (const KeptBlock& b : g_kept) total += b.bytes;
+    // make room by freeing the oldest kept blocks of this device
+    for (size_t q = 0; q < g_kept.size() && (total > kKeepMaxTotal || g_kept.size() >= kKeepMaxCount);) {
+      if (g_kept[q].dev == dev) {
+        total -= g_kept[q].bytes;
+        cudaFree(g_kept[q].p);
+        g_kept.erase(g_kept.begin() + (long)q);
+      } else {
+        ++q;
+      }
+    }
+    if (total <= kKeepMaxTotal && g_kept.size() < kKeepMaxCount) {
+      g_kept.push_back(KeptBlock{dev, p, bytes});
+      return;
+    }
+  }
+  cudaFree(p);
+}
 
 // The table entries are computed on the host in double (glibc log1p / exp2,
 // correctly rounded division) and copied once to each device that uses them.
@@ -761,18 +841,22 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
     md.corr = (double)(tips - 1) * kLn2 - lnfact;
     m->n_segments_known = d->n_nodes;
   }
+  cudaGetDevice(&m->dev);
   if (blob) {
     if (d->fixed_mult) blob += align_up(8 * (size_t)d->n_nodes, 256);
-    cudaError_t e = cudaMalloc(&m->dev_blob, blob);
+    cudaError_t e = block_alloc(&m->dev_blob, &m->blob_bytes, blob);
     if (e != cudaSuccess) {
       delete m;
       return cuda_fail(e, "cudaMalloc(model data)");
     }
-    char* p = (char*)m->dev_blob;
+    // the arrays are laid out in a host copy of the block, then copied at once
+    std::vector<char> host(blob, 0);
+    size_t off = 0;
     auto put = [&](const void* src, size_t bytes) -> void* {
-      void* dst = p;
-      if (cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
-      p += align_up(bytes, 256);
+      if (off + bytes > blob) return nullptr;
+      std::memcpy(host.data() + off, src, bytes);
+      void* dst = (char*)m->dev_blob + off;
+      off += align_up(bytes, 256);
       return dst;
     };
     bool ok = true;
@@ -799,14 +883,15 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
       if (ok) ok = (md.branch = (const BranchRec*)put(br.data(), sizeof(BranchRec) * M)) != nullptr;
       if (ok && d->fixed_mult) ok = (md.fixed_mult = (const double*)put(d->fixed_mult, 8 * M)) != nullptr;
     }
+    if (ok) ok = cudaMemcpy(m->dev_blob, host.data(), blob, cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
-      cudaFree(m->dev_blob);
+      block_free(m->dev_blob, m->blob_bytes, m->dev);
       delete m;
       return set_error(SMC_ECUDA, "copying model data to the device failed");
     }
   }
   if (cudaEventCreate(&m->ev0) != cudaSuccess || cudaEventCreate(&m->ev1) != cudaSuccess) {
-    if (m->dev_blob) cudaFree(m->dev_blob);
+    block_free(m->dev_blob, m->blob_bytes, m->dev);
     delete m;
     return set_error(SMC_ECUDA, "cudaEventCreate failed");
   }
@@ -817,8 +902,8 @@ extern "C" smc_status smc_model_register(const smc_model_desc* d, smc_model_t* o
 extern "C" void smc_model_destroy(smc_model_t m) {
   if (!m) return;
   graph_cache_clear(&m->graph);
-  if (m->ws) cudaFree(m->ws);
-  if (m->dev_blob) cudaFree(m->dev_blob);
+  block_free(m->ws, m->ws_bytes, m->dev);
+  block_free(m->dev_blob, m->blob_bytes, m->dev);
   if (m->ev0) cudaEventDestroy(m->ev0);
   if (m->ev1) cudaEventDestroy(m->ev1);
   for (cudaEvent_t e : m->ev_seg) cudaEventDestroy(e);
@@ -869,13 +954,15 @@ extern "C" smc_status smc_run(smc_model_t m, const smc_run_cfg* c, smc_result* r
     ws = (char*)c->workspace;
   } else {
     if (m->ws_bytes < need) {
-      if (m->ws) cudaFree(m->ws);
+      graph_cache_clear(&m->graph);  // a captured graph addresses the old workspace
+      block_free(m->ws, m->ws_bytes, m->dev);
       m->ws = nullptr;
       m->ws_bytes = 0;
-      cudaError_t e = cudaMalloc(&m->ws, need);
-      if (e != cudaSuccess)
+      cudaError_t e = block_alloc(&m->ws, &m->ws_bytes, need);
+      if (e != cudaSuccess) {
+        m->ws_bytes = 0;
         return set_error(SMC_ENOMEM, "workspace cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
-      m->ws_bytes = need;
+      }
     }
     ws = (char*)m->ws;
   }

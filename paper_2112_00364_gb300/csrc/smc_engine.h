@@ -94,6 +94,11 @@ struct GraphCache {
 };
 void graph_cache_clear(GraphCache* g);
 
+// Device blocks through a small cache of blocks freed by destroyed model
+// handles (smc_engine.cu): *got receives the block's size (at least bytes).
+cudaError_t block_alloc(void** p, size_t* got, size_t bytes);
+void block_free(void* p, size_t bytes, int dev);
+
 // A whole run in one launch (smc_small.cu): for runs of 32-particle tiles, at
 // most small_run_max_tiles(kind, launch_mode) of them; launch_mode
 // SMC_LAUNCH_ONE_CTA (grid 1) or SMC_LAUNCH_CLUSTER (one thread-block cluster).
@@ -108,7 +113,9 @@ struct smc_model_s {
   smc::ModelDev md;
   int32_t n_real, n_int, stack_cap, n_segments_known;
   int32_t n_real_state;  // real fields kept in PSTATE (>= n_real; extra ones are internal)
+  int dev = 0;                // the device the handle's memory is on
   void* dev_blob = nullptr;  // observations / tree arrays
+  size_t blob_bytes = 0;
   void* ws = nullptr;        // cached workspace of smc_run
   size_t ws_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
