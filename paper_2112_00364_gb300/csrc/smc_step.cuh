@@ -431,7 +431,7 @@ __device__ __forceinline__ void step_tile(const RunDev& A, const int t, const in
 // KIND 0 dispatches on each run's model; a KIND of SMC_MODEL_* is the kernel of
 // waves whose runs all run that model (only its block table is compiled in).
 template <typename R, int TPB, int KIND>
-__global__ void __launch_bounds__(TPB, 768 / TPB) wave_kernel(const RunDev* __restrict__ runs,
+__global__ void __launch_bounds__(TPB, (sizeof(R) == 4 ? 1024 : 768) / TPB) wave_kernel(const RunDev* __restrict__ runs,
                                                    const int2* __restrict__ cta_map, unsigned wave) {
   __shared__ __align__(16) RunDev sr;
   __shared__ double sh[TPB / 32 + 2 + TPB + 1];
