@@ -491,8 +491,10 @@ smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uin
  * bits) the fixed-point weight round(e^x[i] 2^54) for x[i] <= 0, 6 = computed
  * on the integer pipes (what the segment kernel uses), 7 = the table exponential
  * rounded to the same grid; fn 8 gives round(e^x[i] 2^54) from the two-table
- * integer exponential, fn 9 round(e^x[i] 2^50) as smc_resample forms its weights
- * with it (the argument in 2^-52 units); fn 10 gives e^-x[i]
+ * integer exponential, fn 9 round(e^x[i] 2^50) from it with the argument in
+ * 2^-52 units; fn 23 gives round(e^x[i] 2^50) as smc_resample forms its weights
+ * (the argument in 2^-52 units, a 9216-entry table of e^(-j/256) and a degree-5
+ * polynomial); fn 10 gives e^-x[i]
  * (a double, x[i] in [0, 64)) from the same integer exponential, as the Poisson
  * sampler forms it.  fn 11..16 are the FP32 mode's own single-precision
  * functions of x[i] rounded to float (the result widened to f64): 11 log,

@@ -83,6 +83,8 @@ __host__ __device__ __forceinline__ Block4 philox(uint32_t c0, uint32_t c1, uint
 // table so that a short Taylor polynomial, evaluated in Estrin form, finishes
 // the job in ~8 dependent operations.  Both are within ~2 ulp of the correctly
 // rounded result; special and extreme arguments go to the library functions.
+constexpr int kRsExpN = 36 * 256;      // table points of e^(-j/256), j < kRsExpN
+constexpr int kRsExpPad = kRsExpN + 4;  // then zeros (whole 16-byte pairs)
 struct MathTab {
   double log_f[192];    // log(j/128), j = 90..181 used
   double inv_f[192];    // 128 / j, j = 90..181 used
@@ -95,6 +97,10 @@ struct MathTab {
   double lfact[32];                      // log k!, k < 32 (sums of logs in order)
   double exp2_j[32];    // 2^(j/32)
   double inv_int[256];  // 1 / k (entry 0 unused)
+  // The standalone resampler's exponential: round(e^(-j/256) 2^56) for
+  // j < kRsExpN, zero from there on (e^-36 2^50 < 1/2: the weights past it round
+  // to zero).
+  __align__(16) unsigned long long rs_exp_q56[kRsExpPad];
 };
 
 constexpr double kLn2Hi = 0x1.62e42fefa3800p-1;   // ln 2 to 42 bits: e * kLn2Hi exact, |e| < 2^11

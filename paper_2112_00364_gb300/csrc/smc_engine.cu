@@ -200,6 +200,12 @@ smc_status math_table(const MathTab** out) {
     }
     h.inv_int[0] = 0.0;
     for (int k = 1; k < 256; ++k) h.inv_int[k] = 1.0 / (double)k;
+    // e^(-j/256) 2^56 from the long-double exponential (64 or more significand
+    // bits): within a fraction of a unit of the exact value before rounding
+    for (int j = 0; j < kRsExpPad; ++j)
+      h.rs_exp_q56[j] = j < kRsExpN ? (unsigned long long)std::llroundl(
+                                          std::ldexp(std::exp(-(long double)j / 256.0L), 56))
+                                    : 0ull;
     SMC_CUDA_TRY(cudaMemcpyToSymbol(g_math_tab, &h, sizeof(MathTab)));
     void* p = nullptr;
     SMC_CUDA_TRY(cudaGetSymbolAddress(&p, g_math_tab));

@@ -590,7 +590,9 @@ def math_eval(fn: str, x):
     they make, reduced on the integer pipes / through the table log of the double), or
     exp_fix54 / table_exp_fix54: round(e^x 2^54) as int64 for x <= 0 (integer pipes /
     table exponential rounded to that grid), or exp2t_fix54 / exp2t_fix50: round(e^x
-    2^54) / round(e^x 2^50) from the two-table integer exponential, or exp_neg_int:
+    2^54) / round(e^x 2^50) from the two-table integer exponential, or rs_fix50:
+    round(e^x 2^50) as smc_resample forms its weights (one table of e^(-j/256) and a
+    degree-5 polynomial), or exp_neg_int:
     e^-x (double, 0 <= x < 64) from the same integer exponential, or q_ratio: x an
     [n, 2] array of (S, N) integers, returns [n, 2] uint64 (integer part, fraction
     bits) of floor(S 2^64 / N)."""
@@ -602,7 +604,7 @@ def math_eval(fn: str, x):
             # the FP32 mode's own single-precision functions, and CUDA's for comparison
             "f32_log": 11, "f32_exp": 12, "f32_cos2pi": 13, "f32_log1p": 14, "f32_expm1": 15,
             "f32_lfact": 16, "cuda_logf": 17, "cuda_expf": 18, "cuda_cos2pif": 19,
-            "cuda_log1pf": 20, "cuda_expm1f": 21, "q_ratio": 22}[fn]
+            "cuda_log1pf": 20, "cuda_expm1f": 21, "q_ratio": 22, "rs_fix50": 23}[fn]
     if code == 22:
         x = np.ascontiguousarray(x, dtype=np.uint64).reshape(-1).view(np.float64)
     if code in (4, 5):
@@ -613,7 +615,7 @@ def math_eval(fn: str, x):
     out = y.cpu().numpy()
     if code == 22:
         return out.view(np.uint64).reshape(-1, 2)
-    return out.view(np.int64) if 6 <= code <= 9 else out
+    return out.view(np.int64) if 6 <= code <= 9 or code == 23 else out
 
 
 def set_tile_bands(bands) -> None:

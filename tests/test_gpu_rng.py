@@ -223,6 +223,35 @@ def test_two_table_fixed_point_exponential(bits):
     assert np.all(np.diff(g) >= 0)
 
 
+def test_resampler_table_exponential():
+    """smc_resample's weights: round(e^d 2^50) from the argument in 2^-52 units,
+    one 9216-entry table of e^(-j/256) in units of 2^-56 and a degree-5
+    polynomial in the remainder: within one unit of the exact rounding (decimal
+    arithmetic at 60 digits) over the whole range and at every table point, 2^50
+    exactly at d = 0, 0 from e^-36 on, and non-increasing in d over a fine
+    sorted grid."""
+    from decimal import Decimal, getcontext
+
+    from paper_2112_00364_gb300 import smc
+
+    getcontext().prec = 60
+    rng = np.random.default_rng(31)
+    d = np.concatenate([-rng.uniform(0, 36.5, 20_000), -rng.uniform(0, 1e-3, 2_000),
+                        -rng.uniform(0, 0.7, 8_000), -np.arange(9300) / 256.0,
+                        -np.arange(9300) / 256.0 - 2.0**-9, -np.arange(1, 9300) / 256.0 + 2.0**-40,
+                        [0.0, -1e-300, -35.3, -35.36, -35.9, -36.0, -36.01, -1000.0,
+                         -0.6931471805599453]])
+    got = smc.math_eval("rs_fix50", d)
+    scale = Decimal(2) ** 50
+    ref = np.array([int((Decimal(float(x)).exp() * scale).to_integral_value()) for x in d])
+    assert np.abs(got - ref).max() <= 1
+    assert got[np.flatnonzero(d == 0.0)[0]] == 1 << 50
+    assert got[d <= -36.0].max() == 0
+    grid = -np.sort(rng.uniform(0, 3.0, 50_000))[::-1]
+    g = smc.math_eval("rs_fix50", grid)
+    assert np.all(np.diff(g) >= 0)
+
+
 def test_integer_pipe_exponential_double():
     """The FP64 Poisson sampler forms e^-mean on the integer pipes (two-table
     exponential, then one rounding of a 61-bit significand to 53 bits and an
