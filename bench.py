@@ -88,11 +88,11 @@ RS_BYTES = 20          # logw read twice (normaliser, scan) + ancestor written, 
 # rate for the delayed-sampling CRBD (FP64 pipe busy 36-44% of a launch).  The
 # traffic holds only for the kernel sources with the recorded digest.
 NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=113.9, fp64_flop_per_pstep=18.8,
-                      bytes_per_launch=3.295e6, fp64_pipe_elapsed=0.185,
-                      src_digest="470cbd0d0ecb1069"),
+                      bytes_per_launch=2.963e6, fp64_pipe_elapsed=0.185,
+                      src_digest="fc844398542168c5"),
        "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=110.2, fp64_flop_per_pstep=169.1,
-                          bytes_per_launch=5.41e6, fp64_pipe_elapsed=0.353,
-                          src_digest="470cbd0d0ecb1069")}
+                          bytes_per_launch=4.953e6, fp64_pipe_elapsed=0.353,
+                          src_digest="fc844398542168c5")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
@@ -109,7 +109,7 @@ RS_SOURCES = ("smc_prims.cu", "smc_device.cuh", "smc_combine.cuh")
 # DRAM traffic of one smc_resample call at 2^24 (the three kernels' dram__bytes
 # read + write in one ncu capture, profiles folder), valid for the sources with
 # the recorded digest.
-RS_NCU = dict(bytes_per_call=3.529e8, src_digest="9d459fcec27c2c1f")
+RS_NCU = dict(bytes_per_call=2.353e8, src_digest="84e4a804f220f1c5")
 
 
 def code_text(src: str) -> str:
@@ -642,7 +642,7 @@ def run_resample(args, work: Work, smc, torch, dist, ws: int, rank: int, local: 
             "frac": rs_gbs / peaks["hbm_gbs"],
             "traffic": RS_NCU["bytes_per_call"] if RS_NCU["src_digest"] == src_digest(RS_SOURCES)
             else None,
-            "kernel": "smc_resample (rs_tile_reduce + rs_combine + rs_ancestors)",
+            "kernel": "smc_resample (rs_tile_reduce + rs_combine + rs_ancestors<true>)",
             "bytes_per_particle": RS_BYTES, "avg_call_us": rs_s * 1e6,
             "peak_source": peaks["source"],
             "gather": {"achieved": g_gbs, "frac": g_gbs / peaks["hbm_gbs"], "avg_call_us": g_s * 1e6,

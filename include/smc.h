@@ -374,17 +374,21 @@ void smc_server_destroy(smc_server_t s);
  * These are the normaliser / scan / systematic search / gather of Section 3.3 as
  * standalone HBM-streaming kernels.  All pointers are device pointers. */
 
-/* Scratch bytes smc_resample needs for a population of N (8 bytes per particle
- * for the tiles' running sums, kept between its first and third kernel, plus
- * the per-tile records and offsets). */
+/* Scratch bytes smc_resample needs for a population of N: about 5 bytes per
+ * particle, kept between its first and third kernel (each running sum's top 32
+ * bits after normalising by its tile total's leading zeros, and the exact
+ * running sum before every 8 particles), plus the per-tile records and
+ * offsets. */
 size_t smc_resample_workspace_bytes(int64_t N);
 
 /* Systematic resampling of one population (Section 3.3, parallel systematic
- * resampling): with the power-of-two reference m = k ln 2, k = ceil(max logw / ln 2),
+ * resampling): with the power-of-two reference m = k ln 2 (k = max over tiles
+ * of the tile's k_t >= ceil(max logw / ln 2), chosen from the log-weights' high
+ * words),
  * S = sum exp(logw - m) and P_j the running sum, ancestors[i] = min{ j : P_j (N / S)
  * > i + u } (N - 1 if none); the log-Z increment is m + (log S - log N).  The sums
- * are exact integer sums of the weights rounded to 2^-54 of their tile's
- * power-of-two reference (within n_tiles 2^-52 of the FP64 sum).  logw [N] f64 in
+ * are exact integer sums of the weights rounded to 2^-50 of their tile's
+ * power-of-two reference (each within one unit of the exact rounding).  logw [N] f64 in
  * (16-byte aligned), ancestors [N] int32 out, out3 [3] f64 out = {m, S, m + (log S
  * - log N)}, n_near [1] int64 out (offsets within 1e-12 N of a boundary).  u in
  * (0,1).  workspace: device memory of smc_resample_workspace_bytes(N) bytes,
