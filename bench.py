@@ -92,7 +92,11 @@ NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=113.9, fp64_flop_per_ps
                       src_digest="fc844398542168c5"),
        "crbd_ds128": dict(basis="fp64", warp_inst_per_pstep=110.2, fp64_flop_per_pstep=169.1,
                           bytes_per_launch=4.953e6, fp64_pipe_elapsed=0.353,
-                          src_digest="fc844398542168c5")}
+                          src_digest="fc844398542168c5"),
+       # FP32 waves of 2^20 particles: bound by memory latency (long-scoreboard
+       # stalls), reported against HBM; 72-75 warp instructions per particle-step
+       "rateshift256": dict(basis="hbm", warp_inst_per_pstep=73.5, bytes_per_launch=1.182e8,
+                            src_digest="fc844398542168c5")}
 
 # 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM (2 DFMA/clk/SM) = GB300's FP64 rate
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
