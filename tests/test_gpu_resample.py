@@ -1,5 +1,7 @@
 """Standalone resampling primitives vs the oracle (GPU): FP64 normaliser,
 scan and systematic search, and the stack-bounded particle gather."""
+import math
+
 import numpy as np
 import pytest
 
@@ -37,6 +39,94 @@ def test_resample_matches_oracle(N, dead):
     assert abs((o3[0] + np.log(o3[1])) - (m + np.log(S))) <= 1e-12 * max(1.0, abs(m))
     assert abs(o3[2] - incr) <= 1e-12 * max(1.0, abs(incr))
     assert np.all(np.diff(a_g) >= 0) and a_g.min() >= 0 and a_g.max() < N
+
+
+def _adversarial_logw(kind, N, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "dominant":  # one particle holds nearly all the weight: one tile spans ~N offsets
+        lw = rng.normal(0.0, 1.0, N)
+        lw[N // 3] = 40.0
+    elif kind == "two_level":  # half the weights ~e^-30 of the rest: flat running sums up to the cap
+        lw = np.where(rng.random(N) < 0.5, 0.0, -30.0) + rng.normal(0.0, 1e-3, N)
+    elif kind == "wide":  # log-weights spread over +-100: a few particles per tile matter
+        lw = rng.normal(0.0, 30.0, N)
+    elif kind == "steps":  # every tile a different reference, far apart
+        lw = -0.75 * (np.arange(N) // 4096) + rng.normal(0.0, 0.5, N)
+    else:  # "ties": many exactly equal log-weights, boundaries on exact multiples
+        lw = rng.integers(-3, 1, N).astype(np.float64)
+    return lw
+
+
+def _exact_tied_ancestors(lw, u, offsets):
+    """a_i = min{ j : P_j N / S > i + u } in exact arithmetic for log-weights
+    taking a few integer values: each class weight e^k to 2^-120 (decimal
+    arithmetic at 60 digits), running sums from the classes' running counts,
+    compared with (i + u) S as exact rationals."""
+    from decimal import Decimal, getcontext
+    from fractions import Fraction
+
+    getcontext().prec = 60
+    ks = sorted({int(v) for v in np.unique(lw)})
+    W = {k: int(Decimal(k).exp() * (Decimal(2) ** 120)) for k in ks}
+    cnt = {k: np.cumsum(lw == k) for k in ks}
+    N = lw.size
+
+    def P(j):
+        return sum(int(cnt[k][j]) * W[k] for k in ks)
+
+    S, uf = P(N - 1), Fraction(u)
+    out = []
+    for i in offsets:
+        target = (int(i) + uf) * S
+        lo, hi = 0, N - 1
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if P(mid) * N > target:
+                hi = mid
+            else:
+                lo = mid + 1
+        out.append(lo)
+    return np.array(out, dtype=np.int64)
+
+
+@pytest.mark.parametrize("kind", ["dominant", "two_level", "wide", "steps", "ties"])
+@pytest.mark.parametrize("u", [1e-9, 0.5, 1.0 - 1e-9])
+def test_resample_adversarial_weights(kind, u):
+    """The 32-bit offset counts of smc_resample's third pass and their exact
+    fallback on weight shapes that push elements to it (tiles spanning most of
+    the offsets, flat running sums near a tile's end, widely spread and tied
+    weights, offsets at the ends of (0, 1)): every ancestor against the oracle
+    (differences only at flagged offsets), the allocation-free form equal to
+    the workspace form."""
+    import torch
+    from paper_2112_00364_gb300 import smc
+
+    N = (1 << 20) + 12345
+    lw = _adversarial_logw(kind, N, seed=sum(map(ord, kind)))
+    x = torch.from_numpy(lw).cuda()
+    anc, o3, nn = smc.resample(x, u)
+    a_g = anc.cpu().numpy()
+    a_o, flag, incr, m, S, rc = oracle.resample(lw, u)
+    assert rc == 0
+    diff = a_g != a_o
+    unflagged = np.flatnonzero(diff & (flag == 0))
+    if kind == "ties":
+        # a million tied terms make the oracle's left-to-right FP64 running sum
+        # drift past the 1e-12 N band: where it differs unflagged, the GPU must
+        # give the exact ancestor
+        exact = _exact_tied_ancestors(lw, u, unflagged)
+        np.testing.assert_array_equal(a_g[unflagged], exact)
+    else:
+        assert unflagged.size == 0, unflagged[:10]
+    assert np.all(np.diff(a_g) >= 0) and a_g[0] >= 0 and a_g[-1] < N
+    # the increment against log-sum-exp with a correctly rounded sum (math.fsum):
+    # on a million tied terms the oracle's left-to-right FP64 sum drifts by ~1e-11
+    mx = lw.max()
+    ref = mx + math.log(math.fsum(np.exp(lw - mx))) - math.log(N)
+    assert abs(o3[2].item() - ref) <= 1e-12 * max(1.0, abs(ref))
+    assert abs(incr - ref) <= 1e-9 * max(1.0, abs(ref))
+    a_s, o3_s, nn_s = smc.resample_static(x, u)
+    assert torch.equal(a_s, anc) and torch.equal(o3_s, o3) and torch.equal(nn_s, nn)
 
 
 @pytest.mark.parametrize("N", [1, 5, 4096, 4097, 1 << 16])
