@@ -21,7 +21,7 @@ def _gpu_resample(lw, u):
     return anc.cpu().numpy(), o3.cpu().numpy(), int(nn.cpu()[0])
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 33, 4095, 4096, 4097, 100_003, 1 << 20])
+@pytest.mark.parametrize("N", [1, 2, 3, 33, 4095, 4096, 4097, 100_003, 1 << 20, (1 << 24) + 4097])
 @pytest.mark.parametrize("dead", [0.0, 0.3])
 def test_resample_matches_oracle(N, dead):
     lw = inputs.random_logw(N, seed=N, scale=2.0, dead_frac=dead if N > 3 else 0.0)
