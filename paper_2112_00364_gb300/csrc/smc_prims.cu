@@ -2,13 +2,16 @@
 // HBM-streaming kernels, the particle-duplication gather, the random-number
 // parity hooks, and the library's error plumbing.
 //
-// smc_resample (parallel systematic resampling, three launches), in the
-// segment kernel's integer arithmetic (smc_combine.cuh):
-//   1. rs_tile_reduce: per tile of TPB*IT weights, M_t = max, its power-of-two
-//      reference k_t = ceil(M_t / ln 2), the weights round(exp(x - k_t ln 2)
-//      2^50) on the integer pipes (two-table exponential), their exact tile
-//      running sums E_j and total (smc_resample keeps the E_j in its
-//      workspace for pass 3)
+// smc_resample (parallel systematic resampling, three launches chained by
+// programmatic dependent launch), in the segment kernel's integer arithmetic
+// (smc_combine.cuh):
+//   1. rs_tile_reduce (persistent): per tile of 4096 weights, the power-of-two
+//      reference k_t from the largest high word of its log-weights (k_t ln 2 at
+//      least 2^-19 above their maximum), the weights round(exp(x - k_t ln 2)
+//      2^50) on the integer pipes (a table of e^(-j/256) in shared memory and
+//      a degree-5 polynomial), their exact tile running sums E_j and total;
+//      smc_resample keeps each E_j's top 32 bits, normalised by the total's
+//      leading zeros, and the exact sum before every 8 elements for pass 3
 //   2. rs_combine (one CTA): k = max k_t, integer offsets O_t of the totals in
 //      the common unit U, S = O_T, out3 = {k ln 2, S U 2^-k, log-Z increment},
 //      and the scale N / S as a 64-bit mantissa and shift
@@ -16,12 +19,14 @@
 //      [Q_{j-1}, Q_j), Q_j = B_j N / S in 64.64 offset units, with
 //      B_j = min(O_t + E_j 2^-(k - k_t + G), O_{t+1}) (the first element of a
 //      tile from the previous tile's last boundary, the last element of the
-//      population everything above): c_j = #{ i : i + u < Q_j } = ceil(Q_j - u).
-//      Each element with a non-empty range marks its first offset in shared
-//      memory; an inclusive max-scan over the marks gives every offset its
-//      element, written out coalesced.  Every i is written exactly once and
-//      a_i = min{ j : Q_j > i + u }, the segment kernel's rule up to the
-//      rounding of N / S (below 2^-62 relative, far inside the 1e-12 band).
+//      population everything above): c_j = #{ i : i + u < Q_j } = ceil(Q_j - u),
+//      from one 32 x 32-bit product of E_j's top word wherever its error bound
+//      decides c_j, exactly otherwise (tile_fast).  Each element with a
+//      non-empty range marks its first offset in shared memory; an inclusive
+//      max-scan over the marks gives every offset its element, written out
+//      coalesced.  Every i is written exactly once and a_i = min{ j : Q_j > i
+//      + u }, the segment kernel's rule up to the rounding of N / S (below
+//      2^-62 relative, far inside the 1e-12 band).
 #include <cuda_runtime.h>
 
 #include <algorithm>
