@@ -102,6 +102,8 @@ NCU = {"crbd64": dict(basis="issue", warp_inst_per_pstep=113.9, fp64_flop_per_ps
 FP64_PEAK_FLOPS = 152 * 2070e6 * 4
 # 152 SMs x 4 schedulers x 2070 MHz, one warp instruction per scheduler per clock
 ISSUE_PEAK = 152 * 4 * 2070e6
+# the compute-peak probe's steps per chain (about 5-20 ms a launch on GB300)
+PROBE_ITERS = {0: 2000, 1: 100000, 2: 20000, 3: 50000, 4: 5000}
 
 
 # the segment kernel's sources (the standalone resampling kernels are not among them)
@@ -678,6 +680,18 @@ def run_resample(args, work: Work, smc, torch, dist, ws: int, rank: int, local: 
     return 0
 
 
+def compute_peaks(smc) -> dict:
+    """The arithmetic peaks measured on this GPU by the library's probe: FP64
+    and FP32 fused multiply-add (TFLOP/s), the special function unit's ex2, the
+    32-bit integer multiply-add and the 64-bit multiply-high (T ops/s)."""
+    out = {}
+    for k, (name, unit, flop) in smc.PEAK_KINDS.items():
+        out[name] = {"value": smc.peak_probe(k, PROBE_ITERS[k]) * (flop or 1) / 1e12, "unit": unit}
+    out["how"] = ("smc_peak_probe: 8 x 256 threads per SM, 8 independent chains of one "
+                  "operation per thread, best of 3 launches timed with CUDA events")
+    return out
+
+
 def load_peaks() -> dict:
     """The HBM copy bandwidth the roofline divides by: the driver's measurement
     on the GB300s when its file is present, else the recipe's fallback."""
@@ -845,10 +859,14 @@ def segment_roofline(work: Work, meas: dict, peaks: dict, name: str) -> dict:
                      "per_unit": f"{info['warp_inst_per_pstep']} warp instructions per "
                                  f"particle-step (ncu)",
                      "peak_source": "derived: 152 SMs x 4 schedulers x 2070 MHz"}
-        fp64_obj = {"achieved": fp64 / 1e12, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                    "frac": fp64 / FP64_PEAK_FLOPS,
+        fp64_peak = peaks.get("fp64_flops", FP64_PEAK_FLOPS)
+        fp64_obj = {"achieved": fp64 / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                    "frac": fp64 / fp64_peak,
                     "per_unit": f"{info['fp64_flop_per_pstep']} FP64 flop per particle-step (ncu)",
-                    "peak_source": "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM"}
+                    "peak_source": ("measured: the FP64 multiply-add probe (compute_peaks)"
+                                    if "fp64_flops" in peaks else
+                                    "derived: 152 SMs x 2070 MHz x 4 FP64 flop/clk/SM"),
+                    "derived_peak": FP64_PEAK_FLOPS / 1e12}
         main = issue_obj if info["basis"] == "issue" else fp64_obj
         return {"bound": "alu", **{k: main[k] for k in ("achieved", "peak", "unit", "frac")},
                 "basis": "instruction issue" if info["basis"] == "issue" else "FP64 pipe",
@@ -1056,6 +1074,8 @@ def main() -> int:
             dist.destroy_process_group()
         return 0
 
+    cpk = compute_peaks(smc)
+    peaks["fp64_flops"] = cpk["fp64_fma"]["value"] * 1e12
     equal_error = None
     if work.w["kind"] == "crbd_ds":
         equal_error = equal_error_comparison(work, smc, torch, bench.stream)
@@ -1106,6 +1126,7 @@ def main() -> int:
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": meas["clocks"],
+        "compute_peaks": cpk,
     }
     if plain:
         line["plain_one_run_per_launch"] = plain

@@ -512,6 +512,19 @@ smc_status smc_sample(int32_t dist, int32_t precision, double p1, double p2, uin
  * Errors: SMC_EINVAL, SMC_ECUDA. */
 smc_status smc_math_eval(int32_t fn, const double *x, double *y, int64_t n, void *stream);
 
+/* Compute-peak probe (the roofline denominators of the arithmetic the path
+ * uses; the paper has no counterpart): one launch of 8 x 256-thread CTAs per SM,
+ * each thread running 8 independent dependency chains of `iters` steps of one
+ * operation: kind 0 = FP64 fused multiply-add, 1 = FP32 fused multiply-add,
+ * 2 = FP32 ex2.approx (special function unit), 3 = 32-bit integer multiply-add,
+ * 4 = 64-bit unsigned multiply-high.  The caller times the launch (e.g. CUDA
+ * events on `stream`); operations = smc_peak_probe_threads() x 8 x iters.
+ * sink: device f64 [smc_peak_probe_threads()] (each thread's chain sum, so that
+ * nothing is optimised away).  Errors: SMC_EINVAL (kind outside 0..4, iters < 1,
+ * NULL sink), SMC_ECUDA. */
+int64_t smc_peak_probe_threads(void);
+smc_status smc_peak_probe(int32_t kind, int64_t iters, double *sink, void *stream);
+
 /* Thread-local description of the calling thread's last error ("" if none). */
 const char *smc_last_error(void);
 

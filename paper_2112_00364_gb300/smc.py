@@ -163,6 +163,10 @@ def lib():
         L.smc_sample.restype = C.c_int32
         L.smc_math_eval.argtypes = [C.c_int32, _vp, _vp, C.c_int64, _vp]
         L.smc_math_eval.restype = C.c_int32
+        L.smc_peak_probe_threads.argtypes = []
+        L.smc_peak_probe_threads.restype = C.c_int64
+        L.smc_peak_probe.argtypes = [C.c_int32, C.c_int64, _vp, _vp]
+        L.smc_peak_probe.restype = C.c_int32
         L.smc_shard_records_bytes.argtypes = [C.c_int64]
         L.smc_shard_records_bytes.restype = C.c_size_t
         L.smc_shard_reduce.argtypes = [_vp, C.c_int64, _vp, _vp]
@@ -616,6 +620,38 @@ def math_eval(fn: str, x):
     if code == 22:
         return out.view(np.uint64).reshape(-1, 2)
     return out.view(np.int64) if 6 <= code <= 9 or code == 23 else out
+
+
+# the probe's operations: (name, unit, flop per operation or None)
+PEAK_KINDS = {0: ("fp64_fma", "TFLOP/s", 2), 1: ("fp32_fma", "TFLOP/s", 2),
+              2: ("fp32_ex2_sfu", "T ops/s", None), 3: ("int32_imad", "T ops/s", None),
+              4: ("u64_mulhi", "T ops/s", None)}
+
+
+def peak_probe(kind: int, iters: int, repeats: int = 3) -> float:
+    """Operations per second of one arithmetic operation at full occupancy on
+    every SM (smc_peak_probe; best of `repeats` launches timed with CUDA
+    events after one warm-up launch)."""
+    import torch
+
+    L = lib()
+    n = int(L.smc_peak_probe_threads())
+    if n <= 0:
+        raise RuntimeError("no CUDA device for the peak probe")
+    sink = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    _check(L.smc_peak_probe(kind, 16, _ptr(sink), _vp(stream.cuda_stream)))
+    best = None
+    for _ in range(repeats):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _check(L.smc_peak_probe(kind, iters, _ptr(sink), _vp(stream.cuda_stream)))
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        best = t if best is None else min(best, t)
+    return n * 8.0 * iters / best
 
 
 def set_tile_bands(bands) -> None:

@@ -72,6 +72,9 @@ def test_resample_argument_checks():
     assert L.smc_resample_workspace_bytes(1 << 20) > 0
     assert L.smc_gather(None, None, None, None, 10, 1, 8, None) == smc.EINVAL
     assert L.smc_sample(9, 0, 0.0, 0.0, 1, 0, 10, None, None, None) == smc.EINVAL
+    # the compute-peak probe rejects bad arguments before touching a device
+    assert L.smc_peak_probe(5, 10, None, None) == smc.EINVAL
+    assert L.smc_peak_probe(0, 0, None, None) == smc.EINVAL
 
 
 def test_particle_limit_agrees_across_header_engine_and_binding():
