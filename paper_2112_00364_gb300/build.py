@@ -22,7 +22,8 @@ INCLUDE = PKG.parent / "include"
 BUILD = PKG / "_build"
 LIB = PKG / "libsmc.so"
 LIB_DEBUG = PKG / "libsmc_debug.so"
-SOURCES = ["smc_engine.cu", "smc_waves_kind.cu", "smc_small.cu", "smc_prims.cu", "smc_server.cu"]
+SOURCES = ["smc_engine.cu", "smc_waves_kind.cu", "smc_small.cu", "smc_prims.cu", "smc_server.cu",
+           "smc_probe.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
